@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the voxel-gravity forward model on one GB300 (or N replicas).
+
+Default workload: 128^3 voxels of 250 m with an exponential-covariance random
+density (correlation length 2 km, sigma 150 kg/m^3), midpoint rule
+(2,097,152 sources), observers = 512^2 surface stations plus every voxel
+centre (2,359,296).  A timed step is one whole pass of the path on resident
+inputs: the plan build (observer Morton keys, sort, box tables, lists) and
+the forward solve (sources, upward sweep, M2L, downward sweep, evaluation,
+near field, near+far combine), then the plan's release.
+
+Metric: effective interactions/s = N_sources * M_observers / step time.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM per clock
+FP64_TFLOPS_NOMINAL = 1.25       # GB300 FP64 (vector and tensor) rate
+FLOPS_PER_PAIR = 20.0            # the paper's count: 5 add, 7 mul, 1 sqrt ~ 20 mul-equivalents
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
+    ap.add_argument("--n", type=int, default=128, help="voxels per axis")
+    ap.add_argument("--stations", type=int, default=512)
+    ap.add_argument("--mode", default="auto", choices=["auto", "fmm", "direct"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--leaf-vox", type=int, default=0)
+    ap.add_argument("--sample-obs", type=int, default=1024,
+                    help="observers in the oracle's bounded sample")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled: bool):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if not enabled:
+            return
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(args):
+    from paper_1107_5951_gb300 import workloads as wl
+    return wl.grf_volume(n=args.n, stations=args.stations)
+
+
+def oracle_sample(wk, args, seed=17):
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(wk.n_obs, size=min(args.sample_obs, wk.n_obs), replace=False))
+    return idx
+
+
+def run_cpu_oracle(wk, idx):
+    from oracle import direct
+    t0 = time.perf_counter()
+    g = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs[idx], wk.G)
+    dt = time.perf_counter() - t0
+    return g, dt, direct.max_threads()
+
+
+# ------------------------------------------------------------------ reference arm
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return
+    wk = make_workload(args)
+    n_src = wk.n_sources
+    idx_all = oracle_sample(wk, args)
+    # each step evaluates a bounded sample of observers against every source
+    per_step = max(64, len(idx_all) // 4)
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = idx_all[(s * per_step) % len(idx_all):][:per_step]
+        _, dt, cores = run_cpu_oracle(wk, idx)
+        if s >= args.warmup:
+            times.append((dt, len(idx)))
+    tot_t = sum(t for t, _ in times)
+    tot_pairs = sum(n * n_src for _, n in times)
+    value = tot_pairs / tot_t
+    sample = "%d observers per step (seeded subset of %d) x all %d sources" % (per_step, wk.n_obs, n_src)
+    line = {"impl": "reference", "metric": "effective interactions/s", "value": value,
+            "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wk.name, "N_sources": n_src, "M_observers": wk.n_obs,
+                       "parallelism": "replicas", "l2_flush": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def bench_gf(args, rank, world):
+    import torch
+
+    import paper_1107_5951_gb300 as pkg
+
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    peaks = load_peaks()
+    wk = make_workload(args)
+    N, M = wk.n_sources, wk.n_obs
+    units = float(N) * float(M)
+
+    mode = args.mode
+    if mode == "auto":
+        mode = "fmm"
+    stream = torch.cuda.Stream(device=dev)
+    obs_d = torch.tensor(wk.obs, dtype=torch.float64, device=dev)
+    rho_dtype = torch.float32 if args.precision == "mixed" else torch.float64
+    rho_d = torch.tensor(wk.rho, dtype=rho_dtype, device=dev)
+    g_d = torch.empty((M, 3), dtype=torch.float64, device=dev)
+
+    def make_plan():
+        return pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode=mode,
+                        precision=args.precision, p=args.p, leaf_vox=args.leaf_vox, G=wk.G,
+                        stream=stream)
+
+    try:
+        probe = make_plan()
+    except pkg.GfError as e:
+        if mode == "fmm" and args.mode == "auto" and e.status == 4:
+            mode = "direct"
+            probe = make_plan()
+        else:
+            raise
+    plan_info = probe.info
+    probe.close()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        with torch.cuda.stream(stream):
+            plan = make_plan()
+            plan.forward(rho_d, g=g_d, stream=stream)
+            plan.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank, not args.no_clocks)
+    launches0 = pkg.gf_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))          # evict L2 between timed steps
+        torch.cuda.synchronize()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.gf_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * units * args.steps / (tot_ms * 1e-3)
+
+    # warm forward with the plan built, and the dominant kernel's duration
+    plan = make_plan()
+    fwd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        fwd_ev[k][0].record(stream)
+        plan.forward(rho_d, g=g_d, stream=stream)
+        fwd_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b in fwd_ev]))
+
+    # accuracy on the oracle's sample (rank 0 only)
+    idx = oracle_sample(wk, args)
+    g_host = g_d.cpu().numpy()
+    cpu = None
+    rel_err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ref, dt, cores = run_cpu_oracle(wk, idx)
+        rel_err = float(np.linalg.norm(g_host[idx] - ref) / np.linalg.norm(ref))
+        cpu = {"value": N * len(idx) / dt, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+               "sample": "%d seeded observers of %d x all %d sources (%.1f s)" % (len(idx), M, N, dt)}
+
+    # roofline of the dominant kernel
+    if mode == "direct":
+        flops = FLOPS_PER_PAIR * units
+        if args.precision == "mixed":
+            peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            peak_note = "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % peaks["_source"]
+        else:
+            peak = FP64_TFLOPS_NOMINAL
+            peak_note = "FP64 nominal 1.25 TFLOP/s"
+        achieved = flops / (fwd_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "direct_fwd_%s" % ("mixed" if args.precision == "mixed" else "f64"),
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_note,
+                "algorithmic": "%.0f flops/pair x N*M pairs" % FLOPS_PER_PAIR}
+    else:
+        roof = plan.roofline(peaks) if hasattr(plan, "roofline") else None
+    plan.close()
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        obs_h = torch.tensor(wk.obs, dtype=torch.float64).pin_memory()
+        rho_h = torch.tensor(wk.rho, dtype=rho_dtype).pin_memory()
+        g_h = torch.empty((M, 3), dtype=torch.float64).pin_memory()
+        obs_e = torch.empty_like(obs_d)
+        rho_e = torch.empty_like(rho_d)
+        e_ev = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                obs_e.copy_(obs_h, non_blocking=True)
+                rho_e.copy_(rho_h, non_blocking=True)
+                pl = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_e, mode=mode,
+                              precision=args.precision, p=args.p, leaf_vox=args.leaf_vox, G=wk.G,
+                              stream=stream)
+                pl.forward(rho_e, g=g_d, stream=stream)
+                g_h.copy_(g_d, non_blocking=True)
+                pl.close()
+            b.record(stream)
+            e_ev.append((a, b))
+        torch.cuda.synchronize()
+        e_ms = float(np.mean([a.elapsed_time(b) for a, b in e_ev]))
+        e2e = {"value": world * units / (e_ms * 1e-3), "unit": "interactions/s",
+               "h2d_bytes_per_step": int(obs_h.numel() * 8 + rho_h.numel() * rho_h.element_size()),
+               "d2h_bytes_per_step": int(g_h.numel() * 8), "ms_per_step": e_ms}
+
+    if rank != 0:
+        return
+    line = {"metric": "effective interactions/s", "value": value, "unit": "interactions/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wk.name, "mode": mode, "precision": args.precision,
+                       "p": args.p if mode == "fmm" else None,
+                       "leaf_vox": int(plan_info.leaf_vox) if mode == "fmm" else None,
+                       "N_sources": N, "M_observers": M, "parallelism": "replicas" if world > 1 else "single",
+                       "l2_flush": "256 MiB buffer written between timed steps",
+                       "step": "plan build + forward + release"},
+            "ms_per_solve": fwd_ms, "rel_err_vs_oracle_sample": rel_err,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        bench_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    try:
+        bench_gf(args, rank, world)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

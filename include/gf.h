@@ -1,0 +1,208 @@
+/*
+ * gf.h -- C ABI of the GB300 voxel-gravity forward model.
+ *
+ * The library evaluates the discretised gravity integral of Eq. 1
+ *
+ *     g(r) = G * Int rho(x) (r - x) / |r - x|^3 dV
+ *
+ * for a brick of constant-density voxels (Sec. 2.1) sampled at a per-voxel
+ * quadrature rule, in the N-body form of Eqs. 7-8, at arbitrary observation
+ * points -- either by direct summation (Sec. 2.1, SUM-G1/SUM-G2) or by the
+ * fast multipole method of Sec. 2.3 (near/far split of Eq. 10, expansions of
+ * Eq. 9, octree upward and downward sweeps).  Conventions:
+ *
+ *   * units are SI; g points along (r - x), i.e. from the mass to the
+ *     observer, exactly as Eq. 1 is written; z is up;
+ *   * a quadrature point that coincides exactly with an observer contributes
+ *     nothing to that observer (the direct-work count of Eq. 14 excludes self
+ *     pairs);
+ *   * the mass of quadrature point q of voxel v is rho_v * V_v * w_q / sum(w).
+ *
+ * Memory and ownership.  Every pointer named *_dev is a device pointer owned
+ * by the caller, on the device that was current when the plan was created,
+ * and must stay valid until the work enqueued on `stream` has finished.
+ * Host pointers (*_host and the quadrature arrays) are read during the call
+ * only.  A plan owns its tree, lists, expansion workspaces and operator
+ * tables; nothing a plan owns is visible to the caller except through the
+ * query functions below.  `stream` is a cudaStream_t (NULL = the legacy
+ * default stream).  Work is enqueued asynchronously; no call except
+ * gf_plan_create, gf_plan_destroy and gf_plan_check waits for the device.
+ *
+ * Errors.  Every call returns a gf_status.  On failure nothing is enqueued
+ * (or, for GF_ERR_CUDA, the CUDA error is reported and the plan must be
+ * destroyed) and gf_last_error() returns a one-line message for the calling
+ * thread.  No exception or device trap crosses the ABI.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GF_VERSION 1
+
+typedef enum {
+    GF_OK = 0,
+    GF_ERR_INVALID_ARG = 1,   /* bad pointer, size, option or dtype          */
+    GF_ERR_OOM = 2,           /* device allocation failed                    */
+    GF_ERR_CUDA = 3,          /* a CUDA call failed (message has the name)   */
+    GF_ERR_UNSUPPORTED = 4,   /* valid request outside what is implemented   */
+    GF_ERR_TIMEOUT = 5,       /* a bounded device wait gave up               */
+    GF_ERR_DEVICE_CHECK = 6,  /* a device-side check failed (e.g. NaN rho)   */
+    GF_ERR_BUSY = 7           /* admission refused: not enough free memory  */
+} gf_status;
+
+/* Voxel brick of Sec. 2.1: voxel (i,j,k) spans origin + [i,i+1)*h along each
+ * axis; density arrays are [nz][ny][nx] with x fastest. */
+typedef struct {
+    int64_t n[3];       /* nx, ny, nz >= 1                                 */
+    double origin[3];   /* lower corner of voxel (0,0,0), metres           */
+    double h[3];        /* voxel edge lengths, metres, > 0                 */
+} gf_grid;
+
+/* Per-voxel quadrature rule of Sec. 2.1 (1-point Gauss = SUM-G1, 2x2x2 Gauss
+ * = SUM-G2): node q sits at centre + (h/2) * xi[q] with xi in [-1,1]^3.
+ * Host arrays, copied at plan creation. */
+typedef struct {
+    int32_t nq;         /* 1..64 nodes                                     */
+    const double *xi;   /* [nq][3]                                         */
+    const double *w;    /* [nq] positive weights (normalised internally)   */
+} gf_quad;
+
+enum { GF_MODE_DIRECT = 0, GF_MODE_FMM = 1 };
+/* GF_PREC_FP64: every stage in FP64.  GF_PREC_MIXED: FP32 near field with
+ * compensated accumulation, split-TF32 tensor-core M2L with FP32
+ * accumulation, FP64 for the top-level translations and the final near+far
+ * sum. */
+enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1 };
+enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
+
+typedef struct {
+    int32_t mode;        /* GF_MODE_DIRECT or GF_MODE_FMM                  */
+    int32_t precision;   /* GF_PREC_FP64 or GF_PREC_MIXED                  */
+    int32_t p;           /* FMM expansion degree (Eq. 9 series), 1..16;    */
+                         /* K = (p+1)^2 coefficients per expansion         */
+    int32_t leaf_vox;    /* FMM leaf edge in voxels (leaf = leaf_vox^3     */
+                         /* voxels), 0 = library default                   */
+    int32_t max_batch;   /* largest B passed to gf_forward/gf_adjoint, >=1 */
+    int32_t reserved0;
+    double G;            /* gravitational constant; 0 = 6.67428e-11        */
+} gf_options;
+
+typedef struct gf_plan_s *gf_plan_t;
+
+/*
+ * gf_plan_create -- build everything that depends on the geometry only.
+ *   grid, quad : the voxel brick and its quadrature rule (Sec. 2.1)
+ *   obs_dev    : [M][3] FP64 observer coordinates x'_j of Eq. 7 (device)
+ *   M          : number of observers, >= 0
+ *   opt        : mode, precision, expansion degree, batch capacity, G
+ * In FMM mode this builds the Morton-sorted octree of Sec. 2.3 on the
+ * device: observer keys and their stable sort, the occupied boxes of every
+ * level, the near lists and the interaction lists ("cells of the same level
+ * that are not nearest neighbours but are children of the nearest neighbours
+ * of the parent", starting at level 2), and the translation operators.
+ * Waits for the device.  On success *plan receives the new plan.
+ */
+gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad,
+                         const double *obs_dev, int64_t M,
+                         const gf_options *opt, void *stream,
+                         gf_plan_t *plan);
+
+/*
+ * gf_forward -- evaluate Eq. 1 (discretised, Eq. 7 form) for B densities.
+ *   rho_dev   : [B][nz][ny][nx] densities, FP64 or FP32 per rho_dtype
+ *   B         : 1..opt.max_batch
+ *   g_dev     : [B][M][3] FP64 output, observers in caller order, or NULL
+ *   gz_dev    : [B][M] FP64 vertical component, or NULL (not both NULL)
+ * Enqueues on `stream` and returns; allocates nothing, so it may be captured
+ * in a CUDA graph.  Direct mode sums every pair (Sec. 2.1); FMM mode runs
+ * P2M, M2M, M2L, L2L, L2P and the near-field P2P (Sec. 2.3, Fig. 3) and adds
+ * near and far parts (Eq. 10).
+ */
+gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype,
+                     int32_t B, double *g_dev, double *gz_dev, void *stream);
+
+/*
+ * gf_adjoint -- transpose of gf_forward (Eq. 1 is linear in rho):
+ *   grad_v = sum_j sum_c r_jc * d g_c(x'_j) / d rho_v
+ *   r_dev    : [B][M][ncomp] FP64 weights on the outputs; ncomp = 1 weights
+ *              g_z only, ncomp = 3 weights the full vector
+ *   grad_dev : [B][nz][ny][nx] FP64 output
+ * In FMM mode this runs the exact algebraic transpose of the forward FMM
+ * (observers act as sources, voxel quadrature points as targets), so that
+ * <A x, y> = <x, A^T y> holds to rounding.  Enqueues and returns.
+ */
+gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp,
+                     int32_t B, double *grad_dev, void *stream);
+
+/* Release a plan and everything it owns (waits for its device work). */
+gf_status gf_plan_destroy(gf_plan_t plan);
+
+/* Wait for the plan's device work and report any device-side check that
+ * failed since the last call (GF_ERR_DEVICE_CHECK, e.g. a non-finite
+ * density or a bounded wait that gave up), then clear it. */
+gf_status gf_plan_check(gf_plan_t plan, void *stream);
+
+/* One-line message describing the calling thread's last failure. */
+const char *gf_last_error(void);
+
+/* Device bytes a plan with these inputs would hold (upper bound), without
+ * allocating; used for admission by memory footprint. */
+gf_status gf_plan_bytes(const gf_grid *grid, const gf_quad *quad, int64_t M,
+                        const gf_options *opt, size_t *bytes);
+
+/* Octree geometry chosen by a FMM plan (zeros in direct mode). */
+typedef struct {
+    int32_t mode, precision, p, K;    /* K = (p+1)^2                       */
+    int32_t L;                        /* leaf level; 2^L leaves per axis   */
+    int32_t leaf_vox;                 /* voxels per leaf edge              */
+    int64_t voxel_offset[3];          /* voxel (0,0,0) sits at tree voxel  */
+                                      /* coordinates voxel_offset          */
+    double lo[3];                     /* root cube lower corner, metres    */
+    double leaf_side;                 /* leaf edge, metres                 */
+    double inv_leaf_side;             /* 1/leaf_side used for the keys     */
+    int64_t n_target_boxes[24];       /* occupied observer boxes per level */
+    int64_t src_lo[24][3];            /* source boxes per level: inclusive */
+    int64_t src_hi[24][3];            /* integer bounds of the dense block */
+    int64_t M, n_sources;
+    size_t device_bytes;
+} gf_plan_info;
+
+gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info);
+
+/*
+ * Copy a FMM plan's tree to host buffers (verification aid; waits):
+ *   perm_host  : [M] int32, observers in (Morton key, original index) order
+ *   keys_host  : [M] uint64 leaf key of each sorted observer
+ *   level      : 2..L
+ *   box_keys_host : [n_target_boxes[level]] uint64 occupied boxes, ascending
+ *   ilist_host : [n_target_boxes[level]][316] int64 source box per
+ *                interaction-list offset (offset order: dz, dy, dx each
+ *                ascending over -3..3, skipping max-norm <= 1), as the
+ *                source box's Morton key, or -1 when that offset is not in
+ *                the box's list or falls outside the source block
+ *   near_host  : [n_target_boxes[L]][27] int64 (only for level == L): the
+ *                near-list source leaf key per offset (dz,dy,dx ascending
+ *                over -1..1), or -1
+ * Any pointer may be NULL to skip that array.
+ */
+gf_status gf_plan_export_tree(gf_plan_t plan, int32_t level, int32_t *perm_host,
+                              uint64_t *keys_host, uint64_t *box_keys_host,
+                              int64_t *ilist_host, int64_t *near_host);
+
+int32_t gf_version(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all plans and threads); lets a caller count the library's launches in a
+ * timed region. */
+int64_t gf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF_H */

@@ -1,0 +1,13 @@
+"""GB300-native voxel-gravity forward model (May & Knepley, arXiv 1107.5951).
+
+The compute path is the CUDA library ``libgf.so`` (C ABI in ``include/gf.h``);
+this package is its Python binding (:mod:`.gf`) plus the seeded synthetic
+workload generators (:mod:`.workloads`).
+"""
+from .gf import (GfError, Plan, gf_adjoint, gf_forward, gf_last_error, gf_plan_bytes,  # noqa: F401
+                 gf_plan_check, gf_plan_create, gf_plan_destroy, gf_plan_export_tree,
+                 gf_plan_get_info, gf_version, gf_launch_count, load, plan_bytes)
+
+__all__ = ["GfError", "Plan", "gf_adjoint", "gf_forward", "gf_last_error", "gf_plan_bytes",
+           "gf_plan_check", "gf_plan_create", "gf_plan_destroy", "gf_plan_export_tree",
+           "gf_plan_get_info", "gf_version", "gf_launch_count", "load", "plan_bytes"]

@@ -1,0 +1,360 @@
+// gf_api.cu -- the C ABI of gf.h: argument validation, plan lifetime,
+// dispatch to the direct and FMM paths, error reporting.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+static thread_local char g_errbuf[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_errbuf, sizeof(g_errbuf), fmt, ap);
+    va_end(ap);
+}
+
+const char *get_error() { return g_errbuf; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static void keep_pool_memory(int device) {
+    static std::atomic<unsigned long long> done{0};
+    if (device < 0 || device >= 64) return;
+    const unsigned long long bit = 1ull << device;
+    if (done.load() & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done.fetch_or(bit);
+}
+
+gf_status DeviceArena::alloc(void **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 16;
+    n = (n + 255) & ~size_t(255);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);
+    cudaError_t e = cudaMallocAsync(p, n, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("device allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GF_ERR_OOM : GF_ERR_CUDA;
+    }
+    blocks.push_back(*p);
+    bytes += n;
+    return GF_OK;
+}
+
+// Called only once the device is idle (plan destruction or a failed
+// build), so the blocks are returned on the legacy stream: the creation
+// stream may no longer exist.
+void DeviceArena::release() {
+    for (void *p : blocks) cudaFreeAsync(p, 0);
+    blocks.clear();
+    bytes = 0;
+}
+
+// The plan's quadrature rule lives in device memory right after the status
+// word; kernels read it through this pointer.
+const QuadRule *quad_device(gf_plan_s *plan) {
+    return reinterpret_cast<const QuadRule *>(plan->d_status + 64);
+}
+
+static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
+                          const gf_options *opt) {
+    if (!grid || !quad || !opt) {
+        set_error("grid, quad and opt must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (grid->n[a] < 1 || grid->n[a] > (int64_t(1) << 22)) {
+            set_error("grid.n[%d] = %lld out of range [1, 2^22]", a, (long long)grid->n[a]);
+            return GF_ERR_INVALID_ARG;
+        }
+        if (!(grid->h[a] > 0.0) || !isfinite(grid->h[a]) || !isfinite(grid->origin[a])) {
+            set_error("grid.h[%d] must be finite and positive, origin finite", a);
+            return GF_ERR_INVALID_ARG;
+        }
+    }
+    if (quad->nq < 1 || quad->nq > kMaxQuad || !quad->xi || !quad->w) {
+        set_error("quad.nq = %d must be in [1, %d] with non-NULL xi and w", quad->nq, kMaxQuad);
+        return GF_ERR_INVALID_ARG;
+    }
+    for (int q = 0; q < quad->nq; ++q) {
+        if (!(quad->w[q] > 0.0) || !isfinite(quad->w[q])) {
+            set_error("quad.w[%d] must be finite and positive", q);
+            return GF_ERR_INVALID_ARG;
+        }
+        for (int a = 0; a < 3; ++a)
+            if (!(fabs(quad->xi[3 * q + a]) <= 1.0)) {
+                set_error("quad.xi[%d][%d] must lie in [-1, 1]", q, a);
+                return GF_ERR_INVALID_ARG;
+            }
+    }
+    if (M < 0 || M > (int64_t(1) << 31) - 1) {
+        set_error("M = %lld out of range [0, 2^31)", (long long)M);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (opt->mode != GF_MODE_DIRECT && opt->mode != GF_MODE_FMM) {
+        set_error("opt.mode = %d is neither GF_MODE_DIRECT nor GF_MODE_FMM", opt->mode);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (opt->precision != GF_PREC_FP64 && opt->precision != GF_PREC_MIXED) {
+        set_error("opt.precision = %d is neither GF_PREC_FP64 nor GF_PREC_MIXED", opt->precision);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (opt->max_batch < 1 || opt->max_batch > 64) {
+        set_error("opt.max_batch = %d out of range [1, 64]", opt->max_batch);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (opt->G < 0.0 || !isfinite(opt->G)) {
+        set_error("opt.G must be finite and >= 0 (0 selects 6.67428e-11)");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (opt->mode == GF_MODE_FMM) {
+        if (opt->p < 1 || opt->p > kMaxP) {
+            set_error("opt.p = %d out of range [1, %d]", opt->p, kMaxP);
+            return GF_ERR_INVALID_ARG;
+        }
+        if (opt->leaf_vox < 0 || opt->leaf_vox > 64) {
+            set_error("opt.leaf_vox = %d out of range [0, 64]", opt->leaf_vox);
+            return GF_ERR_INVALID_ARG;
+        }
+        if (!(grid->h[0] == grid->h[1] && grid->h[1] == grid->h[2])) {
+            set_error("FMM mode needs cubic voxels (h[0] == h[1] == h[2])");
+            return GF_ERR_UNSUPPORTED;
+        }
+    }
+    return GF_OK;
+}
+
+}  // namespace gf
+
+using namespace gf;
+
+extern "C" {
+
+int32_t gf_version(void) { return GF_VERSION; }
+
+int64_t gf_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char *gf_last_error(void) { return get_error(); }
+
+gf_status gf_plan_bytes(const gf_grid *grid, const gf_quad *quad, int64_t M,
+                        const gf_options *opt, size_t *bytes) {
+    GF_TRY(validate(grid, quad, M, opt));
+    if (!bytes) {
+        set_error("bytes must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    size_t b = 4096 + sizeof(QuadRule) + 256;
+    if (opt->mode == GF_MODE_DIRECT) {
+        b += (size_t)M * 3 * sizeof(double) + 512;
+        if (opt->precision == GF_PREC_MIXED) b += (size_t)M * 6 * sizeof(float) + 512;
+    } else {
+        b += fmm_bytes_estimate(grid, quad->nq, M, opt);
+    }
+    *bytes = b;
+    return GF_OK;
+}
+
+gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double *obs_dev,
+                         int64_t M, const gf_options *opt, void *stream, gf_plan_t *out) {
+    if (!out) {
+        set_error("plan output pointer is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    GF_TRY(validate(grid, quad, M, opt));
+    if (M > 0 && !obs_dev) {
+        set_error("obs_dev is NULL with M = %lld", (long long)M);
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    gf_plan_s *p = new (std::nothrow) gf_plan_s();
+    if (!p) {
+        set_error("host allocation failed");
+        return GF_ERR_OOM;
+    }
+    cudaGetDevice(&p->device);
+    p->arena.stream = st;
+    p->grid = *grid;
+    p->opt = *opt;
+    p->G = opt->G > 0.0 ? opt->G : 6.67428e-11;
+    p->M = M;
+    p->nvox = grid->n[0] * grid->n[1] * grid->n[2];
+    QuadRule &qr = p->quad;
+    memset(&qr, 0, sizeof(qr));
+    qr.nq = quad->nq;
+    double wsum = 0.0;
+    for (int q = 0; q < quad->nq; ++q) wsum += quad->w[q];
+    for (int q = 0; q < quad->nq; ++q) {
+        qr.wn[q] = quad->w[q] / wsum;
+        qr.wnf[q] = (float)qr.wn[q];
+        for (int a = 0; a < 3; ++a) {
+            qr.xi[q][a] = quad->xi[3 * q + a];
+            qr.offf[q][a] = (float)(0.5 + 0.5 * quad->xi[3 * q + a]);
+        }
+    }
+    gf_status s = GF_OK;
+    // status word (64 ints) followed by the quadrature rule
+    s = p->arena.alloc(reinterpret_cast<void **>(&p->d_status), 64 * sizeof(int) + sizeof(QuadRule));
+    if (s == GF_OK) {
+        cudaError_t e = cudaMemsetAsync(p->d_status, 0, 64 * sizeof(int), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_status + 64, &qr, sizeof(QuadRule), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            set_error("plan setup copy failed: %s", cudaGetErrorString(e));
+            s = GF_ERR_CUDA;
+        }
+    }
+    if (s == GF_OK) {
+        if (opt->mode == GF_MODE_DIRECT)
+            s = direct_prepare(p, obs_dev, st);
+        else
+            s = fmm_create(p, obs_dev, st);
+    }
+    if (s == GF_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("plan build failed on the device: %s", cudaGetErrorString(e));
+            s = GF_ERR_CUDA;
+        }
+    }
+    if (s != GF_OK) {
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        char keep[512];
+        snprintf(keep, sizeof(keep), "%s", get_error());
+        fmm_destroy(p);
+        p->arena.release();
+        delete p;
+        set_error("%s", keep);
+        return s;
+    }
+    p->device_bytes = p->arena.bytes;
+    *out = p;
+    return GF_OK;
+}
+
+gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int32_t B,
+                     double *g_dev, double *gz_dev, void *stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (!rho_dev || (!g_dev && !gz_dev)) {
+        set_error("rho_dev must be non-NULL and at least one of g_dev, gz_dev given");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (rho_dtype != GF_DTYPE_F64 && rho_dtype != GF_DTYPE_F32) {
+        set_error("rho_dtype = %d is neither GF_DTYPE_F64 nor GF_DTYPE_F32", rho_dtype);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (B < 1 || B > plan->opt.max_batch) {
+        set_error("B = %d out of range [1, max_batch = %d]", B, plan->opt.max_batch);
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->opt.mode == GF_MODE_DIRECT)
+        return direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st);
+    return fmm_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st);
+}
+
+gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp, int32_t B,
+                     double *grad_dev, void *stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((!r_dev && plan->M > 0) || !grad_dev) {
+        set_error("r_dev and grad_dev must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (ncomp != 1 && ncomp != 3) {
+        set_error("ncomp = %d must be 1 (weights on g_z) or 3 (weights on g)", ncomp);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (B < 1 || B > plan->opt.max_batch) {
+        set_error("B = %d out of range [1, max_batch = %d]", B, plan->opt.max_batch);
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->opt.mode == GF_MODE_DIRECT)
+        return direct_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
+    return fmm_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
+}
+
+gf_status gf_plan_check(gf_plan_t plan, void *stream) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int flags[4] = {0, 0, 0, 0};
+    GF_CUDA(cudaMemcpyAsync(flags, plan->d_status, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    GF_CUDA(cudaStreamSynchronize(st));
+    if (flags[0] || flags[1] || flags[2] || flags[3]) {
+        GF_CUDA(cudaMemsetAsync(plan->d_status, 0, sizeof(flags), st));
+        GF_CUDA(cudaStreamSynchronize(st));
+        set_error("device check failed: non-finite density %d, bounded wait %d, index %d, other %d",
+                  flags[0], flags[1], flags[2], flags[3]);
+        return GF_ERR_DEVICE_CHECK;
+    }
+    return GF_OK;
+}
+
+gf_status gf_plan_destroy(gf_plan_t plan) {
+    if (!plan) return GF_OK;
+    int cur = 0;
+    const int dev = plan->device;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    fmm_destroy(plan);
+    plan->arena.release();
+    delete plan;
+    if (cur != dev) cudaSetDevice(cur);
+    return GF_OK;
+}
+
+gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info) {
+    if (!plan || !info) {
+        set_error("plan and info must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    memset(info, 0, sizeof(*info));
+    info->mode = plan->opt.mode;
+    info->precision = plan->opt.precision;
+    info->M = plan->M;
+    info->n_sources = plan->nvox * plan->quad.nq;
+    info->device_bytes = plan->arena.bytes;
+    if (plan->opt.mode == GF_MODE_FMM) return fmm_info(plan, info);
+    return GF_OK;
+}
+
+gf_status gf_plan_export_tree(gf_plan_t plan, int32_t level, int32_t *perm, uint64_t *keys,
+                              uint64_t *box_keys, int64_t *ilist, int64_t *near_) {
+    if (!plan || plan->opt.mode != GF_MODE_FMM) {
+        set_error("gf_plan_export_tree needs a FMM plan");
+        return GF_ERR_INVALID_ARG;
+    }
+    return fmm_export_tree(plan, level, perm, keys, box_keys, ilist, near_);
+}
+
+}  // extern "C"

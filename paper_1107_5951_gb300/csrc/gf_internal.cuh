@@ -1,0 +1,121 @@
+// gf_internal.cuh -- shared declarations of the CUDA library behind gf.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gf.h"
+
+namespace gf {
+
+// ----------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+const char *get_error();
+
+#define GF_TRY(expr)                                     \
+    do {                                                 \
+        gf_status _s = (expr);                           \
+        if (_s != GF_OK) return _s;                      \
+    } while (0)
+
+#define GF_CUDA(expr)                                                        \
+    do {                                                                     \
+        cudaError_t _e = (expr);                                             \
+        if (_e != cudaSuccess) {                                             \
+            ::gf::set_error("%s failed: %s (%s:%d)", #expr,                  \
+                            cudaGetErrorString(_e), __FILE__, __LINE__);     \
+            return _e == cudaErrorMemoryAllocation ? GF_ERR_OOM : GF_ERR_CUDA; \
+        }                                                                    \
+    } while (0)
+
+#define GF_LAUNCH_CHECK() GF_CUDA(cudaGetLastError())
+
+constexpr int kMaxQuad = 64;
+constexpr int kMaxLevels = 21;      // Morton keys use 3 bits per level in a u64
+constexpr int kMaxP = 16;
+constexpr int kNumM2LOffsets = 316; // 7^3 - 3^3 interaction-list offsets
+
+// Quadrature rule as the kernels see it (Sec. 2.1): node offsets from the
+// voxel's lower corner in voxel units (0.5 + xi/2) and normalised weights.
+struct QuadRule {
+    int nq;
+    double xi[kMaxQuad][3];    // reference nodes in [-1,1]^3
+    double wn[kMaxQuad];       // w_q / sum(w)
+    float offf[kMaxQuad][3];   // 0.5 + 0.5*xi: node offset from the voxel's
+                               // lower corner in voxel units
+    float wnf[kMaxQuad];
+};
+
+// Bookkeeping for device memory a plan owns.
+// Allocations are stream-ordered (cudaMallocAsync from the device's default
+// pool, which keeps freed memory for reuse), so building and releasing a
+// plan inside a timed loop costs no driver round trips after the first time.
+struct DeviceArena {
+    std::vector<void *> blocks;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    gf_status alloc(void **p, size_t n);
+    template <class T>
+    gf_status alloc_n(T **p, size_t count) {
+        return alloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    }
+    void release();
+};
+
+struct FmmPlan;   // defined in gf_fmm.cuh
+
+}  // namespace gf
+
+struct gf_plan_s {
+    int device = 0;
+    gf_grid grid{};
+    gf_options opt{};
+    double G = 0;
+    int64_t M = 0;
+    int64_t nvox = 0;
+    gf::QuadRule quad{};
+    gf::DeviceArena arena;
+    // direct mode: observers in caller order
+    double *d_obs = nullptr;     // [M][3] FP64
+    int32_t *d_obs_ivox = nullptr;   // [M][3] floor of voxel coordinates (mixed)
+    float *d_obs_fvox = nullptr;     // [M][3] fractional voxel coordinates (mixed)
+    gf::FmmPlan *fmm = nullptr;
+    int *d_status = nullptr;     // device-side check word
+    size_t device_bytes = 0;
+};
+
+namespace gf {
+
+// Direct-mode kernels (gf_direct.cu)
+gf_status direct_prepare(gf_plan_s *plan, const double *obs_dev, cudaStream_t st);
+gf_status direct_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
+                         double *g, double *gz, cudaStream_t st);
+gf_status direct_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B,
+                         double *grad, cudaStream_t st);
+
+// FMM (gf_fmm.cu)
+gf_status fmm_create(gf_plan_s *plan, const double *obs_dev, cudaStream_t st);
+gf_status fmm_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
+                      double *g, double *gz, cudaStream_t st);
+gf_status fmm_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B,
+                      double *grad, cudaStream_t st);
+void fmm_destroy(gf_plan_s *plan);
+gf_status fmm_info(const gf_plan_s *plan, gf_plan_info *info);
+gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *keys,
+                          uint64_t *box_keys, int64_t *ilist, int64_t *near_);
+size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt);
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Number of kernels the library has launched (all plans, all threads).
+void count_launch(int n = 1);
+#define GF_KERNEL_DONE() \
+    do {                 \
+        ::gf::count_launch(); \
+        GF_LAUNCH_CHECK();    \
+    } while (0)
+
+}  // namespace gf

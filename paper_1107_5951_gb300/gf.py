@@ -1,0 +1,316 @@
+"""Thin Python binding of the C ABI in ``include/gf.h`` (ctypes).
+
+Argument marshalling only: every step of the forward model runs in the CUDA
+kernels of ``libgf.so``.  PyTorch supplies device memory and streams.  The
+functions ``gf_plan_create``, ``gf_forward``, ``gf_adjoint``,
+``gf_plan_destroy``, ``gf_plan_check``, ``gf_plan_bytes``,
+``gf_plan_get_info``, ``gf_plan_export_tree`` and ``gf_last_error`` mirror
+the C entry points one to one; :class:`Plan` wraps them for tensors.
+
+There is no fallback: if ``libgf.so`` is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+GF_OK, GF_ERR_INVALID_ARG, GF_ERR_OOM, GF_ERR_CUDA = 0, 1, 2, 3
+GF_ERR_UNSUPPORTED, GF_ERR_TIMEOUT, GF_ERR_DEVICE_CHECK, GF_ERR_BUSY = 4, 5, 6, 7
+GF_MODE_DIRECT, GF_MODE_FMM = 0, 1
+GF_PREC_FP64, GF_PREC_MIXED = 0, 1
+GF_DTYPE_F64, GF_DTYPE_F32 = 0, 1
+
+_STATUS_NAMES = {0: "GF_OK", 1: "GF_ERR_INVALID_ARG", 2: "GF_ERR_OOM", 3: "GF_ERR_CUDA",
+                 4: "GF_ERR_UNSUPPORTED", 5: "GF_ERR_TIMEOUT", 6: "GF_ERR_DEVICE_CHECK",
+                 7: "GF_ERR_BUSY"}
+
+
+class GfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class gf_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64 * 3), ("origin", ctypes.c_double * 3),
+                ("h", ctypes.c_double * 3)]
+
+
+class gf_quad(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int32), ("xi", ctypes.POINTER(ctypes.c_double)),
+                ("w", ctypes.POINTER(ctypes.c_double))]
+
+
+class gf_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("leaf_vox", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("G", ctypes.c_double)]
+
+
+class gf_plan_info(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("L", ctypes.c_int32), ("leaf_vox", ctypes.c_int32),
+                ("voxel_offset", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3),
+                ("leaf_side", ctypes.c_double), ("inv_leaf_side", ctypes.c_double),
+                ("n_target_boxes", ctypes.c_int64 * 24), ("src_lo", (ctypes.c_int64 * 3) * 24),
+                ("src_hi", (ctypes.c_int64 * 3) * 24), ("M", ctypes.c_int64),
+                ("n_sources", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgf.so (building it with nvcc first if it is missing or
+    stale).  Raises if it cannot be built or loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and _build.is_stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libgf.so is not built (run __graft_entry__.build())")
+        lib = ctypes.CDLL(_build.LIB)
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        P = ctypes.POINTER
+        lib.gf_plan_create.argtypes = [P(gf_grid), P(gf_quad), _vp, i64, P(gf_options), _vp, P(_vp)]
+        lib.gf_forward.argtypes = [_vp, _vp, i32, i32, _vp, _vp, _vp]
+        lib.gf_adjoint.argtypes = [_vp, _vp, i32, i32, _vp, _vp]
+        lib.gf_plan_destroy.argtypes = [_vp]
+        lib.gf_plan_check.argtypes = [_vp, _vp]
+        lib.gf_plan_bytes.argtypes = [P(gf_grid), P(gf_quad), i64, P(gf_options), P(ctypes.c_size_t)]
+        lib.gf_plan_get_info.argtypes = [_vp, P(gf_plan_info)]
+        lib.gf_plan_export_tree.argtypes = [_vp, i32, _vp, _vp, _vp, _vp, _vp]
+        for name in ("gf_plan_create", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
+                     "gf_plan_bytes", "gf_plan_get_info", "gf_plan_export_tree"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.gf_last_error.argtypes = []
+        lib.gf_last_error.restype = ctypes.c_char_p
+        lib.gf_version.restype = ctypes.c_int32
+        lib.gf_launch_count.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def gf_last_error() -> str:
+    return load().gf_last_error().decode(errors="replace")
+
+
+def _check(status: int):
+    if status != GF_OK:
+        raise GfError(status, gf_last_error())
+
+
+# ------------------------------------------------------------ raw entry points
+def gf_plan_create(grid: gf_grid, quad: gf_quad, obs_ptr: int, M: int, opt: gf_options,
+                   stream: int = 0) -> int:
+    plan = _vp()
+    _check(load().gf_plan_create(ctypes.byref(grid), ctypes.byref(quad), _vp(obs_ptr), M,
+                                 ctypes.byref(opt), _vp(stream), ctypes.byref(plan)))
+    return plan.value
+
+
+def gf_forward(plan: int, rho_ptr: int, rho_dtype: int, B: int, g_ptr: int, gz_ptr: int,
+               stream: int = 0):
+    _check(load().gf_forward(_vp(plan), _vp(rho_ptr), rho_dtype, B, _vp(g_ptr or None),
+                             _vp(gz_ptr or None), _vp(stream)))
+
+
+def gf_adjoint(plan: int, r_ptr: int, ncomp: int, B: int, grad_ptr: int, stream: int = 0):
+    _check(load().gf_adjoint(_vp(plan), _vp(r_ptr or None), ncomp, B, _vp(grad_ptr), _vp(stream)))
+
+
+def gf_plan_destroy(plan: int):
+    _check(load().gf_plan_destroy(_vp(plan)))
+
+
+def gf_plan_check(plan: int, stream: int = 0):
+    _check(load().gf_plan_check(_vp(plan), _vp(stream)))
+
+
+def gf_plan_bytes(grid: gf_grid, quad: gf_quad, M: int, opt: gf_options) -> int:
+    out = ctypes.c_size_t()
+    _check(load().gf_plan_bytes(ctypes.byref(grid), ctypes.byref(quad), M, ctypes.byref(opt),
+                                ctypes.byref(out)))
+    return int(out.value)
+
+
+def gf_plan_get_info(plan: int) -> gf_plan_info:
+    info = gf_plan_info()
+    _check(load().gf_plan_get_info(_vp(plan), ctypes.byref(info)))
+    return info
+
+
+def gf_plan_export_tree(plan: int, level: int, perm_ptr=None, keys_ptr=None, box_keys_ptr=None,
+                        ilist_ptr=None, near_ptr=None):
+    _check(load().gf_plan_export_tree(_vp(plan), level, _vp(perm_ptr), _vp(keys_ptr),
+                                      _vp(box_keys_ptr), _vp(ilist_ptr), _vp(near_ptr)))
+
+
+def gf_version() -> int:
+    return int(load().gf_version())
+
+
+def gf_launch_count() -> int:
+    return int(load().gf_launch_count())
+
+
+# ------------------------------------------------------------ marshalling
+def make_grid(shape, origin, h) -> gf_grid:
+    g = gf_grid()
+    for a in range(3):
+        g.n[a] = int(shape[a])
+        g.origin[a] = float(origin[a])
+        g.h[a] = float(h[a])
+    return g
+
+
+class _Quad:
+    """Keeps the host arrays of a gf_quad alive."""
+
+    def __init__(self, xi, w):
+        self.xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
+        self.w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+        self.c = gf_quad()
+        self.c.nq = int(self.w.shape[0])
+        self.c.xi = self.xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.c.w = self.w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_options(mode="fmm", precision="fp64", p=8, leaf_vox=0, max_batch=1, G=0.0) -> gf_options:
+    o = gf_options()
+    o.mode = {"direct": GF_MODE_DIRECT, "fmm": GF_MODE_FMM}[mode] if isinstance(mode, str) else int(mode)
+    o.precision = ({"fp64": GF_PREC_FP64, "mixed": GF_PREC_MIXED}[precision]
+                   if isinstance(precision, str) else int(precision))
+    o.p = int(p)
+    o.leaf_vox = int(leaf_vox)
+    o.max_batch = int(max_batch)
+    o.G = float(G)
+    return o
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A forward-model plan for one voxel grid, quadrature rule and
+    observer set (see ``gf_plan_create``).
+
+    obs must be a CUDA float64 tensor of shape (M, 3)."""
+
+    def __init__(self, shape, origin, h, xi, w, obs, mode="fmm", precision="fp64", p=8,
+                 leaf_vox=0, max_batch=1, G=0.0, stream=None):
+        import torch
+        if not (isinstance(obs, torch.Tensor) and obs.is_cuda):
+            raise TypeError("obs must be a CUDA tensor")
+        obs = obs.to(torch.float64).contiguous().reshape(-1, 3)
+        self.shape = tuple(int(s) for s in shape)
+        self.M = int(obs.shape[0])
+        self.max_batch = int(max_batch)
+        self.device = obs.device
+        self._grid = make_grid(shape, origin, h)
+        self._quad = _Quad(xi, w)
+        self._opt = make_options(mode, precision, p, leaf_vox, max_batch, G)
+        self.handle = None
+        with torch.cuda.device(self.device):
+            self.handle = gf_plan_create(self._grid, self._quad.c, obs.data_ptr(), self.M, self._opt,
+                                         _stream_handle(stream))
+
+    @property
+    def info(self) -> gf_plan_info:
+        return gf_plan_get_info(self.handle)
+
+    def forward(self, rho, g=None, gz=None, want_g=True, want_gz=False, stream=None):
+        """rho: CUDA tensor (nz, ny, nx) or (B, nz, ny, nx), float32/float64.
+        Returns (g, gz) with g (B?, M, 3) and gz (B?, M) float64 (None for
+        an output not requested)."""
+        import torch
+        single = rho.dim() == 3
+        nx, ny, nz = self.shape
+        rho = rho.contiguous().reshape(-1, nz, ny, nx)
+        B = int(rho.shape[0])
+        if rho.dtype == torch.float64:
+            dt = GF_DTYPE_F64
+        elif rho.dtype == torch.float32:
+            dt = GF_DTYPE_F32
+        else:
+            raise TypeError("rho must be float32 or float64")
+        if want_g and g is None:
+            g = torch.empty((B, self.M, 3), dtype=torch.float64, device=rho.device)
+        if want_gz and gz is None:
+            gz = torch.empty((B, self.M), dtype=torch.float64, device=rho.device)
+        gf_forward(self.handle, rho.data_ptr(), dt, B, g.data_ptr() if g is not None else 0,
+                   gz.data_ptr() if gz is not None else 0, _stream_handle(stream))
+        if single:
+            g = g[0] if g is not None else None
+            gz = gz[0] if gz is not None else None
+        return g, gz
+
+    def adjoint(self, r, ncomp=1, grad=None, stream=None):
+        """r: CUDA float64 (B?, M) for ncomp = 1 or (B?, M, 3) for ncomp = 3.
+        Returns grad (B?, nz, ny, nx) float64."""
+        import torch
+        nx, ny, nz = self.shape
+        single = r.dim() == (1 if ncomp == 1 else 2)
+        r = r.to(torch.float64).contiguous().reshape(-1, self.M, ncomp)
+        B = int(r.shape[0])
+        if grad is None:
+            grad = torch.empty((B, nz, ny, nx), dtype=torch.float64, device=r.device)
+        gf_adjoint(self.handle, r.data_ptr(), ncomp, B, grad.data_ptr(), _stream_handle(stream))
+        return grad[0] if single else grad
+
+    def check(self, stream=None):
+        gf_plan_check(self.handle, _stream_handle(stream))
+
+    def export_tree(self, level):
+        """Host copies of the observer order, leaf keys, occupied boxes of
+        `level`, their interaction lists and (level == L) near lists."""
+        info = self.info
+        nb = int(info.n_target_boxes[level])
+        perm = np.zeros(self.M, dtype=np.int32)
+        keys = np.zeros(self.M, dtype=np.uint64)
+        boxes = np.zeros(nb, dtype=np.uint64)
+        il = np.zeros((nb, 316), dtype=np.int64)
+        near = np.zeros((nb, 27), dtype=np.int64) if level == info.L else None
+        gf_plan_export_tree(self.handle, level, perm.ctypes.data, keys.ctypes.data, boxes.ctypes.data,
+                            il.ctypes.data, near.ctypes.data if near is not None else None)
+        return perm, keys, boxes, il, near
+
+    def close(self):
+        if self.handle:
+            gf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def plan_bytes(shape, origin, h, xi, w, M, **opts) -> int:
+    q = _Quad(xi, w)
+    return gf_plan_bytes(make_grid(shape, origin, h), q.c, int(M), make_options(**opts))

@@ -1,0 +1,99 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+entry point include/gf.h declares, and rejects bad arguments on the host
+before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1107_5951_gb300 as pkg
+from paper_1107_5951_gb300 import gf, workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(gf_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    lib = pkg.load()
+    declared = _declared()
+    assert "gf_forward" in declared and "gf_plan_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the public structs have the C sizes and offsets."""
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include "gf.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
+                    'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gf_grid), sizeof(gf_quad),'
+                    ' sizeof(gf_options), sizeof(gf_plan_info), offsetof(gf_plan_info, M),'
+                    ' offsetof(gf_options, G)); return 0;}')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out == [ctypes.sizeof(gf.gf_grid), ctypes.sizeof(gf.gf_quad), ctypes.sizeof(gf.gf_options),
+                   ctypes.sizeof(gf.gf_plan_info), gf.gf_plan_info.M.offset, gf.gf_options.G.offset]
+
+
+def _args(**kw):
+    grid = gf.make_grid((4, 4, 4), (0, 0, 0), (1, 1, 1))
+    q = gf._Quad(*wl.gauss_rule(1))
+    opt = gf.make_options(**kw)
+    return grid, q, opt
+
+
+@pytest.mark.parametrize("bad", [
+    dict(mode="direct", max_batch=0),
+    dict(mode=7),
+    dict(mode="fmm", p=0),
+    dict(mode="fmm", p=99),
+    dict(mode="direct", precision=5),
+    dict(mode="direct", G=-1.0),
+])
+def test_invalid_options_rejected_on_host(bad):
+    grid, q, opt = _args(**bad)
+    with pytest.raises(gf.GfError) as e:
+        gf.gf_plan_bytes(grid, q.c, 10, opt)
+    assert e.value.status == gf.GF_ERR_INVALID_ARG
+
+
+def test_invalid_grid_and_quadrature_rejected():
+    grid, q, opt = _args(mode="direct")
+    grid.n[1] = 0
+    with pytest.raises(gf.GfError) as e:
+        gf.gf_plan_bytes(grid, q.c, 10, opt)
+    assert e.value.status == gf.GF_ERR_INVALID_ARG
+    grid, q, opt = _args(mode="direct")
+    q.w[0] = -1.0
+    with pytest.raises(gf.GfError):
+        gf.gf_plan_bytes(grid, q.c, 10, opt)
+    grid, q, opt = _args(mode="fmm", p=6)
+    grid.h[2] = 2.0
+    with pytest.raises(gf.GfError) as e:
+        gf.gf_plan_bytes(grid, q.c, 10, opt)
+    assert e.value.status == gf.GF_ERR_UNSUPPORTED
+
+
+def test_null_plan_and_null_outputs_rejected():
+    lib = pkg.load()
+    assert lib.gf_forward(None, None, 0, 1, None, None, None) == gf.GF_ERR_INVALID_ARG
+    assert "plan is NULL" in gf.gf_last_error()
+    assert lib.gf_plan_destroy(None) == gf.GF_OK
+
+
+def test_plan_bytes_grows_with_problem():
+    grid, q, opt = _args(mode="direct", precision="mixed")
+    small = gf.gf_plan_bytes(grid, q.c, 1000, opt)
+    big = gf.gf_plan_bytes(grid, q.c, 100000, opt)
+    assert big > small > 0
