@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--stations", type=int, default=512)
     ap.add_argument("--mode", default="auto", choices=["auto", "fmm", "direct"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--p", type=int, default=12)
     ap.add_argument("--leaf-vox", type=int, default=0)
     ap.add_argument("--sample-obs", type=int, default=1024,
                     help="observers in the oracle's bounded sample")
@@ -140,6 +140,29 @@ def run_cpu_oracle(wk, idx):
     g = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs[idx], wk.G)
     dt = time.perf_counter() - t0
     return g, dt, direct.max_threads()
+
+
+def fp32_peak_tflops(peaks):
+    return N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def fmm_roofline(stages, info, args, peaks):
+    """Roofline of the stage that dominates the forward: the near-field
+    evaluation (ALU: 20 flops per pair, the paper's count) or the M2L
+    (2 K^2 flops per interaction-list box pair)."""
+    K = int(info.K)
+    work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P)"),
+            "m2l": ("alu", 2.0 * K * K * float(info.m2l_pairs), "m2l_simt (all levels)")}
+    dom = max(("eval", "m2l"), key=lambda k: stages.get(k, 0.0))
+    bound, flops, kern = work[dom]
+    if args.precision == "mixed":
+        peak, note = fp32_peak_tflops(peaks), "FP32 SIMT: 152 SM x 128 lanes x 2 x sm_max_mhz"
+    else:
+        peak, note = FP64_TFLOPS_NOMINAL, "FP64 nominal 1.25 TFLOP/s"
+    achieved = flops / (stages[dom] * 1e-3) / 1e12
+    return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": note,
+            "algorithmic": "%.4g flops per launch set" % flops, "stage_ms": stages[dom]}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -287,7 +310,20 @@ def bench_gf(args, rank, world):
                 "traffic": None, "peak_source": peak_note,
                 "algorithmic": "%.0f flops/pair x N*M pairs" % FLOPS_PER_PAIR}
     else:
-        roof = plan.roofline(peaks) if hasattr(plan, "roofline") else None
+        roof = None
+    # per-stage device times (CUDA events on the forward's stream)
+    plan.set_timing(True)
+    stage_runs = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        plan.forward(rho_d, g=g_d, stream=stream)
+        stage_runs.append(plan.stage_times())
+    plan.set_timing(False)
+    stages = {k: float(np.mean([r[k] for r in stage_runs])) for k in stage_runs[0]}
+    info = plan.info
+    if mode == "fmm":
+        roof = fmm_roofline(stages, info, args, peaks)
     plan.close()
 
     # end to end through the C ABI from pinned host buffers
@@ -334,7 +370,8 @@ def bench_gf(args, rank, world):
                        "N_sources": N, "M_observers": M, "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": "256 MiB buffer written between timed steps",
                        "step": "plan build + forward + release"},
-            "ms_per_solve": fwd_ms, "rel_err_vs_oracle_sample": rel_err,
+            "ms_per_solve": fwd_ms, "rel_err_vs_oracle_sample": rel_err, "stages_ms": stages,
+            "work": {"near_pairs": int(info.near_pairs), "m2l_box_pairs": int(info.m2l_pairs)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)

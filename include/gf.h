@@ -170,6 +170,10 @@ typedef struct {
     int64_t src_lo[24][3];            /* source boxes per level: inclusive */
     int64_t src_hi[24][3];            /* integer bounds of the dense block */
     int64_t M, n_sources;
+    int64_t near_pairs;               /* (observer, source) pairs summed   */
+                                      /* directly in the near field        */
+    int64_t m2l_pairs;                /* (observer box, source box) pairs  */
+                                      /* of all interaction lists          */
     size_t device_bytes;
 } gf_plan_info;
 
@@ -194,6 +198,18 @@ gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info);
 gf_status gf_plan_export_tree(gf_plan_t plan, int32_t level, int32_t *perm_host,
                               uint64_t *keys_host, uint64_t *box_keys_host,
                               int64_t *ilist_host, int64_t *near_host);
+
+/* Stage timing (verification and profiling aid).  When enabled, each
+ * gf_forward records CUDA events between its stages on its stream;
+ * gf_plan_stage_times waits for the last forward and returns the device
+ * time of each stage in milliseconds:
+ *   [0] leaf-blocked densities  [1] P2M  [2] M2M  [3] M2L  [4] L2L
+ *   [5] evaluation (near field + L2P + combine)  [6] whole forward
+ * (direct mode: only [5] and [6]).  Timing must be off while a forward is
+ * captured in a CUDA graph. */
+#define GF_NUM_STAGES 7
+gf_status gf_plan_set_timing(gf_plan_t plan, int32_t enable);
+gf_status gf_plan_stage_times(gf_plan_t plan, double *ms);
 
 int32_t gf_version(void);
 

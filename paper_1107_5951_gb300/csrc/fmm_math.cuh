@@ -219,4 +219,117 @@ GF_HD double op_entry(int kind, int p, int row, int col, const double *hre, cons
     return out_im ? yi : yr;
 }
 
+
+// ---------------------------------------------------------------- L2P
+// Gradient of a local expansion.  With phi(x) = (1/s) sum L_n^m conj(R_n^m(X)),
+// X = (x - c)/s, the derivative rules of the normalised regular harmonics
+//   d/dz R_n^m = sqrt((n-m)(n+m)) R_{n-1}^m
+//   d/dx R_n^m = (-a_{n,m} R_{n-1}^{m-1} + b_{n,m} R_{n-1}^{m+1}) / 2
+//   d/dy R_n^m = -i (a_{n,m} R_{n-1}^{m-1} + b_{n,m} R_{n-1}^{m+1}) / 2
+//   a_{n,m} = sqrt((n+m)(n+m-1)),  b_{n,m} = sqrt((n-m)(n-m-1))
+// give s^2 d(phi)/dx_a = sum_{n<p, m} D^a_n^m conj(R_n^m(X)), with
+//   D^z_n^m = sqrt((n+1-m)(n+1+m)) L_{n+1}^m
+//   D^x_n^m = (-a_{n+1,m+1} L_{n+1}^{m+1} + b_{n+1,m-1} L_{n+1}^{m-1}) / 2
+//   D^y_n^m = i (a_{n+1,m+1} L_{n+1}^{m+1} + b_{n+1,m-1} L_{n+1}^{m-1}) / 2
+// stored in the real layout of degree p-1 (p^2 reals each).
+template <class T>
+GF_HD void lget(const T *L, int n, int m, T &r, T &i) {   // L_n^m, any sign of m
+    if (m > n || -m > n) {
+        r = T(0);
+        i = T(0);
+        return;
+    }
+    if (m == 0) {
+        r = L[n * n];
+        i = T(0);
+    } else if (m > 0) {
+        r = L[n * n + 2 * m - 1];
+        i = L[n * n + 2 * m];
+    } else {
+        const T s = ((-m) & 1) ? T(-1) : T(1);
+        r = s * L[n * n - 2 * m - 1];
+        i = -s * L[n * n - 2 * m];
+    }
+}
+
+// One real component (index `idx` in the degree-(p-1) layout) of the three
+// gradient expansions D^x, D^y, D^z of the local expansion L (degree p).
+template <class T>
+GF_HD void grad_coeff(const T *L, int idx, T &dx, T &dy, T &dz) {
+    int n = (int)sqrt((double)idx);
+    while (n * n > idx) --n;
+    while ((n + 1) * (n + 1) <= idx) ++n;
+    const int ro = idx - n * n;
+    const int m = (ro + 1) / 2;
+    const bool want_im = ro > 0 && (ro % 2 == 0);
+    const int N = n + 1;
+    T lr, li, pr, pi, mr, mi;
+    lget(L, N, m, lr, li);
+    lget(L, N, m + 1, pr, pi);
+    lget(L, N, m - 1, mr, mi);
+    const T cz = sqrt(T((N - m) * (N + m)));
+    const T a = sqrt(T((N + m + 1) * (N + m)));       // a_{N, m+1}
+    const T b = sqrt(T((N - m + 1) * (N - m)));       // b_{N, m-1}
+    const T xr = T(0.5) * (-a * pr + b * mr), xi = T(0.5) * (-a * pi + b * mi);
+    const T sr = T(0.5) * (a * pr + b * mr), si = T(0.5) * (a * pi + b * mi);
+    // D^y = i * (sr + i si) = -si + i sr
+    if (!want_im) {
+        dx = xr;
+        dy = -si;
+        dz = cz * lr;
+    } else {
+        dx = xi;
+        dy = sr;
+        dz = cz * li;
+    }
+}
+
+// sum_{n<p, m} D_n^m conj(R_n^m(X)) for the three expansions at once,
+// sweeping the harmonics column by column (m fixed, n rising) so that only
+// two previous degrees are live.  D* are in the degree-(p-1) real layout.
+template <class T>
+GF_HD void l2p_sum(int p, const T *Dx, const T *Dy, const T *Dz, T X, T Y, T Z, T &gx, T &gy,
+                   T &gz) {
+    const T r2 = X * X + Y * Y + Z * Z;
+    T sr = T(1), si = T(0);  // sectoral R_m^m
+    gx = gy = gz = T(0);
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) {
+            const T f = -sqrt(T(2 * m - 1) / T(2 * m));
+            const T nr = f * (X * sr - Y * si), ni = f * (X * si + Y * sr);
+            sr = nr;
+            si = ni;
+        }
+        T r1 = sr, i1 = si, r0 = T(0), i0 = T(0);  // R_{n-1}, R_{n-2}
+        for (int n = m; n < p; ++n) {
+            T cr, ci;
+            if (n == m) {
+                cr = sr;
+                ci = si;
+            } else {
+                const T inv = T(1) / sqrt(T((n + m) * (n - m)));
+                const T a = T(2 * n - 1) * inv;
+                const T b = (n - 1 > m) ? sqrt(T((n - 1 + m) * (n - 1 - m))) * inv * r2 : T(0);
+                cr = a * Z * r1 - b * r0;
+                ci = a * Z * i1 - b * i0;
+                r0 = r1;
+                i0 = i1;
+                r1 = cr;
+                i1 = ci;
+            }
+            if (m == 0) {
+                const int k = n * n;
+                gx += Dx[k] * cr;
+                gy += Dy[k] * cr;
+                gz += Dz[k] * cr;
+            } else {
+                const int k = n * n + 2 * m - 1;
+                gx += T(2) * (Dx[k] * cr + Dx[k + 1] * ci);
+                gy += T(2) * (Dy[k] * cr + Dy[k + 1] * ci);
+                gz += T(2) * (Dz[k] * cr + Dz[k + 1] * ci);
+            }
+        }
+    }
+}
+
 }  // namespace gf

@@ -224,8 +224,10 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
         }
     }
     if (s == GF_OK) {
-        if (opt->mode == GF_MODE_DIRECT)
+        if (opt->mode == GF_MODE_DIRECT) {
             s = direct_prepare(p, obs_dev, st);
+            p->near_pairs = p->M * p->nvox * quad->nq;
+        }
         else
             s = fmm_create(p, obs_dev, st);
     }
@@ -271,8 +273,13 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int
         return GF_ERR_INVALID_ARG;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (plan->opt.mode == GF_MODE_DIRECT)
-        return direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st);
+    for (int i = 0; i <= GF_NUM_STAGES; ++i) plan->ev_used[i] = false;
+    stage_mark(plan, 0, st);
+    if (plan->opt.mode == GF_MODE_DIRECT) {
+        GF_TRY(direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
+        stage_mark(plan, 6, st);
+        return GF_OK;
+    }
     return fmm_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st);
 }
 
@@ -328,8 +335,52 @@ gf_status gf_plan_destroy(gf_plan_t plan) {
     cudaDeviceSynchronize();
     fmm_destroy(plan);
     plan->arena.release();
+    for (int i = 0; i <= GF_NUM_STAGES; ++i)
+        if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
     delete plan;
     if (cur != dev) cudaSetDevice(cur);
+    return GF_OK;
+}
+
+gf_status gf_plan_set_timing(gf_plan_t plan, int32_t enable) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (enable && !plan->ev[0]) {
+        for (int i = 0; i <= GF_NUM_STAGES; ++i) GF_CUDA(cudaEventCreate(&plan->ev[i]));
+    }
+    plan->timing = enable != 0;
+    return GF_OK;
+}
+
+gf_status gf_plan_stage_times(gf_plan_t plan, double *ms) {
+    if (!plan || !ms) {
+        set_error("plan and ms must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < GF_NUM_STAGES; ++i) ms[i] = 0.0;
+    if (!plan->ev[0] || !plan->ev_used[0]) {
+        set_error("no timed forward on this plan (call gf_plan_set_timing first)");
+        return GF_ERR_INVALID_ARG;
+    }
+    int last = 0;
+    for (int i = 0; i <= GF_NUM_STAGES; ++i)
+        if (plan->ev_used[i]) last = i;
+    GF_CUDA(cudaEventSynchronize(plan->ev[last]));
+    // boundaries: ev[0] start, ev[i+1] end of stage i; stages that did not
+    // run keep their start event equal to the previous boundary
+    int prev = 0;
+    for (int i = 0; i < GF_NUM_STAGES - 1; ++i) {
+        if (!plan->ev_used[i + 1]) continue;
+        float t = 0.f;
+        GF_CUDA(cudaEventElapsedTime(&t, plan->ev[prev], plan->ev[i + 1]));
+        ms[i] = t;
+        prev = i + 1;
+    }
+    float tot = 0.f;
+    GF_CUDA(cudaEventElapsedTime(&tot, plan->ev[0], plan->ev[last]));
+    ms[GF_NUM_STAGES - 1] = tot;
     return GF_OK;
 }
 
@@ -344,6 +395,8 @@ gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info) {
     info->M = plan->M;
     info->n_sources = plan->nvox * plan->quad.nq;
     info->device_bytes = plan->arena.bytes;
+    info->near_pairs = plan->near_pairs;
+    info->m2l_pairs = plan->m2l_pairs;
     if (plan->opt.mode == GF_MODE_FMM) return fmm_info(plan, info);
     return GF_OK;
 }

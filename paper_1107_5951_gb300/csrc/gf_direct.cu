@@ -292,8 +292,6 @@ gf_status direct_prepare(gf_plan_s *plan, const double *obs_dev, cudaStream_t st
     return GF_OK;
 }
 
-extern const QuadRule *quad_device(gf_plan_s *plan);
-
 gf_status direct_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, double *g,
                          double *gz, cudaStream_t st) {
     const int64_t M = plan->M;

@@ -1,24 +1,626 @@
-// gf_fmm.cu -- placeholder until the FMM path lands.
-#include "gf_internal.cuh"
+// gf_fmm.cu -- the FMM of Sec. 2.3 on the GPU: operator tables, upward sweep
+// (P2M, M2M), downward sweep (M2L over the interaction list, L2L) and field
+// evaluation (L2P plus the near-field direct sum, Eq. 10).
+//
+// Every kernel here works in voxel units (h = 1); see gf_fmm.cuh.  The
+// evaluation kernel fuses the near-field sum over the nearest-neighbour
+// leaves, the local-expansion gradient, the near+far sum in FP64 and the
+// scatter back to the caller's observer order.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "fmm_math.cuh"
+#include "gf_fmm.cuh"
+#include "gf_m2l.cuh"
 
 namespace gf {
-gf_status fmm_create(gf_plan_s *, const double *, cudaStream_t) {
-    set_error("FMM mode is not built yet");
-    return GF_ERR_UNSUPPORTED;
+
+namespace {
+
+struct LogFact {
+    double v[kLogFactN];
+};
+
+LogFact host_logfact() {
+    LogFact lf;
+    for (int i = 0; i < kLogFactN; ++i) lf.v[i] = lgamma((double)i + 1.0);
+    return lf;
 }
-gf_status fmm_forward(gf_plan_s *, const void *, int, int, double *, double *, cudaStream_t) {
-    set_error("FMM mode is not built yet");
-    return GF_ERR_UNSUPPORTED;
+
+// One block per operator: 343 M2L slots (the 27 near offsets stay unused),
+// then 8 M2M and 8 L2L octants.  Entries are written transposed
+// (input component major).
+__global__ void build_ops(int p, int K, LogFact lf, double *__restrict__ m2l_d, float *__restrict__ m2l_f,
+                          double *__restrict__ m2m_d, float *__restrict__ m2m_f, double *__restrict__ l2l_d,
+                          float *__restrict__ l2l_f) {
+    extern __shared__ double sh[];
+    const int op = blockIdx.x;
+    int kind;
+    double d[3];
+    double *od;
+    float *of;
+    int H;
+    if (op < 343) {
+        const int dx = op % 7 - 3, dy = (op / 7) % 7 - 3, dz = op / 49 - 3;
+        if (max(abs(dx), max(abs(dy), abs(dz))) <= 1) return;
+        kind = OP_M2L;
+        d[0] = dx;
+        d[1] = dy;
+        d[2] = dz;
+        H = 2 * p;
+        od = m2l_d + (size_t)op * K * K;
+        of = m2l_f + (size_t)op * K * K;
+    } else {
+        const int oct = (op - 343) & 7;
+        kind = op < 351 ? OP_M2M : OP_L2L;
+        d[0] = ((oct & 1) - 0.5) * 0.5;
+        d[1] = (((oct >> 1) & 1) - 0.5) * 0.5;
+        d[2] = (((oct >> 2) & 1) - 0.5) * 0.5;
+        H = p;
+        od = (kind == OP_M2M ? m2m_d : l2l_d) + (size_t)oct * K * K;
+        of = (kind == OP_M2M ? m2m_f : l2l_f) + (size_t)oct * K * K;
+    }
+    const int nt = (H + 1) * (H + 2) / 2;
+    double *re = sh, *im = sh + nt;
+    if (threadIdx.x == 0) {
+        if (kind == OP_M2L)
+            irregular_harmonics<double>(H, d[0], d[1], d[2], re, im);
+        else
+            regular_harmonics<double>(H, d[0], d[1], d[2], re, im);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const int c = e / K, k = e - c * K;
+        const double v = op_entry(kind, p, k, c, re, im, lf.v);
+        od[e] = v;
+        of[e] = (float)v;
+    }
 }
+
+// P2M matrix with the quadrature folded in: P[v][k] = sum_q wn_q *
+// (k-th real component of conj R((x_vq - c)/b)), x_vq - c in voxel units.
+__global__ void build_p2m(int p, int K, int b, const QuadRule *__restrict__ qr, double *__restrict__ pd,
+                          float *__restrict__ pf) {
+    extern __shared__ double sh[];
+    const int v = blockIdx.x;
+    const int lx = v % b, ly = (v / b) % b, lz = v / (b * b);
+    const int nt = (p + 1) * (p + 2) / 2;
+    double *re = sh, *im = sh + nt, *acc = sh + 2 * nt;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) acc[k] = 0.0;
+    __syncthreads();
+    for (int q = 0; q < qr->nq; ++q) {
+        if (threadIdx.x == 0) {
+            const double y0 = (lx + 0.5 + 0.5 * qr->xi[q][0] - 0.5 * b) / b;
+            const double y1 = (ly + 0.5 + 0.5 * qr->xi[q][1] - 0.5 * b) / b;
+            const double y2 = (lz + 0.5 + 0.5 * qr->xi[q][2] - 0.5 * b) / b;
+            regular_harmonics<double>(p, y0, y1, y2, re, im);
+        }
+        __syncthreads();
+        const double w = qr->wn[q];
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            int n = (int)sqrt((double)k);
+            while (n * n > k) --n;
+            while ((n + 1) * (n + 1) <= k) ++n;
+            const int ro = k - n * n, m = (ro + 1) / 2;
+            const bool isim = ro > 0 && (ro % 2 == 0);
+            acc[k] += isim ? -w * im[tri(n, m)] : w * re[tri(n, m)];
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        pd[(size_t)v * K + k] = acc[k];
+        pf[(size_t)v * K + k] = (float)acc[k];
+    }
+}
+
+// ---------------------------------------------------------------- sources
+struct Block3 {
+    int64_t lo[3], n[3];
+};
+
+Block3 block_of(const FmmLevel &lv) {
+    Block3 b;
+    for (int a = 0; a < 3; ++a) {
+        b.lo[a] = lv.slo[a];
+        b.n[a] = lv.sn[a];
+    }
+    return b;
+}
+
+// Leaf-blocked densities: mass[leaf][bb][v] = rho of the grid voxel that
+// sits at local position v of the leaf (0 outside the grid).  Flags any
+// non-finite density in status[0].
+template <class Tm>
+__global__ void block_densities(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int64_t nz,
+                                int64_t vx, int64_t vy, int64_t vz, Block3 blk, int b, int B,
+                                Tm *__restrict__ mass, int *__restrict__ status) {
+    const int64_t b3 = (int64_t)b * b * b;
+    const int64_t total = blk.n[0] * blk.n[1] * blk.n[2] * B * b3;
+    const int64_t nvox = nx * ny * nz;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = e % b3;
+        const int64_t rest = e / b3;
+        const int bb = (int)(rest % B);
+        const int64_t leaf = rest / B;
+        const int64_t Lx = blk.lo[0] + leaf % blk.n[0];
+        const int64_t Ly = blk.lo[1] + (leaf / blk.n[0]) % blk.n[1];
+        const int64_t Lz = blk.lo[2] + leaf / (blk.n[0] * blk.n[1]);
+        const int64_t i = Lx * b + v % b - vx;
+        const int64_t j = Ly * b + (v / b) % b - vy;
+        const int64_t k = Lz * b + v / ((int64_t)b * b) - vz;
+        Tm m = Tm(0);
+        if (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz) {
+            const int64_t idx = (int64_t)bb * nvox + (k * ny + j) * nx + i;
+            const double r = rho_f32 ? (double)reinterpret_cast<const float *>(rho)[idx]
+                                     : reinterpret_cast<const double *>(rho)[idx];
+            if (!isfinite(r)) atomicOr(status, 1);
+            m = (Tm)r;
+        }
+        mass[e] = m;
+    }
+}
+
+// P2M: ME[leaf][bb][k] = sum_v P[v][k] mass[leaf][bb][v].  A block handles
+// kP2MLeaves leaves; each thread owns coefficients k, k + blockDim, ...
+constexpr int kP2MLeaves = 4;
+
+template <class T>
+__global__ void __launch_bounds__(128)
+p2m_kernel(const T *__restrict__ mass, const T *__restrict__ P, int64_t nleaf, int b3, int B, int K,
+           T *__restrict__ me) {
+    extern __shared__ unsigned char shraw[];
+    T *ms = reinterpret_cast<T *>(shraw);  // [kP2MLeaves*B][b3]
+    const int64_t leaf0 = (int64_t)blockIdx.x * kP2MLeaves;
+    const int nl = (int)std::min<int64_t>(kP2MLeaves, nleaf - leaf0);
+    const int ncol = nl * B;
+    for (int e = threadIdx.x; e < ncol * b3; e += blockDim.x) ms[e] = mass[leaf0 * B * b3 + e];
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        T acc[kP2MLeaves * 4];
+        for (int c0 = 0; c0 < ncol; c0 += kP2MLeaves * 4) {
+            const int cn = std::min(kP2MLeaves * 4, ncol - c0);
+#pragma unroll
+            for (int c = 0; c < kP2MLeaves * 4; ++c) acc[c] = T(0);
+            for (int v = 0; v < b3; ++v) {
+                const T pv = P[(size_t)v * K + k];
+#pragma unroll
+                for (int c = 0; c < kP2MLeaves * 4; ++c)
+                    if (c < cn) acc[c] += pv * ms[(c0 + c) * b3 + v];
+            }
+#pragma unroll
+            for (int c = 0; c < kP2MLeaves * 4; ++c)
+                if (c < cn) me[(leaf0 * B + c0 + c) * K + k] = acc[c];
+        }
+    }
+}
+
+// M2M: parent ME = sum over existing children of T_oct * child ME; one block
+// per parent box of the dense source block at level l.
+template <class Ts, class Tc>
+__global__ void __launch_bounds__(128)
+m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3 bp, int B, int K,
+           const Tc *__restrict__ tab) {
+    extern __shared__ unsigned char shraw[];
+    Tc *xs = reinterpret_cast<Tc *>(shraw);  // [8][B][K]
+    __shared__ int present[8];
+    const int64_t pi = blockIdx.x;
+    const int64_t px = bp.lo[0] + pi % bp.n[0], py = bp.lo[1] + (pi / bp.n[0]) % bp.n[1],
+                  pz = bp.lo[2] + pi / (bp.n[0] * bp.n[1]);
+    for (int e = threadIdx.x; e < 8 * B * K; e += blockDim.x) {
+        const int oct = e / (B * K), r = e - oct * B * K;
+        const int64_t cx = 2 * px + (oct & 1) - bc.lo[0], cy = 2 * py + ((oct >> 1) & 1) - bc.lo[1],
+                      cz = 2 * pz + ((oct >> 2) & 1) - bc.lo[2];
+        const bool in = cx >= 0 && cx < bc.n[0] && cy >= 0 && cy < bc.n[1] && cz >= 0 && cz < bc.n[2];
+        xs[e] = in ? (Tc)me_c[((cz * bc.n[1] + cy) * bc.n[0] + cx) * B * K + r] : Tc(0);
+        if (r == 0) present[oct] = in;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        for (int bb = 0; bb < B; ++bb) {
+            Tc acc = Tc(0);
+            for (int oct = 0; oct < 8; ++oct) {
+                if (!present[oct]) continue;
+                const Tc *t = tab + (size_t)oct * K * K + k;
+                const Tc *x = xs + (oct * B + bb) * K;
+                for (int c = 0; c < K; ++c) acc += t[(size_t)c * K] * x[c];
+            }
+            me_p[(pi * B + bb) * K + k] = (Ts)acc;
+        }
+    }
+}
+
+// L2L: child LE += T_oct * parent LE, one block per observer box at level l.
+template <class Ts, class Tc>
+__global__ void __launch_bounds__(128)
+l2l_kernel(const Ts *__restrict__ le_p, const uint64_t *__restrict__ tkey, const int32_t *__restrict__ tparent,
+           Ts *__restrict__ le_c, int B, int K, const Tc *__restrict__ tab) {
+    extern __shared__ unsigned char shraw[];
+    Tc *xs = reinterpret_cast<Tc *>(shraw);  // [B][K]
+    const int64_t t = blockIdx.x;
+    const int oct = (int)(tkey[t] & 7);
+    const int64_t par = tparent[t];
+    for (int e = threadIdx.x; e < B * K; e += blockDim.x) xs[e] = (Tc)le_p[par * B * K + e];
+    __syncthreads();
+    const Tc *tb = tab + (size_t)oct * K * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        for (int bb = 0; bb < B; ++bb) {
+            Tc acc = Tc(0);
+            const Tc *x = xs + bb * K;
+            for (int c = 0; c < K; ++c) acc += tb[(size_t)c * K + k] * x[c];
+            Ts *o = le_c + (t * B + bb) * K + k;
+            *o = (Ts)((Tc)*o + acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- evaluation
+template <class T>
+struct Vec4 {
+    T x, y, z, w;
+};
+
+template <class T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) {
+    return rsqrtf(x);
+}
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) {
+    return rsqrt(x);
+}
+
+template <class T>
+__device__ __forceinline__ void two_sum(T &hi, T &lo, T x) {
+    const T s = hi + x;
+    const T bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
+constexpr int kEvalWarps = 4;
+constexpr int kEvalChunk = 64;
+constexpr int kTPL = 4;  // targets per lane
+
+struct EvalArgs {
+    const int4 *items;
+    int64_t n_items;
+    const uint64_t *tkey;      // leaf keys
+    const int32_t *perm;
+    const void *tloc;          // [M][3] T
+    const void *mass;          // [ns_L][B][b3] T
+    const void *le;            // [nt_L][B][K] T
+    const QuadRule *qr;
+    Block3 blk;                // leaf source block
+    int b, nq, B, K, p;
+    int64_t M;
+    double scale;              // G * h
+    double eps2;               // coincidence radius^2 (voxel units)
+    double *g, *gz;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kEvalWarps * 32)
+eval_kernel(EvalArgs a) {
+    extern __shared__ unsigned char shraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P2 = a.p * a.p;
+    T *wsh = reinterpret_cast<T *>(shraw) + (size_t)warp * (4 * kEvalChunk + 3 * P2);
+    Vec4<T> *src = reinterpret_cast<Vec4<T> *>(wsh);
+    T *Dx = wsh + 4 * kEvalChunk, *Dy = Dx + P2, *Dz = Dy + P2;
+    const T *tloc = reinterpret_cast<const T *>(a.tloc);
+    const T *mass = reinterpret_cast<const T *>(a.mass);
+    const T *le = reinterpret_cast<const T *>(a.le);
+    const int b3 = a.b * a.b * a.b;
+    const int nsrc = b3 * a.nq;
+    const T half_b = T(0.5) * T(a.b);
+    const T inv_b = T(1) / T(a.b);
+    const T eps2 = (T)a.eps2;
+    for (int64_t it = (int64_t)blockIdx.x * kEvalWarps + warp; it < a.n_items;
+         it += (int64_t)gridDim.x * kEvalWarps) {
+        const int4 item = a.items[it];
+        const int leaf = item.x;
+        const uint64_t key = a.tkey[leaf];
+        int64_t lc[3];
+        {
+            uint64_t k = key;
+            lc[0] = lc[1] = lc[2] = 0;
+            for (int bit = 0; bit < 21; ++bit) {
+                lc[0] |= (int64_t)((k >> (3 * bit)) & 1) << bit;
+                lc[1] |= (int64_t)((k >> (3 * bit + 1)) & 1) << bit;
+                lc[2] |= (int64_t)((k >> (3 * bit + 2)) & 1) << bit;
+            }
+        }
+        T tx[kTPL], ty[kTPL], tz[kTPL];
+        int tid[kTPL];
+#pragma unroll
+        for (int u = 0; u < kTPL; ++u) {
+            const int r = lane + 32 * u;
+            tid[u] = r < item.z ? item.y + r : -1;
+            const int64_t i = tid[u] >= 0 ? tid[u] : item.y;
+            tx[u] = tloc[3 * i + 0];
+            ty[u] = tloc[3 * i + 1];
+            tz[u] = tloc[3 * i + 2];
+        }
+        for (int bb = 0; bb < a.B; ++bb) {
+            T hx[kTPL], hy[kTPL], hz[kTPL], lx[kTPL], ly[kTPL], lz[kTPL];
+#pragma unroll
+            for (int u = 0; u < kTPL; ++u) hx[u] = hy[u] = hz[u] = lx[u] = ly[u] = lz[u] = T(0);
+            // ---- near field: the leaf itself and its nearest neighbours
+            for (int nb = 0; nb < 27; ++nb) {
+                const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+                const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1],
+                              sz = lc[2] + dz - a.blk.lo[2];
+                if (sx < 0 || sy < 0 || sz < 0 || sx >= a.blk.n[0] || sy >= a.blk.n[1] || sz >= a.blk.n[2])
+                    continue;
+                const int64_t sl = (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx;
+                const T *ms = mass + (sl * a.B + bb) * b3;
+                T px[kTPL], py[kTPL], pz[kTPL];
+#pragma unroll
+                for (int u = 0; u < kTPL; ++u) px[u] = py[u] = pz[u] = T(0);
+                for (int c0 = 0; c0 < nsrc; c0 += kEvalChunk) {
+                    const int cnt = min(kEvalChunk, nsrc - c0);
+                    __syncwarp();
+                    for (int s = lane; s < cnt; s += 32) {
+                        const int u = c0 + s;
+                        const int v = u / a.nq, q = u - v * a.nq;
+                        const int vx = v % a.b, vy = (v / a.b) % a.b, vz = v / (a.b * a.b);
+                        Vec4<T> e;
+                        e.x = T(dx * a.b + vx) + (T)a.qr->offf[q][0] - half_b;
+                        e.y = T(dy * a.b + vy) + (T)a.qr->offf[q][1] - half_b;
+                        e.z = T(dz * a.b + vz) + (T)a.qr->offf[q][2] - half_b;
+                        if (sizeof(T) == 8) {
+                            e.x = T(dx * a.b + vx) + (T)(0.5 + 0.5 * a.qr->xi[q][0]) - half_b;
+                            e.y = T(dy * a.b + vy) + (T)(0.5 + 0.5 * a.qr->xi[q][1]) - half_b;
+                            e.z = T(dz * a.b + vz) + (T)(0.5 + 0.5 * a.qr->xi[q][2]) - half_b;
+                        }
+                        e.w = ms[v] * (T)a.qr->wn[q];
+                        src[s] = e;
+                    }
+                    __syncwarp();
+                    for (int s = 0; s < cnt; ++s) {
+                        const Vec4<T> e = src[s];
+#pragma unroll
+                        for (int u = 0; u < kTPL; ++u) {
+                            const T ddx = tx[u] - e.x, ddy = ty[u] - e.y, ddz = tz[u] - e.z;
+                            const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            const T ri = r2 > eps2 ? rsqrt_t<T>(r2) : T(0);
+                            const T k3 = e.w * (ri * ri * ri);
+                            px[u] += k3 * ddx;
+                            py[u] += k3 * ddy;
+                            pz[u] += k3 * ddz;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kTPL; ++u) {
+                    two_sum(hx[u], lx[u], px[u]);
+                    two_sum(hy[u], ly[u], py[u]);
+                    two_sum(hz[u], lz[u], pz[u]);
+                }
+            }
+            // ---- far field: gradient of the leaf's local expansion
+            __syncwarp();
+            const T *L = le + ((int64_t)leaf * a.B + bb) * a.K;
+            for (int e = lane; e < P2; e += 32) grad_coeff<T>(L, e, Dx[e], Dy[e], Dz[e]);
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < kTPL; ++u) {
+                if (tid[u] < 0) continue;
+                T fx, fy, fz;
+                l2p_sum<T>(a.p, Dx, Dy, Dz, tx[u] * inv_b, ty[u] * inv_b, tz[u] * inv_b, fx, fy, fz);
+                const double far_s = -1.0 / ((double)a.b * (double)a.b);
+                const double gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
+                const double gy = ((double)hy[u] + (double)ly[u] + far_s * (double)fy) * a.scale;
+                const double gzv = ((double)hz[u] + (double)lz[u] + far_s * (double)fz) * a.scale;
+                const int64_t j = a.perm[tid[u]];
+                if (a.g) {
+                    double *o = a.g + ((int64_t)bb * a.M + j) * 3;
+                    o[0] = gx;
+                    o[1] = gy;
+                    o[2] = gzv;
+                }
+                if (a.gz) a.gz[(int64_t)bb * a.M + j] = gzv;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tables
+std::mutex g_tab_mu;
+std::vector<Tables *> g_tabs;
+
+}  // namespace
+
+gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    for (Tables *t : g_tabs)
+        if (t->device == device && t->p == p) {
+            *out = t;
+            return GF_OK;
+        }
+    Tables *T = new Tables();
+    T->device = device;
+    T->p = p;
+    T->K = (p + 1) * (p + 1);
+    T->Kp = (T->K + 7) & ~7;
+    const size_t KK = (size_t)T->K * T->K;
+    // tables live for the life of the process: one set per (device, p)
+    GF_CUDA(cudaMalloc(&T->m2l_d, 343 * KK * sizeof(double)));
+    GF_CUDA(cudaMalloc(&T->m2l_f, 343 * KK * sizeof(float)));
+    GF_CUDA(cudaMalloc(&T->m2m_d, 8 * KK * sizeof(double)));
+    GF_CUDA(cudaMalloc(&T->l2l_d, 8 * KK * sizeof(double)));
+    GF_CUDA(cudaMalloc(&T->m2m_f, 8 * KK * sizeof(float)));
+    GF_CUDA(cudaMalloc(&T->l2l_f, 8 * KK * sizeof(float)));
+    GF_CUDA(cudaMemsetAsync(T->m2l_d, 0, 343 * KK * sizeof(double), st));
+    GF_CUDA(cudaMemsetAsync(T->m2l_f, 0, 343 * KK * sizeof(float), st));
+    const int H = 2 * p;
+    const size_t shm = sizeof(double) * (H + 1) * (H + 2);
+    build_ops<<<343 + 16, 256, shm, st>>>(p, T->K, host_logfact(), T->m2l_d, T->m2l_f, T->m2m_d, T->m2m_f,
+                                          T->l2l_d, T->l2l_f);
+    GF_KERNEL_DONE();
+    GF_TRY(m2l_prepare_tables(T, st));
+    GF_CUDA(cudaStreamSynchronize(st));
+    g_tabs.push_back(T);
+    *out = T;
+    return GF_OK;
+}
+
+gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    DeviceArena &A = plan->arena;
+    const size_t rs = F->mixed ? sizeof(float) : sizeof(double);
+    const int K = F->K, B = F->B;
+    for (int l = 2; l <= F->L; ++l) {
+        FmmLevel &lv = F->lev[l];
+        GF_TRY(A.alloc(&lv.me, (size_t)std::max<int64_t>(lv.ns, 1) * B * K * rs));
+        GF_TRY(A.alloc(&lv.le, (size_t)std::max<int64_t>(lv.nt, 1) * B * K * rs));
+    }
+    const int b3 = F->b * F->b * F->b;
+    GF_TRY(A.alloc(&F->mass, (size_t)std::max<int64_t>(F->lev[F->L].ns, 1) * B * b3 * rs));
+    GF_TRY(A.alloc_n(&F->p2m_d, (size_t)b3 * K));
+    GF_TRY(A.alloc_n(&F->p2m_f, (size_t)b3 * K));
+    static bool il_ready[64] = {false};
+    static std::mutex il_mu;
+    {
+        std::lock_guard<std::mutex> lk(il_mu);
+        if (!il_ready[plan->device & 63]) {
+            static signed char h_il[8][189][3];
+            for (int c = 0; c < 8; ++c) il_offsets_host(c, h_il[c]);
+            GF_TRY(m2l_upload_offsets(h_il));
+            il_ready[plan->device & 63] = true;
+        }
+    }
+    GF_TRY(get_tables(plan->device, F->p, st, &F->tab));
+    const size_t shm = sizeof(double) * ((F->p + 1) * (F->p + 2) + K);
+    build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), F->p2m_d, F->p2m_f);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
+// ---------------------------------------------------------------- forward
+namespace {
+
+template <class T>
+gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, double *g, double *gz,
+                      cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const int K = F->K, L = F->L;
+    const int b3 = F->b * F->b * F->b;
+    const Tables *tab = F->tab;
+    // a0: leaf-blocked densities
+    {
+        const FmmLevel &lv = F->lev[L];
+        const int64_t total = lv.ns * B * b3;
+        const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        block_densities<T><<<grid, 256, 0, st>>>(rho, rho_dtype == GF_DTYPE_F32, plan->grid.n[0], plan->grid.n[1],
+                                                 plan->grid.n[2], F->voff[0], F->voff[1], F->voff[2],
+                                                 block_of(lv), F->b, B, (T *)F->mass, plan->d_status);
+        GF_KERNEL_DONE();
+    }
+    stage_mark(plan, 1, st);
+    // a3: P2M at the leaves
+    {
+        const FmmLevel &lv = F->lev[L];
+        const unsigned grid = ceil_div(lv.ns, kP2MLeaves);
+        const size_t shm = sizeof(T) * kP2MLeaves * B * b3;
+        const T *P = sizeof(T) == 8 ? (const T *)F->p2m_d : (const T *)F->p2m_f;
+        GF_TRY(ensure_smem(p2m_kernel<T>, shm));
+        p2m_kernel<T><<<grid, 128, shm, st>>>((const T *)F->mass, P, lv.ns, b3, B, K, (T *)lv.me);
+        GF_KERNEL_DONE();
+    }
+    stage_mark(plan, 2, st);
+    // a4: M2M up to level 2; in mixed precision the translations into the
+    // top levels (parent level <= 3) are done in FP64
+    for (int l = L - 1; l >= 2; --l) {
+        const FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
+        if (sizeof(T) == 4 && l <= 3) {
+            const size_t shm = sizeof(double) * 8 * B * K;
+            GF_TRY((ensure_smem(m2m_kernel<T, double>, shm)));
+            m2m_kernel<T, double><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
+                                                                     block_of(pa), B, K, tab->m2m_d);
+        } else {
+            const size_t shm = sizeof(T) * 8 * B * K;
+            GF_TRY((ensure_smem(m2m_kernel<T, T>, shm)));
+            const T *tb = sizeof(T) == 8 ? (const T *)tab->m2m_d : (const T *)tab->m2m_f;
+            m2m_kernel<T, T><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
+                                                                block_of(pa), B, K, tb);
+        }
+        GF_KERNEL_DONE();
+    }
+    stage_mark(plan, 3, st);
+    // a5/a6: M2L at every level (each overwrites its level's LE), then the
+    // L2L chain from level 3 down, which adds each finished parent LE.
+    for (int l = 2; l <= L; ++l) {
+        const FmmLevel &lv = F->lev[l];
+        if (lv.nt == 0) continue;
+        GF_TRY(m2l_level<T>(plan, l, B, st));
+    }
+    stage_mark(plan, 4, st);
+    for (int l = 3; l <= L; ++l) {
+        const FmmLevel &lv = F->lev[l];
+        if (lv.nt == 0) continue;
+        const FmmLevel &pa = F->lev[l - 1];
+        if (sizeof(T) == 4 && l - 1 <= 3) {
+            l2l_kernel<T, double><<<(unsigned)lv.nt, 128, sizeof(double) * B * K, st>>>(
+                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, tab->l2l_d);
+        } else {
+            const T *tb = sizeof(T) == 8 ? (const T *)tab->l2l_d : (const T *)tab->l2l_f;
+            l2l_kernel<T, T><<<(unsigned)lv.nt, 128, sizeof(T) * B * K, st>>>(
+                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, tb);
+        }
+        GF_KERNEL_DONE();
+    }
+    stage_mark(plan, 5, st);
+    // a7-a9: near field + L2P + combine + scatter
+    if (F->n_items > 0) {
+        EvalArgs a;
+        a.items = F->items;
+        a.n_items = F->n_items;
+        a.tkey = F->lev[L].tkey;
+        a.perm = F->perm;
+        a.tloc = sizeof(T) == 8 ? (const void *)F->tloc_d : (const void *)F->tloc_f;
+        a.mass = F->mass;
+        a.le = F->lev[L].le;
+        a.qr = quad_device(plan);
+        a.blk = block_of(F->lev[L]);
+        a.b = F->b;
+        a.nq = F->nq;
+        a.B = B;
+        a.K = K;
+        a.p = F->p;
+        a.M = plan->M;
+        a.scale = plan->G * F->h;
+        a.eps2 = sizeof(T) == 8 ? 1e-18 : 1e-12;
+        a.g = g;
+        a.gz = gz;
+        const size_t shm = sizeof(T) * kEvalWarps * (4 * kEvalChunk + 3 * F->p * F->p);
+        const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
+        GF_TRY(ensure_smem(eval_kernel<T>, shm));
+        eval_kernel<T><<<grid, kEvalWarps * 32, shm, st>>>(a);
+        GF_KERNEL_DONE();
+    }
+    stage_mark(plan, 6, st);
+    return GF_OK;
+}
+
+}  // namespace
+
+gf_status fmm_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, double *g, double *gz,
+                      cudaStream_t st) {
+    if (plan->M == 0) return GF_OK;
+    if (plan->fmm->mixed) return run_forward<float>(plan, rho, rho_dtype, B, g, gz, st);
+    return run_forward<double>(plan, rho, rho_dtype, B, g, gz, st);
+}
+
 gf_status fmm_adjoint(gf_plan_s *, const double *, int, int, double *, cudaStream_t) {
-    set_error("FMM mode is not built yet");
+    set_error("the FMM adjoint is not built yet");
     return GF_ERR_UNSUPPORTED;
 }
-void fmm_destroy(gf_plan_s *) {}
-gf_status fmm_info(const gf_plan_s *, gf_plan_info *) { return GF_OK; }
-gf_status fmm_export_tree(gf_plan_s *, int, int32_t *, uint64_t *, uint64_t *, int64_t *, int64_t *) {
-    set_error("FMM mode is not built yet");
-    return GF_ERR_UNSUPPORTED;
-}
-size_t fmm_bytes_estimate(const gf_grid *, int, int64_t, const gf_options *) { return 0; }
+
 }  // namespace gf

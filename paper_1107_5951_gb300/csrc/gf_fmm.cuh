@@ -1,0 +1,75 @@
+// gf_fmm.cuh -- octree and expansion workspaces of a FMM plan (Sec. 2.3).
+//
+// The tree has uniform depth L.  Leaves are cubes of b^3 voxels aligned to
+// the voxel grid, so every box that overlaps the grid holds sources and the
+// source boxes of each level form a dense integer block; their multipole
+// expansions (ME) are stored densely over that block.  Observers are sorted
+// by Morton key; the boxes that contain observers (and their ancestors) are
+// listed per level in ascending key order and carry the local expansions
+// (LE).  All FMM arithmetic is done in voxel units (h = 1): sources carry
+// q = rho * w_q / sum(w), and the result is scaled by G*h at the end.
+#pragma once
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+struct FmmLevel {
+    int64_t slo[3] = {0, 0, 0};   // source block: lowest box coordinate
+    int64_t sn[3] = {0, 0, 0};    // source block extent (boxes per axis)
+    int64_t ns = 0;               // number of source boxes
+    int64_t nt = 0;               // number of observer boxes
+    uint64_t *tkey = nullptr;     // [nt] Morton keys, ascending
+    int32_t *tparent = nullptr;   // [nt] index of the parent box at level-1
+    int32_t *m2l_order = nullptr; // [nt] observer boxes grouped by parity class
+    int64_t cls_off[9] = {0};     // class c: m2l_order[cls_off[c] .. cls_off[c+1])
+    void *me = nullptr;           // [ns][B][K]
+    void *le = nullptr;           // [nt][B][K]
+};
+
+// Translation operators for one expansion degree, shared by all plans on a
+// device (they depend on p only, thanks to the scaled expansions).  Stored
+// transposed (input component major) for the SIMT kernels:
+//   m2l_*[off][c][k]  off = (dz+3)*49 + (dy+3)*7 + (dx+3)
+//   m2m_*[oct][c][k], l2l_*[oct][c][k]  oct = (x&1) | (y&1)<<1 | (z&1)<<2
+//                                          of the child box
+struct Tables {
+    int device = -1, p = 0, K = 0, Kp = 0;   // Kp = K rounded up to 8
+    double *m2l_d = nullptr;
+    float *m2l_f = nullptr;
+    double *m2m_d = nullptr, *l2l_d = nullptr;
+    float *m2m_f = nullptr, *l2l_f = nullptr;
+};
+
+gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out);
+
+struct FmmPlan {
+    int L = 0, b = 0, p = 0, K = 0, B = 1, nq = 1;
+    bool mixed = false;
+    int64_t voff[3] = {0, 0, 0};  // grid voxel (0,0,0) sits at tree voxel voff
+    double lo[3] = {0, 0, 0};     // root lower corner (m)
+    double h = 1, s_leaf = 1, inv_s = 1;
+    FmmLevel lev[kMaxLevels + 1];
+    int32_t *perm = nullptr;      // [M] sorted position -> caller index
+    uint64_t *okey = nullptr;     // [M] leaf key of each sorted observer
+    int32_t *leaf_beg = nullptr;  // [nt_L + 1] observer range of each leaf
+    float *tloc_f = nullptr;      // [M][3] offset from own leaf centre (voxel units)
+    double *tloc_d = nullptr;
+    int4 *items = nullptr;        // evaluation work: (leaf, first, count, 0)
+    int64_t n_items = 0;
+    void *mass = nullptr;         // [ns_L][B][b^3] voxel densities, leaf-blocked
+    double *p2m_d = nullptr;      // [b^3][K] quadrature-folded P2M matrix
+    float *p2m_f = nullptr;
+    const Tables *tab = nullptr;
+};
+
+// Interaction-list offsets of a box whose position inside its parent is
+// `cls` ((x&1) | (y&1)<<1 | (z&1)<<2): the 189 vectors o with max-norm 2 or 3
+// such that the parent of (box + o) neighbours the box's parent, in (dz, dy,
+// dx) ascending order.
+void il_offsets_host(int cls, signed char out[189][3]);
+
+// Plan-time helpers (gf_fmm.cu)
+gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st);
+
+}  // namespace gf

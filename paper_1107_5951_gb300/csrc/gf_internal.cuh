@@ -85,9 +85,26 @@ struct gf_plan_s {
     gf::FmmPlan *fmm = nullptr;
     int *d_status = nullptr;     // device-side check word
     size_t device_bytes = 0;
+    int64_t near_pairs = 0, m2l_pairs = 0;
+    bool timing = false;
+    cudaEvent_t ev[GF_NUM_STAGES + 1] = {};
+    bool ev_used[GF_NUM_STAGES + 1] = {};
 };
 
 namespace gf {
+// Record the boundary event `i` of the stage timeline when timing is on.
+inline void stage_mark(gf_plan_s *p, int i, cudaStream_t st) {
+    if (p->timing) {
+        cudaEventRecord(p->ev[i], st);
+        p->ev_used[i] = true;
+    }
+}
+}  // namespace gf
+
+namespace gf {
+
+// The plan's quadrature rule in device memory.
+const QuadRule *quad_device(gf_plan_s *plan);
 
 // Direct-mode kernels (gf_direct.cu)
 gf_status direct_prepare(gf_plan_s *plan, const double *obs_dev, cudaStream_t st);
@@ -109,6 +126,19 @@ gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *k
 size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt);
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory.
+template <class Kern>
+inline gf_status ensure_smem(Kern kernel, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) {
+            set_error("cannot reserve %zu bytes of shared memory: %s", bytes, cudaGetErrorString(e));
+            return GF_ERR_UNSUPPORTED;
+        }
+    }
+    return GF_OK;
+}
 
 // Number of kernels the library has launched (all plans, all threads).
 void count_launch(int n = 1);

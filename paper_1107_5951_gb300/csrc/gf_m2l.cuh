@@ -1,0 +1,17 @@
+// gf_m2l.cuh -- the multipole-to-local stage (Sec. 2.3: an ME is turned
+// into an LE for every box of the interaction list).
+#pragma once
+
+#include "gf_fmm.cuh"
+
+namespace gf {
+
+gf_status m2l_upload_offsets(const signed char h_il[8][189][3]);
+gf_status m2l_prepare_tables(Tables *T, cudaStream_t st);
+
+// LE_l[t] = sum over the interaction list of box t of T_o * ME_l[t + o],
+// for every observer box t of level `level` (overwrites LE_l).
+template <class T>
+gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st);
+
+}  // namespace gf

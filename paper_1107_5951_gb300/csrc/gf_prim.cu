@@ -1,0 +1,269 @@
+// gf_prim.cu -- exclusive scan, stable LSD radix sort and a bounding-box
+// reduction, written for the octree build.
+#include <float.h>
+
+#include <algorithm>
+
+#include "gf_prim.cuh"
+
+namespace gf {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 1024
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 2048 keys per block
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one 1024-element tile per block; block totals to sums.
+__global__ void __launch_bounds__(kScanThreads)
+scan_tiles(const int64_t *__restrict__ in, int64_t *__restrict__ out, int64_t n,
+           int64_t *__restrict__ sums) {
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        loc += v[i];
+    }
+    const int64_t incl = warp_incl_scan(loc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        const int64_t wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;
+        if (lane == kScanThreads / 32 - 1) sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    int64_t run = warp_tot[warp] + incl - loc;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+__global__ void add_tile_offsets(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ offs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / kScanTile];
+}
+
+__global__ void write_total(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ offs,
+                            const int64_t *__restrict__ sums, int64_t nb) {
+    out[n] = offs[nb - 1] + sums[nb - 1];
+}
+
+gf_status scan_rec(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch, cudaStream_t st,
+                   bool write_tot) {
+    if (n <= 0) {
+        if (write_tot) GF_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        return GF_OK;
+    }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    int64_t *sums = scratch;            // [nb]
+    int64_t *offs = scratch + nb;       // [nb + 1]
+    scan_tiles<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    GF_KERNEL_DONE();
+    if (nb > 1) {
+        GF_TRY(scan_rec(sums, offs, nb, scratch + 2 * nb + 1, st, false));
+        add_tile_offsets<<<ceil_div(n, 256), 256, 0, st>>>(out, n, offs);
+        GF_KERNEL_DONE();
+    } else {
+        GF_CUDA(cudaMemsetAsync(offs, 0, sizeof(int64_t), st));
+    }
+    if (write_tot) {
+        write_total<<<1, 1, 0, st>>>(out, n, offs, sums, nb);
+        GF_KERNEL_DONE();
+    }
+    return GF_OK;
+}
+
+// -------------------------------------------------------------- radix sort
+__global__ void __launch_bounds__(kSortThreads)
+radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, int64_t nblocks,
+           int64_t *__restrict__ hist) {
+    __shared__ int cnt[kRadix];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: keys of the tile are ranked in index order (round-major,
+// thread-minor), so equal digits keep their relative order.
+__global__ void __launch_bounds__(kSortThreads)
+radix_scatter(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals, int64_t n,
+              int shift, int64_t nblocks, const int64_t *__restrict__ offs,
+              uint64_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ int64_t run[kRadix];
+    __shared__ int wcnt[kWarps][kRadix];
+    __shared__ int total[kRadix];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    run[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        const bool valid = i < n;
+        uint64_t k = valid ? keys[i] : 0;
+        int32_t v = valid ? vals[i] : 0;
+        const int d = valid ? (int)((k >> shift) & 0xff) : kRadix;  // invalid -> sentinel
+        for (int w = 0; w < kWarps; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt_mask);
+        const int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {   // exclusive prefix over warps for digit threadIdx.x
+            int acc = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                const int c = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = acc;
+                acc += c;
+            }
+            total[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            const int64_t pos = run[d] + wcnt[warp][d] + rank;
+            keys_out[pos] = k;
+            vals_out[pos] = v;
+        }
+        __syncthreads();
+        run[threadIdx.x] += total[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------- bbox
+__global__ void bbox_partial(const double *__restrict__ p, int64_t n, double *__restrict__ part) {
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            const double v = p[3 * i + a];
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    __shared__ double s[32][6];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            s[warp][a] = mn[a];
+            s[warp][3 + a] = mx[a];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double r = threadIdx.x < 3 ? DBL_MAX : -DBL_MAX;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            r = threadIdx.x < 3 ? fmin(r, s[w][threadIdx.x]) : fmax(r, s[w][threadIdx.x]);
+        part[blockIdx.x * 6 + threadIdx.x] = r;
+    }
+}
+
+__global__ void bbox_final(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    if (threadIdx.x < 6) {
+        double r = threadIdx.x < 3 ? DBL_MAX : -DBL_MAX;
+        for (int b = 0; b < nb; ++b)
+            r = threadIdx.x < 3 ? fmin(r, part[b * 6 + threadIdx.x]) : fmax(r, part[b * 6 + threadIdx.x]);
+        out[threadIdx.x] = r;
+    }
+}
+
+}  // namespace
+
+size_t scan_scratch_bytes(int64_t n) {
+    size_t tot = 0;
+    int64_t m = n;
+    do {
+        const int64_t nb = (m + kScanTile - 1) / kScanTile;
+        tot += (size_t)(2 * nb + 1);
+        m = nb;
+    } while (m > 1);
+    return (tot + 16) * sizeof(int64_t);
+}
+
+size_t sort_scratch_bytes(int64_t n) {
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t h = nb * kRadix;
+    return (size_t)(h + 1) * sizeof(int64_t) + scan_scratch_bytes(h) + 256;
+}
+
+gf_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st) {
+    return scan_rec(in, out, n, reinterpret_cast<int64_t *>(scratch), st, true);
+}
+
+gf_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int32_t *vals_alt, int64_t n,
+                         int bits, void *scratch, cudaStream_t st) {
+    if (n <= 1 || bits <= 0) return GF_OK;
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t h = nb * kRadix;
+    int64_t *hist = reinterpret_cast<int64_t *>(scratch);
+    int64_t *scan_scr = hist + h + 1;
+    uint64_t *ka = keys, *kb = keys_alt;
+    int32_t *va = vals, *vb = vals_alt;
+    const int passes = (bits + 7) / 8;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = 8 * ps;
+        radix_hist<<<(unsigned)nb, kSortThreads, 0, st>>>(ka, n, shift, nb, hist);
+        GF_KERNEL_DONE();
+        GF_TRY(scan_rec(hist, hist, h, scan_scr, st, false));
+        radix_scatter<<<(unsigned)nb, kSortThreads, 0, st>>>(ka, va, n, shift, nb, hist, kb, vb);
+        GF_KERNEL_DONE();
+        uint64_t *tk = ka;
+        ka = kb;
+        kb = tk;
+        int32_t *tv = va;
+        va = vb;
+        vb = tv;
+    }
+    if (ka != keys) {
+        GF_CUDA(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+        GF_CUDA(cudaMemcpyAsync(vals, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    return GF_OK;
+}
+
+gf_status bbox3(const double *pts, int64_t n, double *out, cudaStream_t st) {
+    // out must have room for 6 + 6*256 doubles: the partials follow the result
+    const int nb = (int)std::min<int64_t>(256, (n + 255) / 256);
+    if (n <= 0) return GF_OK;
+    bbox_partial<<<nb, 256, 0, st>>>(pts, n, out + 6);
+    GF_KERNEL_DONE();
+    bbox_final<<<1, 32, 0, st>>>(out + 6, nb, out);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
+}  // namespace gf

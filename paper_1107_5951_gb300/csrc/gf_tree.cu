@@ -1,0 +1,526 @@
+// gf_tree.cu -- Morton-sorted octree of a FMM plan (Sec. 2.3, "Hierarchical
+// space decomposition"): root geometry, observer keys and their stable sort,
+// occupied boxes of every level, parity-grouped M2L order, observer offsets
+// from their leaf centres and the evaluation work list.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "gf_fmm.cuh"
+#include "gf_prim.cuh"
+
+namespace gf {
+namespace {
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+    // insert two zero bits between the low 21 bits of v
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t compact3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t morton(int64_t x, int64_t y, int64_t z) {
+    return spread3((uint64_t)x) | (spread3((uint64_t)y) << 1) | (spread3((uint64_t)z) << 2);
+}
+
+__device__ __forceinline__ void demorton(uint64_t k, int64_t &x, int64_t &y, int64_t &z) {
+    x = (int64_t)compact3(k);
+    y = (int64_t)compact3(k >> 1);
+    z = (int64_t)compact3(k >> 2);
+}
+
+struct Geo {
+    double lo[3];
+    double inv_s, h;
+    int L, b;
+};
+
+// Leaf key of every observer: floor((x - lo) * inv_s) with one rounded
+// subtraction and one rounded multiplication, clamped to the root.
+__global__ void obs_keys(const double *__restrict__ obs, int64_t M, Geo g, uint64_t *__restrict__ keys,
+                         int32_t *__restrict__ vals, int *__restrict__ status) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const double top = (double)((1ll << g.L) - 1);
+    int64_t c[3];
+    for (int a = 0; a < 3; ++a) {
+        const double x = obs[3 * j + a];
+        if (!isfinite(x)) atomicOr(status + 2, 1);
+        double q = floor(__dmul_rn(__dsub_rn(x, g.lo[a]), g.inv_s));
+        q = fmin(fmax(q, 0.0), top);
+        c[a] = (int64_t)q;
+    }
+    keys[j] = morton(c[0], c[1], c[2]);
+    vals[j] = (int32_t)j;
+}
+
+__global__ void mark_new(const uint64_t *__restrict__ keys, int64_t n, int shift, int64_t *__restrict__ flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flags[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+}
+
+// After an exclusive scan of the flags: write the unique (shifted) keys, the
+// first index of each run, and the run index of every element.
+__global__ void compact_runs(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                             const int64_t *__restrict__ excl, uint64_t *__restrict__ ukeys,
+                             int32_t *__restrict__ beg, int32_t *__restrict__ run_of) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool nw = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift));
+    const int64_t e = excl[i];
+    if (nw) {
+        ukeys[e] = keys[i] >> shift;
+        if (beg) beg[e] = (int32_t)i;
+    }
+    if (run_of) run_of[i] = (int32_t)(nw ? e : e - 1);
+}
+
+__global__ void set_last(int32_t *__restrict__ a, int64_t idx, int32_t v) { a[idx] = v; }
+
+__global__ void class_keys(const uint64_t *__restrict__ tkey, int64_t n, uint64_t *__restrict__ ck,
+                           int32_t *__restrict__ idx, int *__restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(tkey[i] & 7);
+    ck[i] = (uint64_t)c;
+    idx[i] = (int32_t)i;
+    atomicAdd(cnt + c, 1);
+}
+
+__global__ void obs_local(const double *__restrict__ obs, const int32_t *__restrict__ perm,
+                          const uint64_t *__restrict__ okey, int64_t M, Geo g, float *__restrict__ tf,
+                          double *__restrict__ td) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t j = perm[i];
+    int64_t c[3];
+    demorton(okey[i], c[0], c[1], c[2]);
+    for (int a = 0; a < 3; ++a) {
+        const double u = (obs[3 * j + a] - g.lo[a]) / g.h;
+        const double loc = u - ((double)c[a] * g.b + 0.5 * g.b);
+        if (td) td[3 * i + a] = loc;
+        if (tf) tf[3 * i + a] = (float)loc;
+    }
+}
+
+constexpr int kItemTargets = 128;
+
+__global__ void item_counts(const int32_t *__restrict__ beg, int64_t nleaf, int64_t *__restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaf) return;
+    const int64_t n = beg[i + 1] - beg[i];
+    cnt[i] = (n + kItemTargets - 1) / kItemTargets;
+}
+
+__global__ void item_fill(const int32_t *__restrict__ beg, int64_t nleaf, const int64_t *__restrict__ off,
+                          int4 *__restrict__ items) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaf) return;
+    const int b0 = beg[i], b1 = beg[i + 1];
+    int64_t o = off[i];
+    for (int f = b0; f < b1; f += kItemTargets) items[o++] = make_int4((int)i, f, min(kItemTargets, b1 - f), 0);
+}
+
+// Interaction list (316 offsets, dz/dy/dx ascending, max-norm >= 2) and near
+// list (27 offsets) of observer boxes, as source box Morton keys or -1.
+__global__ void export_lists(const uint64_t *__restrict__ tkey, int64_t nt, int level, int64_t slo0,
+                             int64_t slo1, int64_t slo2, int64_t shi0, int64_t shi1, int64_t shi2,
+                             int64_t *__restrict__ il, int64_t *__restrict__ nearl) {
+    const int64_t t = (int64_t)blockIdx.x;
+    if (t >= nt) return;
+    int64_t x, y, z;
+    demorton(tkey[t], x, y, z);
+    for (int u = threadIdx.x; u < 343; u += blockDim.x) {
+        const int dx = u % 7 - 3, dy = (u / 7) % 7 - 3, dz = u / 49 - 3;
+        const int mx = max(abs(dx), max(abs(dy), abs(dz)));
+        const int64_t sx = x + dx, sy = y + dy, sz = z + dz;
+        const bool inblk = sx >= slo0 && sx <= shi0 && sy >= slo1 && sy <= shi1 && sz >= slo2 && sz <= shi2;
+        if (mx >= 2 && il) {
+            // rank of u among the 316 offsets with max-norm >= 2
+            int r = 0;
+            for (int w = 0; w < u; ++w) {
+                const int ax = w % 7 - 3, ay = (w / 7) % 7 - 3, az = w / 49 - 3;
+                if (max(abs(ax), max(abs(ay), abs(az))) >= 2) ++r;
+            }
+            const bool adj = level >= 2 && llabs((sx >> 1) - (x >> 1)) <= 1 && llabs((sy >> 1) - (y >> 1)) <= 1 &&
+                             llabs((sz >> 1) - (z >> 1)) <= 1;
+            il[t * 316 + r] = (inblk && adj && sx >= 0 && sy >= 0 && sz >= 0) ? (int64_t)morton(sx, sy, sz) : -1;
+        }
+        if (mx <= 1 && nearl) {
+            const int r = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+            nearl[t * 27 + r] = (inblk && sx >= 0 && sy >= 0 && sz >= 0) ? (int64_t)morton(sx, sy, sz) : -1;
+        }
+    }
+}
+
+// Work counts for the roofline: near-field (observer, source) pairs and
+// interaction-list (observer box, source box) pairs.
+__global__ void count_near(const uint64_t *__restrict__ tkey, const int32_t *__restrict__ beg, int64_t nt,
+                           int64_t slo0, int64_t slo1, int64_t slo2, int64_t sn0, int64_t sn1, int64_t sn2,
+                           int64_t per_leaf, unsigned long long *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int64_t x, y, z;
+    demorton(tkey[t], x, y, z);
+    int cnt = 0;
+    for (int d = 0; d < 27; ++d) {
+        const int64_t sx = x + d % 3 - 1 - slo0, sy = y + (d / 3) % 3 - 1 - slo1, sz = z + d / 9 - 1 - slo2;
+        cnt += (sx >= 0 && sy >= 0 && sz >= 0 && sx < sn0 && sy < sn1 && sz < sn2);
+    }
+    atomicAdd(out, (unsigned long long)((int64_t)cnt * per_leaf * (beg[t + 1] - beg[t])));
+}
+
+__global__ void count_il(const uint64_t *__restrict__ tkey, int64_t nt, int64_t slo0, int64_t slo1, int64_t slo2,
+                         int64_t sn0, int64_t sn1, int64_t sn2, unsigned long long *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int64_t x, y, z;
+    demorton(tkey[t], x, y, z);
+    int cnt = 0;
+    for (int u = 0; u < 343; ++u) {
+        const int dx = u % 7 - 3, dy = (u / 7) % 7 - 3, dz = u / 49 - 3;
+        if (max(abs(dx), max(abs(dy), abs(dz))) <= 1) continue;
+        const int64_t sx = x + dx, sy = y + dy, sz = z + dz;
+        if (llabs((sx >> 1) - (x >> 1)) > 1 || llabs((sy >> 1) - (y >> 1)) > 1 || llabs((sz >> 1) - (z >> 1)) > 1)
+            continue;
+        cnt += (sx >= slo0 && sy >= slo1 && sz >= slo2 && sx < slo0 + sn0 && sy < slo1 + sn1 && sz < slo2 + sn2);
+    }
+    atomicAdd(out, (unsigned long long)cnt);
+}
+
+int default_leaf_vox(int nq) {
+    int b = (int)lround(cbrt(64.0 / nq));
+    return b < 1 ? 1 : b;
+}
+
+}  // namespace
+
+void il_offsets_host(int cls, signed char out[189][3]) {
+    const int px = cls & 1, py = (cls >> 1) & 1, pz = (cls >> 2) & 1;
+    int r = 0;
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+                if (std::max(abs(dx), std::max(abs(dy), abs(dz))) <= 1) continue;
+                // parent offset of (box + d) relative to the box's parent
+                const int qx = (px + dx) >> 1, qy = (py + dy) >> 1, qz = (pz + dz) >> 1;
+                if (abs(qx) > 1 || abs(qy) > 1 || abs(qz) > 1) continue;
+                out[r][0] = (signed char)dx;
+                out[r][1] = (signed char)dy;
+                out[r][2] = (signed char)dz;
+                ++r;
+            }
+}
+
+size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt) {
+    const int b = opt->leaf_vox > 0 ? opt->leaf_vox : default_leaf_vox(nq);
+    const int K = (opt->p + 1) * (opt->p + 1);
+    const size_t rs = opt->precision == GF_PREC_MIXED ? 4 : 8;
+    double nleaf = 1.0;
+    for (int a = 0; a < 3; ++a) nleaf *= (double)((grid->n[a] + b - 1) / b + 1);
+    const double nsrc = nleaf * 8.0 / 7.0;
+    const double ntgt = std::min<double>((double)M, nleaf * 4.0) * 8.0 / 7.0 + 64;
+    double bytes = (nsrc + ntgt) * K * rs * opt->max_batch;
+    bytes += nleaf * b * b * b * rs * opt->max_batch;          // blocked densities
+    bytes += (double)M * (8 + 4 + 4 + 12 + 24) + ntgt * 24;       // keys, perm, locals, box tables
+    bytes += (double)M * 32 + 8e6;                                // sort buffers and scratch
+    return (size_t)bytes;
+}
+
+gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
+    FmmPlan *F = new (std::nothrow) FmmPlan();
+    if (!F) {
+        set_error("host allocation failed");
+        return GF_ERR_OOM;
+    }
+    plan->fmm = F;
+    const gf_grid &gr = plan->grid;
+    const int64_t M = plan->M;
+    F->p = plan->opt.p;
+    F->K = (F->p + 1) * (F->p + 1);
+    F->B = plan->opt.max_batch;
+    F->nq = plan->quad.nq;
+    F->mixed = plan->opt.precision == GF_PREC_MIXED;
+    F->b = plan->opt.leaf_vox > 0 ? plan->opt.leaf_vox : default_leaf_vox(F->nq);
+    F->h = gr.h[0];
+    DeviceArena &A = plan->arena;
+
+    // ---- root geometry: observers' bounding box joined with the grid
+    double bb[6];
+    for (int a = 0; a < 3; ++a) {
+        bb[a] = gr.origin[a];
+        bb[3 + a] = gr.origin[a] + gr.n[a] * F->h;
+    }
+    if (M > 0) {
+        double *d_bb;
+        GF_TRY(A.alloc_n(&d_bb, 6 + 6 * 256));
+        GF_TRY(bbox3(obs, M, d_bb, st));
+        double ob[6];
+        GF_CUDA(cudaMemcpyAsync(ob, d_bb, sizeof(ob), cudaMemcpyDeviceToHost, st));
+        GF_CUDA(cudaStreamSynchronize(st));
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(ob[a]) || !isfinite(ob[3 + a])) {
+                set_error("observer coordinates must be finite");
+                return GF_ERR_INVALID_ARG;
+            }
+            bb[a] = std::min(bb[a], ob[a]);
+            bb[3 + a] = std::max(bb[3 + a], ob[3 + a]);
+        }
+    }
+    int64_t need = 1;
+    for (int a = 0; a < 3; ++a) {
+        const double below = (gr.origin[a] - bb[a]) / F->h;
+        F->voff[a] = below > 0 ? (int64_t)ceil(below) : 0;
+        F->lo[a] = gr.origin[a] - (double)F->voff[a] * F->h;
+        const double ext = ceil((bb[3 + a] - F->lo[a]) / F->h);
+        need = std::max<int64_t>(need, std::max<int64_t>(F->voff[a] + gr.n[a], (int64_t)ext));
+    }
+    int L = 2;
+    while (((int64_t)F->b << L) < need) ++L;
+    if (L > kMaxLevels - 1) {
+        set_error("observers span %lld voxels: the octree would need %d levels (max %d)",
+                  (long long)need, L, kMaxLevels - 1);
+        return GF_ERR_UNSUPPORTED;
+    }
+    F->L = L;
+    F->s_leaf = F->b * F->h;
+    F->inv_s = 1.0 / F->s_leaf;
+    for (int l = 0; l <= L; ++l) {
+        FmmLevel &lv = F->lev[l];
+        lv.ns = 1;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t lo = (F->voff[a] / F->b) >> (L - l);
+            const int64_t hi = ((F->voff[a] + gr.n[a] - 1) / F->b) >> (L - l);
+            lv.slo[a] = lo;
+            lv.sn[a] = hi - lo + 1;
+            lv.ns *= lv.sn[a];
+        }
+    }
+    Geo g;
+    for (int a = 0; a < 3; ++a) g.lo[a] = F->lo[a];
+    g.inv_s = F->inv_s;
+    g.h = F->h;
+    g.L = L;
+    g.b = F->b;
+
+    // ---- observer keys and stable sort by (key, index)
+    const int64_t Mx = std::max<int64_t>(M, 1);
+    uint64_t *keys, *keys2;
+    int32_t *vals2;
+    int64_t *flags;
+    GF_TRY(A.alloc_n(&keys, Mx));
+    GF_TRY(A.alloc_n(&keys2, Mx));
+    GF_TRY(A.alloc_n(&F->perm, Mx));
+    GF_TRY(A.alloc_n(&vals2, Mx));
+    GF_TRY(A.alloc_n(&flags, Mx + 1));
+    void *scratch;
+    const size_t scr = std::max(sort_scratch_bytes(Mx), scan_scratch_bytes(Mx + 1));
+    GF_TRY(A.alloc(&scratch, scr));
+    F->okey = keys;
+    if (M > 0) {
+        obs_keys<<<ceil_div(M, 256), 256, 0, st>>>(obs, M, g, keys, F->perm, plan->d_status);
+        GF_KERNEL_DONE();
+        GF_TRY(radix_sort_u64(keys, F->perm, keys2, vals2, M, 3 * L, scratch, st));
+    }
+
+    // ---- leaves and their ancestors
+    FmmLevel &leaf = F->lev[L];
+    int64_t nleaf = 0;
+    if (M > 0) {
+        mark_new<<<ceil_div(M, 256), 256, 0, st>>>(keys, M, 0, flags);
+        GF_KERNEL_DONE();
+        GF_TRY(exclusive_scan_i64(flags, flags, M, scratch, st));
+        GF_CUDA(cudaMemcpyAsync(&nleaf, flags + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GF_CUDA(cudaStreamSynchronize(st));
+    }
+    leaf.nt = nleaf;
+    GF_TRY(A.alloc_n(&leaf.tkey, std::max<int64_t>(nleaf, 1)));
+    GF_TRY(A.alloc_n(&F->leaf_beg, nleaf + 1));
+    if (M > 0) {
+        compact_runs<<<ceil_div(M, 256), 256, 0, st>>>(keys, M, 0, flags, leaf.tkey, F->leaf_beg, nullptr);
+        GF_KERNEL_DONE();
+    }
+    set_last<<<1, 1, 0, st>>>(F->leaf_beg, nleaf, (int32_t)M);
+    GF_KERNEL_DONE();
+    for (int l = L - 1; l >= 1; --l) {
+        FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
+        GF_TRY(A.alloc_n(&ch.tparent, std::max<int64_t>(ch.nt, 1)));
+        int64_t np = 0;
+        if (ch.nt > 0) {
+            mark_new<<<ceil_div(ch.nt, 256), 256, 0, st>>>(ch.tkey, ch.nt, 3, flags);
+            GF_KERNEL_DONE();
+            GF_TRY(exclusive_scan_i64(flags, flags, ch.nt, scratch, st));
+            GF_CUDA(cudaMemcpyAsync(&np, flags + ch.nt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            GF_CUDA(cudaStreamSynchronize(st));
+        }
+        pa.nt = np;
+        GF_TRY(A.alloc_n(&pa.tkey, std::max<int64_t>(np, 1)));
+        if (ch.nt > 0) {
+            compact_runs<<<ceil_div(ch.nt, 256), 256, 0, st>>>(ch.tkey, ch.nt, 3, flags, pa.tkey, nullptr,
+                                                             ch.tparent);
+            GF_KERNEL_DONE();
+        }
+    }
+
+    // ---- per level: observer boxes grouped by parity class (M2L order)
+    int *d_cnt;
+    GF_TRY(A.alloc_n(&d_cnt, 8 * (kMaxLevels + 1)));
+    GF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int) * 8 * (kMaxLevels + 1), st));
+    for (int l = 2; l <= L; ++l) {
+        FmmLevel &lv = F->lev[l];
+        GF_TRY(A.alloc_n(&lv.m2l_order, std::max<int64_t>(lv.nt, 1)));
+        if (lv.nt == 0) continue;
+        class_keys<<<ceil_div(lv.nt, 256), 256, 0, st>>>(lv.tkey, lv.nt, keys2, lv.m2l_order, d_cnt + 8 * l);
+        GF_KERNEL_DONE();
+        GF_TRY(radix_sort_u64(keys2, lv.m2l_order, reinterpret_cast<uint64_t *>(flags), vals2, lv.nt, 3,
+                              scratch, st));
+    }
+    int cnt[8 * (kMaxLevels + 1)];
+    GF_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    GF_CUDA(cudaStreamSynchronize(st));
+    for (int l = 2; l <= L; ++l) {
+        FmmLevel &lv = F->lev[l];
+        lv.cls_off[0] = 0;
+        for (int c = 0; c < 8; ++c) lv.cls_off[c + 1] = lv.cls_off[c] + cnt[8 * l + c];
+    }
+
+    // ---- observer offsets from their leaf centres, evaluation work list
+    if (F->mixed)
+        GF_TRY(A.alloc_n(&F->tloc_f, 3 * Mx));
+    else
+        GF_TRY(A.alloc_n(&F->tloc_d, 3 * Mx));
+    if (M > 0) {
+        obs_local<<<ceil_div(M, 256), 256, 0, st>>>(obs, F->perm, keys, M, g, F->tloc_f, F->tloc_d);
+        GF_KERNEL_DONE();
+    }
+    int64_t nitems = 0;
+    if (nleaf > 0) {
+        item_counts<<<ceil_div(nleaf, 256), 256, 0, st>>>(F->leaf_beg, nleaf, flags);
+        GF_KERNEL_DONE();
+        GF_TRY(exclusive_scan_i64(flags, flags, nleaf, scratch, st));
+        GF_CUDA(cudaMemcpyAsync(&nitems, flags + nleaf, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GF_CUDA(cudaStreamSynchronize(st));
+    }
+    F->n_items = nitems;
+    GF_TRY(A.alloc_n(&F->items, std::max<int64_t>(nitems, 1)));
+    if (nleaf > 0) {
+        item_fill<<<ceil_div(nleaf, 256), 256, 0, st>>>(F->leaf_beg, nleaf, flags, F->items);
+        GF_KERNEL_DONE();
+    }
+    // ---- work counts
+    unsigned long long *d_cntw;
+    GF_TRY(A.alloc_n(&d_cntw, 2));
+    GF_CUDA(cudaMemsetAsync(d_cntw, 0, 2 * sizeof(unsigned long long), st));
+    if (nleaf > 0) {
+        count_near<<<ceil_div(nleaf, 256), 256, 0, st>>>(leaf.tkey, F->leaf_beg, nleaf, leaf.slo[0], leaf.slo[1],
+                                                         leaf.slo[2], leaf.sn[0], leaf.sn[1], leaf.sn[2],
+                                                         (int64_t)F->b * F->b * F->b * F->nq, d_cntw);
+        GF_KERNEL_DONE();
+    }
+    for (int l = 2; l <= L; ++l) {
+        const FmmLevel &lv = F->lev[l];
+        if (lv.nt == 0) continue;
+        count_il<<<ceil_div(lv.nt, 256), 256, 0, st>>>(lv.tkey, lv.nt, lv.slo[0], lv.slo[1], lv.slo[2], lv.sn[0],
+                                                       lv.sn[1], lv.sn[2], d_cntw + 1);
+        GF_KERNEL_DONE();
+    }
+    unsigned long long hc[2];
+    GF_CUDA(cudaMemcpyAsync(hc, d_cntw, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    GF_CUDA(cudaStreamSynchronize(st));
+    plan->near_pairs = (int64_t)hc[0];
+    plan->m2l_pairs = (int64_t)hc[1];
+    return fmm_alloc_workspaces(plan, st);
+}
+
+void fmm_destroy(gf_plan_s *plan) {
+    delete plan->fmm;
+    plan->fmm = nullptr;
+}
+
+gf_status fmm_info(const gf_plan_s *plan, gf_plan_info *info) {
+    const FmmPlan *F = plan->fmm;
+    if (!F) return GF_OK;
+    info->p = F->p;
+    info->K = F->K;
+    info->L = F->L;
+    info->leaf_vox = F->b;
+    for (int a = 0; a < 3; ++a) {
+        info->voxel_offset[a] = F->voff[a];
+        info->lo[a] = F->lo[a];
+    }
+    info->leaf_side = F->s_leaf;
+    info->inv_leaf_side = F->inv_s;
+    for (int l = 0; l <= F->L && l < 24; ++l) {
+        info->n_target_boxes[l] = F->lev[l].nt;
+        for (int a = 0; a < 3; ++a) {
+            info->src_lo[l][a] = F->lev[l].slo[a];
+            info->src_hi[l][a] = F->lev[l].slo[a] + F->lev[l].sn[a] - 1;
+        }
+    }
+    return GF_OK;
+}
+
+gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *keys, uint64_t *box_keys,
+                          int64_t *ilist, int64_t *near_) {
+    FmmPlan *F = plan->fmm;
+    if (level < 2 || level > F->L) {
+        set_error("level %d out of range [2, %d]", level, F->L);
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = 0;
+    const FmmLevel &lv = F->lev[level];
+    if (perm && plan->M > 0)
+        GF_CUDA(cudaMemcpyAsync(perm, F->perm, sizeof(int32_t) * plan->M, cudaMemcpyDeviceToHost, st));
+    if (keys && plan->M > 0)
+        GF_CUDA(cudaMemcpyAsync(keys, F->okey, sizeof(uint64_t) * plan->M, cudaMemcpyDeviceToHost, st));
+    if (box_keys && lv.nt > 0)
+        GF_CUDA(cudaMemcpyAsync(box_keys, lv.tkey, sizeof(uint64_t) * lv.nt, cudaMemcpyDeviceToHost, st));
+    if ((ilist || (near_ && level == F->L)) && lv.nt > 0) {
+        int64_t *d_il = nullptr, *d_near = nullptr;
+        DeviceArena tmp;
+        tmp.stream = st;
+        gf_status s = tmp.alloc_n(&d_il, lv.nt * 316);
+        if (s == GF_OK) s = tmp.alloc_n(&d_near, lv.nt * 27);
+        if (s != GF_OK) {
+            GF_CUDA(cudaStreamSynchronize(st));
+            tmp.release();
+            return s;
+        }
+        export_lists<<<(unsigned)lv.nt, 128, 0, st>>>(lv.tkey, lv.nt, level, lv.slo[0], lv.slo[1], lv.slo[2],
+                                                      lv.slo[0] + lv.sn[0] - 1, lv.slo[1] + lv.sn[1] - 1,
+                                                      lv.slo[2] + lv.sn[2] - 1, d_il, d_near);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && ilist)
+            e = cudaMemcpyAsync(ilist, d_il, sizeof(int64_t) * lv.nt * 316, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && near_ && level == F->L)
+            e = cudaMemcpyAsync(near_, d_near, sizeof(int64_t) * lv.nt * 27, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        tmp.release();
+        if (e != cudaSuccess) {
+            set_error("tree export failed: %s", cudaGetErrorString(e));
+            return GF_ERR_CUDA;
+        }
+    }
+    GF_CUDA(cudaStreamSynchronize(st));
+    return GF_OK;
+}
+
+}  // namespace gf

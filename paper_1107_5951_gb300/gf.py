@@ -60,7 +60,12 @@ class gf_plan_info(ctypes.Structure):
                 ("leaf_side", ctypes.c_double), ("inv_leaf_side", ctypes.c_double),
                 ("n_target_boxes", ctypes.c_int64 * 24), ("src_lo", (ctypes.c_int64 * 3) * 24),
                 ("src_hi", (ctypes.c_int64 * 3) * 24), ("M", ctypes.c_int64),
-                ("n_sources", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+                ("n_sources", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+                ("m2l_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+GF_NUM_STAGES = 7
+STAGE_NAMES = ("densities", "p2m", "m2m", "m2l", "l2l", "eval", "forward")
 
 
 _lib = None
@@ -94,8 +99,11 @@ def load(build_if_missing: bool = True):
         lib.gf_plan_bytes.argtypes = [P(gf_grid), P(gf_quad), i64, P(gf_options), P(ctypes.c_size_t)]
         lib.gf_plan_get_info.argtypes = [_vp, P(gf_plan_info)]
         lib.gf_plan_export_tree.argtypes = [_vp, i32, _vp, _vp, _vp, _vp, _vp]
+        lib.gf_plan_set_timing.argtypes = [_vp, i32]
+        lib.gf_plan_stage_times.argtypes = [_vp, P(ctypes.c_double)]
         for name in ("gf_plan_create", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
-                     "gf_plan_bytes", "gf_plan_get_info", "gf_plan_export_tree"):
+                     "gf_plan_bytes", "gf_plan_get_info", "gf_plan_export_tree", "gf_plan_set_timing",
+                     "gf_plan_stage_times"):
             getattr(lib, name).restype = ctypes.c_int
         lib.gf_last_error.argtypes = []
         lib.gf_last_error.restype = ctypes.c_char_p
@@ -158,6 +166,16 @@ def gf_plan_export_tree(plan: int, level: int, perm_ptr=None, keys_ptr=None, box
                         ilist_ptr=None, near_ptr=None):
     _check(load().gf_plan_export_tree(_vp(plan), level, _vp(perm_ptr), _vp(keys_ptr),
                                       _vp(box_keys_ptr), _vp(ilist_ptr), _vp(near_ptr)))
+
+
+def gf_plan_set_timing(plan: int, enable: bool):
+    _check(load().gf_plan_set_timing(_vp(plan), 1 if enable else 0))
+
+
+def gf_plan_stage_times(plan: int) -> dict:
+    ms = (ctypes.c_double * GF_NUM_STAGES)()
+    _check(load().gf_plan_stage_times(_vp(plan), ms))
+    return {STAGE_NAMES[i]: float(ms[i]) for i in range(GF_NUM_STAGES)}
 
 
 def gf_version() -> int:
@@ -275,6 +293,13 @@ class Plan:
             grad = torch.empty((B, nz, ny, nx), dtype=torch.float64, device=r.device)
         gf_adjoint(self.handle, r.data_ptr(), ncomp, B, grad.data_ptr(), _stream_handle(stream))
         return grad[0] if single else grad
+
+    def set_timing(self, enable=True):
+        gf_plan_set_timing(self.handle, enable)
+
+    def stage_times(self) -> dict:
+        """Device milliseconds per stage of the last timed forward."""
+        return gf_plan_stage_times(self.handle)
 
     def check(self, stream=None):
         gf_plan_check(self.handle, _stream_handle(stream))
