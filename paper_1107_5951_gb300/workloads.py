@@ -120,7 +120,7 @@ def exp_cov_grf(n: int, h: float, corr_len: float, sigma: float, seed: int,
     lam = np.fft.rfftn(c).real
     np.maximum(lam, 0.0, out=lam)
     white = rng.standard_normal((m, m, m))
-    f = np.fft.irfftn(np.sqrt(lam) * np.fft.rfftn(white), s=(m, m, m))
+    f = np.fft.irfftn(np.sqrt(lam) * np.fft.rfftn(white), s=(m, m, m), axes=(0, 1, 2))
     return np.ascontiguousarray(f[:n, :n, :n], dtype=dtype)
 
 
@@ -135,7 +135,7 @@ def periodic_grf(n: int, h: float, corr_len: float, sigma: float, seed: int,
     lam = np.fft.rfftn(np.exp(-r / corr_len)).real
     np.maximum(lam, 0.0, out=lam)
     white = rng.standard_normal((n, n, n))
-    f = np.fft.irfftn(np.sqrt(lam) * np.fft.rfftn(white), s=(n, n, n))
+    f = np.fft.irfftn(np.sqrt(lam) * np.fft.rfftn(white), s=(n, n, n), axes=(0, 1, 2))
     f *= sigma / max(float(f.std()), 1e-30)
     return np.ascontiguousarray(f, dtype=dtype)
 
