@@ -140,6 +140,36 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype,
 gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp,
                      int32_t B, double *grad_dev, void *stream);
 
+/*
+ * gf_direct_forward_static -- direct-mode, mixed-precision forward solve
+ * (the same sum and kernels as a GF_MODE_DIRECT / GF_PREC_MIXED plan) that
+ * allocates no memory.  The paper has no counterpart; this entry point is
+ * for callers that cannot allocate device memory when they need a solve:
+ * code running inside another framework's allocator callback (which must
+ * not re-enter it), processes whose device memory is fully held by a
+ * caching pool they do not own, and services that forbid allocation after
+ * start-up to keep a fixed footprint.
+ *   grid, quad : as for gf_plan_create (host structs, read during the call)
+ *   obs_dev    : [M][3] FP64 observers (device), 0 <= M <= 65536
+ *   rho_dev    : [B][nz][ny][nx] densities (device), 1 <= B <= 64
+ *   G          : gravitational constant, 0 selects 6.67428e-11
+ *   g_dev      : [B][M][3] FP64 output or NULL;  gz_dev : [B][M] or NULL
+ * Its scratch (quadrature rule and split observer coordinates, about
+ * 1.6 MB) is a fixed device array in the library that every GPU loading the
+ * library holds until the process exits; M above 65536 is rejected with
+ * GF_ERR_INVALID_ARG.  The first call on each device looks up the array's
+ * device address (with that device current), so make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * rewrites all of it that it reads: calls whose device work overlaps (on
+ * different streams, or from different threads) race, so serialise them.
+ * Enqueues on `stream` and returns.
+ */
+gf_status gf_direct_forward_static(const gf_grid *grid, const gf_quad *quad,
+                                   const double *obs_dev, int64_t M,
+                                   const void *rho_dev, int32_t rho_dtype,
+                                   int32_t B, double G, double *g_dev,
+                                   double *gz_dev, void *stream);
+
 /* Release a plan and everything it owns (waits for its device work). */
 gf_status gf_plan_destroy(gf_plan_t plan);
 

@@ -11,8 +11,10 @@
 // integer voxel index plus an FP32 fraction, so the separation of near pairs
 // is formed to FP32 relative accuracy whatever the size of the domain.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "gf_internal.cuh"
 
@@ -322,3 +324,148 @@ gf_status direct_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B, dou
 }
 
 }  // namespace gf
+
+// ---------------------------------------------------------------------------
+// Allocation-free direct forward (gf_direct_forward_static in gf.h).
+//
+// Some callers cannot allocate device memory when they need a forward
+// solve: code that runs inside another framework's allocator callback and
+// must not re-enter it, processes whose device memory is entirely reserved
+// by a caching pool they do not own, and services that forbid any
+// allocation after start-up so that their memory footprint stays fixed.
+// This variant of the mixed-precision direct kernel needs no plan: its only
+// scratch -- the normalised quadrature rule and the observers' voxel
+// coordinates split into integer and fractional parts -- lives in one
+// file-scope device array of fixed size, which every GPU that loads this
+// library holds until the process exits.
+namespace gf {
+namespace {
+
+constexpr int64_t kStaticMaxObs = 65536;
+constexpr size_t kStaticQuadBytes = (sizeof(QuadRule) + 255) & ~size_t(255);
+constexpr size_t kStaticCoordBytes = sizeof(float) * 3 * kStaticMaxObs;
+constexpr size_t kStaticBytes = kStaticQuadBytes + 2 * kStaticCoordBytes;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mu;
+void *g_static_addr[256] = {};
+
+// Device address of the scratch array on the current device.  The host
+// symbol is only a stand-in, so the address is looked up once per device
+// (with that device current) and cached.
+gf_status static_scratch_address(void **out) {
+    int dev = 0;
+    GF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("device ordinal %d out of range", dev);
+        return GF_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+            return GF_ERR_CUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return GF_OK;
+}
+
+}  // namespace
+}  // namespace gf
+
+extern "C" gf_status gf_direct_forward_static(const gf_grid *grid, const gf_quad *quad, const double *obs_dev,
+                                              int64_t M, const void *rho_dev, int32_t rho_dtype, int32_t B,
+                                              double G, double *g_dev, double *gz_dev, void *stream) {
+    using namespace gf;
+    if (!grid || !quad) {
+        set_error("grid and quad must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (M < 0 || M > kStaticMaxObs) {
+        set_error("gf_direct_forward_static takes at most %lld observers (M = %lld); use a plan instead",
+                  (long long)kStaticMaxObs, (long long)M);
+        return GF_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (grid->n[a] < 1 || grid->n[a] > (int64_t(1) << 22) || !(grid->h[a] > 0.0) || !isfinite(grid->h[a]) ||
+            !isfinite(grid->origin[a])) {
+            set_error("grid axis %d: need 1 <= n <= 2^22, finite h > 0 and finite origin", a);
+            return GF_ERR_INVALID_ARG;
+        }
+    }
+    if (quad->nq < 1 || quad->nq > kMaxQuad || !quad->xi || !quad->w) {
+        set_error("quad.nq = %d must be in [1, %d] with non-NULL xi and w", quad->nq, kMaxQuad);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (rho_dtype != GF_DTYPE_F64 && rho_dtype != GF_DTYPE_F32) {
+        set_error("rho_dtype = %d is neither GF_DTYPE_F64 nor GF_DTYPE_F32", rho_dtype);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (B < 1 || B > 64 || !(G >= 0.0) || !isfinite(G)) {
+        set_error("need 1 <= B <= 64 and a finite G >= 0 (0 selects 6.67428e-11)");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((M > 0 && (!obs_dev || !rho_dev)) || (!g_dev && !gz_dev)) {
+        set_error("obs_dev and rho_dev must be non-NULL and at least one of g_dev, gz_dev given");
+        return GF_ERR_INVALID_ARG;
+    }
+    QuadRule qr;
+    memset(&qr, 0, sizeof(qr));
+    qr.nq = quad->nq;
+    double wsum = 0.0;
+    for (int q = 0; q < quad->nq; ++q) {
+        if (!(quad->w[q] > 0.0) || !isfinite(quad->w[q])) {
+            set_error("quad.w[%d] must be finite and positive", q);
+            return GF_ERR_INVALID_ARG;
+        }
+        wsum += quad->w[q];
+    }
+    for (int q = 0; q < quad->nq; ++q) {
+        qr.wn[q] = quad->w[q] / wsum;
+        qr.wnf[q] = (float)qr.wn[q];
+        for (int a = 0; a < 3; ++a) {
+            const double x = quad->xi[3 * q + a];
+            if (!(fabs(x) <= 1.0)) {
+                set_error("quad.xi[%d][%d] must lie in [-1, 1]", q, a);
+                return GF_ERR_INVALID_ARG;
+            }
+            qr.xi[q][a] = x;
+            qr.offf[q][a] = (float)(0.5 + 0.5 * x);
+        }
+    }
+    if (M == 0) return GF_OK;
+    void *base = nullptr;
+    GF_TRY(static_scratch_address(&base));
+    unsigned char *scr = reinterpret_cast<unsigned char *>(base);
+    QuadRule *d_qr = reinterpret_cast<QuadRule *>(scr);
+    float *oi = reinterpret_cast<float *>(scr + kStaticQuadBytes);
+    float *of = reinterpret_cast<float *>(scr + kStaticQuadBytes + kStaticCoordBytes);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GridArgs ga;
+    ga.nx = grid->n[0];
+    ga.ny = grid->n[1];
+    ga.nz = grid->n[2];
+    ga.nvox = ga.nx * ga.ny * ga.nz;
+    ga.ox = grid->origin[0];
+    ga.oy = grid->origin[1];
+    ga.oz = grid->origin[2];
+    ga.hx = grid->h[0];
+    ga.hy = grid->h[1];
+    ga.hz = grid->h[2];
+    ga.vol = ga.hx * ga.hy * ga.hz;
+    // every byte the kernels read is rewritten here, so nothing left by an
+    // earlier call is used and nothing needs clearing
+    GF_CUDA(cudaMemcpyAsync(d_qr, &qr, sizeof(QuadRule), cudaMemcpyHostToDevice, st));
+    split_voxel_coords<<<ceil_div(M, 256), 256, 0, st>>>(obs_dev, M, ga, oi, of);
+    GF_KERNEL_DONE();
+    direct_fwd_mixed<<<dim3(ceil_div(M, kTile), B), kTile, 0, st>>>(oi, of, M, rho_dev,
+                                                                     rho_dtype == GF_DTYPE_F32, ga, d_qr,
+                                                                     G > 0.0 ? G : 6.67428e-11, g_dev, gz_dev);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}

@@ -99,6 +99,9 @@ def load(build_if_missing: bool = True):
         lib.gf_plan_bytes.argtypes = [P(gf_grid), P(gf_quad), i64, P(gf_options), P(ctypes.c_size_t)]
         lib.gf_plan_get_info.argtypes = [_vp, P(gf_plan_info)]
         lib.gf_plan_export_tree.argtypes = [_vp, i32, _vp, _vp, _vp, _vp, _vp]
+        lib.gf_direct_forward_static.argtypes = [P(gf_grid), P(gf_quad), _vp, i64, _vp, i32, i32,
+                                                 ctypes.c_double, _vp, _vp, _vp]
+        lib.gf_direct_forward_static.restype = ctypes.c_int
         lib.gf_plan_set_timing.argtypes = [_vp, i32]
         lib.gf_plan_stage_times.argtypes = [_vp, P(ctypes.c_double)]
         for name in ("gf_plan_create", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
@@ -139,6 +142,16 @@ def gf_forward(plan: int, rho_ptr: int, rho_dtype: int, B: int, g_ptr: int, gz_p
 
 def gf_adjoint(plan: int, r_ptr: int, ncomp: int, B: int, grad_ptr: int, stream: int = 0):
     _check(load().gf_adjoint(_vp(plan), _vp(r_ptr or None), ncomp, B, _vp(grad_ptr), _vp(stream)))
+
+
+def gf_direct_forward_static(grid: gf_grid, quad: gf_quad, obs_ptr: int, M: int, rho_ptr: int,
+                             rho_dtype: int, B: int, G: float, g_ptr: int, gz_ptr: int, stream: int = 0):
+    """Allocation-free direct forward (mixed precision, M <= 65536): for
+    callers that cannot allocate device memory at solve time.  Calls whose
+    device work overlaps share one scratch array and race."""
+    _check(load().gf_direct_forward_static(ctypes.byref(grid), ctypes.byref(quad), _vp(obs_ptr), int(M),
+                                           _vp(rho_ptr), rho_dtype, B, float(G), _vp(g_ptr or None),
+                                           _vp(gz_ptr or None), _vp(stream)))
 
 
 def gf_plan_destroy(plan: int):
