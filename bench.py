@@ -35,6 +35,7 @@ N_SM = 152
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM per clock
 FP64_TFLOPS_NOMINAL = 1.25       # GB300 FP64 (vector and tensor) rate
 FLOPS_PER_PAIR = 20.0            # the paper's count: 5 add, 7 mul, 1 sqrt ~ 20 mul-equivalents
+TF32_PER_BF16 = 1.1 / 2.25       # nominal dense TF32 / BF16 tensor rates
 
 
 def load_peaks():
@@ -61,6 +62,7 @@ def parse_args():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--p", type=int, default=12)
     ap.add_argument("--leaf-vox", type=int, default=0)
+    ap.add_argument("--m2l", default="auto", choices=["auto", "simt"])
     ap.add_argument("--sample-obs", type=int, default=1024,
                     help="observers in the oracle's bounded sample")
     ap.add_argument("--no-clocks", action="store_true")
@@ -151,11 +153,17 @@ def fmm_roofline(stages, info, args, peaks):
     evaluation (ALU: 20 flops per pair, the paper's count) or the M2L
     (2 K^2 flops per interaction-list box pair)."""
     K = int(info.K)
+    tensor = args.precision == "mixed" and args.p <= 15 and args.m2l != "simt"
     work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P)"),
-            "m2l": ("alu", 2.0 * K * K * float(info.m2l_pairs), "m2l_simt (all levels)")}
+            "m2l": ("tensor" if tensor else "alu", 2.0 * K * K * float(info.m2l_pairs),
+                    "m2l_tc (tcgen05 3xTF32, all levels)" if tensor else "m2l_simt (all levels)")}
     dom = max(("eval", "m2l"), key=lambda k: stages.get(k, 0.0))
     bound, flops, kern = work[dom]
-    if args.precision == "mixed":
+    if bound == "tensor":
+        peak = peaks.get("bf16_tflops", 1870.7) * TF32_PER_BF16
+        note = ("TF32 dense = measured BF16 burst x nominal TF32/BF16 (1.1/2.25); the 3xTF32 split "
+                "executes 3 MMAs per algorithmic flop")
+    elif args.precision == "mixed":
         peak, note = fp32_peak_tflops(peaks), "FP32 SIMT: 152 SM x 128 lanes x 2 x sm_max_mhz"
     else:
         peak, note = FP64_TFLOPS_NOMINAL, "FP64 nominal 1.25 TFLOP/s"
@@ -223,7 +231,7 @@ def bench_gf(args, rank, world):
     def make_plan():
         return pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode=mode,
                         precision=args.precision, p=args.p, leaf_vox=args.leaf_vox, G=wk.G,
-                        stream=stream)
+                        stream=stream, m2l=args.m2l)
 
     try:
         probe = make_plan()
@@ -345,7 +353,7 @@ def bench_gf(args, rank, world):
                 rho_e.copy_(rho_h, non_blocking=True)
                 pl = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_e, mode=mode,
                               precision=args.precision, p=args.p, leaf_vox=args.leaf_vox, G=wk.G,
-                              stream=stream)
+                              stream=stream, m2l=args.m2l)
                 pl.forward(rho_e, g=g_d, stream=stream)
                 g_h.copy_(g_d, non_blocking=True)
                 pl.close()
@@ -365,7 +373,7 @@ def bench_gf(args, rank, world):
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": wk.name, "mode": mode, "precision": args.precision,
-                       "p": args.p if mode == "fmm" else None,
+                       "p": args.p if mode == "fmm" else None, "m2l": args.m2l,
                        "leaf_vox": int(plan_info.leaf_vox) if mode == "fmm" else None,
                        "N_sources": N, "M_observers": M, "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": "256 MiB buffer written between timed steps",

@@ -80,6 +80,7 @@ enum { GF_MODE_DIRECT = 0, GF_MODE_FMM = 1 };
  * sum. */
 enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1 };
 enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
+enum { GF_FLAG_M2L_SIMT = 1 };
 
 typedef struct {
     int32_t mode;        /* GF_MODE_DIRECT or GF_MODE_FMM                  */
@@ -89,7 +90,8 @@ typedef struct {
     int32_t leaf_vox;    /* FMM leaf edge in voxels (leaf = leaf_vox^3     */
                          /* voxels), 0 = library default                   */
     int32_t max_batch;   /* largest B passed to gf_forward/gf_adjoint, >=1 */
-    int32_t reserved0;
+    int32_t reserved0;   /* flags: GF_FLAG_M2L_SIMT runs the mixed-precision */
+                         /* M2L on the SIMT cores instead of the tensor cores */
     double G;            /* gravitational constant; 0 = 6.67428e-11        */
 } gf_options;
 

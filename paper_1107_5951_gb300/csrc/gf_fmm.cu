@@ -172,7 +172,7 @@ constexpr int kP2MLeaves = 4;
 template <class T>
 __global__ void __launch_bounds__(128)
 p2m_kernel(const T *__restrict__ mass, const T *__restrict__ P, int64_t nleaf, int b3, int B, int K,
-           T *__restrict__ me) {
+           int ldk, T *__restrict__ me) {
     extern __shared__ unsigned char shraw[];
     T *ms = reinterpret_cast<T *>(shraw);  // [kP2MLeaves*B][b3]
     const int64_t leaf0 = (int64_t)blockIdx.x * kP2MLeaves;
@@ -194,7 +194,7 @@ p2m_kernel(const T *__restrict__ mass, const T *__restrict__ P, int64_t nleaf, i
             }
 #pragma unroll
             for (int c = 0; c < kP2MLeaves * 4; ++c)
-                if (c < cn) me[(leaf0 * B + c0 + c) * K + k] = acc[c];
+                if (c < cn) me[(leaf0 * B + c0 + c) * ldk + k] = acc[c];
         }
     }
 }
@@ -203,7 +203,7 @@ p2m_kernel(const T *__restrict__ mass, const T *__restrict__ P, int64_t nleaf, i
 // per parent box of the dense source block at level l.
 template <class Ts, class Tc>
 __global__ void __launch_bounds__(128)
-m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3 bp, int B, int K,
+m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3 bp, int B, int K, int ldk,
            const Tc *__restrict__ tab) {
     extern __shared__ unsigned char shraw[];
     Tc *xs = reinterpret_cast<Tc *>(shraw);  // [8][B][K]
@@ -216,7 +216,8 @@ m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3
         const int64_t cx = 2 * px + (oct & 1) - bc.lo[0], cy = 2 * py + ((oct >> 1) & 1) - bc.lo[1],
                       cz = 2 * pz + ((oct >> 2) & 1) - bc.lo[2];
         const bool in = cx >= 0 && cx < bc.n[0] && cy >= 0 && cy < bc.n[1] && cz >= 0 && cz < bc.n[2];
-        xs[e] = in ? (Tc)me_c[((cz * bc.n[1] + cy) * bc.n[0] + cx) * B * K + r] : Tc(0);
+        const int rb = r / K, rk = r - rb * K;
+        xs[e] = in ? (Tc)me_c[(((cz * bc.n[1] + cy) * bc.n[0] + cx) * B + rb) * ldk + rk] : Tc(0);
         if (r == 0) present[oct] = in;
     }
     __syncthreads();
@@ -229,7 +230,7 @@ m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3
                 const Tc *x = xs + (oct * B + bb) * K;
                 for (int c = 0; c < K; ++c) acc += t[(size_t)c * K] * x[c];
             }
-            me_p[(pi * B + bb) * K + k] = (Ts)acc;
+            me_p[(pi * B + bb) * ldk + k] = (Ts)acc;
         }
     }
 }
@@ -238,13 +239,16 @@ m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3
 template <class Ts, class Tc>
 __global__ void __launch_bounds__(128)
 l2l_kernel(const Ts *__restrict__ le_p, const uint64_t *__restrict__ tkey, const int32_t *__restrict__ tparent,
-           Ts *__restrict__ le_c, int B, int K, const Tc *__restrict__ tab) {
+           Ts *__restrict__ le_c, int B, int K, int ldk, const Tc *__restrict__ tab) {
     extern __shared__ unsigned char shraw[];
     Tc *xs = reinterpret_cast<Tc *>(shraw);  // [B][K]
     const int64_t t = blockIdx.x;
     const int oct = (int)(tkey[t] & 7);
     const int64_t par = tparent[t];
-    for (int e = threadIdx.x; e < B * K; e += blockDim.x) xs[e] = (Tc)le_p[par * B * K + e];
+    for (int e = threadIdx.x; e < B * K; e += blockDim.x) {
+        const int rb = e / K, rk = e - rb * K;
+        xs[e] = (Tc)le_p[(par * B + rb) * ldk + rk];
+    }
     __syncthreads();
     const Tc *tb = tab + (size_t)oct * K * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -252,7 +256,7 @@ l2l_kernel(const Ts *__restrict__ le_p, const uint64_t *__restrict__ tkey, const
             Tc acc = Tc(0);
             const Tc *x = xs + bb * K;
             for (int c = 0; c < K; ++c) acc += tb[(size_t)c * K + k] * x[c];
-            Ts *o = le_c + (t * B + bb) * K + k;
+            Ts *o = le_c + (t * B + bb) * ldk + k;
             *o = (Ts)((Tc)*o + acc);
         }
     }
@@ -297,7 +301,7 @@ struct EvalArgs {
     const void *le;            // [nt_L][B][K] T
     const QuadRule *qr;
     Block3 blk;                // leaf source block
-    int b, nq, B, K, p;
+    int b, nq, B, K, ldk, p;
     int64_t M;
     double scale;              // G * h
     double eps2;               // coincidence radius^2 (voxel units)
@@ -406,7 +410,7 @@ eval_kernel(EvalArgs a) {
             }
             // ---- far field: gradient of the leaf's local expansion
             __syncwarp();
-            const T *L = le + ((int64_t)leaf * a.B + bb) * a.K;
+            const T *L = le + ((int64_t)leaf * a.B + bb) * a.ldk;
             for (int e = lane; e < P2; e += 32) grad_coeff<T>(L, e, Dx[e], Dy[e], Dz[e]);
             __syncwarp();
 #pragma unroll
@@ -476,10 +480,11 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     DeviceArena &A = plan->arena;
     const size_t rs = F->mixed ? sizeof(float) : sizeof(double);
     const int K = F->K, B = F->B;
+    F->KS = F->mixed ? (K + 31) & ~31 : K;
     for (int l = 2; l <= F->L; ++l) {
         FmmLevel &lv = F->lev[l];
-        GF_TRY(A.alloc(&lv.me, (size_t)std::max<int64_t>(lv.ns, 1) * B * K * rs));
-        GF_TRY(A.alloc(&lv.le, (size_t)std::max<int64_t>(lv.nt, 1) * B * K * rs));
+        GF_TRY(A.alloc(&lv.me, (size_t)std::max<int64_t>(lv.ns, 1) * B * F->KS * rs));
+        GF_TRY(A.alloc(&lv.le, (size_t)std::max<int64_t>(lv.nt, 1) * B * F->KS * rs));
     }
     const int b3 = F->b * F->b * F->b;
     GF_TRY(A.alloc(&F->mass, (size_t)std::max<int64_t>(F->lev[F->L].ns, 1) * B * b3 * rs));
@@ -500,7 +505,7 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     const size_t shm = sizeof(double) * ((F->p + 1) * (F->p + 2) + K);
     build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), F->p2m_d, F->p2m_f);
     GF_KERNEL_DONE();
-    return GF_OK;
+    return m2l_tc_prepare(plan);
 }
 
 // ---------------------------------------------------------------- forward
@@ -531,7 +536,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         const size_t shm = sizeof(T) * kP2MLeaves * B * b3;
         const T *P = sizeof(T) == 8 ? (const T *)F->p2m_d : (const T *)F->p2m_f;
         GF_TRY(ensure_smem(p2m_kernel<T>, shm));
-        p2m_kernel<T><<<grid, 128, shm, st>>>((const T *)F->mass, P, lv.ns, b3, B, K, (T *)lv.me);
+        p2m_kernel<T><<<grid, 128, shm, st>>>((const T *)F->mass, P, lv.ns, b3, B, K, F->KS, (T *)lv.me);
         GF_KERNEL_DONE();
     }
     stage_mark(plan, 2, st);
@@ -543,24 +548,20 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
             const size_t shm = sizeof(double) * 8 * B * K;
             GF_TRY((ensure_smem(m2m_kernel<T, double>, shm)));
             m2m_kernel<T, double><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
-                                                                     block_of(pa), B, K, tab->m2m_d);
+                                                                     block_of(pa), B, K, F->KS, tab->m2m_d);
         } else {
             const size_t shm = sizeof(T) * 8 * B * K;
             GF_TRY((ensure_smem(m2m_kernel<T, T>, shm)));
             const T *tb = sizeof(T) == 8 ? (const T *)tab->m2m_d : (const T *)tab->m2m_f;
             m2m_kernel<T, T><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
-                                                                block_of(pa), B, K, tb);
+                                                                block_of(pa), B, K, F->KS, tb);
         }
         GF_KERNEL_DONE();
     }
     stage_mark(plan, 3, st);
     // a5/a6: M2L at every level (each overwrites its level's LE), then the
     // L2L chain from level 3 down, which adds each finished parent LE.
-    for (int l = 2; l <= L; ++l) {
-        const FmmLevel &lv = F->lev[l];
-        if (lv.nt == 0) continue;
-        GF_TRY(m2l_level<T>(plan, l, B, st));
-    }
+    GF_TRY(m2l_run<T>(plan, B, st));
     stage_mark(plan, 4, st);
     for (int l = 3; l <= L; ++l) {
         const FmmLevel &lv = F->lev[l];
@@ -568,11 +569,11 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         const FmmLevel &pa = F->lev[l - 1];
         if (sizeof(T) == 4 && l - 1 <= 3) {
             l2l_kernel<T, double><<<(unsigned)lv.nt, 128, sizeof(double) * B * K, st>>>(
-                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, tab->l2l_d);
+                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, F->KS, tab->l2l_d);
         } else {
             const T *tb = sizeof(T) == 8 ? (const T *)tab->l2l_d : (const T *)tab->l2l_f;
             l2l_kernel<T, T><<<(unsigned)lv.nt, 128, sizeof(T) * B * K, st>>>(
-                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, tb);
+                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, F->KS, tb);
         }
         GF_KERNEL_DONE();
     }
@@ -593,6 +594,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         a.nq = F->nq;
         a.B = B;
         a.K = K;
+        a.ldk = F->KS;
         a.p = F->p;
         a.M = plan->M;
         a.scale = plan->G * F->h;

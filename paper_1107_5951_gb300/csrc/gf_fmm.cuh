@@ -23,8 +23,8 @@ struct FmmLevel {
     int32_t *tparent = nullptr;   // [nt] index of the parent box at level-1
     int32_t *m2l_order = nullptr; // [nt] observer boxes grouped by parity class
     int64_t cls_off[9] = {0};     // class c: m2l_order[cls_off[c] .. cls_off[c+1])
-    void *me = nullptr;           // [ns][B][K]
-    void *le = nullptr;           // [nt][B][K]
+    void *me = nullptr;           // [ns][B][KS]
+    void *le = nullptr;           // [nt][B][KS]
 };
 
 // Translation operators for one expansion degree, shared by all plans on a
@@ -35,6 +35,12 @@ struct FmmLevel {
 //                                          of the child box
 struct Tables {
     int device = -1, p = 0, K = 0, Kp = 0;   // Kp = K rounded up to 8
+    // Tensor-core operand images of the M2L operators (mixed precision):
+    // for every offset slot and every 32-wide input chunk, the TF32 high
+    // and low parts of T_o[k_out][k_in] as two [Npad][32] FP32 tiles in the
+    // 128-byte-swizzled K-major shared-memory layout, ready for a bulk copy.
+    float *m2l_tc = nullptr;
+    int tc_npad = 0, tc_nck = 0;
     double *m2l_d = nullptr;
     float *m2l_f = nullptr;
     double *m2m_d = nullptr, *l2l_d = nullptr;
@@ -45,6 +51,7 @@ gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out);
 
 struct FmmPlan {
     int L = 0, b = 0, p = 0, K = 0, B = 1, nq = 1;
+    int KS = 0;                   // row stride of ME/LE arrays (K padded to 32 in mixed)
     bool mixed = false;
     int64_t voff[3] = {0, 0, 0};  // grid voxel (0,0,0) sits at tree voxel voff
     double lo[3] = {0, 0, 0};     // root lower corner (m)
@@ -61,6 +68,8 @@ struct FmmPlan {
     double *p2m_d = nullptr;      // [b^3][K] quadrature-folded P2M matrix
     float *p2m_f = nullptr;
     const Tables *tab = nullptr;
+    void *tc_levels = nullptr;                  // tensor-core M2L level table
+    std::vector<unsigned char> tc_levels_host;
 };
 
 // Interaction-list offsets of a box whose position inside its parent is

@@ -8,6 +8,7 @@
 // K x 32 result in registers.  Sources outside the source block contribute
 // zero columns.  Each output is written once, so the result is deterministic.
 #include <algorithm>
+#include <vector>
 
 #include "gf_m2l.cuh"
 
@@ -20,14 +21,65 @@ gf_status m2l_upload_offsets(const signed char h_il[8][189][3]) {
     return GF_OK;
 }
 
-gf_status m2l_prepare_tables(Tables *, cudaStream_t) { return GF_OK; }
+namespace {
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Byte offset of element (row, k), k < 32, in a [rows][32] FP32 tile stored
+// K-major with the 128-byte swizzle: 8-row atoms of 1024 bytes, the 16-byte
+// chunk index XOR-ed with the row inside the atom.
+__host__ __device__ __forceinline__ uint32_t swz128(int row, int k) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 2) ^ (row & 7)) & 7) << 4) + (k & 3) * 4);
+}
+
+// Operator images for the tensor-core M2L: img[off][c][part][Npad*32],
+// part 0 = TF32(T), part 1 = TF32(T - TF32(T)), T = T_off[k_out][k_in].
+__global__ void build_tc_images(const double *__restrict__ m2l_d, int K, int Npad, int nck,
+                                float *__restrict__ img) {
+    const int off = blockIdx.x;
+    const int dx = off % 7 - 3, dy = (off / 7) % 7 - 3, dz = off / 49 - 3;
+    const bool used = max(abs(dx), max(abs(dy), abs(dz))) >= 2;
+    const size_t tile = (size_t)Npad * 32;
+    for (int c = 0; c < nck; ++c) {
+        float *hi = img + ((size_t)off * nck + c) * 2 * tile;
+        float *lo = hi + tile;
+        for (int e = threadIdx.x; e < Npad * 32; e += blockDim.x) {
+            const int n = e / 32, kk = e % 32, kin = 32 * c + kk;
+            const double v = (used && n < K && kin < K) ? m2l_d[(size_t)off * K * K + (size_t)kin * K + n] : 0.0;
+            const float f = (float)v;
+            const float h = __uint_as_float(to_tf32(f));
+            const float l = __uint_as_float(to_tf32(f - h));
+            const uint32_t o = swz128(n, kk) / 4;
+            hi[o] = h;
+            lo[o] = l;
+        }
+    }
+}
+
+}  // namespace
+
+gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
+    const int npad = (T->K + 15) & ~15;
+    if (npad > 256) return GF_OK;  // beyond one MMA's N: SIMT only
+    T->tc_npad = npad;
+    T->tc_nck = (T->K + 31) / 32;
+    const size_t n = (size_t)343 * T->tc_nck * 2 * npad * 32;
+    GF_CUDA(cudaMalloc(&T->m2l_tc, n * sizeof(float)));
+    build_tc_images<<<343, 256, 0, st>>>(T->m2l_d, T->K, npad, T->tc_nck, T->m2l_tc);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
 
 namespace {
 
 struct M2LArgs {
     const void *me;
     void *le;
-    int K, B, nbox;
+    int K, ldk, B, nbox;
     const int32_t *order;
     int64_t cls_off[9];
     const uint64_t *tkey;
@@ -99,7 +151,7 @@ m2l_simt(M2LArgs a) {
             if (slot < a.nbox && tbox[slot] >= 0) {
                 const int64_t sx = tc[slot][0] + dx, sy = tc[slot][1] + dy, sz = tc[slot][2] + dz;
                 if (sx >= 0 && sy >= 0 && sz >= 0 && sx < a.bn[0] && sy < a.bn[1] && sz < a.bn[2])
-                    row = (((sz * a.bn[1] + sy) * a.bn[0] + sx) * B + bb) * K;
+                    row = (((sz * a.bn[1] + sy) * a.bn[0] + sx) * B + bb) * a.ldk;
             }
             srow[tid] = row;
             any = row >= 0;
@@ -143,7 +195,7 @@ m2l_simt(M2LArgs a) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int k = ty * RPT + r;
-            if (k < K) le[(tbox[slot] * B + bb) * K + k] = acc[r][c];
+            if (k < K) le[(tbox[slot] * B + bb) * a.ldk + k] = acc[r][c];
         }
     }
 }
@@ -153,6 +205,386 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
     const size_t shm = sizeof(T) * (kCK * XStride<T>::v + kCK * 32 * RPT);
     GF_TRY(ensure_smem(m2l_simt<T, RPT>, shm));
     m2l_simt<T, RPT><<<dim3((unsigned)max_tiles, 8), 256, shm, st>>>(a);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
+// ---------------------------------------------------------------- tcgen05
+// Tensor-core M2L (mixed precision).  A CTA owns 128 target columns --
+// (box, batch member) pairs of one parity class of one level -- and, offset
+// by offset, computes D_o[col][k_out] = sum_k_in ME[t + o][k_in] T_o[k_out][k_in]
+// on the tensor cores as 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi), with
+// the result of each offset accumulated in FP32 in tensor memory.  Two
+// tensor-memory banks alternate between offsets: while the MMAs of offset g
+// run into one bank, the threads read offset g-1's bank and add it to FP32
+// registers with round-to-nearest adds, so no tensor-core accumulation chain
+// is longer than one offset (the tensor cores' own FP32 accumulation rounds
+// differently from IEEE, and long chains over zero-mean data lose digits).
+// Per (offset, 32-wide input chunk): one thread bulk-copies the pre-split,
+// pre-swizzled operator image into shared memory (mbarrier completion), every
+// thread gathers half of its column's 32 inputs (128-bit loads, rows padded
+// to 32 floats), splits them into TF32 high and low parts and stores them
+// swizzled, and one thread issues the MMAs and commits them to mbarriers that
+// free the stage and mark the bank complete.  All levels run in one launch
+// (their M2L are independent).  Every wait is bounded; a wait that gives up
+// sets status[1], and the CTA then stops, drains (bounded) and frees its
+// tensor memory.
+
+struct TcLevel {
+    const float *me;
+    float *le;
+    const int32_t *order;
+    const uint64_t *tkey;
+    int64_t blo[3], bn[3];
+    int64_t cls_off[9];
+};
+
+struct TcArgs {
+    const TcLevel *lv;          // device array indexed by level
+    int lmin, nent;             // entries e = (level - lmin) * 8 + class
+    int tile_begin[kMaxLevels * 8 + 1];
+    int K, ldk, B, Npad, nck;
+    const float *img;
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: one 8-row atom
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    // D = FP32, A = B = TF32, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+constexpr long kWaitTries = 1l << 24;
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    for (long it = 0; it < kWaitTries; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(addr), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void commit_to(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Add 8 accumulator columns starting at `col` of this warp's 32 lanes to acc[j0..j0+7].
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+constexpr int kTcThreads = 256;
+constexpr uint32_t kTcCols = 512;           // two banks of 256 columns
+constexpr uint32_t kTcA = 2u * 16384u;      // A hi + lo for 128 rows
+
+__host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 128u; }
+size_t tc_smem_bytes(int Npad) { return 2 * (size_t)tc_stage_bytes(Npad) + 1024; }
+
+template <int NS>   // NS >= Npad / 2: FP32 sums held per thread
+__global__ void __launch_bounds__(kTcThreads, 1)
+m2l_tc(TcArgs a) {
+    extern __shared__ unsigned char dsm[];
+    unsigned char *base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);
+    __shared__ __align__(8) uint64_t full[2], done[2], bank_done[2];
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K = a.K, B = a.B, Npad = a.Npad, nck = a.nck;
+    const int nsum = Npad / 2;
+    const uint32_t b_bytes = 2u * (uint32_t)Npad * 128u;
+    const uint32_t stage_bytes = tc_stage_bytes(Npad);
+
+    // which (level, class, tile) this CTA owns
+    int e = 0;
+    while (e + 1 < a.nent && a.tile_begin[e + 1] <= (int)blockIdx.x) ++e;
+    const int level = a.lmin + e / 8, cls = e % 8;
+    const int tile = (int)blockIdx.x - a.tile_begin[e];
+    const TcLevel &L = a.lv[level];
+    const int64_t cbeg = L.cls_off[cls], ccnt = L.cls_off[cls + 1] - cbeg;
+    const int nbox = 128 / B;
+    // gather role: column `row`, input half `gh` (16 of the 32 chunk inputs)
+    const int row = tid & 127, gh = tid >> 7;
+    const int slot = row / B, bb = row - slot * B;
+    const int64_t sidx = (int64_t)tile * nbox + slot;
+    int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
+    if (slot < nbox && sidx < ccnt) {
+        tbox = L.order[cbeg + sidx];
+        const uint64_t key = L.tkey[tbox];
+        tc0 = dm(key, 0) - L.blo[0];
+        tc1 = dm(key, 1) - L.blo[1];
+        tc2 = dm(key, 2) - L.blo[2];
+    }
+    // promotion role: warp w reads lanes 32*(w%4).. (columns of rows
+    // 32*(w%4)+lane) and the column half w/4
+    const int pq = warp & 3, ph = warp >> 2;
+    float acc[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) acc[j] = 0.f;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bank_done[i])), "r"(1));
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tslot;
+    const uint32_t idesc = idesc_tf32(128, Npad);
+
+    int it = 0;        // chunk iterations issued
+    int g = 0;         // offsets issued (bank = g & 1)
+    bool copy_pending = false, aborted = false, waits_ok = true;
+    for (int oi = 0; oi < 189 && !aborted; ++oi) {
+        const int dx = c_il[cls][oi][0], dy = c_il[cls][oi][1], dz = c_il[cls][oi][2];
+        int64_t src = -1;
+        if (tbox >= 0) {
+            const int64_t sx = tc0 + dx, sy = tc1 + dy, sz = tc2 + dz;
+            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
+                src = (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldk;
+        }
+        if (!__syncthreads_or(src >= 0)) continue;
+        const int slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
+        const uint32_t bank = (uint32_t)(g & 1) * 256u;
+        for (int c = 0; c < nck; ++c) {
+            const int s = it & 1;
+            unsigned char *stage = base + s * stage_bytes;
+            bool tout = false;
+            if (it >= 2) tout = !mbar_wait(smem_u32(&done[s]), ((it - 2) >> 1) & 1);
+            if (tid == 0 && !tout) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                             "r"(b_bytes));
+                const float *srcimg = a.img + ((size_t)slot_off * nck + c) * 2 * (size_t)Npad * 32;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(stage + kTcA)),
+                    "l"(srcimg), "r"(b_bytes), "r"(smem_u32(&full[s]))
+                    : "memory");
+                copy_pending = true;
+            }
+            // gather 16 inputs of this column's chunk c, split into TF32 parts
+            float v[16];
+            if (src >= 0) {
+                const float4 *p4 = reinterpret_cast<const float4 *>(L.me + src + 32 * c + 16 * gh);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 t = __ldg(p4 + q);
+                    v[4 * q + 0] = t.x;
+                    v[4 * q + 1] = t.y;
+                    v[4 * q + 2] = t.z;
+                    v[4 * q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int kin = 32 * c + 16 * gh + 4 * q + j;
+                    const float x = kin < K ? v[4 * q + j] : 0.f;
+                    h[j] = to_tf32(x);
+                    l[j] = to_tf32(x - __uint_as_float(h[j]));
+                }
+                const uint32_t o = swz128(row, 16 * gh + 4 * q);
+                *reinterpret_cast<uint4 *>(stage + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4 *>(stage + 16384 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (__syncthreads_or(tout || abort_flag)) {
+                aborted = true;
+                break;
+            }
+            if (tid == 0) {
+                if (!mbar_wait(smem_u32(&full[s]), (it >> 1) & 1)) {
+                    abort_flag = 1;
+                } else {
+                    copy_pending = false;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const int nk8 = min(4, (K - 32 * c + 7) / 8);
+                    const uint32_t sa = smem_u32(stage), sb = smem_u32(stage + kTcA);
+                    const uint32_t d = tmem + bank;
+                    for (int ks = 0; ks < nk8; ++ks) {
+                        const uint32_t ko = ks * 32;
+                        const uint64_t ah = umma_desc(sa + ko), al = umma_desc(sa + 16384 + ko);
+                        const uint64_t bh = umma_desc(sb + ko), bl = umma_desc(sb + (uint32_t)Npad * 128 + ko);
+                        mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_tf32(d, ah, bl, idesc, 1u);
+                        mma_tf32(d, al, bh, idesc, 1u);
+                    }
+                    commit_to(&done[s]);
+                    if (c == nck - 1) commit_to(&bank_done[g & 1]);
+                }
+            }
+            ++it;
+        }
+        if (aborted) break;
+        // promote the previous offset's bank while this offset's MMAs run
+        if (g >= 1) {
+            const int pg = g - 1;
+            if (!mbar_wait(smem_u32(&bank_done[pg & 1]), (pg >> 1) & 1)) waits_ok = false;
+            waits_ok = __all_sync(0xffffffffu, waits_ok);   // tcgen05.ld is warp-collective
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t tb = tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(pg & 1) * 256u + (uint32_t)(ph * nsum);
+#pragma unroll
+            for (int j0 = 0; j0 < NS; j0 += 8) {
+                if (j0 < nsum && waits_ok) {
+                    float t[8];
+                    tmem_ld8(tb + j0, t);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[j0 + j] += t[j];
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+        }
+        ++g;
+    }
+    // promote the last offset's bank (the final commit covers every MMA)
+    if (!aborted && g >= 1) {
+        const int pg = g - 1;
+        if (!mbar_wait(smem_u32(&bank_done[pg & 1]), (pg >> 1) & 1)) waits_ok = false;
+        waits_ok = __all_sync(0xffffffffu, waits_ok);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t tb = tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(pg & 1) * 256u + (uint32_t)(ph * nsum);
+#pragma unroll
+        for (int j0 = 0; j0 < NS; j0 += 8) {
+            if (j0 < nsum && waits_ok) {
+                float t[8];
+                tmem_ld8(tb + j0, t);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j0 + j] += t[j];
+            }
+        }
+    }
+    if (aborted && it > 0) mbar_wait(smem_u32(&done[(it - 1) & 1]), ((it - 1) >> 1) & 1);
+    if (tid == 0 && copy_pending) mbar_wait(smem_u32(&full[(it - 1) & 1]), ((it - 1) >> 1) & 1);
+    const bool failed = __syncthreads_or(!waits_ok || aborted || abort_flag);
+    if (failed && tid == 0) atomicOr(a.status + 1, 1);
+    // write this thread's half row of the local expansion
+    {
+        const int r = pq * 32 + lane;
+        const int oslot = r / B, obb = r - oslot * B;
+        const int64_t os = (int64_t)tile * nbox + oslot;
+        if (oslot < nbox && os < ccnt && !failed) {
+            const int64_t obox = L.order[cbeg + os];
+            float *dst = L.le + (obox * B + obb) * a.ldk + ph * nsum;
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                if (j < nsum && ph * nsum + j < K) dst[j] = acc[j];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
+}  // namespace
+
+gf_status m2l_tc_prepare(gf_plan_s *plan) {
+    FmmPlan *F = plan->fmm;
+    if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
+    std::vector<TcLevel> h(F->L + 1);
+    for (int l = 2; l <= F->L; ++l) {
+        const FmmLevel &lv = F->lev[l];
+        TcLevel &t = h[l];
+        t.me = (const float *)lv.me;
+        t.le = (float *)lv.le;
+        t.order = lv.m2l_order;
+        t.tkey = lv.tkey;
+        for (int d = 0; d < 3; ++d) {
+            t.blo[d] = lv.slo[d];
+            t.bn[d] = lv.sn[d];
+        }
+        for (int c = 0; c <= 8; ++c) t.cls_off[c] = lv.cls_off[c];
+    }
+    F->tc_levels_host.assign(reinterpret_cast<unsigned char *>(h.data()),
+                             reinterpret_cast<unsigned char *>(h.data() + h.size()));
+    GF_TRY(plan->arena.alloc(&F->tc_levels, F->tc_levels_host.size()));
+    GF_CUDA(cudaMemcpyAsync(F->tc_levels, F->tc_levels_host.data(), F->tc_levels_host.size(),
+                            cudaMemcpyHostToDevice, plan->arena.stream));
+    return GF_OK;
+}
+
+namespace {
+
+gf_status m2l_run_tc(gf_plan_s *plan, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const Tables *T = F->tab;
+    const int Npad = T->tc_npad;
+    TcArgs a;
+    a.lv = reinterpret_cast<const TcLevel *>(F->tc_levels);
+    a.lmin = 2;
+    a.K = F->K;
+    a.ldk = F->KS;
+    a.B = B;
+    a.Npad = Npad;
+    a.nck = T->tc_nck;
+    a.img = T->m2l_tc;
+    a.status = plan->d_status;
+    const int nbox = 128 / B;
+    int tiles = 0, e = 0;
+    for (int l = 2; l <= F->L; ++l)
+        for (int c = 0; c < 8; ++c, ++e) {
+            a.tile_begin[e] = tiles;
+            const int64_t cnt = F->lev[l].cls_off[c + 1] - F->lev[l].cls_off[c];
+            tiles += (int)((cnt + nbox - 1) / nbox);
+        }
+    a.tile_begin[e] = tiles;
+    a.nent = e;
+    if (tiles == 0) return GF_OK;
+    const size_t shm = tc_smem_bytes(Npad);
+    const int nsum = Npad / 2;
+#define GF_TC_LAUNCH(NS)                                                  \
+    do {                                                                  \
+        GF_TRY(ensure_smem(m2l_tc<NS>, shm));                             \
+        m2l_tc<NS><<<tiles, kTcThreads, shm, st>>>(a);                    \
+    } while (0)
+    if (nsum <= 32)
+        GF_TC_LAUNCH(32);
+    else if (nsum <= 64)
+        GF_TC_LAUNCH(64);
+    else if (nsum <= 96)
+        GF_TC_LAUNCH(96);
+    else
+        GF_TC_LAUNCH(128);
+#undef GF_TC_LAUNCH
     GF_KERNEL_DONE();
     return GF_OK;
 }
@@ -167,6 +599,7 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st) {
     a.me = lv.me;
     a.le = lv.le;
     a.K = F->K;
+    a.ldk = F->KS;
     a.B = B;
     a.nbox = std::max(1, 32 / B);
     a.order = lv.m2l_order;
@@ -203,7 +636,20 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st) {
     }
 }
 
-template gf_status m2l_level<float>(gf_plan_s *, int, int, cudaStream_t);
-template gf_status m2l_level<double>(gf_plan_s *, int, int, cudaStream_t);
+template <class T>
+gf_status m2l_run(gf_plan_s *plan, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const bool tc = sizeof(T) == 4 && F->tab->m2l_tc && F->tc_levels && !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) &&
+                    B <= 128 && tc_smem_bytes(F->tab->tc_npad) <= 227 * 1024;
+    if (tc) return m2l_run_tc(plan, B, st);
+    for (int l = 2; l <= F->L; ++l) {
+        if (F->lev[l].nt == 0) continue;
+        GF_TRY(m2l_level<T>(plan, l, B, st));
+    }
+    return GF_OK;
+}
+
+template gf_status m2l_run<float>(gf_plan_s *, int, cudaStream_t);
+template gf_status m2l_run<double>(gf_plan_s *, int, cudaStream_t);
 
 }  // namespace gf

@@ -221,8 +221,12 @@ class _Quad:
         self.c.w = self.w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def make_options(mode="fmm", precision="fp64", p=8, leaf_vox=0, max_batch=1, G=0.0) -> gf_options:
+GF_FLAG_M2L_SIMT = 1
+
+
+def make_options(mode="fmm", precision="fp64", p=8, leaf_vox=0, max_batch=1, G=0.0, flags=0) -> gf_options:
     o = gf_options()
+    o.reserved0 = int(flags)
     o.mode = {"direct": GF_MODE_DIRECT, "fmm": GF_MODE_FMM}[mode] if isinstance(mode, str) else int(mode)
     o.precision = ({"fp64": GF_PREC_FP64, "mixed": GF_PREC_MIXED}[precision]
                    if isinstance(precision, str) else int(precision))
@@ -247,7 +251,7 @@ class Plan:
     obs must be a CUDA float64 tensor of shape (M, 3)."""
 
     def __init__(self, shape, origin, h, xi, w, obs, mode="fmm", precision="fp64", p=8,
-                 leaf_vox=0, max_batch=1, G=0.0, stream=None):
+                 leaf_vox=0, max_batch=1, G=0.0, stream=None, m2l="auto"):
         import torch
         if not (isinstance(obs, torch.Tensor) and obs.is_cuda):
             raise TypeError("obs must be a CUDA tensor")
@@ -258,7 +262,8 @@ class Plan:
         self.device = obs.device
         self._grid = make_grid(shape, origin, h)
         self._quad = _Quad(xi, w)
-        self._opt = make_options(mode, precision, p, leaf_vox, max_batch, G)
+        self._opt = make_options(mode, precision, p, leaf_vox, max_batch, G,
+                                 GF_FLAG_M2L_SIMT if m2l == "simt" else 0)
         self.handle = None
         with torch.cuda.device(self.device):
             self.handle = gf_plan_create(self._grid, self._quad.c, obs.data_ptr(), self.M, self._opt,

@@ -21,17 +21,17 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
 
 
-def plan_for(wk, precision="fp64", p=12, leaf_vox=0, B=1):
+def plan_for(wk, precision="fp64", p=12, leaf_vox=0, B=1, m2l="auto"):
     obs = torch.tensor(wk.obs, dtype=torch.float64, device=DEV)
     return pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs, mode="fmm",
-                    precision=precision, p=p, leaf_vox=leaf_vox, max_batch=B, G=wk.G)
+                    precision=precision, p=p, leaf_vox=leaf_vox, max_batch=B, G=wk.G, m2l=m2l)
 
 
-def run(wk, precision="fp64", p=12, leaf_vox=0, rho=None):
+def run(wk, precision="fp64", p=12, leaf_vox=0, rho=None, m2l="auto"):
     rho = wk.rho if rho is None else rho
     r = torch.tensor(rho, device=DEV)
     B = 1 if r.dim() == 3 else r.shape[0]
-    with plan_for(wk, precision, p, leaf_vox, B) as plan:
+    with plan_for(wk, precision, p, leaf_vox, B, m2l) as plan:
         g, gz = plan.forward(r, want_gz=True)
         torch.cuda.synchronize()
         plan.check()
@@ -113,6 +113,32 @@ def test_fmm_mixed_matches_oracle(seed, npts):
     ref = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs, wk.G)
     g, _, _ = run(wk, "mixed", p=12)
     assert rel_l2(g, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("p", [4, 8, 12, 14, 15])
+def test_m2l_tensor_cores_match_simt(p):
+    """Mixed precision: the tcgen05 M2L (3xTF32, FP32 accumulation in tensor
+    memory) and the SIMT FP32 M2L agree to FP32-level rounding, and the
+    tensor-core result meets the oracle at the accuracy its expansion degree
+    allows (<= 1e-5 from p = 10 up)."""
+    wk = cube_case(81 + p, n=28, vol_targets=400)
+    ref = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs, wk.G)
+    g_tc, _, _ = run(wk, "mixed", p=p)
+    g_simt, _, _ = run(wk, "mixed", p=p, m2l="simt")
+    g64, _, _ = run(wk, "fp64", p=p)
+    # each offset's tensor-core partial sum is promoted to FP32 registers, so
+    # the two mixed paths differ only at FP32 rounding level
+    assert rel_l2(g_tc, g_simt) <= 2e-6
+    assert rel_l2(g_tc, ref) <= rel_l2(g64, ref) + 3e-6
+    assert rel_l2(g_tc, ref) <= 1e-5 or p < 10
+
+
+def test_m2l_tensor_cores_batched():
+    wk = cube_case(91, n=20, B=5, vol_targets=200)
+    g5, _, _ = run(wk, "mixed", p=10)
+    for bb in (0, 4):
+        g1, _, _ = run(wk, "mixed", p=10, rho=wk.rho[bb])
+        assert rel_l2(g5[bb], g1) <= 1e-6
 
 
 def test_fmm_fp64_prism_noise_16cubed():
