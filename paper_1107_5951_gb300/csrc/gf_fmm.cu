@@ -289,7 +289,8 @@ __device__ __forceinline__ void two_sum(T &hi, T &lo, T x) {
 
 constexpr int kEvalWarps = 4;
 constexpr int kEvalChunk = 64;
-constexpr int kTPL = 4;  // targets per lane
+constexpr int kTPL = 2;            // targets per lane: a work item has <= 64 targets
+constexpr int kSrcTable = 512;     // per-block table of a leaf's source offsets
 
 struct EvalArgs {
     const int4 *items;
@@ -298,7 +299,7 @@ struct EvalArgs {
     const int32_t *perm;
     const void *tloc;          // [M][3] T
     const void *mass;          // [ns_L][B][b3] T
-    const void *le;            // [nt_L][B][K] T
+    const void *le;            // [nt_L][B][ldk] T
     const QuadRule *qr;
     Block3 blk;                // leaf source block
     int b, nq, B, K, ldk, p;
@@ -308,23 +309,46 @@ struct EvalArgs {
     double *g, *gz;
 };
 
+// Near field + far field of the observers of one leaf, one warp per work
+// item.  The sources of each neighbouring leaf are staged in the warp's
+// shared-memory slice in chunks of 64 (position relative to the target
+// leaf's centre, mass times quadrature weight) and every lane sweeps them
+// for its two observers.  Per-leaf partial sums are merged with TwoSum.
 template <class T>
 __global__ void __launch_bounds__(kEvalWarps * 32)
 eval_kernel(EvalArgs a) {
     extern __shared__ unsigned char shraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int P2 = a.p * a.p;
-    T *wsh = reinterpret_cast<T *>(shraw) + (size_t)warp * (4 * kEvalChunk + 3 * P2);
+    const int b3 = a.b * a.b * a.b;
+    const int nsrc = b3 * a.nq;
+    // block-wide table: offset of source u (voxel u / nq, node u % nq) from
+    // its leaf's centre, quadrature weight, voxel index
+    Vec4<T> *tab = reinterpret_cast<Vec4<T> *>(shraw);
+    int *tvox = reinterpret_cast<int *>(tab + kSrcTable);
+    T *wsh = reinterpret_cast<T *>(tvox + kSrcTable) + (size_t)warp * (4 * kEvalChunk + 3 * P2);
     Vec4<T> *src = reinterpret_cast<Vec4<T> *>(wsh);
     T *Dx = wsh + 4 * kEvalChunk, *Dy = Dx + P2, *Dz = Dy + P2;
     const T *tloc = reinterpret_cast<const T *>(a.tloc);
     const T *mass = reinterpret_cast<const T *>(a.mass);
     const T *le = reinterpret_cast<const T *>(a.le);
-    const int b3 = a.b * a.b * a.b;
-    const int nsrc = b3 * a.nq;
     const T half_b = T(0.5) * T(a.b);
     const T inv_b = T(1) / T(a.b);
     const T eps2 = (T)a.eps2;
+    const bool use_tab = nsrc <= kSrcTable;
+    if (use_tab) {
+        for (int u = threadIdx.x; u < nsrc; u += blockDim.x) {
+            const int v = u / a.nq, q = u - v * a.nq;
+            Vec4<T> e;
+            e.x = T(v % a.b) + (T)(0.5 + 0.5 * a.qr->xi[q][0]) - half_b;
+            e.y = T((v / a.b) % a.b) + (T)(0.5 + 0.5 * a.qr->xi[q][1]) - half_b;
+            e.z = T(v / (a.b * a.b)) + (T)(0.5 + 0.5 * a.qr->xi[q][2]) - half_b;
+            e.w = (T)a.qr->wn[q];
+            tab[u] = e;
+            tvox[u] = v;
+        }
+    }
+    __syncthreads();
     for (int64_t it = (int64_t)blockIdx.x * kEvalWarps + warp; it < a.n_items;
          it += (int64_t)gridDim.x * kEvalWarps) {
         const int4 item = a.items[it];
@@ -364,6 +388,7 @@ eval_kernel(EvalArgs a) {
                     continue;
                 const int64_t sl = (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx;
                 const T *ms = mass + (sl * a.B + bb) * b3;
+                const T ox = T(dx * a.b), oy = T(dy * a.b), oz = T(dz * a.b);
                 T px[kTPL], py[kTPL], pz[kTPL];
 #pragma unroll
                 for (int u = 0; u < kTPL; ++u) px[u] = py[u] = pz[u] = T(0);
@@ -372,21 +397,27 @@ eval_kernel(EvalArgs a) {
                     __syncwarp();
                     for (int s = lane; s < cnt; s += 32) {
                         const int u = c0 + s;
-                        const int v = u / a.nq, q = u - v * a.nq;
-                        const int vx = v % a.b, vy = (v / a.b) % a.b, vz = v / (a.b * a.b);
                         Vec4<T> e;
-                        e.x = T(dx * a.b + vx) + (T)a.qr->offf[q][0] - half_b;
-                        e.y = T(dy * a.b + vy) + (T)a.qr->offf[q][1] - half_b;
-                        e.z = T(dz * a.b + vz) + (T)a.qr->offf[q][2] - half_b;
-                        if (sizeof(T) == 8) {
-                            e.x = T(dx * a.b + vx) + (T)(0.5 + 0.5 * a.qr->xi[q][0]) - half_b;
-                            e.y = T(dy * a.b + vy) + (T)(0.5 + 0.5 * a.qr->xi[q][1]) - half_b;
-                            e.z = T(dz * a.b + vz) + (T)(0.5 + 0.5 * a.qr->xi[q][2]) - half_b;
+                        int v;
+                        if (use_tab) {
+                            e = tab[u];
+                            v = tvox[u];
+                        } else {
+                            v = u / a.nq;
+                            const int q = u - v * a.nq;
+                            e.x = T(v % a.b) + (T)(0.5 + 0.5 * a.qr->xi[q][0]) - half_b;
+                            e.y = T((v / a.b) % a.b) + (T)(0.5 + 0.5 * a.qr->xi[q][1]) - half_b;
+                            e.z = T(v / (a.b * a.b)) + (T)(0.5 + 0.5 * a.qr->xi[q][2]) - half_b;
+                            e.w = (T)a.qr->wn[q];
                         }
-                        e.w = ms[v] * (T)a.qr->wn[q];
+                        e.x += ox;
+                        e.y += oy;
+                        e.z += oz;
+                        e.w *= ms[v];
                         src[s] = e;
                     }
                     __syncwarp();
+#pragma unroll 4
                     for (int s = 0; s < cnt; ++s) {
                         const Vec4<T> e = src[s];
 #pragma unroll
@@ -540,23 +571,20 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         GF_KERNEL_DONE();
     }
     stage_mark(plan, 2, st);
-    // a4: M2M up to level 2; in mixed precision the translations into the
-    // top levels (parent level <= 3) are done in FP64
+    // a4: M2M up to level 2.  In mixed precision the translation into the
+    // top level (2) is done in FP64 on the per-box kernel; the deeper levels
+    // run in the batched kernel in the plan's precision.
     for (int l = L - 1; l >= 2; --l) {
         const FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
-        if (sizeof(T) == 4 && l <= 3) {
+        if (sizeof(T) == 4 && l <= 2) {
             const size_t shm = sizeof(double) * 8 * B * K;
             GF_TRY((ensure_smem(m2m_kernel<T, double>, shm)));
             m2m_kernel<T, double><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
                                                                      block_of(pa), B, K, F->KS, tab->m2m_d);
+            GF_KERNEL_DONE();
         } else {
-            const size_t shm = sizeof(T) * 8 * B * K;
-            GF_TRY((ensure_smem(m2m_kernel<T, T>, shm)));
-            const T *tb = sizeof(T) == 8 ? (const T *)tab->m2m_d : (const T *)tab->m2m_f;
-            m2m_kernel<T, T><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
-                                                                block_of(pa), B, K, F->KS, tb);
+            GF_TRY((translate_run<T, T>(plan, l, 0, B, st)));
         }
-        GF_KERNEL_DONE();
     }
     stage_mark(plan, 3, st);
     // a5/a6: M2L at every level (each overwrites its level's LE), then the
@@ -567,15 +595,13 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         const FmmLevel &lv = F->lev[l];
         if (lv.nt == 0) continue;
         const FmmLevel &pa = F->lev[l - 1];
-        if (sizeof(T) == 4 && l - 1 <= 3) {
+        if (sizeof(T) == 4 && l - 1 <= 2) {
             l2l_kernel<T, double><<<(unsigned)lv.nt, 128, sizeof(double) * B * K, st>>>(
                 (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, F->KS, tab->l2l_d);
+            GF_KERNEL_DONE();
         } else {
-            const T *tb = sizeof(T) == 8 ? (const T *)tab->l2l_d : (const T *)tab->l2l_f;
-            l2l_kernel<T, T><<<(unsigned)lv.nt, 128, sizeof(T) * B * K, st>>>(
-                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, F->KS, tb);
+            GF_TRY((translate_run<T, T>(plan, l, 1, B, st)));
         }
-        GF_KERNEL_DONE();
     }
     stage_mark(plan, 5, st);
     // a7-a9: near field + L2P + combine + scatter
@@ -601,7 +627,8 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         a.eps2 = sizeof(T) == 8 ? 1e-18 : 1e-12;
         a.g = g;
         a.gz = gz;
-        const size_t shm = sizeof(T) * kEvalWarps * (4 * kEvalChunk + 3 * F->p * F->p);
+        const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
+                           sizeof(T) * kEvalWarps * (4 * kEvalChunk + 3 * F->p * F->p);
         const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
         GF_TRY(ensure_smem(eval_kernel<T>, shm));
         eval_kernel<T><<<grid, kEvalWarps * 32, shm, st>>>(a);

@@ -62,7 +62,7 @@ struct FmmPlan {
     int32_t *leaf_beg = nullptr;  // [nt_L + 1] observer range of each leaf
     float *tloc_f = nullptr;      // [M][3] offset from own leaf centre (voxel units)
     double *tloc_d = nullptr;
-    int4 *items = nullptr;        // evaluation work: (leaf, first, count, 0)
+    int4 *items = nullptr;        // evaluation work: (leaf, first, count <= 64, 0)
     int64_t n_items = 0;
     void *mass = nullptr;         // [ns_L][B][b^3] voxel densities, leaf-blocked
     double *p2m_d = nullptr;      // [b^3][K] quadrature-folded P2M matrix

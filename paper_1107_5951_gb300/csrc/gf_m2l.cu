@@ -200,6 +200,136 @@ m2l_simt(M2LArgs a) {
     }
 }
 
+// Batched M2M / L2L translations with the same SIMT tiling: a block takes
+// 32 columns (box, batch member), gathers the K inputs of each column for
+// every translation step into shared memory and multiplies them by the
+// step's K x K operator (streamed in 32-row chunks), accumulating in Tc.
+//   M2M: columns = parent boxes of the dense source block of level l, steps
+//        = the 8 child positions; out = sum_oct T_oct ME_{l+1}[child] (store)
+//   L2L: columns = observer boxes of level l of one parity class (the child
+//        position), one step; out = LE_l + T_class LE_{l-1}[parent] (update)
+struct XArgs {
+    const void *in;
+    void *out;
+    int K, ldk, B, nbox, kind;      // kind 0 = M2M, 1 = L2L
+    int64_t nout;                   // M2M: parents
+    int64_t plo[3], pn[3];          // M2M: parent block
+    int64_t clo[3], cn[3];          // M2M: child block
+    const int32_t *order;           // L2L: class-grouped observer boxes
+    int64_t cls_off[9];
+    const int32_t *tparent;         // L2L
+    const void *tab;                // [8][K][K] input-major
+};
+
+template <class Ts, class Tc, int RPT>
+__global__ void __launch_bounds__(256)
+xlate_simt(XArgs a) {
+    constexpr int S = XStride<Tc>::v;
+    constexpr int KP = 32 * RPT;
+    extern __shared__ unsigned char shraw[];
+    Tc *Xs = reinterpret_cast<Tc *>(shraw);
+    Tc *Ts_ = Xs + kCK * S;
+    __shared__ int64_t obox[32];
+    __shared__ int64_t srow[32];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int K = a.K, B = a.B;
+    int cls = 0;
+    int64_t cbeg = 0, ccnt = a.nout;
+    if (a.kind == 1) {
+        cls = blockIdx.y;
+        cbeg = a.cls_off[cls];
+        ccnt = a.cls_off[cls + 1] - cbeg;
+    }
+    const int64_t tile0 = (int64_t)blockIdx.x * a.nbox;
+    if (tile0 >= ccnt) return;
+    const Ts *in = reinterpret_cast<const Ts *>(a.in);
+    const Tc *tab = reinterpret_cast<const Tc *>(a.tab);
+    if (tid < 32) {
+        const int64_t sidx = tile0 + tid;
+        obox[tid] = (tid < a.nbox && sidx < ccnt) ? (a.kind == 1 ? (int64_t)a.order[cbeg + sidx] : sidx) : -1;
+    }
+    __syncthreads();
+    Tc acc[RPT][4];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = Tc(0);
+    const int nsteps = a.kind == 0 ? 8 : 1;
+    for (int st = 0; st < nsteps; ++st) {
+        const int op = a.kind == 0 ? st : cls;
+        if (tid < 32) {
+            const int slot = tid / B, bb = tid - slot * B;
+            int64_t row = -1;
+            if (slot < a.nbox && obox[slot] >= 0) {
+                const int64_t ob = obox[slot];
+                if (a.kind == 0) {
+                    const int64_t px = a.plo[0] + ob % a.pn[0], py = a.plo[1] + (ob / a.pn[0]) % a.pn[1],
+                                  pz = a.plo[2] + ob / (a.pn[0] * a.pn[1]);
+                    const int64_t cx = 2 * px + (op & 1) - a.clo[0], cy = 2 * py + ((op >> 1) & 1) - a.clo[1],
+                                  cz = 2 * pz + ((op >> 2) & 1) - a.clo[2];
+                    if (cx >= 0 && cy >= 0 && cz >= 0 && cx < a.cn[0] && cy < a.cn[1] && cz < a.cn[2])
+                        row = (((cz * a.cn[1] + cy) * a.cn[0] + cx) * B + bb) * a.ldk;
+                } else {
+                    row = ((int64_t)a.tparent[ob] * B + bb) * a.ldk;
+                }
+            }
+            srow[tid] = row;
+        }
+        __syncthreads();
+        const Tc *tabo = tab + (size_t)op * K * K;
+        for (int c0 = 0; c0 < K; c0 += kCK) {
+            for (int e = tid; e < kCK * 32; e += 256) {
+                const int cc = e % kCK, j = e / kCK;
+                const int64_t row = srow[j];
+                const int c = c0 + cc;
+                Xs[cc * S + j] = (row >= 0 && c < K) ? (Tc)in[row + c] : Tc(0);
+            }
+            for (int e = tid; e < kCK * KP; e += 256) {
+                const int cc = e / KP, k = e - cc * KP;
+                const int c = c0 + cc;
+                Ts_[e] = (c < K && k < K) ? tabo[(size_t)c * K + k] : Tc(0);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int cc = 0; cc < kCK; ++cc) {
+                Tc xv[4], tv[RPT];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xv[c] = Xs[cc * S + tx * 4 + c];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) tv[r] = Ts_[cc * KP + ty * RPT + r];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] += tv[r] * xv[c];
+            }
+            __syncthreads();
+        }
+    }
+    Ts *out = reinterpret_cast<Ts *>(a.out);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int j = tx * 4 + c;
+        const int slot = j / B, bb = j - slot * B;
+        if (slot >= a.nbox || obox[slot] < 0) continue;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int k = ty * RPT + r;
+            if (k >= K) continue;
+            Ts *o = out + (obox[slot] * B + bb) * a.ldk + k;
+            *o = a.kind == 0 ? (Ts)acc[r][c] : (Ts)((Tc)*o + acc[r][c]);
+        }
+    }
+}
+
+template <class Ts, class Tc, int RPT>
+gf_status launch_xlate(const XArgs &a, int64_t tiles, int ny, cudaStream_t st) {
+    const size_t shm = sizeof(Tc) * (kCK * XStride<Tc>::v + kCK * 32 * RPT);
+    GF_TRY(ensure_smem(xlate_simt<Ts, Tc, RPT>, shm));
+    xlate_simt<Ts, Tc, RPT><<<dim3((unsigned)tiles, ny), 256, shm, st>>>(a);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
 template <class T, int RPT>
 gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
     const size_t shm = sizeof(T) * (kCK * XStride<T>::v + kCK * 32 * RPT);
@@ -635,6 +765,69 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st) {
             return GF_ERR_UNSUPPORTED;
     }
 }
+
+template <class Ts, class Tc>
+gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    XArgs a;
+    a.K = F->K;
+    a.ldk = F->KS;
+    a.B = B;
+    a.nbox = std::max(1, 32 / B);
+    a.kind = kind;
+    int64_t tiles;
+    int ny = 1;
+    if (kind == 0) {   // M2M into `level` from level + 1
+        const FmmLevel &pa = F->lev[level], &ch = F->lev[level + 1];
+        a.in = ch.me;
+        a.out = pa.me;
+        a.nout = pa.ns;
+        for (int d = 0; d < 3; ++d) {
+            a.plo[d] = pa.slo[d];
+            a.pn[d] = pa.sn[d];
+            a.clo[d] = ch.slo[d];
+            a.cn[d] = ch.sn[d];
+        }
+        a.order = nullptr;
+        a.tparent = nullptr;
+        a.tab = sizeof(Tc) == 8 ? (const void *)F->tab->m2m_d : (const void *)F->tab->m2m_f;
+        tiles = (pa.ns + a.nbox - 1) / a.nbox;
+    } else {           // L2L into `level` from level - 1
+        const FmmLevel &lv = F->lev[level], &pa = F->lev[level - 1];
+        if (lv.nt == 0) return GF_OK;
+        a.in = pa.le;
+        a.out = lv.le;
+        a.nout = lv.nt;
+        a.order = lv.m2l_order;
+        for (int c = 0; c <= 8; ++c) a.cls_off[c] = lv.cls_off[c];
+        a.tparent = lv.tparent;
+        a.tab = sizeof(Tc) == 8 ? (const void *)F->tab->l2l_d : (const void *)F->tab->l2l_f;
+        int64_t maxc = 0;
+        for (int c = 0; c < 8; ++c) maxc = std::max<int64_t>(maxc, lv.cls_off[c + 1] - lv.cls_off[c]);
+        tiles = (maxc + a.nbox - 1) / a.nbox;
+        ny = 8;
+    }
+    if (tiles == 0) return GF_OK;
+    switch ((F->K + 31) / 32) {
+        case 1: return launch_xlate<Ts, Tc, 1>(a, tiles, ny, st);
+        case 2: return launch_xlate<Ts, Tc, 2>(a, tiles, ny, st);
+        case 3: return launch_xlate<Ts, Tc, 3>(a, tiles, ny, st);
+        case 4: return launch_xlate<Ts, Tc, 4>(a, tiles, ny, st);
+        case 5: return launch_xlate<Ts, Tc, 5>(a, tiles, ny, st);
+        case 6: return launch_xlate<Ts, Tc, 6>(a, tiles, ny, st);
+        case 7: return launch_xlate<Ts, Tc, 7>(a, tiles, ny, st);
+        case 8: return launch_xlate<Ts, Tc, 8>(a, tiles, ny, st);
+        case 9: return launch_xlate<Ts, Tc, 9>(a, tiles, ny, st);
+        case 10: return launch_xlate<Ts, Tc, 10>(a, tiles, ny, st);
+        default:
+            set_error("expansion degree too large for the translation kernel");
+            return GF_ERR_UNSUPPORTED;
+    }
+}
+
+template gf_status translate_run<float, float>(gf_plan_s *, int, int, int, cudaStream_t);
+template gf_status translate_run<float, double>(gf_plan_s *, int, int, int, cudaStream_t);
+template gf_status translate_run<double, double>(gf_plan_s *, int, int, int, cudaStream_t);
 
 template <class T>
 gf_status m2l_run(gf_plan_s *plan, int B, cudaStream_t st) {

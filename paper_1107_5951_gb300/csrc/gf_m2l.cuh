@@ -18,6 +18,11 @@ gf_status m2l_run(gf_plan_s *plan, int B, cudaStream_t st);
 template <class T>
 gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st);
 
+// Batched M2M (kind 0: into `level` from level + 1) or L2L (kind 1: into
+// `level` from level - 1) on the SIMT cores; Ts = storage, Tc = arithmetic.
+template <class Ts, class Tc>
+gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st);
+
 // Plan-time set-up of the tensor-core path (level descriptors on the device).
 gf_status m2l_tc_prepare(gf_plan_s *plan);
 

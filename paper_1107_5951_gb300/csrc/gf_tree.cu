@@ -120,7 +120,7 @@ __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restr
     }
 }
 
-constexpr int kItemTargets = 128;
+constexpr int kItemTargets = 64;   // targets per evaluation work item (2 per lane)
 
 __global__ void item_counts(const int32_t *__restrict__ beg, int64_t nleaf, int64_t *__restrict__ cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
