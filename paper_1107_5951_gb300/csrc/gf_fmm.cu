@@ -264,7 +264,7 @@ l2l_kernel(const Ts *__restrict__ le_p, const uint64_t *__restrict__ tkey, const
 
 // ---------------------------------------------------------------- evaluation
 template <class T>
-struct Vec4 {
+struct __align__(16) Vec4 {
     T x, y, z, w;
 };
 
@@ -326,7 +326,10 @@ eval_kernel(EvalArgs a) {
     // its leaf's centre, quadrature weight, voxel index
     Vec4<T> *tab = reinterpret_cast<Vec4<T> *>(shraw);
     int *tvox = reinterpret_cast<int *>(tab + kSrcTable);
-    T *wsh = reinterpret_cast<T *>(tvox + kSrcTable) + (size_t)warp * (4 * kEvalChunk + 3 * P2);
+    // per-warp slice, a multiple of 8 elements so every slice keeps the
+    // alignment of the vector type
+    const int wstride = (4 * kEvalChunk + 3 * P2 + 7) & ~7;
+    T *wsh = reinterpret_cast<T *>(tvox + kSrcTable) + (size_t)warp * wstride;
     Vec4<T> *src = reinterpret_cast<Vec4<T> *>(wsh);
     T *Dx = wsh + 4 * kEvalChunk, *Dy = Dx + P2, *Dz = Dy + P2;
     const T *tloc = reinterpret_cast<const T *>(a.tloc);
@@ -628,7 +631,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         a.g = g;
         a.gz = gz;
         const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
-                           sizeof(T) * kEvalWarps * (4 * kEvalChunk + 3 * F->p * F->p);
+                           sizeof(T) * kEvalWarps * ((4 * kEvalChunk + 3 * F->p * F->p + 7) & ~7);
         const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
         GF_TRY(ensure_smem(eval_kernel<T>, shm));
         eval_kernel<T><<<grid, kEvalWarps * 32, shm, st>>>(a);
