@@ -48,6 +48,9 @@ def _load():
             lib.gfo_adjoint.argtypes = [i64, i64, i64, _dp, _dp, i32, _dp, _dp,
                                         _dp, i64, _dp, i32, i32, dbl, _dp, i32]
             lib.gfo_adjoint.restype = i32
+            lib.gfo_adjoint_subset.argtypes = [i64, i64, i64, _dp, _dp, i32, _dp, _dp, _dp, i64, _dp, i32, i32,
+                                               dbl, ctypes.POINTER(ctypes.c_long), i64, _dp, i32]
+            lib.gfo_adjoint_subset.restype = i32
             lib.gfo_prism_gz.argtypes = [_dp, _dp, dbl, dbl, _dp]
             lib.gfo_prism_gz.restype = dbl
             lib.gfo_prism_gz_many.argtypes = [_dp, _dp, dbl, dbl, _dp, i64, _dp, i32]
@@ -128,6 +131,34 @@ def adjoint(shape, origin, h, xi, w, obs, r, G, ncomp: int = 1,
                              float(G), _p(out), int(nthreads))
     if rc != 0:
         raise ValueError("gfo_adjoint: bad arguments")
+    return out[0] if single else out
+
+
+def adjoint_subset(shape, origin, h, xi, w, obs, r, G, vox, ncomp: int = 1,
+                   nthreads: int = 0) -> np.ndarray:
+    """:func:`adjoint` evaluated only at the voxels with linear indices
+    `vox` (into [nz][ny][nx]); returns (B, len(vox)) or (len(vox),)."""
+    nx, ny, nz = (int(s) for s in shape)
+    obs = _c(obs).reshape(-1, 3)
+    M = obs.shape[0]
+    r = _c(r)
+    if ncomp == 1:
+        single = r.ndim == 1
+        r = r.reshape(-1, M)
+    else:
+        single = r.ndim == 2
+        r = r.reshape(-1, M, 3)
+    B = r.shape[0]
+    vox = np.ascontiguousarray(vox, dtype=np.int64)
+    xi = _c(xi).reshape(-1, 3)
+    w = _c(w).reshape(-1)
+    out = np.zeros((B, vox.size), dtype=np.float64)
+    rc = _load().gfo_adjoint_subset(nx, ny, nz, _p(_c(origin)), _p(_c(h)), xi.shape[0], _p(xi), _p(w),
+                                    _p(obs), M, _p(_c(r)), ncomp, B, float(G),
+                                    vox.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), vox.size,
+                                    _p(out), int(nthreads))
+    if rc != 0:
+        raise ValueError("gfo_adjoint_subset: bad arguments")
     return out[0] if single else out
 
 

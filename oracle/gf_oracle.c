@@ -201,6 +201,60 @@ int gfo_adjoint(long nx, long ny, long nz, const double *origin,
 }
 
 /*
+ * The transpose sum of gfo_adjoint restricted to a list of voxels
+ * (vox[nv] linear indices into [nz][ny][nx]): grad[b][i] for i < nv.  Used to
+ * check large problems on a sample of voxels.
+ */
+int gfo_adjoint_subset(long nx, long ny, long nz, const double *origin,
+                       const double *h, int nq, const double *xi,
+                       const double *w, const double *obs, long M,
+                       const double *r, int ncomp, int B, double G,
+                       const long *vox, long nv, double *grad, int nthreads) {
+    if (nx < 0 || ny < 0 || nz < 0 || nq <= 0 || B <= 0 || M < 0 || nv < 0) return -1;
+    if (ncomp != 1 && ncomp != 3) return -1;
+    set_threads(nthreads);
+    const double vol = h[0] * h[1] * h[2];
+    double wsum = 0.0;
+    for (int q = 0; q < nq; ++q) wsum += w[q];
+#pragma omp parallel
+    {
+        nsum *acc = (nsum *)malloc(sizeof(nsum) * (size_t)B);
+#pragma omp for schedule(dynamic, 1)
+        for (long iv = 0; iv < nv; ++iv) {
+            const long v = vox[iv];
+            const long i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+            memset(acc, 0, sizeof(nsum) * (size_t)B);
+            for (int q = 0; q < nq; ++q) {
+                double x[3];
+                source_point(origin, h, i, j, k, xi + 3 * q, x);
+                const double wq = w[q] / wsum;
+                for (long s = 0; s < M; ++s) {
+                    const double d0 = obs[3 * s + 0] - x[0],
+                                 d1 = obs[3 * s + 1] - x[1],
+                                 d2 = obs[3 * s + 2] - x[2];
+                    const double rr = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (rr == 0.0) continue;
+                    const double rinv = 1.0 / sqrt(rr);
+                    const double k3 = rinv * rinv * rinv * vol * wq;
+                    for (int b = 0; b < B; ++b) {
+                        const double *rb = r + ((long)b * M + s) * ncomp;
+                        double t;
+                        if (ncomp == 1)
+                            t = rb[0] * d2;
+                        else
+                            t = rb[0] * d0 + rb[1] * d1 + rb[2] * d2;
+                        nsum_add(&acc[b], t * k3);
+                    }
+                }
+            }
+            for (int b = 0; b < B; ++b) grad[(long)b * nv + iv] = G * nsum_val(&acc[b]);
+        }
+        free(acc);
+    }
+    return 0;
+}
+
+/*
  * Closed-form g_z of a constant-density rectangular prism (the analytic
  * reference of Sec. 2.1 / Sec. 3, SUM-AN).  Derived here from Eq. 1:
  * with u = x - r_x, v = y - r_y, w = z - r_z (source minus observer),

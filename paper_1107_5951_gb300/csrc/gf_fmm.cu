@@ -469,6 +469,26 @@ eval_kernel(EvalArgs a) {
     }
 }
 
+// Adjoint tables: adj[slot][i*K + o] = fwd[mslot][o*K + i], where mslot is
+// the slot of -offset for M2L and the same octant for M2M/L2L.
+__global__ void transpose_ops(const double *__restrict__ fwd, double *__restrict__ adjd, float *__restrict__ adjf,
+                              int K, int nslots, int negate) {
+    const int slot = blockIdx.x;
+    int mslot = slot;
+    if (negate) {
+        const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+        mslot = (-dz + 3) * 49 + (-dy + 3) * 7 + (-dx + 3);
+    }
+    const size_t KK = (size_t)K * K;
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const int i = e / K, o = e - i * K;
+        const double v = fwd[(size_t)mslot * KK + (size_t)o * K + i];
+        adjd[(size_t)slot * KK + e] = v;
+        adjf[(size_t)slot * KK + e] = (float)v;
+    }
+    (void)nslots;
+}
+
 // ---------------------------------------------------------------- tables
 std::mutex g_tab_mu;
 std::vector<Tables *> g_tabs;
@@ -501,6 +521,18 @@ gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out) {
     const size_t shm = sizeof(double) * (H + 1) * (H + 2);
     build_ops<<<343 + 16, 256, shm, st>>>(p, T->K, host_logfact(), T->m2l_d, T->m2l_f, T->m2m_d, T->m2m_f,
                                           T->l2l_d, T->l2l_f);
+    GF_KERNEL_DONE();
+    GF_CUDA(cudaMalloc(&T->am2l_d, 343 * KK * sizeof(double)));
+    GF_CUDA(cudaMalloc(&T->am2l_f, 343 * KK * sizeof(float)));
+    GF_CUDA(cudaMalloc(&T->am2m_d, 8 * KK * sizeof(double)));
+    GF_CUDA(cudaMalloc(&T->am2m_f, 8 * KK * sizeof(float)));
+    GF_CUDA(cudaMalloc(&T->al2l_d, 8 * KK * sizeof(double)));
+    GF_CUDA(cudaMalloc(&T->al2l_f, 8 * KK * sizeof(float)));
+    transpose_ops<<<343, 256, 0, st>>>(T->m2l_d, T->am2l_d, T->am2l_f, T->K, 343, 1);
+    GF_KERNEL_DONE();
+    transpose_ops<<<8, 256, 0, st>>>(T->m2m_d, T->am2m_d, T->am2m_f, T->K, 8, 0);
+    GF_KERNEL_DONE();
+    transpose_ops<<<8, 256, 0, st>>>(T->l2l_d, T->al2l_d, T->al2l_f, T->K, 8, 0);
     GF_KERNEL_DONE();
     GF_TRY(m2l_prepare_tables(T, st));
     GF_CUDA(cudaStreamSynchronize(st));
@@ -539,6 +571,7 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     const size_t shm = sizeof(double) * ((F->p + 1) * (F->p + 2) + K);
     build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), F->p2m_d, F->p2m_f);
     GF_KERNEL_DONE();
+    GF_TRY(fmm_adjoint_prepare(plan, st));
     return m2l_tc_prepare(plan);
 }
 
@@ -592,7 +625,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     stage_mark(plan, 3, st);
     // a5/a6: M2L at every level (each overwrites its level's LE), then the
     // L2L chain from level 3 down, which adds each finished parent LE.
-    GF_TRY(m2l_run<T>(plan, B, st));
+    GF_TRY(m2l_run<T>(plan, B, false, st));
     stage_mark(plan, 4, st);
     for (int l = 3; l <= L; ++l) {
         const FmmLevel &lv = F->lev[l];
@@ -650,9 +683,5 @@ gf_status fmm_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     return run_forward<double>(plan, rho, rho_dtype, B, g, gz, st);
 }
 
-gf_status fmm_adjoint(gf_plan_s *, const double *, int, int, double *, cudaStream_t) {
-    set_error("the FMM adjoint is not built yet");
-    return GF_ERR_UNSUPPORTED;
-}
 
 }  // namespace gf

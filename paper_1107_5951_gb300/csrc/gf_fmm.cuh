@@ -45,6 +45,12 @@ struct Tables {
     float *m2l_f = nullptr;
     double *m2m_d = nullptr, *l2l_d = nullptr;
     float *m2m_f = nullptr, *l2l_f = nullptr;
+    // Transposed operators for the adjoint, in the same input-major layout:
+    //   am2l[slot(o')] = (T_{-o'})^T, o' = observer box - source box
+    //   am2m[oct] = (T_M2M,oct)^T,  al2l[oct] = (T_L2L,oct)^T
+    double *am2l_d = nullptr, *am2m_d = nullptr, *al2l_d = nullptr;
+    float *am2l_f = nullptr, *am2m_f = nullptr, *al2l_f = nullptr;
+    float *am2l_tc = nullptr;
 };
 
 gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out);
@@ -70,7 +76,20 @@ struct FmmPlan {
     const Tables *tab = nullptr;
     void *tc_levels = nullptr;                  // tensor-core M2L level table
     std::vector<unsigned char> tc_levels_host;
+    // adjoint: per level, observer-box index over the source block widened
+    // by 3 boxes (-1 where no observer box), the children of each observer
+    // box (8 slots by position, -1 if absent), and the source boxes' count
+    // per parity class (prefix sums)
+    int32_t *imap[kMaxLevels + 1] = {};
+    int64_t mlo[kMaxLevels + 1][3] = {}, mn[kMaxLevels + 1][3] = {};
+    int32_t *child[kMaxLevels + 1] = {};
+    int64_t scls_off[kMaxLevels + 1][9] = {};
+    void *tc_levels_adj = nullptr;
+    std::vector<unsigned char> tc_levels_adj_host;
 };
+
+// adjoint set-up and driver (gf_adjoint.cu)
+gf_status fmm_adjoint_prepare(gf_plan_s *plan, cudaStream_t st);
 
 // Interaction-list offsets of a box whose position inside its parent is
 // `cls` ((x&1) | (y&1)<<1 | (z&1)<<2): the 189 vectors o with max-norm 2 or 3

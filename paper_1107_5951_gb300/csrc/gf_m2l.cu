@@ -7,6 +7,8 @@
 // K x 32 matrix of gathered source expansions ME[t + o], accumulating the
 // K x 32 result in registers.  Sources outside the source block contribute
 // zero columns.  Each output is written once, so the result is deterministic.
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -71,20 +73,26 @@ gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
     GF_CUDA(cudaMalloc(&T->m2l_tc, n * sizeof(float)));
     build_tc_images<<<343, 256, 0, st>>>(T->m2l_d, T->K, npad, T->tc_nck, T->m2l_tc);
     GF_KERNEL_DONE();
+    GF_CUDA(cudaMalloc(&T->am2l_tc, n * sizeof(float)));
+    build_tc_images<<<343, 256, 0, st>>>(T->am2l_d, T->K, npad, T->tc_nck, T->am2l_tc);
+    GF_KERNEL_DONE();
     return GF_OK;
 }
 
 namespace {
 
 struct M2LArgs {
-    const void *me;
-    void *le;
+    const void *me;    // input rows (forward: ME_l; adjoint: LE_l duals)
+    void *le;          // output rows (forward: LE_l; adjoint: ME_l duals)
     int K, ldk, B, nbox;
     const int32_t *order;
     int64_t cls_off[9];
     const uint64_t *tkey;
-    int64_t blo[3], bn[3];
+    int64_t blo[3], bn[3];   // source block of the level
     const void *tab;   // [343][K][K], input component major
+    int adj;           // adjoint: columns are source boxes, inputs via imap
+    const int32_t *imap;
+    int64_t mlo[3], mn[3];
 };
 
 constexpr int kCK = 32;  // input components per shared-memory chunk
@@ -102,6 +110,27 @@ __device__ __forceinline__ int64_t dm(uint64_t k, int s) {
     int64_t c = 0;
     for (int bit = 0; bit < 21; ++bit) c |= (int64_t)((k >> (3 * bit + s)) & 1) << bit;
     return c;
+}
+
+// Boxes of a dense block [lo, lo + n) whose coordinates have the parities of
+// class `cls` (bit a = parity on axis a): per-axis first offset and count.
+__host__ __device__ __forceinline__ void class_lattice(int cls, const int64_t *lo, const int64_t *n, int64_t *i0,
+                                                       int64_t *cnt) {
+    for (int a = 0; a < 3; ++a) {
+        const int64_t par = (cls >> a) & 1;
+        i0[a] = (par - (lo[a] & 1) + 2) & 1;
+        cnt[a] = n[a] > i0[a] ? (n[a] - i0[a] + 1) / 2 : 0;
+    }
+}
+
+// j-th box of class `cls` in a dense block: coordinates relative to lo.
+__device__ __forceinline__ void class_box(int cls, const int64_t *lo, const int64_t *n, int64_t j, int64_t &x,
+                                          int64_t &y, int64_t &z) {
+    int64_t i0[3], c[3];
+    class_lattice(cls, lo, n, i0, c);
+    x = i0[0] + 2 * (j % c[0]);
+    y = i0[1] + 2 * ((j / c[0]) % c[1]);
+    z = i0[2] + 2 * (j / (c[0] * c[1]));
 }
 
 template <class T, int RPT>
@@ -126,12 +155,21 @@ m2l_simt(M2LArgs a) {
     if (tid < 32) {
         const int64_t s = tile0 + tid;
         if (tid < a.nbox && s < ccnt) {
-            const int64_t t = a.order[cbeg + s];
-            tbox[tid] = t;
-            const uint64_t key = a.tkey[t];
-            tc[tid][0] = (int)(dm(key, 0) - a.blo[0]);
-            tc[tid][1] = (int)(dm(key, 1) - a.blo[1]);
-            tc[tid][2] = (int)(dm(key, 2) - a.blo[2]);
+            if (!a.adj) {
+                const int64_t t = a.order[cbeg + s];
+                tbox[tid] = t;
+                const uint64_t key = a.tkey[t];
+                tc[tid][0] = (int)(dm(key, 0) - a.blo[0]);
+                tc[tid][1] = (int)(dm(key, 1) - a.blo[1]);
+                tc[tid][2] = (int)(dm(key, 2) - a.blo[2]);
+            } else {
+                int64_t x, y, z;
+                class_box(cls, a.blo, a.bn, s, x, y, z);
+                tbox[tid] = (z * a.bn[1] + y) * a.bn[0] + x;
+                tc[tid][0] = (int)x;
+                tc[tid][1] = (int)y;
+                tc[tid][2] = (int)z;
+            }
         } else {
             tbox[tid] = -1;
         }
@@ -150,8 +188,17 @@ m2l_simt(M2LArgs a) {
             int64_t row = -1;
             if (slot < a.nbox && tbox[slot] >= 0) {
                 const int64_t sx = tc[slot][0] + dx, sy = tc[slot][1] + dy, sz = tc[slot][2] + dz;
-                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < a.bn[0] && sy < a.bn[1] && sz < a.bn[2])
-                    row = (((sz * a.bn[1] + sy) * a.bn[0] + sx) * B + bb) * a.ldk;
+                if (!a.adj) {
+                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < a.bn[0] && sy < a.bn[1] && sz < a.bn[2])
+                        row = (((sz * a.bn[1] + sy) * a.bn[0] + sx) * B + bb) * a.ldk;
+                } else {
+                    const int64_t wx = sx + a.blo[0] - a.mlo[0], wy = sy + a.blo[1] - a.mlo[1],
+                                  wz = sz + a.blo[2] - a.mlo[2];
+                    if (wx >= 0 && wy >= 0 && wz >= 0 && wx < a.mn[0] && wy < a.mn[1] && wz < a.mn[2]) {
+                        const int32_t m = a.imap[(wz * a.mn[1] + wy) * a.mn[0] + wx];
+                        if (m >= 0) row = ((int64_t)m * B + bb) * a.ldk;
+                    }
+                }
             }
             srow[tid] = row;
             any = row >= 0;
@@ -211,13 +258,14 @@ m2l_simt(M2LArgs a) {
 struct XArgs {
     const void *in;
     void *out;
-    int K, ldk, B, nbox, kind;      // kind 0 = M2M, 1 = L2L
-    int64_t nout;                   // M2M: parents
-    int64_t plo[3], pn[3];          // M2M: parent block
-    int64_t clo[3], cn[3];          // M2M: child block
+    int K, ldk, B, nbox, kind;      // 0 M2M, 1 L2L, 2 M2M^T, 3 L2L^T
+    int64_t nout;                   // M2M: parents; L2L^T: observer boxes
+    int64_t plo[3], pn[3];          // M2M, M2M^T: parent block
+    int64_t clo[3], cn[3];          // M2M, M2M^T: child block
     const int32_t *order;           // L2L: class-grouped observer boxes
-    int64_t cls_off[9];
+    int64_t cls_off[9];             // L2L: observer classes; M2M^T: source classes
     const int32_t *tparent;         // L2L
+    const int32_t *child;           // L2L^T: [nout][8] child box or -1
     const void *tab;                // [8][K][K] input-major
 };
 
@@ -235,7 +283,7 @@ xlate_simt(XArgs a) {
     const int K = a.K, B = a.B;
     int cls = 0;
     int64_t cbeg = 0, ccnt = a.nout;
-    if (a.kind == 1) {
+    if (a.kind == 1 || a.kind == 2) {
         cls = blockIdx.y;
         cbeg = a.cls_off[cls];
         ccnt = a.cls_off[cls + 1] - cbeg;
@@ -246,7 +294,19 @@ xlate_simt(XArgs a) {
     const Tc *tab = reinterpret_cast<const Tc *>(a.tab);
     if (tid < 32) {
         const int64_t sidx = tile0 + tid;
-        obox[tid] = (tid < a.nbox && sidx < ccnt) ? (a.kind == 1 ? (int64_t)a.order[cbeg + sidx] : sidx) : -1;
+        int64_t ob = -1;
+        if (tid < a.nbox && sidx < ccnt) {
+            if (a.kind == 1) {
+                ob = a.order[cbeg + sidx];
+            } else if (a.kind == 2) {
+                int64_t x, y, z;
+                class_box(cls, a.clo, a.cn, sidx, x, y, z);
+                ob = (z * a.cn[1] + y) * a.cn[0] + x;
+            } else {
+                ob = sidx;
+            }
+        }
+        obox[tid] = ob;
     }
     __syncthreads();
     Tc acc[RPT][4];
@@ -254,9 +314,9 @@ xlate_simt(XArgs a) {
     for (int r = 0; r < RPT; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = Tc(0);
-    const int nsteps = a.kind == 0 ? 8 : 1;
+    const int nsteps = (a.kind == 0 || a.kind == 3) ? 8 : 1;
     for (int st = 0; st < nsteps; ++st) {
-        const int op = a.kind == 0 ? st : cls;
+        const int op = (a.kind == 0 || a.kind == 3) ? st : cls;
         if (tid < 32) {
             const int slot = tid / B, bb = tid - slot * B;
             int64_t row = -1;
@@ -269,8 +329,16 @@ xlate_simt(XArgs a) {
                                   cz = 2 * pz + ((op >> 2) & 1) - a.clo[2];
                     if (cx >= 0 && cy >= 0 && cz >= 0 && cx < a.cn[0] && cy < a.cn[1] && cz < a.cn[2])
                         row = (((cz * a.cn[1] + cy) * a.cn[0] + cx) * B + bb) * a.ldk;
-                } else {
+                } else if (a.kind == 1) {
                     row = ((int64_t)a.tparent[ob] * B + bb) * a.ldk;
+                } else if (a.kind == 2) {
+                    const int64_t x = a.clo[0] + ob % a.cn[0], y = a.clo[1] + (ob / a.cn[0]) % a.cn[1],
+                                  z = a.clo[2] + ob / (a.cn[0] * a.cn[1]);
+                    const int64_t px = (x >> 1) - a.plo[0], py = (y >> 1) - a.plo[1], pz = (z >> 1) - a.plo[2];
+                    row = (((pz * a.pn[1] + py) * a.pn[0] + px) * B + bb) * a.ldk;
+                } else {
+                    const int32_t c = a.child[ob * 8 + st];
+                    if (c >= 0) row = ((int64_t)c * B + bb) * a.ldk;
                 }
             }
             srow[tid] = row;
@@ -316,7 +384,8 @@ xlate_simt(XArgs a) {
             const int k = ty * RPT + r;
             if (k >= K) continue;
             Ts *o = out + (obox[slot] * B + bb) * a.ldk + k;
-            *o = a.kind == 0 ? (Ts)acc[r][c] : (Ts)((Tc)*o + acc[r][c]);
+            const bool update = a.kind == 1 || a.kind == 2;
+            *o = update ? (Ts)((Tc)*o + acc[r][c]) : (Ts)acc[r][c];
         }
     }
 }
@@ -361,12 +430,15 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 // tensor memory.
 
 struct TcLevel {
-    const float *me;
-    float *le;
+    const float *me;      // input rows (forward ME_l, adjoint LE_l duals)
+    float *le;            // output rows (forward LE_l, adjoint ME_l duals)
     const int32_t *order;
     const uint64_t *tkey;
     int64_t blo[3], bn[3];
     int64_t cls_off[9];
+    int adj;
+    const int32_t *imap;
+    int64_t mlo[3], mn[3];
 };
 
 struct TcArgs {
@@ -464,11 +536,16 @@ m2l_tc(TcArgs a) {
     const int64_t sidx = (int64_t)tile * nbox + slot;
     int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
     if (slot < nbox && sidx < ccnt) {
-        tbox = L.order[cbeg + sidx];
-        const uint64_t key = L.tkey[tbox];
-        tc0 = dm(key, 0) - L.blo[0];
-        tc1 = dm(key, 1) - L.blo[1];
-        tc2 = dm(key, 2) - L.blo[2];
+        if (!L.adj) {
+            tbox = L.order[cbeg + sidx];
+            const uint64_t key = L.tkey[tbox];
+            tc0 = dm(key, 0) - L.blo[0];
+            tc1 = dm(key, 1) - L.blo[1];
+            tc2 = dm(key, 2) - L.blo[2];
+        } else {
+            class_box(cls, L.blo, L.bn, sidx, tc0, tc1, tc2);
+            tbox = (tc2 * L.bn[1] + tc1) * L.bn[0] + tc0;
+        }
     }
     // promotion role: warp w reads lanes 32*(w%4).. (columns of rows
     // 32*(w%4)+lane) and the column half w/4
@@ -505,8 +582,17 @@ m2l_tc(TcArgs a) {
         int64_t src = -1;
         if (tbox >= 0) {
             const int64_t sx = tc0 + dx, sy = tc1 + dy, sz = tc2 + dz;
-            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
-                src = (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldk;
+            if (!L.adj) {
+                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
+                    src = (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldk;
+            } else {
+                const int64_t wx = sx + L.blo[0] - L.mlo[0], wy = sy + L.blo[1] - L.mlo[1],
+                              wz = sz + L.blo[2] - L.mlo[2];
+                if (wx >= 0 && wy >= 0 && wz >= 0 && wx < L.mn[0] && wy < L.mn[1] && wz < L.mn[2]) {
+                    const int32_t m = L.imap[(wz * L.mn[1] + wy) * L.mn[0] + wx];
+                    if (m >= 0) src = ((int64_t)m * B + bb) * a.ldk;
+                }
+            }
         }
         if (!__syncthreads_or(src >= 0)) continue;
         const int slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
@@ -633,7 +719,14 @@ m2l_tc(TcArgs a) {
         const int oslot = r / B, obb = r - oslot * B;
         const int64_t os = (int64_t)tile * nbox + oslot;
         if (oslot < nbox && os < ccnt && !failed) {
-            const int64_t obox = L.order[cbeg + os];
+            int64_t obox;
+            if (!L.adj) {
+                obox = L.order[cbeg + os];
+            } else {
+                int64_t ox, oy, oz;
+                class_box(cls, L.blo, L.bn, os, ox, oy, oz);
+                obox = (oz * L.bn[1] + oy) * L.bn[0] + ox;
+            }
             float *dst = L.le + (obox * B + obb) * a.ldk + ph * nsum;
 #pragma unroll
             for (int j = 0; j < NS; ++j)
@@ -650,50 +743,58 @@ m2l_tc(TcArgs a) {
 gf_status m2l_tc_prepare(gf_plan_s *plan) {
     FmmPlan *F = plan->fmm;
     if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
-    std::vector<TcLevel> h(F->L + 1);
-    for (int l = 2; l <= F->L; ++l) {
-        const FmmLevel &lv = F->lev[l];
-        TcLevel &t = h[l];
-        t.me = (const float *)lv.me;
-        t.le = (float *)lv.le;
-        t.order = lv.m2l_order;
-        t.tkey = lv.tkey;
-        for (int d = 0; d < 3; ++d) {
-            t.blo[d] = lv.slo[d];
-            t.bn[d] = lv.sn[d];
+    for (int adj = 0; adj < 2; ++adj) {
+        std::vector<TcLevel> h(F->L + 1);
+        memset(h.data(), 0, h.size() * sizeof(TcLevel));
+        for (int l = 2; l <= F->L; ++l) {
+            const FmmLevel &lv = F->lev[l];
+            TcLevel &t = h[l];
+            t.me = (const float *)(adj ? lv.le : lv.me);
+            t.le = (float *)(adj ? lv.me : lv.le);
+            t.order = lv.m2l_order;
+            t.tkey = lv.tkey;
+            t.adj = adj;
+            t.imap = F->imap[l];
+            for (int d = 0; d < 3; ++d) {
+                t.blo[d] = lv.slo[d];
+                t.bn[d] = lv.sn[d];
+                t.mlo[d] = F->mlo[l][d];
+                t.mn[d] = F->mn[l][d];
+            }
+            for (int c = 0; c <= 8; ++c) t.cls_off[c] = adj ? F->scls_off[l][c] : lv.cls_off[c];
         }
-        for (int c = 0; c <= 8; ++c) t.cls_off[c] = lv.cls_off[c];
+        std::vector<unsigned char> &hb = adj ? F->tc_levels_adj_host : F->tc_levels_host;
+        void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
+        hb.assign(reinterpret_cast<unsigned char *>(h.data()), reinterpret_cast<unsigned char *>(h.data() + h.size()));
+        GF_TRY(plan->arena.alloc(&dev, hb.size()));
+        GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
     }
-    F->tc_levels_host.assign(reinterpret_cast<unsigned char *>(h.data()),
-                             reinterpret_cast<unsigned char *>(h.data() + h.size()));
-    GF_TRY(plan->arena.alloc(&F->tc_levels, F->tc_levels_host.size()));
-    GF_CUDA(cudaMemcpyAsync(F->tc_levels, F->tc_levels_host.data(), F->tc_levels_host.size(),
-                            cudaMemcpyHostToDevice, plan->arena.stream));
     return GF_OK;
 }
 
 namespace {
 
-gf_status m2l_run_tc(gf_plan_s *plan, int B, cudaStream_t st) {
+gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     const Tables *T = F->tab;
     const int Npad = T->tc_npad;
     TcArgs a;
-    a.lv = reinterpret_cast<const TcLevel *>(F->tc_levels);
+    a.lv = reinterpret_cast<const TcLevel *>(adj ? F->tc_levels_adj : F->tc_levels);
     a.lmin = 2;
     a.K = F->K;
     a.ldk = F->KS;
     a.B = B;
     a.Npad = Npad;
     a.nck = T->tc_nck;
-    a.img = T->m2l_tc;
+    a.img = adj ? T->am2l_tc : T->m2l_tc;
     a.status = plan->d_status;
     const int nbox = 128 / B;
     int tiles = 0, e = 0;
     for (int l = 2; l <= F->L; ++l)
         for (int c = 0; c < 8; ++c, ++e) {
             a.tile_begin[e] = tiles;
-            const int64_t cnt = F->lev[l].cls_off[c + 1] - F->lev[l].cls_off[c];
+            const int64_t *off = adj ? F->scls_off[l] : F->lev[l].cls_off;
+            const int64_t cnt = (adj || F->lev[l].nt > 0) ? off[c + 1] - off[c] : 0;
             tiles += (int)((cnt + nbox - 1) / nbox);
         }
     a.tile_begin[e] = tiles;
@@ -722,26 +823,33 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, cudaStream_t st) {
 }  // namespace
 
 template <class T>
-gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st) {
+gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     const FmmLevel &lv = F->lev[level];
     M2LArgs a;
-    a.me = lv.me;
-    a.le = lv.le;
+    a.me = adj ? lv.le : lv.me;
+    a.le = adj ? lv.me : lv.le;
     a.K = F->K;
     a.ldk = F->KS;
     a.B = B;
     a.nbox = std::max(1, 32 / B);
     a.order = lv.m2l_order;
+    a.adj = adj ? 1 : 0;
+    a.imap = F->imap[level];
     int64_t maxc = 0;
-    for (int c = 0; c <= 8; ++c) a.cls_off[c] = lv.cls_off[c];
-    for (int c = 0; c < 8; ++c) maxc = std::max<int64_t>(maxc, lv.cls_off[c + 1] - lv.cls_off[c]);
+    for (int c = 0; c <= 8; ++c) a.cls_off[c] = adj ? F->scls_off[level][c] : lv.cls_off[c];
+    for (int c = 0; c < 8; ++c) maxc = std::max<int64_t>(maxc, a.cls_off[c + 1] - a.cls_off[c]);
     a.tkey = lv.tkey;
     for (int d = 0; d < 3; ++d) {
         a.blo[d] = lv.slo[d];
         a.bn[d] = lv.sn[d];
+        a.mlo[d] = F->mlo[level][d];
+        a.mn[d] = F->mn[level][d];
     }
-    a.tab = sizeof(T) == 8 ? (const void *)F->tab->m2l_d : (const void *)F->tab->m2l_f;
+    if (adj)
+        a.tab = sizeof(T) == 8 ? (const void *)F->tab->am2l_d : (const void *)F->tab->am2l_f;
+    else
+        a.tab = sizeof(T) == 8 ? (const void *)F->tab->m2l_d : (const void *)F->tab->m2l_f;
     if (B > 32) {
         set_error("M2L supports at most 32 batch members");
         return GF_ERR_UNSUPPORTED;
@@ -777,7 +885,38 @@ gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_
     a.kind = kind;
     int64_t tiles;
     int ny = 1;
-    if (kind == 0) {   // M2M into `level` from level + 1
+    a.child = nullptr;
+    if (kind == 2) {   // M2M^T into `level` (children) from level - 1
+        const FmmLevel &ch = F->lev[level], &pa = F->lev[level - 1];
+        a.in = pa.me;
+        a.out = ch.me;
+        a.nout = ch.ns;
+        for (int d = 0; d < 3; ++d) {
+            a.plo[d] = pa.slo[d];
+            a.pn[d] = pa.sn[d];
+            a.clo[d] = ch.slo[d];
+            a.cn[d] = ch.sn[d];
+        }
+        for (int c = 0; c <= 8; ++c) a.cls_off[c] = F->scls_off[level][c];
+        a.order = nullptr;
+        a.tparent = nullptr;
+        a.tab = sizeof(Tc) == 8 ? (const void *)F->tab->am2m_d : (const void *)F->tab->am2m_f;
+        int64_t maxc = 0;
+        for (int c = 0; c < 8; ++c) maxc = std::max<int64_t>(maxc, a.cls_off[c + 1] - a.cls_off[c]);
+        tiles = (maxc + a.nbox - 1) / a.nbox;
+        ny = 8;
+    } else if (kind == 3) {   // L2L^T into `level` (parents) from level + 1
+        const FmmLevel &lv = F->lev[level], &ch = F->lev[level + 1];
+        if (lv.nt == 0) return GF_OK;
+        a.in = ch.le;
+        a.out = lv.le;
+        a.nout = lv.nt;
+        a.child = F->child[level];
+        a.order = nullptr;
+        a.tparent = nullptr;
+        a.tab = sizeof(Tc) == 8 ? (const void *)F->tab->al2l_d : (const void *)F->tab->al2l_f;
+        tiles = (lv.nt + a.nbox - 1) / a.nbox;
+    } else if (kind == 0) {   // M2M into `level` from level + 1
         const FmmLevel &pa = F->lev[level], &ch = F->lev[level + 1];
         a.in = ch.me;
         a.out = pa.me;
@@ -830,19 +969,20 @@ template gf_status translate_run<float, double>(gf_plan_s *, int, int, int, cuda
 template gf_status translate_run<double, double>(gf_plan_s *, int, int, int, cudaStream_t);
 
 template <class T>
-gf_status m2l_run(gf_plan_s *plan, int B, cudaStream_t st) {
+gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
-    const bool tc = sizeof(T) == 4 && F->tab->m2l_tc && F->tc_levels && !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) &&
-                    B <= 128 && tc_smem_bytes(F->tab->tc_npad) <= 227 * 1024;
-    if (tc) return m2l_run_tc(plan, B, st);
+    const bool tc = sizeof(T) == 4 && F->tab->m2l_tc && (adj ? F->tc_levels_adj : F->tc_levels) &&
+                    !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
+                    tc_smem_bytes(F->tab->tc_npad) <= 227 * 1024;
+    if (tc) return m2l_run_tc(plan, B, adj, st);
     for (int l = 2; l <= F->L; ++l) {
-        if (F->lev[l].nt == 0) continue;
-        GF_TRY(m2l_level<T>(plan, l, B, st));
+        if (F->lev[l].nt == 0 && !adj) continue;   // the adjoint writes every source box
+        GF_TRY(m2l_level<T>(plan, l, B, adj, st));
     }
     return GF_OK;
 }
 
-template gf_status m2l_run<float>(gf_plan_s *, int, cudaStream_t);
-template gf_status m2l_run<double>(gf_plan_s *, int, cudaStream_t);
+template gf_status m2l_run<float>(gf_plan_s *, int, bool, cudaStream_t);
+template gf_status m2l_run<double>(gf_plan_s *, int, bool, cudaStream_t);
 
 }  // namespace gf

@@ -13,13 +13,18 @@ gf_status m2l_prepare_tables(Tables *T, cudaStream_t st);
 // for every observer box t of every level (overwrites each LE_l).  Mixed
 // precision runs on the tensor cores (tcgen05, 3xTF32) unless the plan asks
 // for the SIMT kernel; FP64 runs on the SIMT kernel.
+// adj: the transpose, MEdual_l[s] = sum_{o in IL(class of s)} T_{-o}^T LEdual_l[s + o]
+// over every source box s (observer boxes found through the level's map).
 template <class T>
-gf_status m2l_run(gf_plan_s *plan, int B, cudaStream_t st);
+gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st);
 template <class T>
-gf_status m2l_level(gf_plan_s *plan, int level, int B, cudaStream_t st);
+gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st);
 
-// Batched M2M (kind 0: into `level` from level + 1) or L2L (kind 1: into
-// `level` from level - 1) on the SIMT cores; Ts = storage, Tc = arithmetic.
+// Batched translations on the SIMT cores (Ts = storage, Tc = arithmetic):
+//   kind 0  M2M into `level` from level + 1 (store)
+//   kind 1  L2L into `level` from level - 1 (update)
+//   kind 2  M2M^T into `level` from level - 1 (update), over source boxes
+//   kind 3  L2L^T into `level` from level + 1 (store), over observer boxes
 template <class Ts, class Tc>
 gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st);
 

@@ -267,3 +267,15 @@ def test_linearity_and_mirror_symmetry():
     sc = np.abs(g1).max()
     assert np.allclose(g2[:, 0], -g1[:, 0], atol=1e-13 * sc)
     assert np.allclose(g2[:, 1:], g1[:, 1:], atol=1e-13 * sc)
+
+
+def test_adjoint_subset_matches_full_transpose():
+    """The sampled transpose sum returns exactly the full transpose sum's
+    values at the sampled voxels (same arithmetic, same order)."""
+    wk = wl.random_small(41, n=(5, 4, 3), npts=2, n_obs=19, B=1)
+    rng = np.random.default_rng(8)
+    y = rng.normal(size=(2, wk.n_obs, 3))
+    full = direct.adjoint(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.obs, y, 1.0, ncomp=3)
+    vox = np.array([0, 7, 33, 59])
+    sub = direct.adjoint_subset(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.obs, y, 1.0, vox, ncomp=3)
+    assert np.array_equal(sub, full.reshape(2, -1)[:, vox])
