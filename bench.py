@@ -68,6 +68,12 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="volume", choices=["volume", "serving"],
+                    help="volume: one large forward per step; serving: a stream of uneven requests")
+    ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
+    ap.add_argument("--slots", type=int, default=4, help="serving: requests on the device at once")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="serving: Poisson arrival rate in requests/s (0: 70%% of the saturated rate)")
     return ap.parse_args()
 
 
@@ -385,6 +391,129 @@ def bench_gf(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving
+def bench_serving(args, rank, world):
+    """Serving stream: `--requests` forward solves, grid side n log-uniform
+    in [32, 256], 256^2 stations, random-field densities; geometry id = n.
+    Warm-up passes submit the whole stream at once (plans are built and stay
+    resident); timed passes do the same and give solves/s; a last pass
+    submits at Poisson arrival times and gives p50/p99 of completion minus
+    arrival.  Every request copies its densities from pinned host memory
+    and its g_z back, inside the measured latency."""
+    import torch
+
+    import paper_1107_5951_gb300 as pkg
+    from oracle import direct
+    from paper_1107_5951_gb300 import workloads as wl
+
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    reqs = wl.serving_stream(args.requests, stations=256)
+    nmax = max(r["grid"].n[0] for r in reqs)
+    field = wl.periodic_grf(256, reqs[0]["grid"].h[0], 2000.0, 150.0, 4, dtype=np.float32)
+    sizes = [int(np.prod(r["grid"].n)) for r in reqs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    rho_pool = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
+    pool_np = rho_pool.numpy()
+    for i, r in enumerate(reqs):
+        pool_np[offs[i]:offs[i + 1]] = wl.serving_density(r, field).ravel()
+    M = reqs[0]["obs"].shape[0]
+    gz_pool = torch.empty((len(reqs), M), dtype=torch.float64, pin_memory=True)
+    srv = pkg.Server(slots=args.slots, precision=args.precision, p=args.p, use_graphs=True,
+                     device=local_rank)
+    xi, w = wl.gauss_rule(1)
+    for r in reqs:
+        g = r["grid"]
+        srv.register(g.n[0], g.n, g.origin, g.h, xi, w, r["obs"])
+    units = float(sum(sizes)) * M
+
+    def rho_of(i):
+        n = reqs[i]["grid"].n[0]
+        return rho_pool[offs[i]:offs[i + 1]].view(n, n, n)
+
+    def burst():
+        t0 = time.perf_counter()
+        tickets = [srv.submit(r["grid"].n[0], rho_of(i), gz=gz_pool[i]) for i, r in enumerate(reqs)]
+        lat = [srv.wait(t)[2] for t in tickets]
+        return time.perf_counter() - t0, lat
+
+    cold_s, cold_lat = burst()          # first pass builds every plan
+    st_cold = srv.stats()
+    for _ in range(max(0, args.warmup - 1)):
+        burst()
+    clocks = ClockSampler(local_rank, not args.no_clocks)
+    launches0 = pkg.gf_launch_count()
+    pass_s = []
+    for _ in range(args.steps):
+        dt, _ = burst()
+        pass_s.append(dt)
+    launches = pkg.gf_launch_count() - launches0
+    clk = clocks.stop()
+    sat_rate = len(reqs) * args.steps / sum(pass_s)
+    # open loop at Poisson arrival times
+    rate = args.rate if args.rate > 0 else 0.7 * sat_rate
+    arr = np.array([r["arrival_s"] for r in reqs])
+    arr = arr * (100.0 / rate)          # the stream's arrivals are drawn at 100 requests/s
+    t0 = time.perf_counter()
+    tickets = []
+    for i, r in enumerate(reqs):
+        dt = arr[i] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(r["grid"].n[0], rho_of(i), gz=gz_pool[i]))
+    lat = np.array([srv.wait(t)[2] for t in tickets])
+    open_s = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # accuracy of a few requests on a station sample, against the FP64 oracle
+    errs = []
+    if rank == 0 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(11)
+        pick = sorted(rng.choice(len(reqs), 4, replace=False))
+        t_cpu, pairs = 0.0, 0
+        for i in pick:
+            r = reqs[i]
+            g = r["grid"]
+            idx = np.sort(rng.choice(M, 64, replace=False))
+            t1 = time.perf_counter()
+            want = direct.forward(g.n, g.origin, g.h, xi, w, rho_of(i).numpy().astype(np.float64),
+                                  r["obs"][idx], wl.G_PAPER)[:, 2]
+            t_cpu += time.perf_counter() - t1
+            pairs += sizes[i] * len(idx)
+            got = gz_pool[i].numpy()[idx]
+            errs.append(float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+        cpu = {"value": pairs / t_cpu, "unit": "interactions/s", "cores": direct.max_threads(),
+               "kind": "oracle", "sample": "64 stations of 4 requests (sides %s), %.1f s"
+               % ([reqs[i]["grid"].n[0] for i in pick], t_cpu)}
+    else:
+        cpu = None
+    if rank != 0:
+        return
+    h2d = int(sum(sizes) * 4)
+    d2h = int(len(reqs) * M * 8)
+    line = {"metric": "serving solves/s (512-request stream, saturated)", "value": sat_rate * world,
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(pass_s) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "serving_stream_%d_req_n32-%d_256^2_stations" % (len(reqs), nmax),
+                       "precision": args.precision, "p": args.p, "slots": args.slots,
+                       "step": "one pass of the whole stream, submitted at once",
+                       "l2_flush": "inputs larger than L2 (%.1f GB of densities per pass)" % (h2d / 1e9)},
+            "interactions_per_s": units * sat_rate * world / len(reqs),
+            "latency_open_loop": {"rate_hz": rate, "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                                  "max_ms": float(lat.max()), "achieved_hz": len(reqs) / open_s},
+            "cold_pass": {"seconds": cold_s, "plans_created": int(st_cold["plans_created"]),
+                          "solves_per_s": len(reqs) / cold_s},
+            "server": {k: st[k] for k in ("completed", "failed", "plans_created", "plans_evicted",
+                                          "graph_launches", "resident_bytes", "mem_budget")},
+            "rel_err_vs_oracle_sample": errs, "roofline": None, "cpu_baseline": cpu,
+            "e2e": {"value": sat_rate * world, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -396,7 +525,10 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     try:
-        bench_gf(args, rank, world)
+        if args.workload == "serving":
+            bench_serving(args, rank, world)
+        else:
+            bench_gf(args, rank, world)
     finally:
         if world > 1:
             import torch

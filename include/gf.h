@@ -172,6 +172,70 @@ gf_status gf_direct_forward_static(const gf_grid *grid, const gf_quad *quad,
                                    int32_t B, double G, double *g_dev,
                                    double *gz_dev, void *stream);
 
+/*
+ * Serving: continuous batching of forward solves (an inversion issuing
+ * solves on grids of uneven size).  A server owns `max_slots` CUDA streams
+ * and a cache of resident plans -- octree, expansion workspaces, input and
+ * output buffers, and the forward captured once in a CUDA graph -- keyed by
+ * the caller's geometry id.  A background thread admits queued requests as
+ * soon as a slot is free and the device memory the request's plan needs
+ * (its gf_plan_bytes estimate) fits in the budget, evicting idle cached
+ * plans least-recently-used first; requests on different slots run
+ * concurrently on the device.  Kernels accumulate without atomics, so a
+ * request's result is the same alone and in any mix.
+ */
+typedef struct gf_server_s *gf_server_t;
+
+typedef struct {
+    int32_t max_slots;     /* requests on the device at once, 1..64         */
+    int32_t precision;     /* GF_PREC_FP64 or GF_PREC_MIXED (FMM mode)       */
+    int32_t p;             /* expansion degree                               */
+    int32_t leaf_vox;      /* 0 = library default                            */
+    int32_t use_graphs;    /* replay each plan's forward as a CUDA graph     */
+    int32_t device;        /* CUDA device of the server                      */
+    size_t mem_budget;     /* device bytes for resident plans; 0 = 70% of    */
+                           /* the free memory at creation                    */
+    double G;              /* 0 = 6.67428e-11                                */
+} gf_server_options;
+
+/* One forward solve.  Host arrays must stay valid until the request has
+ * completed (page-locked host memory makes the copies asynchronous).
+ * Requests with the same geometry_id must have the same grid, quadrature
+ * and observers: the server reuses the resident plan built for the first. */
+typedef struct {
+    gf_grid grid;
+    gf_quad quad;
+    const double *obs_host;   /* [M][3]                                     */
+    int64_t M;
+    uint64_t geometry_id;
+    const void *rho_host;     /* [nz][ny][nx] densities                     */
+    int32_t rho_dtype;        /* GF_DTYPE_F64 or GF_DTYPE_F32               */
+    int32_t on_device;        /* 1: rho_host/gz_host/g_host are device      */
+                              /* pointers instead of host pointers          */
+    double *gz_host;          /* [M] output, or NULL                        */
+    double *g_host;           /* [M][3] output, or NULL                     */
+} gf_request;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t plans_created, plans_evicted, graph_launches;
+    size_t resident_bytes, mem_budget;
+    double p50_ms, p99_ms, mean_ms;   /* latency: submit -> result on host */
+    double busy_s;                    /* first submit -> last completion   */
+} gf_server_stats;
+
+gf_status gf_server_create(const gf_server_options *opt, gf_server_t *server);
+/* Queue a request (returns at once); *ticket identifies it. */
+gf_status gf_server_submit(gf_server_t server, const gf_request *req,
+                           int64_t *ticket);
+/* Wait for a request (timeout_ms < 0: no limit); latency in ms. Returns
+ * GF_ERR_TIMEOUT if it has not completed in time, or the request's error. */
+gf_status gf_server_wait(gf_server_t server, int64_t ticket, double timeout_ms,
+                         double *latency_ms);
+gf_status gf_server_stats_get(gf_server_t server, gf_server_stats *stats);
+/* Wait for all requests, then release every resident plan and stream. */
+gf_status gf_server_destroy(gf_server_t server);
+
 /* Release a plan and everything it owns (waits for its device work). */
 gf_status gf_plan_destroy(gf_plan_t plan);
 

@@ -69,6 +69,15 @@ void DeviceArena::release() {
     bytes = 0;
 }
 
+// Free a plan whose device work has all completed (no device-wide wait).
+void plan_release(gf_plan_s *plan) {
+    fmm_destroy(plan);
+    plan->arena.release();
+    for (int i = 0; i <= GF_NUM_STAGES; ++i)
+        if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    delete plan;
+}
+
 // The plan's quadrature rule lives in device memory right after the status
 // word; kernels read it through this pointer.
 const QuadRule *quad_device(gf_plan_s *plan) {
@@ -333,11 +342,7 @@ gf_status gf_plan_destroy(gf_plan_t plan) {
     cudaGetDevice(&cur);
     if (cur != dev) cudaSetDevice(dev);
     cudaDeviceSynchronize();
-    fmm_destroy(plan);
-    plan->arena.release();
-    for (int i = 0; i <= GF_NUM_STAGES; ++i)
-        if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
-    delete plan;
+    plan_release(plan);
     if (cur != dev) cudaSetDevice(cur);
     return GF_OK;
 }

@@ -120,6 +120,8 @@ gf_status fmm_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
 gf_status fmm_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B,
                       double *grad, cudaStream_t st);
 void fmm_destroy(gf_plan_s *plan);
+// Free a plan whose device work has all completed (no device-wide wait).
+void plan_release(gf_plan_s *plan);
 gf_status fmm_info(const gf_plan_s *plan, gf_plan_info *info);
 gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *keys,
                           uint64_t *box_keys, int64_t *ilist, int64_t *near_);

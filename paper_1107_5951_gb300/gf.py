@@ -64,6 +64,26 @@ class gf_plan_info(ctypes.Structure):
                 ("m2l_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 
+class gf_server_options(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("precision", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("leaf_vox", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("mem_budget", ctypes.c_size_t), ("G", ctypes.c_double)]
+
+
+class gf_request(ctypes.Structure):
+    _fields_ = [("grid", gf_grid), ("quad", gf_quad), ("obs_host", ctypes.c_void_p), ("M", ctypes.c_int64),
+                ("geometry_id", ctypes.c_uint64), ("rho_host", ctypes.c_void_p), ("rho_dtype", ctypes.c_int32),
+                ("on_device", ctypes.c_int32), ("gz_host", ctypes.c_void_p), ("g_host", ctypes.c_void_p)]
+
+
+class gf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("plans_created", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("resident_bytes", ctypes.c_size_t),
+                ("mem_budget", ctypes.c_size_t), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("busy_s", ctypes.c_double)]
+
+
 GF_NUM_STAGES = 7
 STAGE_NAMES = ("densities", "p2m", "m2m", "m2l", "l2l", "eval", "forward")
 
@@ -104,9 +124,15 @@ def load(build_if_missing: bool = True):
         lib.gf_direct_forward_static.restype = ctypes.c_int
         lib.gf_plan_set_timing.argtypes = [_vp, i32]
         lib.gf_plan_stage_times.argtypes = [_vp, P(ctypes.c_double)]
+        lib.gf_server_create.argtypes = [P(gf_server_options), P(_vp)]
+        lib.gf_server_submit.argtypes = [_vp, P(gf_request), P(i64)]
+        lib.gf_server_wait.argtypes = [_vp, i64, ctypes.c_double, P(ctypes.c_double)]
+        lib.gf_server_stats_get.argtypes = [_vp, P(gf_server_stats)]
+        lib.gf_server_destroy.argtypes = [_vp]
         for name in ("gf_plan_create", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
                      "gf_plan_bytes", "gf_plan_get_info", "gf_plan_export_tree", "gf_plan_set_timing",
-                     "gf_plan_stage_times"):
+                     "gf_plan_stage_times", "gf_server_create", "gf_server_submit", "gf_server_wait",
+                     "gf_server_stats_get", "gf_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         lib.gf_last_error.argtypes = []
         lib.gf_last_error.restype = ctypes.c_char_p
@@ -197,6 +223,34 @@ def gf_version() -> int:
 
 def gf_launch_count() -> int:
     return int(load().gf_launch_count())
+
+
+def gf_server_create(opt: gf_server_options) -> int:
+    h = _vp()
+    _check(load().gf_server_create(ctypes.byref(opt), ctypes.byref(h)))
+    return h.value
+
+
+def gf_server_submit(server: int, req: gf_request) -> int:
+    t = ctypes.c_int64()
+    _check(load().gf_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def gf_server_wait(server: int, ticket: int, timeout_ms: float = -1.0) -> float:
+    lat = ctypes.c_double()
+    _check(load().gf_server_wait(server, int(ticket), float(timeout_ms), ctypes.byref(lat)))
+    return lat.value
+
+
+def gf_server_stats_get(server: int) -> gf_server_stats:
+    st = gf_server_stats()
+    _check(load().gf_server_stats_get(server, ctypes.byref(st)))
+    return st
+
+
+def gf_server_destroy(server: int):
+    _check(load().gf_server_destroy(server))
 
 
 # ------------------------------------------------------------ marshalling
@@ -357,3 +411,105 @@ class Plan:
 def plan_bytes(shape, origin, h, xi, w, M, **opts) -> int:
     q = _Quad(xi, w)
     return gf_plan_bytes(make_grid(shape, origin, h), q.c, int(M), make_options(**opts))
+
+
+class Server:
+    """Continuous-batching forward server (``gf_server_*``): requests for
+    any registered geometry are queued and run concurrently on ``slots``
+    CUDA streams, each geometry's plan kept resident (and its forward
+    replayed as a CUDA graph) until evicted under ``mem_budget``."""
+
+    def __init__(self, slots=4, precision="mixed", p=12, leaf_vox=0, use_graphs=True, device=0,
+                 mem_budget=0, G=0.0):
+        o = gf_server_options()
+        o.max_slots = int(slots)
+        o.precision = {"fp64": GF_PREC_FP64, "mixed": GF_PREC_MIXED}[precision]
+        o.p = int(p)
+        o.leaf_vox = int(leaf_vox)
+        o.use_graphs = 1 if use_graphs else 0
+        o.device = int(device)
+        o.mem_budget = int(mem_budget)
+        o.G = float(G)
+        self._geoms = {}
+        self._pending = {}
+        self.handle = None
+        self.handle = gf_server_create(o)
+
+    def register(self, gid, shape, origin, h, xi, w, obs):
+        """Declare geometry `gid`: grid, quadrature rule, observers (M, 3)."""
+        obs = np.ascontiguousarray(obs, dtype=np.float64).reshape(-1, 3)
+        self._geoms[int(gid)] = (make_grid(shape, origin, h), _Quad(xi, w), obs,
+                                 tuple(int(v) for v in shape))
+
+    def submit(self, gid, rho, gz=None, g=None, want_gz=True, want_g=False) -> int:
+        """Queue a forward of densities `rho` (nz, ny, nx) on geometry `gid`.
+        rho and the outputs are host arrays (numpy, or CPU tensors; pinned
+        ones make the copies asynchronous) or all CUDA tensors.  Returns a
+        ticket for :meth:`wait`."""
+        import torch
+        grid, quad, obs, shape = self._geoms[int(gid)]
+        M = obs.shape[0]
+        if isinstance(rho, torch.Tensor):
+            on_device = rho.is_cuda
+            pin = (not on_device) and rho.is_pinned()
+            rho = rho.contiguous()
+            rdt = {torch.float64: GF_DTYPE_F64, torch.float32: GF_DTYPE_F32}[rho.dtype]
+            if want_gz and gz is None:
+                gz = torch.empty(M, dtype=torch.float64, device=rho.device, pin_memory=pin)
+            if want_g and g is None:
+                g = torch.empty((M, 3), dtype=torch.float64, device=rho.device, pin_memory=pin)
+            ptr = lambda a: a.data_ptr()  # noqa: E731
+        else:
+            on_device = False
+            rho = np.ascontiguousarray(rho)
+            rdt = {np.dtype(np.float64): GF_DTYPE_F64, np.dtype(np.float32): GF_DTYPE_F32}[rho.dtype]
+            if want_gz and gz is None:
+                gz = np.empty(M, dtype=np.float64)
+            if want_g and g is None:
+                g = np.empty((M, 3), dtype=np.float64)
+            ptr = lambda a: a.ctypes.data  # noqa: E731
+        if tuple(rho.shape) != (shape[2], shape[1], shape[0]):
+            raise ValueError("rho must have shape (nz, ny, nx) = %r" % ((shape[2], shape[1], shape[0]),))
+        r = gf_request()
+        r.grid = grid
+        r.quad = quad.c
+        r.obs_host = obs.ctypes.data
+        r.M = M
+        r.geometry_id = int(gid)
+        r.rho_host = ptr(rho)
+        r.rho_dtype = rdt
+        r.on_device = 1 if on_device else 0
+        r.gz_host = ptr(gz) if gz is not None else None
+        r.g_host = ptr(g) if g is not None else None
+        t = gf_server_submit(self.handle, r)
+        self._pending[t] = (gz, g, rho)
+        return t
+
+    def wait(self, ticket, timeout_ms=-1.0):
+        """Wait for a request; returns (gz, g, latency_ms).  Each ticket is
+        waited for once."""
+        lat = gf_server_wait(self.handle, ticket, timeout_ms)
+        gz, g, _ = self._pending.pop(ticket)
+        return gz, g, lat
+
+    def stats(self) -> dict:
+        st = gf_server_stats_get(self.handle)
+        return {k: getattr(st, k) for k, _ in gf_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            gf_server_destroy(self.handle)
+            self.handle = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -236,9 +236,19 @@ def serving_stream(n_requests: int = 512, seed: int = 4, nmin: int = 32, nmax: i
     return reqs
 
 
-def serving_density(req, dtype=np.float32) -> np.ndarray:
+def serving_density(req, field=None, dtype=np.float32) -> np.ndarray:
+    """Densities of one serving request: its own periodic random field
+    (field None), or an n^3 window of a shared periodic field at an offset
+    drawn from the request's seed (indices wrapped on the torus).  A window
+    of a stationary field has the same covariance, so both are draws of the
+    same distribution; the window is far cheaper for large streams."""
     n = req["grid"].n[0]
-    return periodic_grf(n, req["grid"].h[0], 2000.0, 150.0, req["seed"], dtype=dtype)
+    if field is None:
+        return periodic_grf(n, req["grid"].h[0], 2000.0, 150.0, req["seed"], dtype=dtype)
+    m = field.shape[0]
+    off = np.random.Generator(np.random.PCG64(req["seed"])).integers(0, m, size=3)
+    idx = [(o + np.arange(n)) % m for o in off]
+    return np.ascontiguousarray(field[np.ix_(idx[0], idx[1], idx[2])], dtype=dtype)
 
 
 def adjoint_batch(n: int = 128, h: float = 250.0, stations: int = 256, batch: int = 16,
