@@ -56,8 +56,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
-    ap.add_argument("--n", type=int, default=128, help="voxels per axis")
-    ap.add_argument("--stations", type=int, default=512)
+    ap.add_argument("--n", type=int, default=0, help="voxels per axis (0: the workload's own)")
+    ap.add_argument("--stations", type=int, default=0, help="stations per axis (0: the workload's own)")
     ap.add_argument("--mode", default="auto", choices=["auto", "fmm", "direct"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--p", type=int, default=12)
@@ -68,8 +68,9 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "serving"],
-                    help="volume: one large forward per step; serving: a stream of uneven requests")
+    ap.add_argument("--workload", default="volume", choices=["volume", "scale", "serving"],
+                    help="volume: 128^3 random field, stations + voxel centres; scale: 464^3 layered "
+                         "model, 1024^2 stations; serving: a stream of uneven requests")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the device at once")
     ap.add_argument("--rate", type=float, default=0.0,
@@ -133,12 +134,18 @@ class ClockSampler:
 # ------------------------------------------------------------------ workload
 def make_workload(args):
     from paper_1107_5951_gb300 import workloads as wl
-    return wl.grf_volume(n=args.n, stations=args.stations)
+    if args.workload == "scale":
+        return wl.layered_scale(n=args.n or 464, stations=args.stations or 1024)
+    return wl.grf_volume(n=args.n or 128, stations=args.stations or 512)
+
+
+ORACLE_SAMPLE_PAIRS = 2.0e10     # bounds the oracle's sample to ~15 s on 16 cores
 
 
 def oracle_sample(wk, args, seed=17):
     rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(wk.n_obs, size=min(args.sample_obs, wk.n_obs), replace=False))
+    cap = max(16, int(ORACLE_SAMPLE_PAIRS / wk.n_sources))
+    idx = np.sort(rng.choice(wk.n_obs, size=min(args.sample_obs, cap, wk.n_obs), replace=False))
     return idx
 
 

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "fmm_math.cuh"
@@ -279,6 +280,39 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) {
     return rsqrt(x);
 }
 
+// Packed pairs of FP32 values (f32x2 arithmetic of sm_100 and later: one
+// instruction does two FP32 operations, halving the issue slots of the
+// near-field loop).
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// 1/sqrt(x) on the special-function unit, subnormal inputs read as zero
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <class T>
 __device__ __forceinline__ void two_sum(T &hi, T &lo, T x) {
     const T s = hi + x;
@@ -395,6 +429,10 @@ eval_kernel(EvalArgs a) {
                 T px[kTPL], py[kTPL], pz[kTPL];
 #pragma unroll
                 for (int u = 0; u < kTPL; ++u) px[u] = py[u] = pz[u] = T(0);
+                constexpr bool kPacked = std::is_same<T, float>::value;
+                uint64_t qx[kTPL], qy[kTPL], qz[kTPL];   // packed partial sums (FP32)
+#pragma unroll
+                for (int u = 0; u < kTPL; ++u) qx[u] = qy[u] = qz[u] = 0;
                 for (int c0 = 0; c0 < nsrc; c0 += kEvalChunk) {
                     const int cnt = min(kEvalChunk, nsrc - c0);
                     __syncwarp();
@@ -417,7 +455,54 @@ eval_kernel(EvalArgs a) {
                         e.y += oy;
                         e.z += oz;
                         e.w *= ms[v];
-                        src[s] = e;
+                        if constexpr (kPacked) {
+                            // pairs of sources as {x0,x1, y0,y1, z0,z1, w0,w1}
+                            T *rec = wsh + (s >> 1) * 8 + (s & 1);
+                            rec[0] = e.x;
+                            rec[2] = e.y;
+                            rec[4] = e.z;
+                            rec[6] = e.w;
+                        } else {
+                            src[s] = e;
+                        }
+                    }
+                    if constexpr (kPacked) {
+                        // an odd chunk ends with a massless source far away
+                        if ((cnt & 1) && lane == 0) {
+                            T *rec = wsh + (cnt >> 1) * 8 + 1;
+                            rec[0] = rec[2] = rec[4] = T(1.0e4);
+                            rec[6] = T(0);
+                        }
+                        __syncwarp();
+                        uint64_t TX[kTPL], TY[kTPL], TZ[kTPL];
+#pragma unroll
+                        for (int u = 0; u < kTPL; ++u) {
+                            TX[u] = pk2(tx[u], tx[u]);
+                            TY[u] = pk2(ty[u], ty[u]);
+                            TZ[u] = pk2(tz[u], tz[u]);
+                        }
+                        const int npair = (cnt + 1) >> 1;
+#pragma unroll 2
+                        for (int q = 0; q < npair; ++q) {
+                            const ulonglong2 xy = *reinterpret_cast<const ulonglong2 *>(wsh + q * 8);
+                            const ulonglong2 zw = *reinterpret_cast<const ulonglong2 *>(wsh + q * 8 + 4);
+#pragma unroll
+                            for (int u = 0; u < kTPL; ++u) {
+                                const uint64_t DX = sub2(TX[u], xy.x), DY = sub2(TY[u], xy.y),
+                                               DZ = sub2(TZ[u], zw.x);
+                                const uint64_t R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                                float r0, r1;
+                                up2(R2, r0, r1);
+                                const float i0 = r0 > (float)eps2 ? rsqrt_ftz(r0) : 0.f;
+                                const float i1 = r1 > (float)eps2 ? rsqrt_ftz(r1) : 0.f;
+                                const uint64_t RI = pk2(i0, i1);
+                                const uint64_t K3 = mul2(mul2(mul2(RI, RI), RI), zw.y);
+                                qx[u] = fma2(K3, DX, qx[u]);
+                                qy[u] = fma2(K3, DY, qy[u]);
+                                qz[u] = fma2(K3, DZ, qz[u]);
+                            }
+                        }
+                        continue;
                     }
                     __syncwarp();
 #pragma unroll 4
@@ -433,6 +518,18 @@ eval_kernel(EvalArgs a) {
                             py[u] += k3 * ddy;
                             pz[u] += k3 * ddz;
                         }
+                    }
+                }
+                if constexpr (kPacked) {
+#pragma unroll
+                    for (int u = 0; u < kTPL; ++u) {
+                        float a0, a1;
+                        up2(qx[u], a0, a1);
+                        px[u] = a0 + a1;
+                        up2(qy[u], a0, a1);
+                        py[u] = a0 + a1;
+                        up2(qz[u], a0, a1);
+                        pz[u] = a0 + a1;
                     }
                 }
 #pragma unroll

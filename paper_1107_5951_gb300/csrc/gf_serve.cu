@@ -40,6 +40,7 @@ struct Entry {
     void *rho = nullptr;
     double *gz = nullptr, *g = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int kernels = 0;            // kernel nodes of the graph
 };
 
 struct Ticket {
@@ -177,6 +178,20 @@ gf_status build_entry(gf_server_s *s, Ticket *t, cudaStream_t st, Entry **out) {
             ce = cudaStreamEndCapture(st, &graph);
             if (ce == cudaSuccess && fr != GF_OK) ce = cudaErrorStreamCaptureInvalidated;
         }
+        if (ce == cudaSuccess) {
+            // the capture counted launches that did not run: count the
+            // graph's kernels on each replay instead
+            size_t nn = 0;
+            ce = cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (ce == cudaSuccess && nn) ce = cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (size_t i = 0; ce == cudaSuccess && i < nn; ++i) {
+                cudaGraphNodeType ty;
+                ce = cudaGraphNodeGetType(nodes[i], &ty);
+                if (ty == cudaGraphNodeTypeKernel) ++e->kernels;
+            }
+            count_launch(-e->kernels);
+        }
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e->exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (ce == cudaSuccess) ce = cudaGraphUpload(e->exec, st);
@@ -278,8 +293,10 @@ void scheduler(gf_server_s *s) {
         cudaError_t ce = cudaMemcpyAsync(e->rho, r.rho_host, dtype_size(r.rho_dtype) * e->nvox, in, st);
         gf_status fr = GF_OK;
         if (ce == cudaSuccess && e->M > 0) {
-            if (e->exec)
+            if (e->exec) {
                 ce = cudaGraphLaunch(e->exec, st);
+                if (ce == cudaSuccess) count_launch(e->kernels);
+            }
             else
                 fr = gf_forward(e->plan, e->rho, e->rho_dtype, 1, e->g, e->gz, st);
         }
