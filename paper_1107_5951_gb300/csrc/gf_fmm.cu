@@ -200,67 +200,266 @@ p2m_kernel(const T *__restrict__ mass, const T *__restrict__ P, int64_t nleaf, i
     }
 }
 
-// M2M: parent ME = sum over existing children of T_oct * child ME; one block
-// per parent box of the dense source block at level l.
-template <class Ts, class Tc>
-__global__ void __launch_bounds__(128)
-m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3 bp, int B, int K, int ldk,
-           const Tc *__restrict__ tab) {
+// Fused a0 + a3 for leaves of at most 4^3 voxels: a block takes a 4x4x4
+// tile of leaves for one batch member, reads their densities straight from
+// the caller's grid (rows of 4b contiguous voxels), writes the leaf-blocked
+// copy used by the near field, and multiplies the 64 leaves' masses by the
+// P2M matrix held in shared memory: ME[leaf][k] = sum_v P[v][k] mass[leaf][v].
+// Thread (tl, tk) of 16 x 16 owns leaves 4tl..4tl+3 and coefficients
+// tk + 16j, j < RPT.
+constexpr int kFTile = 4;                       // leaves per tile edge
+constexpr int kFLeaves = kFTile * kFTile * kFTile;
+
+__host__ __device__ inline int p2m_fused_pitch(int K) { return (K + 15) & ~15; }
+
+template <class T>
+__host__ __device__ inline size_t p2m_fused_smem(int b3, int K, int ldk) {
+    const size_t in = (size_t)b3 * p2m_fused_pitch(K) + (size_t)b3 * kFLeaves;
+    const size_t out = (size_t)kFLeaves * ldk;
+    return sizeof(T) * (in > out ? in : out);
+}
+
+template <class T, int BV, int RPT>
+__global__ void __launch_bounds__(256)
+p2m_fused(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int64_t nz, int64_t vx, int64_t vy,
+          int64_t vz, Block3 blk, int B, const T *__restrict__ P, int K, int ldk, T *__restrict__ mass,
+          T *__restrict__ me, int *__restrict__ status) {
     extern __shared__ unsigned char shraw[];
-    Tc *xs = reinterpret_cast<Tc *>(shraw);  // [8][B][K]
+    constexpr int b3 = BV * BV * BV;
+    constexpr int e4 = kFTile * BV;   // voxels per tile edge
+    const int KP = p2m_fused_pitch(K);
+    T *Ps = reinterpret_cast<T *>(shraw);   // [b3][KP]
+    T *ms = Ps + (size_t)b3 * KP;           // [b3][64]: voxel-major, leaf-minor
+    T *os = reinterpret_cast<T *>(shraw);   // [64][ldk] (after the product)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bb = blockIdx.y;
+    const int64_t ntx = (blk.n[0] + kFTile - 1) / kFTile, nty = (blk.n[1] + kFTile - 1) / kFTile;
+    const int64_t tile = blockIdx.x;
+    const int64_t l0x = (tile % ntx) * kFTile, l0y = ((tile / ntx) % nty) * kFTile, l0z = tile / (ntx * nty) * kFTile;
+    for (int v = warp; v < b3; v += 8)
+        for (int k = lane; k < KP; k += 32) Ps[v * KP + k] = k < K ? P[(size_t)v * K + k] : T(0);
+    // densities of the tile's (4b)^3 voxels, x fastest (coalesced rows)
+    const int64_t nvox = nx * ny * nz;
+    const int64_t gx0 = (blk.lo[0] + l0x) * BV - vx, gy0 = (blk.lo[1] + l0y) * BV - vy,
+                  gz0 = (blk.lo[2] + l0z) * BV - vz;
+    bool bad = false;
+    for (int e = tid; e < e4 * e4 * e4; e += 256) {
+        const int ix = e % e4, iy = (e / e4) % e4, iz = e / (e4 * e4);
+        const int64_t i = gx0 + ix, j = gy0 + iy, k = gz0 + iz;
+        T m = T(0);
+        if (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz) {
+            const int64_t idx = (int64_t)bb * nvox + (k * ny + j) * nx + i;
+            const double r = rho_f32 ? (double)reinterpret_cast<const float *>(rho)[idx]
+                                     : reinterpret_cast<const double *>(rho)[idx];
+            bad |= !isfinite(r);
+            m = (T)r;
+        }
+        const int leaf = ((iz / BV) * kFTile + iy / BV) * kFTile + ix / BV;
+        const int v = ((iz % BV) * BV + iy % BV) * BV + ix % BV;
+        ms[v * kFLeaves + leaf] = m;
+    }
+    if (bad) atomicOr(status, 1);
+    __syncthreads();
+    // leaf-blocked masses for the near field: mass[leaf][bb][v]
+    for (int e = tid; e < kFLeaves * b3; e += 256) {
+        const int leaf = e / b3, v = e % b3;
+        const int64_t gx = l0x + leaf % kFTile, gy = l0y + (leaf / kFTile) % kFTile, gz = l0z + leaf / (kFTile * kFTile);
+        if (gx >= blk.n[0] || gy >= blk.n[1] || gz >= blk.n[2]) continue;
+        const int64_t gl = (gz * blk.n[1] + gy) * blk.n[0] + gx;
+        mass[(gl * B + bb) * b3 + v] = ms[v * kFLeaves + leaf];
+    }
+    const int tl = tid & 15, tk = tid >> 4;
+    T acc[4][RPT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+    for (int v = 0; v < b3; ++v) {
+        T m4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) m4[i] = ms[v * kFLeaves + 4 * tl + i];
+        const T *pr = Ps + (size_t)v * KP + tk;
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const T pv = (tk + 16 * j < KP) ? pr[16 * j] : T(0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i][j] += pv * m4[i];
+        }
+    }
+    __syncthreads();   // Ps and ms are reused as the output staging area
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int k = tk + 16 * j;
+            if (k < ldk) os[(4 * tl + i) * ldk + k] = k < K ? acc[i][j] : T(0);
+        }
+    __syncthreads();
+    for (int leaf = warp; leaf < kFLeaves; leaf += 8) {
+        const int64_t gx = l0x + leaf % kFTile, gy = l0y + (leaf / kFTile) % kFTile, gz = l0z + leaf / (kFTile * kFTile);
+        if (gx >= blk.n[0] || gy >= blk.n[1] || gz >= blk.n[2]) continue;
+        const int64_t gl = (gz * blk.n[1] + gy) * blk.n[0] + gx;
+        T *dst = me + (gl * B + bb) * ldk;
+        for (int k = lane; k < ldk; k += 32) dst[k] = os[leaf * ldk + k];
+    }
+}
+
+template <class T, int BV>
+gf_status launch_p2m_fused_b(gf_plan_s *plan, const void *rho, int rho_f32, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const FmmLevel &lv = F->lev[F->L];
+    const int K = F->K;
+    const Block3 blk = block_of(lv);
+    const int64_t tiles = ((blk.n[0] + kFTile - 1) / kFTile) * ((blk.n[1] + kFTile - 1) / kFTile) *
+                          ((blk.n[2] + kFTile - 1) / kFTile);
+    const size_t shm = p2m_fused_smem<T>(BV * BV * BV, K, F->KS);
+    const T *P = sizeof(T) == 8 ? (const T *)F->p2m_d : (const T *)F->p2m_f;
+    const dim3 grid((unsigned)tiles, (unsigned)B);
+#define GF_P2M_LAUNCH(R)                                                                                    \
+    do {                                                                                                    \
+        GF_TRY(ensure_smem(p2m_fused<T, BV, R>, shm));                                                      \
+        p2m_fused<T, BV, R><<<grid, 256, shm, st>>>(rho, rho_f32, plan->grid.n[0], plan->grid.n[1],          \
+                                                    plan->grid.n[2], F->voff[0], F->voff[1], F->voff[2], blk, B, \
+                                                    P, K, F->KS, (T *)F->mass, (T *)lv.me, plan->d_status); \
+    } while (0)
+    const int rpt = (p2m_fused_pitch(K) + 15) / 16;
+    if (rpt <= 4)
+        GF_P2M_LAUNCH(4);
+    else if (rpt <= 8)
+        GF_P2M_LAUNCH(8);
+    else if (rpt <= 12)
+        GF_P2M_LAUNCH(12);
+    else
+        GF_P2M_LAUNCH(20);
+#undef GF_P2M_LAUNCH
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
+template <class T>
+gf_status launch_p2m_fused(gf_plan_s *plan, const void *rho, int rho_f32, int B, cudaStream_t st) {
+    switch (plan->fmm->b) {
+        case 1: return launch_p2m_fused_b<T, 1>(plan, rho, rho_f32, B, st);
+        case 2: return launch_p2m_fused_b<T, 2>(plan, rho, rho_f32, B, st);
+        case 3: return launch_p2m_fused_b<T, 3>(plan, rho, rho_f32, B, st);
+        default: return launch_p2m_fused_b<T, 4>(plan, rho, rho_f32, B, st);
+    }
+}
+
+// Whether the fused kernel applies (leaves of at most 4^3 voxels, tables
+// that fit one block's shared memory).
+template <class T>
+bool p2m_fused_ok(const FmmPlan *F) {
+    const int b3 = F->b * F->b * F->b;
+    return F->b <= 4 && p2m_fused_pitch(F->K) <= 320 && p2m_fused_smem<T>(b3, F->K, F->KS) <= 200 * 1024;
+}
+
+// Top-level translations in FP64 (mixed precision keeps the M2M into
+// level 2 and the L2L out of it in double).  The work is small but FP64 is
+// slow, so each block computes 32 output coefficients of one box and its 8
+// warps split the input coefficients; the partial sums meet in shared
+// memory.  Grid: (boxes, ceil(K / 32)), 256 threads.
+constexpr int kTopWarps = 8;
+
+// Batch members [b0, b0 + nb) of B are handled by one launch (nb bounded by
+// shared memory).
+__host__ __device__ inline size_t top_smem(int nexp, int nb, int K) {
+    return sizeof(double) * ((size_t)nexp * nb * K + (size_t)kTopWarps * nb * 32);
+}
+
+// M2M: parent ME[k] = sum over existing children c, inputs i of
+// T_oct(c)[i][k] * child ME[i].
+template <class Ts, class Tc>
+__global__ void __launch_bounds__(kTopWarps * 32)
+m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3 bp, int B, int b0, int nb, int K,
+           int ldk, const Tc *__restrict__ tab) {
+    extern __shared__ unsigned char shraw[];
+    Tc *xs = reinterpret_cast<Tc *>(shraw);   // [8][nb][K] child expansions
+    Tc *red = xs + 8 * nb * K;                // [kTopWarps][nb][32] partial sums
     __shared__ int present[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t pi = blockIdx.x;
+    const int k = blockIdx.y * 32 + lane;
     const int64_t px = bp.lo[0] + pi % bp.n[0], py = bp.lo[1] + (pi / bp.n[0]) % bp.n[1],
                   pz = bp.lo[2] + pi / (bp.n[0] * bp.n[1]);
-    for (int e = threadIdx.x; e < 8 * B * K; e += blockDim.x) {
-        const int oct = e / (B * K), r = e - oct * B * K;
+    for (int e = threadIdx.x; e < 8 * nb * K; e += blockDim.x) {
+        const int oct = e / (nb * K), r = e - oct * nb * K;
         const int64_t cx = 2 * px + (oct & 1) - bc.lo[0], cy = 2 * py + ((oct >> 1) & 1) - bc.lo[1],
                       cz = 2 * pz + ((oct >> 2) & 1) - bc.lo[2];
         const bool in = cx >= 0 && cx < bc.n[0] && cy >= 0 && cy < bc.n[1] && cz >= 0 && cz < bc.n[2];
         const int rb = r / K, rk = r - rb * K;
-        xs[e] = in ? (Tc)me_c[(((cz * bc.n[1] + cy) * bc.n[0] + cx) * B + rb) * ldk + rk] : Tc(0);
+        xs[e] = in ? (Tc)me_c[(((cz * bc.n[1] + cy) * bc.n[0] + cx) * B + b0 + rb) * ldk + rk] : Tc(0);
         if (r == 0) present[oct] = in;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        for (int bb = 0; bb < B; ++bb) {
-            Tc acc = Tc(0);
+    const int per = (K + kTopWarps - 1) / kTopWarps;
+    const int i0 = warp * per, i1 = min(K, i0 + per);
+    for (int bb = 0; bb < nb; ++bb) {
+        Tc acc = Tc(0);
+        if (k < K)
             for (int oct = 0; oct < 8; ++oct) {
                 if (!present[oct]) continue;
                 const Tc *t = tab + (size_t)oct * K * K + k;
-                const Tc *x = xs + (oct * B + bb) * K;
-                for (int c = 0; c < K; ++c) acc += t[(size_t)c * K] * x[c];
+                const Tc *x = xs + (oct * nb + bb) * K;
+                for (int i = i0; i < i1; ++i) acc += t[(size_t)i * K] * x[i];
             }
-            me_p[(pi * B + bb) * ldk + k] = (Ts)acc;
-        }
+        red[(warp * nb + bb) * 32 + lane] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * 32; e += blockDim.x) {
+        const int bb = e / 32, kk = blockIdx.y * 32 + (e & 31);
+        if (kk >= K) continue;
+        Tc acc = Tc(0);
+        for (int w = 0; w < kTopWarps; ++w) acc += red[(w * nb + bb) * 32 + (e & 31)];
+        me_p[(pi * B + b0 + bb) * ldk + kk] = (Ts)acc;
     }
 }
 
-// L2L: child LE += T_oct * parent LE, one block per observer box at level l.
+// L2L: child LE[k] += sum_i T_oct[i][k] * parent LE[i], one block per
+// (observer box of level l, 32 outputs).
 template <class Ts, class Tc>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kTopWarps * 32)
 l2l_kernel(const Ts *__restrict__ le_p, const uint64_t *__restrict__ tkey, const int32_t *__restrict__ tparent,
-           Ts *__restrict__ le_c, int B, int K, int ldk, const Tc *__restrict__ tab) {
+           Ts *__restrict__ le_c, int B, int b0, int nb, int K, int ldk, const Tc *__restrict__ tab) {
     extern __shared__ unsigned char shraw[];
-    Tc *xs = reinterpret_cast<Tc *>(shraw);  // [B][K]
+    Tc *xs = reinterpret_cast<Tc *>(shraw);   // [nb][K]
+    Tc *red = xs + nb * K;                    // [kTopWarps][nb][32]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = blockIdx.x;
+    const int k = blockIdx.y * 32 + lane;
     const int oct = (int)(tkey[t] & 7);
     const int64_t par = tparent[t];
-    for (int e = threadIdx.x; e < B * K; e += blockDim.x) {
+    for (int e = threadIdx.x; e < nb * K; e += blockDim.x) {
         const int rb = e / K, rk = e - rb * K;
-        xs[e] = (Tc)le_p[(par * B + rb) * ldk + rk];
+        xs[e] = (Tc)le_p[(par * B + b0 + rb) * ldk + rk];
     }
     __syncthreads();
-    const Tc *tb = tab + (size_t)oct * K * K;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        for (int bb = 0; bb < B; ++bb) {
-            Tc acc = Tc(0);
-            const Tc *x = xs + bb * K;
-            for (int c = 0; c < K; ++c) acc += tb[(size_t)c * K + k] * x[c];
-            Ts *o = le_c + (t * B + bb) * ldk + k;
-            *o = (Ts)((Tc)*o + acc);
-        }
+    const int per = (K + kTopWarps - 1) / kTopWarps;
+    const int i0 = warp * per, i1 = min(K, i0 + per);
+    const Tc *tb = tab + (size_t)oct * K * K + k;
+    for (int bb = 0; bb < nb; ++bb) {
+        Tc acc = Tc(0);
+        if (k < K)
+            for (int i = i0; i < i1; ++i) acc += tb[(size_t)i * K] * xs[bb * K + i];
+        red[(warp * nb + bb) * 32 + lane] = acc;
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * 32; e += blockDim.x) {
+        const int bb = e / 32, kk = blockIdx.y * 32 + (e & 31);
+        if (kk >= K) continue;
+        Tc acc = Tc(0);
+        for (int w = 0; w < kTopWarps; ++w) acc += red[(w * nb + bb) * 32 + (e & 31)];
+        Ts *o = le_c + (t * B + b0 + bb) * ldk + kk;
+        *o = (Ts)((Tc)*o + acc);
+    }
+}
+
+// Largest batch chunk whose shared memory fits one block.
+inline int top_batch_chunk(int nexp, int B, int K) {
+    int nb = B;
+    while (nb > 1 && top_smem(nexp, nb, K) > 200 * 1024) nb = (nb + 1) / 2;
+    return nb;
 }
 
 // ---------------------------------------------------------------- evaluation
@@ -682,8 +881,14 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     const int K = F->K, L = F->L;
     const int b3 = F->b * F->b * F->b;
     const Tables *tab = F->tab;
+    const bool fused = p2m_fused_ok<T>(F);
+    if (fused) {
+        // a0 + a3: leaf-blocked densities and P2M in one pass (timed as P2M)
+        stage_mark(plan, 1, st);
+        GF_TRY(launch_p2m_fused<T>(plan, rho, rho_dtype == GF_DTYPE_F32, B, st));
+    }
     // a0: leaf-blocked densities
-    {
+    if (!fused) {
         const FmmLevel &lv = F->lev[L];
         const int64_t total = lv.ns * B * b3;
         const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
@@ -692,9 +897,9 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
                                                  block_of(lv), F->b, B, (T *)F->mass, plan->d_status);
         GF_KERNEL_DONE();
     }
-    stage_mark(plan, 1, st);
+    if (!fused) stage_mark(plan, 1, st);
     // a3: P2M at the leaves
-    {
+    if (!fused) {
         const FmmLevel &lv = F->lev[L];
         const unsigned grid = ceil_div(lv.ns, kP2MLeaves);
         const size_t shm = sizeof(T) * kP2MLeaves * B * b3;
@@ -710,11 +915,15 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     for (int l = L - 1; l >= 2; --l) {
         const FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
         if (sizeof(T) == 4 && l <= 2) {
-            const size_t shm = sizeof(double) * 8 * B * K;
-            GF_TRY((ensure_smem(m2m_kernel<T, double>, shm)));
-            m2m_kernel<T, double><<<(unsigned)pa.ns, 128, shm, st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
-                                                                     block_of(pa), B, K, F->KS, tab->m2m_d);
-            GF_KERNEL_DONE();
+            const int nbc = top_batch_chunk(8, B, K);
+            GF_TRY((ensure_smem(m2m_kernel<T, double>, top_smem(8, nbc, K))));
+            for (int b0 = 0; b0 < B; b0 += nbc) {
+                const int nb = std::min(nbc, B - b0);
+                m2m_kernel<T, double><<<dim3((unsigned)pa.ns, ceil_div(K, 32)), kTopWarps * 32,
+                                        top_smem(8, nb, K), st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
+                                                                  block_of(pa), B, b0, nb, K, F->KS, tab->m2m_d);
+                GF_KERNEL_DONE();
+            }
         } else {
             GF_TRY((translate_run<T, T>(plan, l, 0, B, st)));
         }
@@ -729,9 +938,15 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         if (lv.nt == 0) continue;
         const FmmLevel &pa = F->lev[l - 1];
         if (sizeof(T) == 4 && l - 1 <= 2) {
-            l2l_kernel<T, double><<<(unsigned)lv.nt, 128, sizeof(double) * B * K, st>>>(
-                (const T *)pa.le, lv.tkey, lv.tparent, (T *)lv.le, B, K, F->KS, tab->l2l_d);
-            GF_KERNEL_DONE();
+            const int nbc = top_batch_chunk(1, B, K);
+            GF_TRY((ensure_smem(l2l_kernel<T, double>, top_smem(1, nbc, K))));
+            for (int b0 = 0; b0 < B; b0 += nbc) {
+                const int nb = std::min(nbc, B - b0);
+                l2l_kernel<T, double><<<dim3((unsigned)lv.nt, ceil_div(K, 32)), kTopWarps * 32,
+                                        top_smem(1, nb, K), st>>>((const T *)pa.le, lv.tkey, lv.tparent,
+                                                                  (T *)lv.le, B, b0, nb, K, F->KS, tab->l2l_d);
+                GF_KERNEL_DONE();
+            }
         } else {
             GF_TRY((translate_run<T, T>(plan, l, 1, B, st)));
         }

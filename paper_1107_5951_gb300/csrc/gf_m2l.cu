@@ -31,31 +31,32 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// Byte offset of element (row, k), k < 32, in a [rows][32] FP32 tile stored
-// K-major with the 128-byte swizzle: 8-row atoms of 1024 bytes, the 16-byte
-// chunk index XOR-ed with the row inside the atom.
-__host__ __device__ __forceinline__ uint32_t swz128(int row, int k) {
-    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 2) ^ (row & 7)) & 7) << 4) + (k & 3) * 4);
+// Byte offset of element (row, k), k < 16, in a [rows][16] FP32 tile stored
+// K-major with the 64-byte swizzle: 8-row atoms of 512 bytes, the 16-byte
+// chunk index XOR-ed with bits 1-2 of the row inside the atom.
+__host__ __device__ __forceinline__ uint32_t swz64(int row, int k) {
+    return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((((k >> 2) ^ (row >> 1)) & 3) << 4) + (k & 3) * 4);
 }
 
-// Operator images for the tensor-core M2L: img[off][c][part][Npad*32],
-// part 0 = TF32(T), part 1 = TF32(T - TF32(T)), T = T_off[k_out][k_in].
+// Operator images for the tensor-core M2L: img[off][c][part][Npad*16],
+// part 0 = TF32(T), part 1 = TF32(T - TF32(T)), T = T_off[k_out][k_in] for
+// the 16 inputs k_in of chunk c.
 __global__ void build_tc_images(const double *__restrict__ m2l_d, int K, int Npad, int nck,
                                 float *__restrict__ img) {
     const int off = blockIdx.x;
     const int dx = off % 7 - 3, dy = (off / 7) % 7 - 3, dz = off / 49 - 3;
     const bool used = max(abs(dx), max(abs(dy), abs(dz))) >= 2;
-    const size_t tile = (size_t)Npad * 32;
+    const size_t tile = (size_t)Npad * 16;
     for (int c = 0; c < nck; ++c) {
         float *hi = img + ((size_t)off * nck + c) * 2 * tile;
         float *lo = hi + tile;
-        for (int e = threadIdx.x; e < Npad * 32; e += blockDim.x) {
-            const int n = e / 32, kk = e % 32, kin = 32 * c + kk;
+        for (int e = threadIdx.x; e < Npad * 16; e += blockDim.x) {
+            const int n = e / 16, kk = e % 16, kin = 16 * c + kk;
             const double v = (used && n < K && kin < K) ? m2l_d[(size_t)off * K * K + (size_t)kin * K + n] : 0.0;
             const float f = (float)v;
             const float h = __uint_as_float(to_tf32(f));
             const float l = __uint_as_float(to_tf32(f - h));
-            const uint32_t o = swz128(n, kk) / 4;
+            const uint32_t o = swz64(n, kk) / 4;
             hi[o] = h;
             lo[o] = l;
         }
@@ -68,8 +69,8 @@ gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
     const int npad = (T->K + 15) & ~15;
     if (npad > 256) return GF_OK;  // beyond one MMA's N: SIMT only
     T->tc_npad = npad;
-    T->tc_nck = (T->K + 31) / 32;
-    const size_t n = (size_t)343 * T->tc_nck * 2 * npad * 32;
+    T->tc_nck = (T->K + 15) / 16;
+    const size_t n = (size_t)343 * T->tc_nck * 2 * npad * 16;
     GF_CUDA(cudaMalloc(&T->m2l_tc, n * sizeof(float)));
     build_tc_images<<<343, 256, 0, st>>>(T->m2l_d, T->K, npad, T->tc_nck, T->m2l_tc);
     GF_KERNEL_DONE();
@@ -412,22 +413,26 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 // Tensor-core M2L (mixed precision).  A CTA owns 128 target columns --
 // (box, batch member) pairs of one parity class of one level -- and, offset
 // by offset, computes D_o[col][k_out] = sum_k_in ME[t + o][k_in] T_o[k_out][k_in]
-// on the tensor cores as 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi), with
-// the result of each offset accumulated in FP32 in tensor memory.  Two
-// tensor-memory banks alternate between offsets: while the MMAs of offset g
-// run into one bank, the threads read offset g-1's bank and add it to FP32
-// registers with round-to-nearest adds, so no tensor-core accumulation chain
-// is longer than one offset (the tensor cores' own FP32 accumulation rounds
-// differently from IEEE, and long chains over zero-mean data lose digits).
-// Per (offset, 32-wide input chunk): one thread bulk-copies the pre-split,
-// pre-swizzled operator image into shared memory (mbarrier completion), every
-// thread gathers half of its column's 32 inputs (128-bit loads, rows padded
-// to 32 floats), splits them into TF32 high and low parts and stores them
-// swizzled, and one thread issues the MMAs and commits them to mbarriers that
-// free the stage and mark the bank complete.  All levels run in one launch
-// (their M2L are independent).  Every wait is bounded; a wait that gives up
-// sets status[1], and the CTA then stops, drains (bounded) and frees its
-// tensor memory.
+// on the tensor cores as 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi).  Inputs
+// come in chunks of 16 through a ring of shared-memory stages (64-byte
+// swizzle), filled by warp-specialised producers:
+//   warps 0-3   A producers: thread r gathers column r's 16 inputs of the
+//               chunk (two chunks in flight in registers), splits them into
+//               TF32 high and low parts and stores them swizzled;
+//   warp 4      one thread issues the MMAs of a stage and commits them to the
+//               stage's "empty" barrier (and, after an offset's last chunk,
+//               to the bank's "full" barrier);
+//   warp 5      one thread bulk-copies the pre-split, pre-swizzled operator
+//               image of each stage (mbarrier transaction count);
+//   warps 6-13  promoters: after each offset they read the finished bank of
+//               tensor memory and add it into FP32 registers (two banks
+//               alternate, so the tensor cores never accumulate more than one
+//               offset: their FP32 accumulation rounds differently from
+//               IEEE and long chains over zero-mean data lose digits).
+// Offsets whose source boxes are all missing are skipped by every role (a
+// per-tile list built first).  Every wait is bounded and watches an abort
+// flag; a wait that gives up sets status[1], and the CTA then drains its
+// copies and MMAs (bounded) and frees its tensor memory.
 
 struct TcLevel {
     const float *me;      // input rows (forward ME_l, adjoint LE_l duals)
@@ -445,19 +450,21 @@ struct TcArgs {
     const TcLevel *lv;          // device array indexed by level
     int lmin, nent;             // entries e = (level - lmin) * 8 + class
     int tile_begin[kMaxLevels * 8 + 1];
-    int K, ldk, B, Npad, nck;
+    int K, ldk, B, Npad, nck, nst;
     const float *img;
     int *status;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand with the 64-byte
+// swizzle (8-row atoms of 512 bytes).
+__device__ __forceinline__ uint64_t umma_desc64(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)1 << 16;             // leading byte offset (unused, swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: one 8-row atom
+    d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset: one 8-row atom
     d |= (uint64_t)1 << 46;             // descriptor version
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    d |= (uint64_t)4 << 61;             // 64-byte swizzle
     return d;
 }
 
@@ -468,16 +475,35 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 
 constexpr long kWaitTries = 1l << 24;
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(addr), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier that also gives up when
+// another role has set the abort flag; a timeout sets the flag.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t addr, uint32_t parity, volatile int *abort_flag) {
     for (long it = 0; it < kWaitTries; ++it) {
-        uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok)
-                     : "r"(addr), "r"(parity)
-                     : "memory");
-        if (ok) return true;
+        if (mbar_try(addr, parity)) return true;
+        if ((it & 255) == 255 && *abort_flag) return false;
     }
+    *abort_flag = 1;
     return false;
+}
+
+// Bounded wait that ignores the abort flag (used to drain in-flight work).
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    for (long it = 0; it < kWaitTries; ++it)
+        if (mbar_try(addr, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -490,7 +516,7 @@ __device__ __forceinline__ void commit_to(uint64_t *bar) {
                  : "memory");
 }
 
-// Add 8 accumulator columns starting at `col` of this warp's 32 lanes to acc[j0..j0+7].
+// Read 8 accumulator columns starting at address ta (this warp's 32 lanes).
 __device__ __forceinline__ void tmem_ld8(uint32_t ta, float *v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -501,26 +527,36 @@ __device__ __forceinline__ void tmem_ld8(uint32_t ta, float *v) {
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-constexpr int kTcThreads = 256;
+constexpr int kTcWarps = 14;
+constexpr int kTcThreads = kTcWarps * 32;
+constexpr int kTcMaxStages = 8;
 constexpr uint32_t kTcCols = 512;           // two banks of 256 columns
-constexpr uint32_t kTcA = 2u * 16384u;      // A hi + lo for 128 rows
+constexpr uint32_t kTcA = 2u * 8192u;       // A hi + lo: 128 rows x 64 bytes each
 
-__host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 128u; }
-size_t tc_smem_bytes(int Npad) { return 2 * (size_t)tc_stage_bytes(Npad) + 1024; }
+__host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 64u; }
+constexpr size_t kTcSmemBudget = 227 * 1024 - 2048;
+inline int tc_stages(int Npad) {
+    const int n = (int)(kTcSmemBudget / tc_stage_bytes(Npad));
+    return n > kTcMaxStages ? kTcMaxStages : n;
+}
+size_t tc_smem_bytes(int Npad) { return (size_t)tc_stages(Npad) * tc_stage_bytes(Npad) + 1024; }
 
-template <int NS>   // NS >= Npad / 2: FP32 sums held per thread
+template <int NS>   // NS >= Npad / 2: FP32 sums held per promoter thread
 __global__ void __launch_bounds__(kTcThreads, 1)
 m2l_tc(TcArgs a) {
     extern __shared__ unsigned char dsm[];
     unsigned char *base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);
-    __shared__ __align__(8) uint64_t full[2], done[2], bank_done[2];
+    __shared__ __align__(8) uint64_t afull[kTcMaxStages], bfull[kTcMaxStages], empty[kTcMaxStages];
+    __shared__ __align__(8) uint64_t bank_full[2], bank_empty[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
+    __shared__ uint32_t omask[6];   // offsets with at least one source box in this tile
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int K = a.K, B = a.B, Npad = a.Npad, nck = a.nck;
+    const int K = a.K, B = a.B, Npad = a.Npad, nck = a.nck, NST = a.nst;
     const int nsum = Npad / 2;
-    const uint32_t b_bytes = 2u * (uint32_t)Npad * 128u;
+    const uint32_t b_bytes = 2u * (uint32_t)Npad * 64u;
     const uint32_t stage_bytes = tc_stage_bytes(Npad);
+    volatile int *abortp = &abort_flag;
 
     // which (level, class, tile) this CTA owns
     int e = 0;
@@ -530,12 +566,33 @@ m2l_tc(TcArgs a) {
     const TcLevel &L = a.lv[level];
     const int64_t cbeg = L.cls_off[cls], ccnt = L.cls_off[cls + 1] - cbeg;
     const int nbox = 128 / B;
-    // gather role: column `row`, input half `gh` (16 of the 32 chunk inputs)
-    const int row = tid & 127, gh = tid >> 7;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bank_full[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bank_empty[i])), "r"(8));
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (tid < 6) omask[tid] = 0;
+
+    // producer role: column `row` of the tile
+    const int row = tid & 127;
     const int slot = row / B, bb = row - slot * B;
     const int64_t sidx = (int64_t)tile * nbox + slot;
     int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
-    if (slot < nbox && sidx < ccnt) {
+    if (warp < 4 && slot < nbox && sidx < ccnt) {
         if (!L.adj) {
             tbox = L.order[cbeg + sidx];
             const uint64_t key = L.tkey[tbox];
@@ -547,141 +604,193 @@ m2l_tc(TcArgs a) {
             tbox = (tc2 * L.bn[1] + tc1) * L.bn[0] + tc0;
         }
     }
-    // promotion role: warp w reads lanes 32*(w%4).. (columns of rows
-    // 32*(w%4)+lane) and the column half w/4
-    const int pq = warp & 3, ph = warp >> 2;
-    float acc[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) acc[j] = 0.f;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
-                     "r"(kTcCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done[i])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bank_done[i])), "r"(1));
+    // input row of this column at offset oi (-1: none)
+    auto src_row = [&](int oi) -> int64_t {
+        if (tbox < 0) return -1;
+        const int64_t sx = tc0 + c_il[cls][oi][0], sy = tc1 + c_il[cls][oi][1], sz = tc2 + c_il[cls][oi][2];
+        if (!L.adj) {
+            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
+                return (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldk;
+            return -1;
         }
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;");
+        const int64_t wx = sx + L.blo[0] - L.mlo[0], wy = sy + L.blo[1] - L.mlo[1], wz = sz + L.blo[2] - L.mlo[2];
+        if (wx >= 0 && wy >= 0 && wz >= 0 && wx < L.mn[0] && wy < L.mn[1] && wz < L.mn[2]) {
+            const int32_t m = L.imap[(wz * L.mn[1] + wy) * L.mn[0] + wx];
+            if (m >= 0) return ((int64_t)m * B + bb) * a.ldk;
+        }
+        return -1;
+    };
+    __syncthreads();
+    if (warp < 4) {
+        for (int oi = 0; oi < 189; ++oi) {
+            const unsigned any = __ballot_sync(0xffffffffu, src_row(oi) >= 0);
+            if (lane == 0 && any) atomicOr(&omask[oi >> 5], 1u << (oi & 31));
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tslot;
-    const uint32_t idesc = idesc_tf32(128, Npad);
+    int G = 0;
+    for (int w = 0; w < 6; ++w) G += __popc(omask[w]);
+    const int iters = G * nck;
+    // the oi-th valid offset in ascending order, advanced incrementally
+    auto next_off = [&](int oi) -> int {
+        for (++oi; oi < 189; ++oi)
+            if (omask[oi >> 5] & (1u << (oi & 31))) return oi;
+        return 189;
+    };
 
-    int it = 0;        // chunk iterations issued
-    int g = 0;         // offsets issued (bank = g & 1)
-    bool copy_pending = false, aborted = false, waits_ok = true;
-    for (int oi = 0; oi < 189 && !aborted; ++oi) {
-        const int dx = c_il[cls][oi][0], dy = c_il[cls][oi][1], dz = c_il[cls][oi][2];
-        int64_t src = -1;
-        if (tbox >= 0) {
-            const int64_t sx = tc0 + dx, sy = tc1 + dy, sz = tc2 + dz;
-            if (!L.adj) {
-                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
-                    src = (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldk;
-            } else {
-                const int64_t wx = sx + L.blo[0] - L.mlo[0], wy = sy + L.blo[1] - L.mlo[1],
-                              wz = sz + L.blo[2] - L.mlo[2];
-                if (wx >= 0 && wy >= 0 && wz >= 0 && wx < L.mn[0] && wy < L.mn[1] && wz < L.mn[2]) {
-                    const int32_t m = L.imap[(wz * L.mn[1] + wy) * L.mn[0] + wx];
-                    if (m >= 0) src = ((int64_t)m * B + bb) * a.ldk;
-                }
-            }
-        }
-        if (!__syncthreads_or(src >= 0)) continue;
-        const int slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
-        const uint32_t bank = (uint32_t)(g & 1) * 256u;
-        for (int c = 0; c < nck; ++c) {
-            const int s = it & 1;
-            unsigned char *stage = base + s * stage_bytes;
-            bool tout = false;
-            if (it >= 2) tout = !mbar_wait(smem_u32(&done[s]), ((it - 2) >> 1) & 1);
-            if (tid == 0 && !tout) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
-                             "r"(b_bytes));
-                const float *srcimg = a.img + ((size_t)slot_off * nck + c) * 2 * (size_t)Npad * 32;
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(stage + kTcA)),
-                    "l"(srcimg), "r"(b_bytes), "r"(smem_u32(&full[s]))
-                    : "memory");
-                copy_pending = true;
-            }
-            // gather 16 inputs of this column's chunk c, split into TF32 parts
-            float v[16];
-            if (src >= 0) {
-                const float4 *p4 = reinterpret_cast<const float4 *>(L.me + src + 32 * c + 16 * gh);
+    if (warp < 4) {
+        // ---------------- A producers
+        int oi = next_off(-1), c = 0;
+        int64_t src = src_row(oi);
+        float4 cur[4], nxt[4];
+        auto load = [&](int64_t sr, int cc, float4 *v) {
+            if (sr >= 0) {
+                const float4 *p4 = reinterpret_cast<const float4 *>(L.me + sr + 16 * cc);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 t = __ldg(p4 + q);
-                    v[4 * q + 0] = t.x;
-                    v[4 * q + 1] = t.y;
-                    v[4 * q + 2] = t.z;
-                    v[4 * q + 3] = t.w;
-                }
+                for (int q = 0; q < 4; ++q) v[q] = __ldg(p4 + q);
             } else {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                for (int q = 0; q < 4; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
+        };
+        if (iters > 0) load(src, 0, cur);
+        int s = 0;
+        uint32_t ph = 0;
+        for (int it = 0; it < iters; ++it) {
+            // prefetch the next chunk
+            int noi = oi, nc = c + 1;
+            int64_t nsrc = src;
+            if (nc == nck) {
+                nc = 0;
+                noi = next_off(oi);
+                nsrc = noi < 189 ? src_row(noi) : -1;
+            }
+            if (it + 1 < iters) load(nsrc, nc, nxt);
+            if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+            unsigned char *stage = base + (size_t)s * stage_bytes;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                const float x4[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
                 uint32_t h[4], l[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int kin = 32 * c + 16 * gh + 4 * q + j;
-                    const float x = kin < K ? v[4 * q + j] : 0.f;
+                    const int kin = 16 * c + 4 * q + j;
+                    const float x = kin < K ? x4[j] : 0.f;
                     h[j] = to_tf32(x);
                     l[j] = to_tf32(x - __uint_as_float(h[j]));
                 }
-                const uint32_t o = swz128(row, 16 * gh + 4 * q);
+                const uint32_t o = swz64(row, 4 * q);
                 *reinterpret_cast<uint4 *>(stage + o) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4 *>(stage + 16384 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+                *reinterpret_cast<uint4 *>(stage + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (__syncthreads_or(tout || abort_flag)) {
-                aborted = true;
-                break;
+            mbar_arrive(smem_u32(&afull[s]));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+            oi = noi;
+            c = nc;
+            src = nsrc;
+            if (++s == NST) {
+                s = 0;
+                ph ^= 1;
             }
-            if (tid == 0) {
-                if (!mbar_wait(smem_u32(&full[s]), (it >> 1) & 1)) {
-                    abort_flag = 1;
-                } else {
-                    copy_pending = false;
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const int nk8 = min(4, (K - 32 * c + 7) / 8);
-                    const uint32_t sa = smem_u32(stage), sb = smem_u32(stage + kTcA);
-                    const uint32_t d = tmem + bank;
-                    for (int ks = 0; ks < nk8; ++ks) {
-                        const uint32_t ko = ks * 32;
-                        const uint64_t ah = umma_desc(sa + ko), al = umma_desc(sa + 16384 + ko);
-                        const uint64_t bh = umma_desc(sb + ko), bl = umma_desc(sb + (uint32_t)Npad * 128 + ko);
-                        mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_tf32(d, ah, bl, idesc, 1u);
-                        mma_tf32(d, al, bh, idesc, 1u);
-                    }
-                    commit_to(&done[s]);
-                    if (c == nck - 1) commit_to(&bank_done[g & 1]);
+        }
+    } else if (warp == 4) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(128, Npad);
+            int s = 0, c = 0, g = 0;
+            uint32_t ph = 0;
+            int last = -1;
+            for (int it = 0; it < iters; ++it) {
+                if (!mbar_wait_ab(smem_u32(&afull[s]), ph, abortp)) break;
+                if (!mbar_wait_ab(smem_u32(&bfull[s]), ph, abortp)) break;
+                if (c == 0 && g >= 2 && !mbar_wait_ab(smem_u32(&bank_empty[g & 1]), ((g - 2) >> 1) & 1, abortp)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const unsigned char *stage = base + (size_t)s * stage_bytes;
+                const uint32_t sa = smem_u32(stage), sb = smem_u32(stage + kTcA);
+                const uint32_t d = tmem + (uint32_t)(g & 1) * 256u;
+                const int nk8 = min(2, (K - 16 * c + 7) / 8);
+                for (int ks = 0; ks < nk8; ++ks) {
+                    const uint32_t ko = ks * 32;
+                    const uint64_t ah = umma_desc64(sa + ko), al = umma_desc64(sa + 8192 + ko);
+                    const uint64_t bh = umma_desc64(sb + ko), bl = umma_desc64(sb + (uint32_t)Npad * 64 + ko);
+                    mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_tf32(d, ah, bl, idesc, 1u);
+                    mma_tf32(d, al, bh, idesc, 1u);
+                }
+                commit_to(&empty[s]);
+                last = it;
+                if (++c == nck) {
+                    commit_to(&bank_full[g & 1]);
+                    c = 0;
+                    ++g;
+                }
+                if (++s == NST) {
+                    s = 0;
+                    ph ^= 1;
                 }
             }
-            ++it;
+            // drain: the last commit covers every MMA issued
+            if (last >= 0) mbar_wait(smem_u32(&empty[last % NST]), (uint32_t)((last / NST) & 1));
         }
-        if (aborted) break;
-        // promote the previous offset's bank while this offset's MMAs run
-        if (g >= 1) {
-            const int pg = g - 1;
-            if (!mbar_wait(smem_u32(&bank_done[pg & 1]), (pg >> 1) & 1)) waits_ok = false;
-            waits_ok = __all_sync(0xffffffffu, waits_ok);   // tcgen05.ld is warp-collective
+    } else if (warp == 5) {
+        // ---------------- operator images
+        if (lane == 0) {
+            int s = 0, c = 0;
+            int oi = next_off(-1);
+            uint32_t ph = 0;
+            int last = -1;
+            for (int it = 0; it < iters; ++it) {
+                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                const int dx = c_il[cls][oi][0], dy = c_il[cls][oi][1], dz = c_il[cls][oi][2];
+                const int slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
+                unsigned char *stage = base + (size_t)s * stage_bytes;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bfull[s])),
+                             "r"(b_bytes));
+                const float *srcimg = a.img + ((size_t)slot_off * nck + c) * 2 * (size_t)Npad * 16;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(stage + kTcA)),
+                    "l"(srcimg), "r"(b_bytes), "r"(smem_u32(&bfull[s]))
+                    : "memory");
+                last = it;
+                if (++c == nck) {
+                    c = 0;
+                    oi = next_off(oi);
+                }
+                if (++s == NST) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            // drain: every copy issued must have landed before the CTA exits
+            if (last >= 0) mbar_wait(smem_u32(&bfull[last % NST]), (uint32_t)((last / NST) & 1));
+        }
+    }
+    // ---------------- promoters (warps 6-13) and the write-back
+    const int pw = warp - 6;
+    const int pq = warp & 3, ph_half = pw >> 2;   // TMEM lane quarter, column half
+    float acc[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) acc[j] = 0.f;
+    bool ok = true;
+    if (pw >= 0) {
+        for (int g = 0; g < G; ++g) {
+            bool w_ok = mbar_wait_ab(smem_u32(&bank_full[g & 1]), (g >> 1) & 1, abortp);
+            w_ok = __all_sync(0xffffffffu, w_ok);   // tcgen05.ld is warp-collective
+            if (!w_ok) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t tb = tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(pg & 1) * 256u + (uint32_t)(ph * nsum);
+            const uint32_t tb = tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(g & 1) * 256u + (uint32_t)(ph_half * nsum);
 #pragma unroll
             for (int j0 = 0; j0 < NS; j0 += 8) {
-                if (j0 < nsum && waits_ok) {
+                if (j0 < nsum) {
                     float t[8];
                     tmem_ld8(tb + j0, t);
 #pragma unroll
@@ -689,36 +798,17 @@ m2l_tc(TcArgs a) {
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
-        }
-        ++g;
-    }
-    // promote the last offset's bank (the final commit covers every MMA)
-    if (!aborted && g >= 1) {
-        const int pg = g - 1;
-        if (!mbar_wait(smem_u32(&bank_done[pg & 1]), (pg >> 1) & 1)) waits_ok = false;
-        waits_ok = __all_sync(0xffffffffu, waits_ok);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t tb = tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(pg & 1) * 256u + (uint32_t)(ph * nsum);
-#pragma unroll
-        for (int j0 = 0; j0 < NS; j0 += 8) {
-            if (j0 < nsum && waits_ok) {
-                float t[8];
-                tmem_ld8(tb + j0, t);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j0 + j] += t[j];
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bank_empty[g & 1]));
         }
     }
-    if (aborted && it > 0) mbar_wait(smem_u32(&done[(it - 1) & 1]), ((it - 1) >> 1) & 1);
-    if (tid == 0 && copy_pending) mbar_wait(smem_u32(&full[(it - 1) & 1]), ((it - 1) >> 1) & 1);
-    const bool failed = __syncthreads_or(!waits_ok || aborted || abort_flag);
+    const bool failed = __syncthreads_or(!ok || abort_flag);
     if (failed && tid == 0) atomicOr(a.status + 1, 1);
-    // write this thread's half row of the local expansion
-    {
+    if (pw >= 0 && !failed) {
         const int r = pq * 32 + lane;
         const int oslot = r / B, obb = r - oslot * B;
         const int64_t os = (int64_t)tile * nbox + oslot;
-        if (oslot < nbox && os < ccnt && !failed) {
+        if (oslot < nbox && os < ccnt) {
             int64_t obox;
             if (!L.adj) {
                 obox = L.order[cbeg + os];
@@ -727,10 +817,10 @@ m2l_tc(TcArgs a) {
                 class_box(cls, L.blo, L.bn, os, ox, oy, oz);
                 obox = (oz * L.bn[1] + oy) * L.bn[0] + ox;
             }
-            float *dst = L.le + (obox * B + obb) * a.ldk + ph * nsum;
+            float *dst = L.le + (obox * B + obb) * a.ldk + ph_half * nsum;
 #pragma unroll
             for (int j = 0; j < NS; ++j)
-                if (j < nsum && ph * nsum + j < K) dst[j] = acc[j];
+                if (j < nsum && ph_half * nsum + j < K) dst[j] = acc[j];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -786,6 +876,7 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     a.B = B;
     a.Npad = Npad;
     a.nck = T->tc_nck;
+    a.nst = tc_stages(Npad);
     a.img = adj ? T->am2l_tc : T->m2l_tc;
     a.status = plan->d_status;
     const int nbox = 128 / B;
