@@ -209,12 +209,13 @@ p2m_kernel(const T *__restrict__ mass, const T *__restrict__ P, int64_t nleaf, i
 // tk + 16j, j < RPT.
 constexpr int kFTile = 4;                       // leaves per tile edge
 constexpr int kFLeaves = kFTile * kFTile * kFTile;
+constexpr int kFPitch = kFLeaves + 4;           // padded row of the mass tile (bank spread)
 
 __host__ __device__ inline int p2m_fused_pitch(int K) { return (K + 15) & ~15; }
 
 template <class T>
 __host__ __device__ inline size_t p2m_fused_smem(int b3, int K, int ldk) {
-    const size_t in = (size_t)b3 * p2m_fused_pitch(K) + (size_t)b3 * kFLeaves;
+    const size_t in = (size_t)b3 * p2m_fused_pitch(K) + (size_t)b3 * kFPitch;
     const size_t out = (size_t)kFLeaves * ldk;
     return sizeof(T) * (in > out ? in : out);
 }
@@ -229,7 +230,7 @@ p2m_fused(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int
     constexpr int e4 = kFTile * BV;   // voxels per tile edge
     const int KP = p2m_fused_pitch(K);
     T *Ps = reinterpret_cast<T *>(shraw);   // [b3][KP]
-    T *ms = Ps + (size_t)b3 * KP;           // [b3][64]: voxel-major, leaf-minor
+    T *ms = Ps + (size_t)b3 * KP;           // [b3][kFPitch]: voxel-major, leaf-minor
     T *os = reinterpret_cast<T *>(shraw);   // [64][ldk] (after the product)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bb = blockIdx.y;
@@ -256,7 +257,7 @@ p2m_fused(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int
         }
         const int leaf = ((iz / BV) * kFTile + iy / BV) * kFTile + ix / BV;
         const int v = ((iz % BV) * BV + iy % BV) * BV + ix % BV;
-        ms[v * kFLeaves + leaf] = m;
+        ms[v * kFPitch + leaf] = m;
     }
     if (bad) atomicOr(status, 1);
     __syncthreads();
@@ -266,7 +267,7 @@ p2m_fused(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int
         const int64_t gx = l0x + leaf % kFTile, gy = l0y + (leaf / kFTile) % kFTile, gz = l0z + leaf / (kFTile * kFTile);
         if (gx >= blk.n[0] || gy >= blk.n[1] || gz >= blk.n[2]) continue;
         const int64_t gl = (gz * blk.n[1] + gy) * blk.n[0] + gx;
-        mass[(gl * B + bb) * b3 + v] = ms[v * kFLeaves + leaf];
+        mass[(gl * B + bb) * b3 + v] = ms[v * kFPitch + leaf];
     }
     const int tl = tid & 15, tk = tid >> 4;
     T acc[4][RPT];
@@ -277,8 +278,16 @@ p2m_fused(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int
 #pragma unroll 4
     for (int v = 0; v < b3; ++v) {
         T m4[4];
+        if constexpr (sizeof(T) == 4) {
+            const float4 t4 = *reinterpret_cast<const float4 *>(ms + v * kFPitch + 4 * tl);
+            m4[0] = t4.x;
+            m4[1] = t4.y;
+            m4[2] = t4.z;
+            m4[3] = t4.w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) m4[i] = ms[v * kFLeaves + 4 * tl + i];
+            for (int i = 0; i < 4; ++i) m4[i] = ms[v * kFPitch + 4 * tl + i];
+        }
         const T *pr = Ps + (size_t)v * KP + tk;
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
