@@ -38,6 +38,34 @@ FLOPS_PER_PAIR = 20.0            # the paper's count: 5 add, 7 mul, 1 sqrt ~ 20 
 TF32_PER_BF16 = 1.1 / 2.25       # nominal dense TF32 / BF16 tensor rates
 
 
+# DRAM traffic per launch of the dominant kernels, from one ncu capture of
+# the default workload (profiles/m2l_tc_grf_volume128_p12.md,
+# profiles/eval_kernel_grf_volume128_p12.md), with the SHA-1 of the kernel's
+# source file at capture time: once the source changes the figure no longer
+# describes the kernel and the bench reports null.
+NCU_TRAFFIC = {
+    ("m2l", "grf_volume_128^3", 12): (212157184, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
+                                      "20b1b232f5a9738c53754da1065d781d527400e3"),
+    ("eval", "grf_volume_128^3", 12): (87542784, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
+                                       "5975c25c0bc551f5a0282e0d1c61db254055f7cb"),
+}
+
+
+def ncu_traffic(stage, workload, p, precision, m2l):
+    import hashlib
+    key = (stage, workload, p)
+    if precision != "mixed" or m2l != "auto" or key not in NCU_TRAFFIC:
+        return None
+    nbytes, src, sha = NCU_TRAFFIC[key]
+    try:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return nbytes
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -63,14 +91,15 @@ def parse_args():
     ap.add_argument("--p", type=int, default=12)
     ap.add_argument("--leaf-vox", type=int, default=0)
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt"])
-    ap.add_argument("--sample-obs", type=int, default=1024,
+    ap.add_argument("--sample-obs", type=int, default=8192,
                     help="observers in the oracle's bounded sample")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "scale", "serving"],
+    ap.add_argument("--workload", default="volume", choices=["volume", "scale", "serving", "adjoint"],
                     help="volume: 128^3 random field, stations + voxel centres; scale: 464^3 layered "
-                         "model, 1024^2 stations; serving: a stream of uneven requests")
+                         "model, 1024^2 stations; serving: a stream of uneven requests; adjoint: misfit "
+                         "gradients of 16 models at 256^2 stations")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests on the device at once")
     ap.add_argument("--rate", type=float, default=0.0,
@@ -161,7 +190,7 @@ def fp32_peak_tflops(peaks):
     return N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def fmm_roofline(stages, info, args, peaks):
+def fmm_roofline(stages, info, args, peaks, workload):
     """Roofline of the stage that dominates the forward: the near-field
     evaluation (ALU: 20 flops per pair, the paper's count) or the M2L
     (2 K^2 flops per interaction-list box pair)."""
@@ -181,8 +210,11 @@ def fmm_roofline(stages, info, args, peaks):
     else:
         peak, note = FP64_TFLOPS_NOMINAL, "FP64 nominal 1.25 TFLOP/s"
     achieved = flops / (stages[dom] * 1e-3) / 1e12
+    traffic = ncu_traffic(dom, workload, args.p, args.precision, args.m2l)
     return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": note,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_source": note,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture "
+                              "(profiles/), per launch" if traffic else None,
             "algorithmic": "%.4g flops per launch set" % flops, "stage_ms": stages[dom]}
 
 
@@ -344,7 +376,7 @@ def bench_gf(args, rank, world):
     stages = {k: float(np.mean([r[k] for r in stage_runs])) for k in stage_runs[0]}
     info = plan.info
     if mode == "fmm":
-        roof = fmm_roofline(stages, info, args, peaks)
+        roof = fmm_roofline(stages, info, args, peaks, wk.name)
     plan.close()
 
     # end to end through the C ABI from pinned host buffers
@@ -395,6 +427,93 @@ def bench_gf(args, rank, world):
             "work": {"near_pairs": int(info.near_pairs), "m2l_box_pairs": int(info.m2l_pairs)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ adjoint
+def bench_adjoint(args, rank, world):
+    """Misfit gradient for a batch of 16 models (128^3 random fields, 256^2
+    stations): one step = forward of the batch (g_z), residual against data
+    synthesised from a hidden model, and the transposed FMM (gf_adjoint) of
+    the residuals -> d misfit / d rho for all 16 models.  Unit of work: the
+    N x M pairs of one model's forward plus its adjoint."""
+    import torch
+
+    import paper_1107_5951_gb300 as pkg
+    from oracle import direct
+    from paper_1107_5951_gb300 import workloads as wl
+
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B = 16
+    wk = wl.adjoint_batch(n=args.n or 128, stations=args.stations or 256, batch=B)
+    N, M = wk.n_sources, wk.n_obs
+    stream = torch.cuda.Stream(device=dev)
+    obs_d = torch.tensor(wk.obs, dtype=torch.float64, device=dev)
+    rdt = torch.float32 if args.precision == "mixed" else torch.float64
+    models = torch.tensor(wk.rho, dtype=rdt, device=dev)
+    plan = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode="fmm",
+                    precision=args.precision, p=args.p, max_batch=B, G=wk.G, stream=stream)
+    hidden = torch.tensor(wk.extra["hidden"], dtype=rdt, device=dev)
+    _, d = plan.forward(hidden, want_g=False, want_gz=True, stream=stream)
+    gz = torch.empty((B, M), dtype=torch.float64, device=dev)
+    grad = torch.empty((B,) + wk.grid.shape_zyx, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        with torch.cuda.stream(stream):
+            plan.forward(models, gz=gz, want_g=False, want_gz=True, stream=stream)
+            r = gz - d
+            plan.adjoint(r, ncomp=1, grad=grad, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank, not args.no_clocks)
+    launches0 = pkg.gf_launch_count()
+    ev = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    launches = pkg.gf_launch_count() - launches0
+    clk = clocks.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    units = float(B) * N * M * 2
+    # parity on sampled voxels of model 0 against the FP64 CPU transpose sum
+    err, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        r0 = (gz[0] - d).cpu().numpy()
+        rng = np.random.default_rng(23)
+        vox = np.sort(rng.choice(wk.grid.nvox, 4096, replace=False))
+        t1 = time.perf_counter()
+        want = direct.adjoint_subset(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.obs, r0, wk.G, vox)
+        dt = time.perf_counter() - t1
+        got = grad[0].reshape(-1).cpu().numpy()[vox]
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        cpu = {"value": len(vox) * M / dt, "unit": "interactions/s", "cores": direct.max_threads(),
+               "kind": "oracle", "sample": "adjoint at 4096 seeded voxels of model 0 x all %d stations (%.1f s)"
+               % (M, dt)}
+    plan.close()
+    if rank != 0:
+        return
+    line = {"metric": "misfit-gradient interactions/s (forward + adjoint, 16 models)",
+            "value": world * units / (ms * 1e-3), "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wk.name, "precision": args.precision, "p": args.p, "batch": B,
+                       "N_sources": N, "M_observers": M,
+                       "l2_flush": "256 MiB buffer written between timed steps",
+                       "step": "forward of 16 models + residual + adjoint of 16 residuals"},
+            "gradients_per_s": world * B / (ms * 1e-3), "rel_err_vs_oracle_sample": err,
+            "roofline": None, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
 
 
@@ -534,6 +653,8 @@ def main():
     try:
         if args.workload == "serving":
             bench_serving(args, rank, world)
+        elif args.workload == "adjoint":
+            bench_adjoint(args, rank, world)
         else:
             bench_gf(args, rank, world)
     finally:
