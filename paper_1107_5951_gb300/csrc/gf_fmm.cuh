@@ -51,6 +51,7 @@ struct Tables {
     double *am2l_d = nullptr, *am2m_d = nullptr, *al2l_d = nullptr;
     float *am2l_f = nullptr, *am2m_f = nullptr, *al2l_f = nullptr;
     float *am2l_tc = nullptr;
+    float *m2m_tc = nullptr, *l2l_tc = nullptr;   // [8] operator images (tensor-core translations)
 };
 
 gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out);
@@ -86,6 +87,8 @@ struct FmmPlan {
     int64_t scls_off[kMaxLevels + 1][9] = {};
     void *tc_levels_adj = nullptr;
     std::vector<unsigned char> tc_levels_adj_host;
+    void *tc_xlate = nullptr;                    // tensor-core M2M / L2L level tables
+    std::vector<unsigned char> tc_xlate_host;
 };
 
 // adjoint set-up and driver (gf_adjoint.cu)

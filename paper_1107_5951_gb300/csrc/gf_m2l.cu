@@ -41,11 +41,13 @@ __host__ __device__ __forceinline__ uint32_t swz64(int row, int k) {
 // Operator images for the tensor-core M2L: img[off][c][part][Npad*16],
 // part 0 = TF32(T), part 1 = TF32(T - TF32(T)), T = T_off[k_out][k_in] for
 // the 16 inputs k_in of chunk c.
+// With all_used (M2M / L2L: 8 octant operators) every slot is filled; for the
+// M2L's 343 slots only offsets of max-norm >= 2 are.
 __global__ void build_tc_images(const double *__restrict__ m2l_d, int K, int Npad, int nck,
-                                float *__restrict__ img) {
+                                float *__restrict__ img, int all_used = 0) {
     const int off = blockIdx.x;
     const int dx = off % 7 - 3, dy = (off / 7) % 7 - 3, dz = off / 49 - 3;
-    const bool used = max(abs(dx), max(abs(dy), abs(dz))) >= 2;
+    const bool used = all_used || max(abs(dx), max(abs(dy), abs(dz))) >= 2;
     const size_t tile = (size_t)Npad * 16;
     for (int c = 0; c < nck; ++c) {
         float *hi = img + ((size_t)off * nck + c) * 2 * tile;
@@ -76,6 +78,13 @@ gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
     GF_KERNEL_DONE();
     GF_CUDA(cudaMalloc(&T->am2l_tc, n * sizeof(float)));
     build_tc_images<<<343, 256, 0, st>>>(T->am2l_d, T->K, npad, T->tc_nck, T->am2l_tc);
+    GF_KERNEL_DONE();
+    const size_t n8 = (size_t)8 * T->tc_nck * 2 * npad * 16;
+    GF_CUDA(cudaMalloc(&T->m2m_tc, n8 * sizeof(float)));
+    build_tc_images<<<8, 256, 0, st>>>(T->m2m_d, T->K, npad, T->tc_nck, T->m2m_tc, 1);
+    GF_KERNEL_DONE();
+    GF_CUDA(cudaMalloc(&T->l2l_tc, n8 * sizeof(float)));
+    build_tc_images<<<8, 256, 0, st>>>(T->l2l_d, T->K, npad, T->tc_nck, T->l2l_tc, 1);
     GF_KERNEL_DONE();
     return GF_OK;
 }
@@ -410,7 +419,10 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- tcgen05
-// Tensor-core M2L (mixed precision).  A CTA owns 128 target columns --
+// Tensor-core translations (mixed precision): the M2L, and with the same
+// machinery the M2M (8 child positions per parent) and the L2L (one step
+// from the parent, operator chosen by the box's position in its parent).
+// For the M2L, a CTA owns 128 target columns --
 // (box, batch member) pairs of one parity class of one level -- and, offset
 // by offset, computes D_o[col][k_out] = sum_k_in ME[t + o][k_in] T_o[k_out][k_in]
 // on the tensor cores as 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi).  Inputs
@@ -434,9 +446,16 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 // flag; a wait that gives up sets status[1], and the CTA then drains its
 // copies and MMAs (bounded) and frees its tensor memory.
 
+// Translation kinds run by the kernel: the M2L (offsets of the interaction
+// list, all levels in one launch), the M2M into one level (the 8 child
+// positions; targets = every parent box of the dense block, one class) and
+// the L2L into one level (one step: the parent; targets = observer boxes
+// grouped by their position in the parent, which selects the operator).
+enum TcKind { kTcM2L = 0, kTcM2M = 1, kTcL2L = 2 };
+
 struct TcLevel {
-    const float *me;      // input rows (forward ME_l, adjoint LE_l duals)
-    float *le;            // output rows (forward LE_l, adjoint ME_l duals)
+    const float *me;      // input rows (M2L: ME_l or adjoint LE_l duals; M2M: ME_{l+1}; L2L: LE_{l-1})
+    float *le;            // output rows (M2L: LE_l or adjoint ME_l duals; M2M: ME_l; L2L: LE_l, added to)
     const int32_t *order;
     const uint64_t *tkey;
     int64_t blo[3], bn[3];
@@ -444,6 +463,8 @@ struct TcLevel {
     int adj;
     const int32_t *imap;
     int64_t mlo[3], mn[3];
+    int64_t clo[3], cn[3];       // M2M: child source block
+    const int32_t *tparent;      // L2L: parent of each observer box
 };
 
 struct TcArgs {
@@ -451,6 +472,7 @@ struct TcArgs {
     int lmin, nent;             // entries e = (level - lmin) * 8 + class
     int tile_begin[kMaxLevels * 8 + 1];
     int K, ldk, B, Npad, nck, nst;
+    int kind, noff;             // TcKind; offsets per target (189, 8 or 1)
     const float *img;
     int *status;
 };
@@ -593,7 +615,14 @@ m2l_tc(TcArgs a) {
     const int64_t sidx = (int64_t)tile * nbox + slot;
     int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
     if (warp < 4 && slot < nbox && sidx < ccnt) {
-        if (!L.adj) {
+        if (a.kind == kTcM2M) {
+            tbox = sidx;
+            tc0 = sidx % L.bn[0];
+            tc1 = (sidx / L.bn[0]) % L.bn[1];
+            tc2 = sidx / (L.bn[0] * L.bn[1]);
+        } else if (a.kind == kTcL2L) {
+            tbox = L.order[cbeg + sidx];
+        } else if (!L.adj) {
             tbox = L.order[cbeg + sidx];
             const uint64_t key = L.tkey[tbox];
             tc0 = dm(key, 0) - L.blo[0];
@@ -607,6 +636,15 @@ m2l_tc(TcArgs a) {
     // input row of this column at offset oi (-1: none)
     auto src_row = [&](int oi) -> int64_t {
         if (tbox < 0) return -1;
+        if (a.kind == kTcM2M) {   // child at position oi of this parent
+            const int64_t cx = 2 * (tc0 + L.blo[0]) + (oi & 1) - L.clo[0],
+                          cy = 2 * (tc1 + L.blo[1]) + ((oi >> 1) & 1) - L.clo[1],
+                          cz = 2 * (tc2 + L.blo[2]) + ((oi >> 2) & 1) - L.clo[2];
+            if (cx >= 0 && cy >= 0 && cz >= 0 && cx < L.cn[0] && cy < L.cn[1] && cz < L.cn[2])
+                return (((cz * L.cn[1] + cy) * L.cn[0] + cx) * B + bb) * a.ldk;
+            return -1;
+        }
+        if (a.kind == kTcL2L) return ((int64_t)L.tparent[tbox] * B + bb) * a.ldk;
         const int64_t sx = tc0 + c_il[cls][oi][0], sy = tc1 + c_il[cls][oi][1], sz = tc2 + c_il[cls][oi][2];
         if (!L.adj) {
             if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
@@ -621,8 +659,9 @@ m2l_tc(TcArgs a) {
         return -1;
     };
     __syncthreads();
+    const int noff = a.noff;
     if (warp < 4) {
-        for (int oi = 0; oi < 189; ++oi) {
+        for (int oi = 0; oi < noff; ++oi) {
             const unsigned any = __ballot_sync(0xffffffffu, src_row(oi) >= 0);
             if (lane == 0 && any) atomicOr(&omask[oi >> 5], 1u << (oi & 31));
         }
@@ -636,7 +675,7 @@ m2l_tc(TcArgs a) {
     const int iters = G * nck;
     // the oi-th valid offset in ascending order, advanced incrementally
     auto next_off = [&](int oi) -> int {
-        for (++oi; oi < 189; ++oi)
+        for (++oi; oi < noff; ++oi)
             if (omask[oi >> 5] & (1u << (oi & 31))) return oi;
         return 189;
     };
@@ -746,8 +785,13 @@ m2l_tc(TcArgs a) {
             int last = -1;
             for (int it = 0; it < iters; ++it) {
                 if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
-                const int dx = c_il[cls][oi][0], dy = c_il[cls][oi][1], dz = c_il[cls][oi][2];
-                const int slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
+                int slot_off;
+                if (a.kind == kTcM2L) {
+                    const int dx = c_il[cls][oi][0], dy = c_il[cls][oi][1], dz = c_il[cls][oi][2];
+                    slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
+                } else {
+                    slot_off = a.kind == kTcM2M ? oi : cls;   // child position / own position
+                }
                 unsigned char *stage = base + (size_t)s * stage_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bfull[s])),
                              "r"(b_bytes));
@@ -810,7 +854,9 @@ m2l_tc(TcArgs a) {
         const int64_t os = (int64_t)tile * nbox + oslot;
         if (oslot < nbox && os < ccnt) {
             int64_t obox;
-            if (!L.adj) {
+            if (a.kind == kTcM2M) {
+                obox = os;
+            } else if (!L.adj) {
                 obox = L.order[cbeg + os];
             } else {
                 int64_t ox, oy, oz;
@@ -818,9 +864,15 @@ m2l_tc(TcArgs a) {
                 obox = (oz * L.bn[1] + oy) * L.bn[0] + ox;
             }
             float *dst = L.le + (obox * B + obb) * a.ldk + ph_half * nsum;
+            if (a.kind == kTcL2L) {
 #pragma unroll
-            for (int j = 0; j < NS; ++j)
-                if (j < nsum && ph_half * nsum + j < K) dst[j] = acc[j];
+                for (int j = 0; j < NS; ++j)
+                    if (j < nsum && ph_half * nsum + j < K) dst[j] += acc[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    if (j < nsum && ph_half * nsum + j < K) dst[j] = acc[j];
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -859,40 +911,55 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
         GF_TRY(plan->arena.alloc(&dev, hb.size()));
         GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
     }
+    // M2M into level l (entries [0, L]) and L2L into level l (entries [L+1, 2L+1])
+    if (F->tab->m2m_tc && F->tab->l2l_tc) {
+        std::vector<TcLevel> h(2 * (F->L + 1));
+        memset(h.data(), 0, h.size() * sizeof(TcLevel));
+        for (int l = 2; l <= F->L; ++l) {
+            if (l < F->L) {
+                const FmmLevel &pa = F->lev[l], &ch = F->lev[l + 1];
+                TcLevel &t = h[l];
+                t.me = (const float *)ch.me;
+                t.le = (float *)pa.me;
+                for (int d = 0; d < 3; ++d) {
+                    t.blo[d] = pa.slo[d];
+                    t.bn[d] = pa.sn[d];
+                    t.clo[d] = ch.slo[d];
+                    t.cn[d] = ch.sn[d];
+                }
+                t.cls_off[0] = 0;
+                for (int c = 1; c <= 8; ++c) t.cls_off[c] = pa.ns;
+            }
+            if (l > 2) {
+                const FmmLevel &lv = F->lev[l], &pa = F->lev[l - 1];
+                TcLevel &t = h[F->L + 1 + l];
+                t.me = (const float *)pa.le;
+                t.le = (float *)lv.le;
+                t.order = lv.m2l_order;
+                t.tkey = lv.tkey;
+                t.tparent = lv.tparent;
+                for (int d = 0; d < 3; ++d) {
+                    t.blo[d] = lv.slo[d];
+                    t.bn[d] = lv.sn[d];
+                }
+                for (int c = 0; c <= 8; ++c) t.cls_off[c] = lv.cls_off[c];
+            }
+        }
+        F->tc_xlate_host.assign(reinterpret_cast<unsigned char *>(h.data()),
+                                reinterpret_cast<unsigned char *>(h.data() + h.size()));
+        GF_TRY(plan->arena.alloc(&F->tc_xlate, F->tc_xlate_host.size()));
+        GF_CUDA(cudaMemcpyAsync(F->tc_xlate, F->tc_xlate_host.data(), F->tc_xlate_host.size(),
+                                cudaMemcpyHostToDevice, plan->arena.stream));
+    }
     return GF_OK;
 }
 
 namespace {
 
-gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
-    FmmPlan *F = plan->fmm;
-    const Tables *T = F->tab;
-    const int Npad = T->tc_npad;
-    TcArgs a;
-    a.lv = reinterpret_cast<const TcLevel *>(adj ? F->tc_levels_adj : F->tc_levels);
-    a.lmin = 2;
-    a.K = F->K;
-    a.ldk = F->KS;
-    a.B = B;
-    a.Npad = Npad;
-    a.nck = T->tc_nck;
-    a.nst = tc_stages(Npad);
-    a.img = adj ? T->am2l_tc : T->m2l_tc;
-    a.status = plan->d_status;
-    const int nbox = 128 / B;
-    int tiles = 0, e = 0;
-    for (int l = 2; l <= F->L; ++l)
-        for (int c = 0; c < 8; ++c, ++e) {
-            a.tile_begin[e] = tiles;
-            const int64_t *off = adj ? F->scls_off[l] : F->lev[l].cls_off;
-            const int64_t cnt = (adj || F->lev[l].nt > 0) ? off[c + 1] - off[c] : 0;
-            tiles += (int)((cnt + nbox - 1) / nbox);
-        }
-    a.tile_begin[e] = tiles;
-    a.nent = e;
+gf_status tc_launch(TcArgs &a, int tiles, cudaStream_t st) {
     if (tiles == 0) return GF_OK;
-    const size_t shm = tc_smem_bytes(Npad);
-    const int nsum = Npad / 2;
+    const size_t shm = tc_smem_bytes(a.Npad);
+    const int nsum = a.Npad / 2;
 #define GF_TC_LAUNCH(NS)                                                  \
     do {                                                                  \
         GF_TRY(ensure_smem(m2l_tc<NS>, shm));                             \
@@ -909,6 +976,67 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
 #undef GF_TC_LAUNCH
     GF_KERNEL_DONE();
     return GF_OK;
+}
+
+TcArgs tc_args(gf_plan_s *plan, int B) {
+    FmmPlan *F = plan->fmm;
+    const Tables *T = F->tab;
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.K = F->K;
+    a.ldk = F->KS;
+    a.B = B;
+    a.Npad = T->tc_npad;
+    a.nck = T->tc_nck;
+    a.nst = tc_stages(T->tc_npad);
+    a.status = plan->d_status;
+    return a;
+}
+
+gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const Tables *T = F->tab;
+    TcArgs a = tc_args(plan, B);
+    a.lv = reinterpret_cast<const TcLevel *>(adj ? F->tc_levels_adj : F->tc_levels);
+    a.lmin = 2;
+    a.kind = kTcM2L;
+    a.noff = 189;
+    a.img = adj ? T->am2l_tc : T->m2l_tc;
+    const int nbox = 128 / B;
+    int tiles = 0, e = 0;
+    for (int l = 2; l <= F->L; ++l)
+        for (int c = 0; c < 8; ++c, ++e) {
+            a.tile_begin[e] = tiles;
+            const int64_t *off = adj ? F->scls_off[l] : F->lev[l].cls_off;
+            const int64_t cnt = (adj || F->lev[l].nt > 0) ? off[c + 1] - off[c] : 0;
+            tiles += (int)((cnt + nbox - 1) / nbox);
+        }
+    a.tile_begin[e] = tiles;
+    a.nent = e;
+    return tc_launch(a, tiles, st);
+}
+
+// M2M (kind 0) or L2L (kind 1) into `level` on the tensor cores.
+gf_status xlate_run_tc(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const Tables *T = F->tab;
+    TcArgs a = tc_args(plan, B);
+    const TcLevel *base = reinterpret_cast<const TcLevel *>(F->tc_xlate);
+    a.lv = base + (kind == 0 ? 0 : F->L + 1);
+    a.lmin = level;
+    a.kind = kind == 0 ? kTcM2M : kTcL2L;
+    a.noff = kind == 0 ? 8 : 1;
+    a.img = kind == 0 ? T->m2m_tc : T->l2l_tc;
+    const TcLevel &h = reinterpret_cast<const TcLevel *>(F->tc_xlate_host.data())[(kind == 0 ? 0 : F->L + 1) + level];
+    const int nbox = 128 / B;
+    int tiles = 0;
+    for (int c = 0; c < 8; ++c) {
+        a.tile_begin[c] = tiles;
+        tiles += (int)((h.cls_off[c + 1] - h.cls_off[c] + nbox - 1) / nbox);
+    }
+    a.tile_begin[8] = tiles;
+    a.nent = 8;
+    return tc_launch(a, tiles, st);
 }
 
 }  // namespace
@@ -968,6 +1096,10 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st
 template <class Ts, class Tc>
 gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
+    // mixed precision: forward M2M / L2L on the tensor cores (3xTF32)
+    if (sizeof(Ts) == 4 && sizeof(Tc) == 4 && (kind == 0 || kind == 1) && F->tc_xlate &&
+        !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 && tc_stages(F->tab->tc_npad) >= 2)
+        return xlate_run_tc(plan, level, kind, B, st);
     XArgs a;
     a.K = F->K;
     a.ldk = F->KS;

@@ -20,7 +20,9 @@ gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st);
 template <class T>
 gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st);
 
-// Batched translations on the SIMT cores (Ts = storage, Tc = arithmetic):
+// Batched translations (Ts = storage, Tc = arithmetic); in mixed precision
+// the forward M2M / L2L run on the tensor cores (3xTF32), otherwise on the
+// SIMT cores:
 //   kind 0  M2M into `level` from level + 1 (store)
 //   kind 1  L2L into `level` from level - 1 (update)
 //   kind 2  M2M^T into `level` from level - 1 (update), over source boxes
