@@ -346,6 +346,69 @@ gf_status launch_p2m_fused_b(gf_plan_s *plan, const void *rho, int rho_f32, int 
     return GF_OK;
 }
 
+// Leaf-blocked densities only (the P2M then runs on the tensor cores):
+// thread x of block (y, z) copies the BV voxels of row (y, z) of leaf x --
+// consecutive threads read consecutive voxels of the grid row and each
+// writes one BV-wide piece of its leaf's mass row.  Grid: (ceil(nLx/128),
+// nLy*BV, nLz*BV*B).
+template <class T, int BV>
+__global__ void __launch_bounds__(128)
+block_rows(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int64_t nz, int64_t vx, int64_t vy,
+           int64_t vz, Block3 blk, int B, T *__restrict__ mass, int *__restrict__ status) {
+    constexpr int b3 = BV * BV * BV;
+    const int64_t lx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (lx >= blk.n[0]) return;
+    const int yv = blockIdx.y;
+    const int64_t zb = blockIdx.z;
+    const int64_t nzv = blk.n[2] * BV;
+    const int zv = (int)(zb % nzv);
+    const int bb = (int)(zb / nzv);
+    const int64_t j = blk.lo[1] * BV + yv - vy, k = blk.lo[2] * BV + zv - vz;
+    const int64_t i0 = (blk.lo[0] + lx) * BV - vx;
+    const bool row_in = j >= 0 && j < ny && k >= 0 && k < nz;
+    const int64_t base = (int64_t)bb * nx * ny * nz + (k * ny + j) * nx;
+    T m[BV];
+    bool bad = false;
+#pragma unroll
+    for (int x = 0; x < BV; ++x) {
+        const int64_t i = i0 + x;
+        T v = T(0);
+        if (row_in && i >= 0 && i < nx) {
+            const double r = rho_f32 ? (double)reinterpret_cast<const float *>(rho)[base + i]
+                                     : reinterpret_cast<const double *>(rho)[base + i];
+            bad |= !isfinite(r);
+            v = (T)r;
+        }
+        m[x] = v;
+    }
+    if (bad) atomicOr(status, 1);
+    const int64_t leaf = ((int64_t)(zv / BV) * blk.n[1] + yv / BV) * blk.n[0] + lx;
+    T *dst = mass + (leaf * B + bb) * b3 + ((zv % BV) * BV + yv % BV) * BV;
+    if constexpr (BV == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(m[0], m[1], m[2], m[3]);
+    } else {
+#pragma unroll
+        for (int x = 0; x < BV; ++x) dst[x] = m[x];
+    }
+}
+
+template <class T, int BV>
+gf_status launch_blocking(gf_plan_s *plan, const void *rho, int rho_f32, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const Block3 blk = block_of(F->lev[F->L]);
+    const int64_t gz = blk.n[2] * BV * B;
+    if (blk.n[1] * BV > 65535 || gz > 65535) {
+        set_error("leaf block too large for the density re-blocking grid");
+        return GF_ERR_UNSUPPORTED;
+    }
+    const dim3 grid(ceil_div(blk.n[0], 128), (unsigned)(blk.n[1] * BV), (unsigned)gz);
+    block_rows<T, BV><<<grid, 128, 0, st>>>(rho, rho_f32, plan->grid.n[0], plan->grid.n[1], plan->grid.n[2],
+                                            F->voff[0], F->voff[1], F->voff[2], blk, B, (T *)F->mass,
+                                            plan->d_status);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
 template <class T>
 gf_status launch_p2m_fused(gf_plan_s *plan, const void *rho, int rho_f32, int B, cudaStream_t st) {
     switch (plan->fmm->b) {
@@ -892,9 +955,17 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     const Tables *tab = F->tab;
     const bool fused = p2m_fused_ok<T>(F);
     if (fused) {
-        // a0 + a3: leaf-blocked densities and P2M in one pass (timed as P2M)
+        // a0 + a3: leaf-blocked densities and P2M (timed as P2M): on the
+        // tensor cores for 4^3-voxel leaves in mixed precision, else fused
         stage_mark(plan, 1, st);
-        GF_TRY(launch_p2m_fused<T>(plan, rho, rho_dtype == GF_DTYPE_F32, B, st));
+        const Block3 lb = block_of(F->lev[F->L]);
+        if (sizeof(T) == 4 && F->b == 4 && p2m_tc_ok(plan, B) && lb.n[1] * 4 <= 65535 &&
+            lb.n[2] * 4 * B <= 65535) {
+            GF_TRY((launch_blocking<T, 4>(plan, rho, rho_dtype == GF_DTYPE_F32, B, st)));
+            GF_TRY(p2m_run_tc(plan, B, st));
+        } else {
+            GF_TRY(launch_p2m_fused<T>(plan, rho, rho_dtype == GF_DTYPE_F32, B, st));
+        }
     }
     // a0: leaf-blocked densities
     if (!fused) {

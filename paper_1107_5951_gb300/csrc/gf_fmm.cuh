@@ -87,7 +87,8 @@ struct FmmPlan {
     int64_t scls_off[kMaxLevels + 1][9] = {};
     void *tc_levels_adj = nullptr;
     std::vector<unsigned char> tc_levels_adj_host;
-    void *tc_xlate = nullptr;                    // tensor-core M2M / L2L level tables
+    float *p2m_tc = nullptr;                     // tensor-core P2M operator image
+    void *tc_xlate = nullptr;                    // tensor-core M2M / L2L / P2M level tables
     std::vector<unsigned char> tc_xlate_host;
 };
 

@@ -44,7 +44,8 @@ __host__ __device__ __forceinline__ uint32_t swz64(int row, int k) {
 // With all_used (M2M / L2L: 8 octant operators) every slot is filled; for the
 // M2L's 343 slots only offsets of max-norm >= 2 are.
 __global__ void build_tc_images(const double *__restrict__ m2l_d, int K, int Npad, int nck,
-                                float *__restrict__ img, int all_used = 0) {
+                                float *__restrict__ img, int all_used = 0, int Kin = 0) {
+    if (Kin == 0) Kin = K;   // operators [slot][Kin][K], input-component major
     const int off = blockIdx.x;
     const int dx = off % 7 - 3, dy = (off / 7) % 7 - 3, dz = off / 49 - 3;
     const bool used = all_used || max(abs(dx), max(abs(dy), abs(dz))) >= 2;
@@ -54,7 +55,7 @@ __global__ void build_tc_images(const double *__restrict__ m2l_d, int K, int Npa
         float *lo = hi + tile;
         for (int e = threadIdx.x; e < Npad * 16; e += blockDim.x) {
             const int n = e / 16, kk = e % 16, kin = 16 * c + kk;
-            const double v = (used && n < K && kin < K) ? m2l_d[(size_t)off * K * K + (size_t)kin * K + n] : 0.0;
+            const double v = (used && n < K && kin < Kin) ? m2l_d[(size_t)off * Kin * K + (size_t)kin * K + n] : 0.0;
             const float f = (float)v;
             const float h = __uint_as_float(to_tf32(f));
             const float l = __uint_as_float(to_tf32(f - h));
@@ -450,8 +451,9 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 // list, all levels in one launch), the M2M into one level (the 8 child
 // positions; targets = every parent box of the dense block, one class) and
 // the L2L into one level (one step: the parent; targets = observer boxes
-// grouped by their position in the parent, which selects the operator).
-enum TcKind { kTcM2L = 0, kTcM2M = 1, kTcL2L = 2 };
+// grouped by their position in the parent, which selects the operator);
+// and the P2M (one step: the leaf's b^3 voxel masses times the P2M matrix).
+enum TcKind { kTcM2L = 0, kTcM2M = 1, kTcL2L = 2, kTcP2M = 3 };
 
 struct TcLevel {
     const float *me;      // input rows (M2L: ME_l or adjoint LE_l duals; M2M: ME_{l+1}; L2L: LE_{l-1})
@@ -473,6 +475,8 @@ struct TcArgs {
     int tile_begin[kMaxLevels * 8 + 1];
     int K, ldk, B, Npad, nck, nst;
     int kind, noff;             // TcKind; offsets per target (189, 8 or 1)
+    int ntiles;                 // tiles of the launch (persistent kinds)
+    int kin, ldin;              // input coefficients per row and input row stride
     const float *img;
     int *status;
 };
@@ -572,22 +576,39 @@ m2l_tc(TcArgs a) {
     __shared__ __align__(8) uint64_t bank_full[2], bank_empty[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    __shared__ uint32_t omask[6];   // offsets with at least one source box in this tile
+    __shared__ uint32_t omask[6];   // M2L: offsets with at least one source box in this tile
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int K = a.K, B = a.B, Npad = a.Npad, nck = a.nck, NST = a.nst;
     const int nsum = Npad / 2;
     const uint32_t b_bytes = 2u * (uint32_t)Npad * 64u;
     const uint32_t stage_bytes = tc_stage_bytes(Npad);
     volatile int *abortp = &abort_flag;
-
-    // which (level, class, tile) this CTA owns
-    int e = 0;
-    while (e + 1 < a.nent && a.tile_begin[e + 1] <= (int)blockIdx.x) ++e;
-    const int level = a.lmin + e / 8, cls = e % 8;
-    const int tile = (int)blockIdx.x - a.tile_begin[e];
-    const TcLevel &L = a.lv[level];
-    const int64_t cbeg = L.cls_off[cls], ccnt = L.cls_off[cls + 1] - cbeg;
     const int nbox = 128 / B;
+    const int noff = a.noff;
+
+    // The M2L takes one tile per CTA (its offsets are skipped where a whole
+    // tile has no source); the other kinds are persistent: CTA b takes tiles
+    // b, b + gridDim.x, ... and runs every offset of each.
+    const bool persist = a.kind != kTcM2L;
+    const int ntl = persist ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 1;
+    struct Ctx {
+        const TcLevel *L;
+        int cls, tile;
+        int64_t cbeg, ccnt;
+    };
+    // (level, class, tile within the class) of this CTA's j-th tile
+    auto ctx_of = [&](int j) -> Ctx {
+        const int t = (int)blockIdx.x + (persist ? j * (int)gridDim.x : 0);
+        int e = 0;
+        while (e + 1 < a.nent && a.tile_begin[e + 1] <= t) ++e;
+        Ctx c;
+        c.L = &a.lv[a.lmin + e / 8];
+        c.cls = e % 8;
+        c.tile = t - a.tile_begin[e];
+        c.cbeg = c.L->cls_off[c.cls];
+        c.ccnt = c.L->cls_off[c.cls + 1] - c.cbeg;
+        return c;
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
@@ -609,58 +630,68 @@ m2l_tc(TcArgs a) {
     }
     if (tid < 6) omask[tid] = 0;
 
-    // producer role: column `row` of the tile
+    // producer role: column `row` of the current tile
     const int row = tid & 127;
     const int slot = row / B, bb = row - slot * B;
-    const int64_t sidx = (int64_t)tile * nbox + slot;
+    Ctx pc = ctx_of(0);
     int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
-    if (warp < 4 && slot < nbox && sidx < ccnt) {
-        if (a.kind == kTcM2M) {
+    auto set_target = [&]() {
+        tbox = -1;
+        tc0 = tc1 = tc2 = 0;
+        const TcLevel &L = *pc.L;
+        const int64_t sidx = (int64_t)pc.tile * nbox + slot;
+        if (warp >= 4 || slot >= nbox || sidx >= pc.ccnt) return;
+        if (a.kind == kTcP2M) {
+            tbox = sidx;
+        } else if (a.kind == kTcM2M) {
             tbox = sidx;
             tc0 = sidx % L.bn[0];
             tc1 = (sidx / L.bn[0]) % L.bn[1];
             tc2 = sidx / (L.bn[0] * L.bn[1]);
         } else if (a.kind == kTcL2L) {
-            tbox = L.order[cbeg + sidx];
+            tbox = L.order[pc.cbeg + sidx];
         } else if (!L.adj) {
-            tbox = L.order[cbeg + sidx];
+            tbox = L.order[pc.cbeg + sidx];
             const uint64_t key = L.tkey[tbox];
             tc0 = dm(key, 0) - L.blo[0];
             tc1 = dm(key, 1) - L.blo[1];
             tc2 = dm(key, 2) - L.blo[2];
         } else {
-            class_box(cls, L.blo, L.bn, sidx, tc0, tc1, tc2);
+            class_box(pc.cls, L.blo, L.bn, sidx, tc0, tc1, tc2);
             tbox = (tc2 * L.bn[1] + tc1) * L.bn[0] + tc0;
         }
-    }
-    // input row of this column at offset oi (-1: none)
+    };
+    set_target();
+    // input row of this column at offset oi of the current tile (-1: none)
     auto src_row = [&](int oi) -> int64_t {
         if (tbox < 0) return -1;
+        const TcLevel &L = *pc.L;
         if (a.kind == kTcM2M) {   // child at position oi of this parent
             const int64_t cx = 2 * (tc0 + L.blo[0]) + (oi & 1) - L.clo[0],
                           cy = 2 * (tc1 + L.blo[1]) + ((oi >> 1) & 1) - L.clo[1],
                           cz = 2 * (tc2 + L.blo[2]) + ((oi >> 2) & 1) - L.clo[2];
             if (cx >= 0 && cy >= 0 && cz >= 0 && cx < L.cn[0] && cy < L.cn[1] && cz < L.cn[2])
-                return (((cz * L.cn[1] + cy) * L.cn[0] + cx) * B + bb) * a.ldk;
+                return (((cz * L.cn[1] + cy) * L.cn[0] + cx) * B + bb) * a.ldin;
             return -1;
         }
-        if (a.kind == kTcL2L) return ((int64_t)L.tparent[tbox] * B + bb) * a.ldk;
+        if (a.kind == kTcL2L) return ((int64_t)L.tparent[tbox] * B + bb) * a.ldin;
+        if (a.kind == kTcP2M) return (tbox * B + bb) * a.ldin;
+        const int cls = pc.cls;
         const int64_t sx = tc0 + c_il[cls][oi][0], sy = tc1 + c_il[cls][oi][1], sz = tc2 + c_il[cls][oi][2];
         if (!L.adj) {
             if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
-                return (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldk;
+                return (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldin;
             return -1;
         }
         const int64_t wx = sx + L.blo[0] - L.mlo[0], wy = sy + L.blo[1] - L.mlo[1], wz = sz + L.blo[2] - L.mlo[2];
         if (wx >= 0 && wy >= 0 && wz >= 0 && wx < L.mn[0] && wy < L.mn[1] && wz < L.mn[2]) {
             const int32_t m = L.imap[(wz * L.mn[1] + wy) * L.mn[0] + wx];
-            if (m >= 0) return ((int64_t)m * B + bb) * a.ldk;
+            if (m >= 0) return ((int64_t)m * B + bb) * a.ldin;
         }
         return -1;
     };
     __syncthreads();
-    const int noff = a.noff;
-    if (warp < 4) {
+    if (!persist && warp < 4) {
         for (int oi = 0; oi < noff; ++oi) {
             const unsigned any = __ballot_sync(0xffffffffu, src_row(oi) >= 0);
             if (lane == 0 && any) atomicOr(&omask[oi >> 5], 1u << (oi & 31));
@@ -670,24 +701,42 @@ m2l_tc(TcArgs a) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tslot;
-    int G = 0;
-    for (int w = 0; w < 6; ++w) G += __popc(omask[w]);
-    const int iters = G * nck;
-    // the oi-th valid offset in ascending order, advanced incrementally
+    int G = noff;   // offsets per tile
+    if (!persist) {
+        G = 0;
+        for (int w = 0; w < 6; ++w) G += __popc(omask[w]);
+    }
+    const int offs = G * ntl;        // offsets run by this CTA
+    const int iters = offs * nck;    // stages run by this CTA
+    // the next offset to run after oi within a tile (noff when none is left)
     auto next_off = [&](int oi) -> int {
         for (++oi; oi < noff; ++oi)
-            if (omask[oi >> 5] & (1u << (oi & 31))) return oi;
-        return 189;
+            if (persist || (omask[oi >> 5] & (1u << (oi & 31)))) return oi;
+        return noff;
     };
 
     if (warp < 4) {
         // ---------------- A producers
-        int oi = next_off(-1), c = 0;
-        int64_t src = src_row(oi);
-        float4 cur[4], nxt[4];
+        int qj = 0, qo = next_off(-1), qc = 0;
+        int64_t qs = qo < noff ? src_row(qo) : -1;
+        auto take = [&](int &c_out, int64_t &s_out) {   // next chunk in sequence
+            c_out = qc;
+            s_out = qs;
+            if (++qc == nck) {
+                qc = 0;
+                qo = next_off(qo);
+                if (qo >= noff && ++qj < ntl) {
+                    pc = ctx_of(qj);
+                    set_target();
+                    qo = next_off(-1);
+                }
+                qs = (qj < ntl && qo < noff) ? src_row(qo) : -1;
+            }
+        };
+        const float *me = pc.L->me;   // every tile of a launch reads the same input array
         auto load = [&](int64_t sr, int cc, float4 *v) {
             if (sr >= 0) {
-                const float4 *p4 = reinterpret_cast<const float4 *>(L.me + sr + 16 * cc);
+                const float4 *p4 = reinterpret_cast<const float4 *>(me + sr + 16 * cc);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) v[q] = __ldg(p4 + q);
             } else {
@@ -695,19 +744,18 @@ m2l_tc(TcArgs a) {
                 for (int q = 0; q < 4; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         };
-        if (iters > 0) load(src, 0, cur);
+        float4 cur[4], nxt[4];
+        int c0;
+        int64_t s0;
+        take(c0, s0);
+        if (iters > 0) load(s0, c0, cur);
         int s = 0;
         uint32_t ph = 0;
         for (int it = 0; it < iters; ++it) {
-            // prefetch the next chunk
-            int noi = oi, nc = c + 1;
-            int64_t nsrc = src;
-            if (nc == nck) {
-                nc = 0;
-                noi = next_off(oi);
-                nsrc = noi < 189 ? src_row(noi) : -1;
-            }
-            if (it + 1 < iters) load(nsrc, nc, nxt);
+            int c1;
+            int64_t s1;
+            take(c1, s1);   // prefetch the next chunk
+            if (it + 1 < iters) load(s1, c1, nxt);
             if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
             unsigned char *stage = base + (size_t)s * stage_bytes;
 #pragma unroll
@@ -716,8 +764,8 @@ m2l_tc(TcArgs a) {
                 uint32_t h[4], l[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int kin = 16 * c + 4 * q + j;
-                    const float x = kin < K ? x4[j] : 0.f;
+                    const int kin = 16 * c0 + 4 * q + j;
+                    const float x = kin < a.kin ? x4[j] : 0.f;
                     h[j] = to_tf32(x);
                     l[j] = to_tf32(x - __uint_as_float(h[j]));
                 }
@@ -729,9 +777,7 @@ m2l_tc(TcArgs a) {
             mbar_arrive(smem_u32(&afull[s]));
 #pragma unroll
             for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
-            oi = noi;
-            c = nc;
-            src = nsrc;
+            c0 = c1;
             if (++s == NST) {
                 s = 0;
                 ph ^= 1;
@@ -752,7 +798,7 @@ m2l_tc(TcArgs a) {
                 const unsigned char *stage = base + (size_t)s * stage_bytes;
                 const uint32_t sa = smem_u32(stage), sb = smem_u32(stage + kTcA);
                 const uint32_t d = tmem + (uint32_t)(g & 1) * 256u;
-                const int nk8 = min(2, (K - 16 * c + 7) / 8);
+                const int nk8 = min(2, (a.kin - 16 * c + 7) / 8);
                 for (int ks = 0; ks < nk8; ++ks) {
                     const uint32_t ko = ks * 32;
                     const uint64_t ah = umma_desc64(sa + ko), al = umma_desc64(sa + 8192 + ko);
@@ -779,18 +825,23 @@ m2l_tc(TcArgs a) {
     } else if (warp == 5) {
         // ---------------- operator images
         if (lane == 0) {
-            int s = 0, c = 0;
+            int s = 0, c = 0, bj = 0;
             int oi = next_off(-1);
+            int bcls = pc.cls;
             uint32_t ph = 0;
             int last = -1;
             for (int it = 0; it < iters; ++it) {
                 if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
                 int slot_off;
                 if (a.kind == kTcM2L) {
-                    const int dx = c_il[cls][oi][0], dy = c_il[cls][oi][1], dz = c_il[cls][oi][2];
+                    const int dx = c_il[bcls][oi][0], dy = c_il[bcls][oi][1], dz = c_il[bcls][oi][2];
                     slot_off = (dz + 3) * 49 + (dy + 3) * 7 + (dx + 3);
+                } else if (a.kind == kTcM2M) {
+                    slot_off = oi;     // child position
+                } else if (a.kind == kTcL2L) {
+                    slot_off = bcls;   // the box's own position in its parent
                 } else {
-                    slot_off = a.kind == kTcM2M ? oi : cls;   // child position / own position
+                    slot_off = 0;
                 }
                 unsigned char *stage = base + (size_t)s * stage_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bfull[s])),
@@ -805,6 +856,10 @@ m2l_tc(TcArgs a) {
                 if (++c == nck) {
                     c = 0;
                     oi = next_off(oi);
+                    if (oi >= noff && ++bj < ntl) {
+                        bcls = ctx_of(bj).cls;
+                        oi = next_off(-1);
+                    }
                 }
                 if (++s == NST) {
                     s = 0;
@@ -815,66 +870,75 @@ m2l_tc(TcArgs a) {
             if (last >= 0) mbar_wait(smem_u32(&bfull[last % NST]), (uint32_t)((last / NST) & 1));
         }
     }
-    // ---------------- promoters (warps 6-13) and the write-back
+    // ---------------- promoters (warps 6-13) and the write-back of each tile
     const int pw = warp - 6;
     const int pq = warp & 3, ph_half = pw >> 2;   // TMEM lane quarter, column half
-    float acc[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) acc[j] = 0.f;
     bool ok = true;
     if (pw >= 0) {
-        for (int g = 0; g < G; ++g) {
-            bool w_ok = mbar_wait_ab(smem_u32(&bank_full[g & 1]), (g >> 1) & 1, abortp);
-            w_ok = __all_sync(0xffffffffu, w_ok);   // tcgen05.ld is warp-collective
-            if (!w_ok) {
+        float acc[NS];
+        int gg = 0;   // offsets promoted so far (bank gg & 1)
+        for (int j = 0; j < ntl && ok; ++j) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) acc[q] = 0.f;
+            for (int g = 0; g < G; ++g, ++gg) {
+                bool w_ok = mbar_wait_ab(smem_u32(&bank_full[gg & 1]), (gg >> 1) & 1, abortp);
+                w_ok = __all_sync(0xffffffffu, w_ok);   // tcgen05.ld is warp-collective
+                if (!w_ok) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t tb =
+                    tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(gg & 1) * 256u + (uint32_t)(ph_half * nsum);
+#pragma unroll
+                for (int j0 = 0; j0 < NS; j0 += 8) {
+                    if (j0 < nsum) {
+                        float t[8];
+                        tmem_ld8(tb + j0, t);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc[j0 + q] += t[q];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bank_empty[gg & 1]));
+            }
+            if (!ok || *abortp) {
                 ok = false;
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t tb = tmem + ((uint32_t)(pq * 32) << 16) + (uint32_t)(g & 1) * 256u + (uint32_t)(ph_half * nsum);
+            // write this tile's rows
+            const Ctx oc = ctx_of(j);
+            const TcLevel &L = *oc.L;
+            const int r = pq * 32 + lane;
+            const int oslot = r / B, obb = r - oslot * B;
+            const int64_t os = (int64_t)oc.tile * nbox + oslot;
+            if (oslot < nbox && os < oc.ccnt) {
+                int64_t obox;
+                if (a.kind == kTcM2M || a.kind == kTcP2M) {   // dense targets
+                    obox = os;
+                } else if (!L.adj) {
+                    obox = L.order[oc.cbeg + os];
+                } else {
+                    int64_t ox, oy, oz;
+                    class_box(oc.cls, L.blo, L.bn, os, ox, oy, oz);
+                    obox = (oz * L.bn[1] + oy) * L.bn[0] + ox;
+                }
+                float *dst = L.le + (obox * B + obb) * a.ldk + ph_half * nsum;
+                if (a.kind == kTcL2L) {
 #pragma unroll
-            for (int j0 = 0; j0 < NS; j0 += 8) {
-                if (j0 < nsum) {
-                    float t[8];
-                    tmem_ld8(tb + j0, t);
+                    for (int q = 0; q < NS; ++q)
+                        if (q < nsum && ph_half * nsum + q < K) dst[q] += acc[q];
+                } else {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[j0 + j] += t[j];
+                    for (int q = 0; q < NS; ++q)
+                        if (q < nsum && ph_half * nsum + q < K) dst[q] = acc[q];
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bank_empty[g & 1]));
         }
     }
     const bool failed = __syncthreads_or(!ok || abort_flag);
     if (failed && tid == 0) atomicOr(a.status + 1, 1);
-    if (pw >= 0 && !failed) {
-        const int r = pq * 32 + lane;
-        const int oslot = r / B, obb = r - oslot * B;
-        const int64_t os = (int64_t)tile * nbox + oslot;
-        if (oslot < nbox && os < ccnt) {
-            int64_t obox;
-            if (a.kind == kTcM2M) {
-                obox = os;
-            } else if (!L.adj) {
-                obox = L.order[cbeg + os];
-            } else {
-                int64_t ox, oy, oz;
-                class_box(cls, L.blo, L.bn, os, ox, oy, oz);
-                obox = (oz * L.bn[1] + oy) * L.bn[0] + ox;
-            }
-            float *dst = L.le + (obox * B + obb) * a.ldk + ph_half * nsum;
-            if (a.kind == kTcL2L) {
-#pragma unroll
-                for (int j = 0; j < NS; ++j)
-                    if (j < nsum && ph_half * nsum + j < K) dst[j] += acc[j];
-            } else {
-#pragma unroll
-                for (int j = 0; j < NS; ++j)
-                    if (j < nsum && ph_half * nsum + j < K) dst[j] = acc[j];
-            }
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
@@ -911,9 +975,10 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
         GF_TRY(plan->arena.alloc(&dev, hb.size()));
         GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
     }
-    // M2M into level l (entries [0, L]) and L2L into level l (entries [L+1, 2L+1])
+    // M2M into level l (entries [0, L]), L2L into level l (entries [L+1, 2L+1])
+    // and the P2M (entry 2L+2)
     if (F->tab->m2m_tc && F->tab->l2l_tc) {
-        std::vector<TcLevel> h(2 * (F->L + 1));
+        std::vector<TcLevel> h(2 * (F->L + 1) + 1);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
         for (int l = 2; l <= F->L; ++l) {
             if (l < F->L) {
@@ -945,6 +1010,22 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
                 for (int c = 0; c <= 8; ++c) t.cls_off[c] = lv.cls_off[c];
             }
         }
+        {
+            const FmmLevel &lv = F->lev[F->L];
+            TcLevel &t = h[2 * (F->L + 1)];
+            t.me = (const float *)F->mass;
+            t.le = (float *)lv.me;
+            t.cls_off[0] = 0;
+            for (int c = 1; c <= 8; ++c) t.cls_off[c] = lv.ns;
+            const int b3 = F->b * F->b * F->b;
+            if (b3 % 16 == 0) {
+                const int nck_in = b3 / 16;
+                GF_TRY(plan->arena.alloc_n(&F->p2m_tc, (size_t)nck_in * 2 * F->tab->tc_npad * 16));
+                build_tc_images<<<1, 256, 0, plan->arena.stream>>>(F->p2m_d, F->K, F->tab->tc_npad, nck_in,
+                                                                   F->p2m_tc, 1, b3);
+                GF_KERNEL_DONE();
+            }
+        }
         F->tc_xlate_host.assign(reinterpret_cast<unsigned char *>(h.data()),
                                 reinterpret_cast<unsigned char *>(h.data() + h.size()));
         GF_TRY(plan->arena.alloc(&F->tc_xlate, F->tc_xlate_host.size()));
@@ -958,12 +1039,15 @@ namespace {
 
 gf_status tc_launch(TcArgs &a, int tiles, cudaStream_t st) {
     if (tiles == 0) return GF_OK;
+    a.ntiles = tiles;
+    // the M2L runs one tile per CTA; the other kinds loop over tiles, one CTA per SM
+    const int grid = a.kind == kTcM2L ? tiles : std::min(tiles, 152);
     const size_t shm = tc_smem_bytes(a.Npad);
     const int nsum = a.Npad / 2;
 #define GF_TC_LAUNCH(NS)                                                  \
     do {                                                                  \
         GF_TRY(ensure_smem(m2l_tc<NS>, shm));                             \
-        m2l_tc<NS><<<tiles, kTcThreads, shm, st>>>(a);                    \
+        m2l_tc<NS><<<grid, kTcThreads, shm, st>>>(a);                     \
     } while (0)
     if (nsum <= 32)
         GF_TC_LAUNCH(32);
@@ -989,6 +1073,8 @@ TcArgs tc_args(gf_plan_s *plan, int B) {
     a.Npad = T->tc_npad;
     a.nck = T->tc_nck;
     a.nst = tc_stages(T->tc_npad);
+    a.kin = F->K;
+    a.ldin = F->KS;
     a.status = plan->d_status;
     return a;
 }
@@ -1013,6 +1099,27 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
         }
     a.tile_begin[e] = tiles;
     a.nent = e;
+    return tc_launch(a, tiles, st);
+}
+
+gf_status p2m_run_tc_impl(gf_plan_s *plan, int B, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    TcArgs a = tc_args(plan, B);
+    const int b3 = F->b * F->b * F->b;
+    a.lv = reinterpret_cast<const TcLevel *>(F->tc_xlate) + 2 * (F->L + 1);
+    a.lmin = 0;
+    a.kind = kTcP2M;
+    a.noff = 1;
+    a.kin = b3;
+    a.ldin = b3;
+    a.nck = b3 / 16;
+    a.img = F->p2m_tc;
+    const int nbox = 128 / B;
+    const int64_t ns = F->lev[F->L].ns;
+    const int tiles = (int)((ns + nbox - 1) / nbox);
+    a.tile_begin[0] = 0;
+    for (int c = 1; c <= 8; ++c) a.tile_begin[c] = tiles;
+    a.nent = 8;
     return tc_launch(a, tiles, st);
 }
 
@@ -1092,6 +1199,14 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st
             return GF_ERR_UNSUPPORTED;
     }
 }
+
+bool p2m_tc_ok(const gf_plan_s *plan, int B) {
+    const FmmPlan *F = plan->fmm;
+    return F && F->mixed && F->p2m_tc && F->tc_xlate && !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
+           tc_stages(F->tab->tc_npad) >= 2;
+}
+
+gf_status p2m_run_tc(gf_plan_s *plan, int B, cudaStream_t st) { return p2m_run_tc_impl(plan, B, st); }
 
 template <class Ts, class Tc>
 gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st) {

@@ -33,4 +33,10 @@ gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_
 // Plan-time set-up of the tensor-core path (level descriptors on the device).
 gf_status m2l_tc_prepare(gf_plan_s *plan);
 
+// P2M on the tensor cores (mixed precision, leaves of 16k voxels): ME of
+// every leaf = P^T x its leaf-blocked masses.  p2m_tc_ok says whether the
+// plan and batch size allow it.
+bool p2m_tc_ok(const gf_plan_s *plan, int B);
+gf_status p2m_run_tc(gf_plan_s *plan, int B, cudaStream_t st);
+
 }  // namespace gf
