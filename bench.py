@@ -84,7 +84,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
-    ap.add_argument("--n", type=int, default=0, help="voxels per axis (0: the workload's own)")
+    ap.add_argument("--side", type=int, default=0, help="voxels per axis (0: the workload's own)")
     ap.add_argument("--stations", type=int, default=0, help="stations per axis (0: the workload's own)")
     ap.add_argument("--mode", default="auto", choices=["auto", "fmm", "direct"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -160,12 +160,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(x, world, device="cpu"):
+    """The largest value of x over the ranks (a job's time is that of its
+    slowest rank); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processed units_per_rank in at most
+    `seconds` (replicas, weak scaling)."""
+    return world * float(units_per_rank) / float(seconds)
+
+
 # ------------------------------------------------------------------ workload
 def make_workload(args):
     from paper_1107_5951_gb300 import workloads as wl
     if args.workload == "scale":
-        return wl.layered_scale(n=args.n or 464, stations=args.stations or 1024)
-    return wl.grf_volume(n=args.n or 128, stations=args.stations or 512)
+        return wl.layered_scale(n=args.side or 464, stations=args.stations or 1024)
+    return wl.grf_volume(n=args.side or 128, stations=args.stations or 512)
 
 
 ORACLE_SAMPLE_PAIRS = 2.0e10     # bounds the oracle's sample to ~15 s on 16 cores
@@ -300,8 +324,7 @@ def bench_gf(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     clocks = ClockSampler(local_rank, not args.no_clocks)
     launches0 = pkg.gf_launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -317,12 +340,9 @@ def bench_gf(args, rank, world):
     launches = pkg.gf_launch_count() - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * units * args.steps / (tot_ms * 1e-3)
+    torch.cuda.synchronize()
+    tot_ms = max_over_ranks(float(sum(step_ms)), world, dev)
+    value = job_rate(units * args.steps, world, tot_ms * 1e-3)
 
     # warm forward with the plan built, and the dominant kernel's duration
     plan = make_plan()
@@ -405,8 +425,8 @@ def bench_gf(args, rank, world):
             b.record(stream)
             e_ev.append((a, b))
         torch.cuda.synchronize()
-        e_ms = float(np.mean([a.elapsed_time(b) for a, b in e_ev]))
-        e2e = {"value": world * units / (e_ms * 1e-3), "unit": "interactions/s",
+        e_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in e_ev])), world, dev)
+        e2e = {"value": job_rate(units, world, e_ms * 1e-3), "unit": "interactions/s",
                "h2d_bytes_per_step": int(obs_h.numel() * 8 + rho_h.numel() * rho_h.element_size()),
                "d2h_bytes_per_step": int(g_h.numel() * 8), "ms_per_step": e_ms}
 
@@ -447,7 +467,7 @@ def bench_adjoint(args, rank, world):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     B = 16
-    wk = wl.adjoint_batch(n=args.n or 128, stations=args.stations or 256, batch=B)
+    wk = wl.adjoint_batch(n=args.side or 128, stations=args.stations or 256, batch=B)
     N, M = wk.n_sources, wk.n_obs
     stream = torch.cuda.Stream(device=dev)
     obs_d = torch.tensor(wk.obs, dtype=torch.float64, device=dev)
@@ -470,6 +490,7 @@ def bench_adjoint(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    barrier(world)
     clocks = ClockSampler(local_rank, not args.no_clocks)
     launches0 = pkg.gf_launch_count()
     ev = []
@@ -484,7 +505,7 @@ def bench_adjoint(args, rank, world):
     torch.cuda.synchronize()
     launches = pkg.gf_launch_count() - launches0
     clk = clocks.stop()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
     units = float(B) * N * M * 2
     # parity on sampled voxels of model 0 against the FP64 CPU transpose sum
     err, cpu = None, None
@@ -504,7 +525,7 @@ def bench_adjoint(args, rank, world):
     if rank != 0:
         return
     line = {"metric": "misfit-gradient interactions/s (forward + adjoint, 16 models)",
-            "value": world * units / (ms * 1e-3), "unit": "interactions/s", "n_gpus": world,
+            "value": job_rate(units, world, ms * 1e-3), "unit": "interactions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
@@ -567,6 +588,7 @@ def bench_serving(args, rank, world):
     st_cold = srv.stats()
     for _ in range(max(0, args.warmup - 1)):
         burst()
+    barrier(world)
     clocks = ClockSampler(local_rank, not args.no_clocks)
     launches0 = pkg.gf_launch_count()
     pass_s = []
@@ -575,7 +597,8 @@ def bench_serving(args, rank, world):
         pass_s.append(dt)
     launches = pkg.gf_launch_count() - launches0
     clk = clocks.stop()
-    sat_rate = len(reqs) * args.steps / sum(pass_s)
+    sat_s = max_over_ranks(sum(pass_s), world, torch.device("cuda", local_rank))
+    sat_rate = len(reqs) * args.steps / sat_s
     # open loop at Poisson arrival times
     rate = args.rate if args.rate > 0 else 0.7 * sat_rate
     arr = np.array([r["arrival_s"] for r in reqs])
