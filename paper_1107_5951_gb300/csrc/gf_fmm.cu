@@ -611,6 +611,9 @@ struct EvalArgs {
     int64_t M;
     double scale;              // G * h
     double eps2;               // coincidence radius^2 (voxel units)
+    int guard_all;             // quadrature nodes on voxel faces: every leaf may hold
+                               // a source coincident with an observer (else only
+                               // the observer's own leaf can)
     double *g, *gz;
 };
 
@@ -753,26 +756,43 @@ eval_kernel(EvalArgs a) {
                             TZ[u] = pk2(tz[u], tz[u]);
                         }
                         const int npair = (cnt + 1) >> 1;
+                        // Only the observer's own leaf (or any leaf, when nodes lie
+                        // on voxel faces) can hold a source at the observer's
+                        // position; elsewhere r2 > 0 and the coincidence test is
+                        // dropped from the pair loop.
+                        auto sweep = [&](auto guarded) {
+                            constexpr bool kGuard = decltype(guarded)::value;
 #pragma unroll 2
-                        for (int q = 0; q < npair; ++q) {
-                            const ulonglong2 xy = *reinterpret_cast<const ulonglong2 *>(wsh + q * 8);
-                            const ulonglong2 zw = *reinterpret_cast<const ulonglong2 *>(wsh + q * 8 + 4);
+                            for (int q = 0; q < npair; ++q) {
+                                const ulonglong2 xy = *reinterpret_cast<const ulonglong2 *>(wsh + q * 8);
+                                const ulonglong2 zw = *reinterpret_cast<const ulonglong2 *>(wsh + q * 8 + 4);
 #pragma unroll
-                            for (int u = 0; u < kTPL; ++u) {
-                                const uint64_t DX = sub2(TX[u], xy.x), DY = sub2(TY[u], xy.y),
-                                               DZ = sub2(TZ[u], zw.x);
-                                const uint64_t R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
-                                float r0, r1;
-                                up2(R2, r0, r1);
-                                const float i0 = r0 > (float)eps2 ? rsqrt_ftz(r0) : 0.f;
-                                const float i1 = r1 > (float)eps2 ? rsqrt_ftz(r1) : 0.f;
-                                const uint64_t RI = pk2(i0, i1);
-                                const uint64_t K3 = mul2(mul2(mul2(RI, RI), RI), zw.y);
-                                qx[u] = fma2(K3, DX, qx[u]);
-                                qy[u] = fma2(K3, DY, qy[u]);
-                                qz[u] = fma2(K3, DZ, qz[u]);
+                                for (int u = 0; u < kTPL; ++u) {
+                                    const uint64_t DX = sub2(TX[u], xy.x), DY = sub2(TY[u], xy.y),
+                                                   DZ = sub2(TZ[u], zw.x);
+                                    const uint64_t R2 = fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+                                    float r0, r1;
+                                    up2(R2, r0, r1);
+                                    float i0, i1;
+                                    if constexpr (kGuard) {
+                                        i0 = r0 > (float)eps2 ? rsqrt_ftz(r0) : 0.f;
+                                        i1 = r1 > (float)eps2 ? rsqrt_ftz(r1) : 0.f;
+                                    } else {
+                                        i0 = rsqrt_ftz(r0);
+                                        i1 = rsqrt_ftz(r1);
+                                    }
+                                    const uint64_t RI = pk2(i0, i1);
+                                    const uint64_t K3 = mul2(mul2(mul2(RI, RI), RI), zw.y);
+                                    qx[u] = fma2(K3, DX, qx[u]);
+                                    qy[u] = fma2(K3, DY, qy[u]);
+                                    qz[u] = fma2(K3, DZ, qz[u]);
+                                }
                             }
-                        }
+                        };
+                        if (a.guard_all || nb == 13)
+                            sweep(std::true_type{});
+                        else
+                            sweep(std::false_type{});
                         continue;
                     }
                     __syncwarp();
@@ -1053,6 +1073,10 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         a.M = plan->M;
         a.scale = plan->G * F->h;
         a.eps2 = sizeof(T) == 8 ? 1e-18 : 1e-12;
+        a.guard_all = 0;
+        for (int q = 0; q < plan->quad.nq; ++q)
+            for (int d = 0; d < 3; ++d)
+                if (fabs(plan->quad.xi[q][d]) >= 1.0) a.guard_all = 1;
         a.g = g;
         a.gz = gz;
         const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
