@@ -436,7 +436,9 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 //               stage's "empty" barrier (and, after an offset's last chunk,
 //               to the bank's "full" barrier);
 //   warp 5      one thread bulk-copies the pre-split, pre-swizzled operator
-//               image of each stage (mbarrier transaction count);
+//               image of each stage (transaction count on the same "full"
+//               barrier the producers arrive on, so the issuer checks one
+//               barrier per stage);
 //   warps 6-13  promoters: after each offset they read the finished bank of
 //               tensor memory and add it into FP32 registers (two banks
 //               alternate, so the tensor cores never accumulate more than one
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 m2l_tc(TcArgs a) {
     extern __shared__ unsigned char dsm[];
     unsigned char *base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);
-    __shared__ __align__(8) uint64_t afull[kTcMaxStages], bfull[kTcMaxStages], empty[kTcMaxStages];
+    __shared__ __align__(8) uint64_t afull[kTcMaxStages], empty[kTcMaxStages];
     __shared__ __align__(8) uint64_t bank_full[2], bank_empty[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
@@ -617,8 +619,8 @@ m2l_tc(TcArgs a) {
     }
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(128));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[i])), "r"(1));
+            // 128 producer threads + the operator copy's expect-tx arrival
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(129));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
         }
         for (int i = 0; i < 2; ++i) {
@@ -792,7 +794,6 @@ m2l_tc(TcArgs a) {
             int last = -1;
             for (int it = 0; it < iters; ++it) {
                 if (!mbar_wait_ab(smem_u32(&afull[s]), ph, abortp)) break;
-                if (!mbar_wait_ab(smem_u32(&bfull[s]), ph, abortp)) break;
                 if (c == 0 && g >= 2 && !mbar_wait_ab(smem_u32(&bank_empty[g & 1]), ((g - 2) >> 1) & 1, abortp)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const unsigned char *stage = base + (size_t)s * stage_bytes;
@@ -844,13 +845,13 @@ m2l_tc(TcArgs a) {
                     slot_off = 0;
                 }
                 unsigned char *stage = base + (size_t)s * stage_bytes;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bfull[s])),
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&afull[s])),
                              "r"(b_bytes));
                 const float *srcimg = a.img + ((size_t)slot_off * nck + c) * 2 * (size_t)Npad * 16;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         smem_u32(stage + kTcA)),
-                    "l"(srcimg), "r"(b_bytes), "r"(smem_u32(&bfull[s]))
+                    "l"(srcimg), "r"(b_bytes), "r"(smem_u32(&afull[s]))
                     : "memory");
                 last = it;
                 if (++c == nck) {
@@ -866,8 +867,11 @@ m2l_tc(TcArgs a) {
                     ph ^= 1;
                 }
             }
-            // drain: every copy issued must have landed before the CTA exits
-            if (last >= 0) mbar_wait(smem_u32(&bfull[last % NST]), (uint32_t)((last / NST) & 1));
+            // drain: every copy issued must have landed before the CTA exits (the
+            // stage completes once its copy has landed and the producers have
+            // arrived; after an abort, producers that stopped never arrive and
+            // the drain waits out its bound, long after the copy landed)
+            if (last >= 0) mbar_wait(smem_u32(&afull[last % NST]), (uint32_t)((last / NST) & 1));
         }
     }
     // ---------------- promoters (warps 6-13) and the write-back of each tile
