@@ -928,15 +928,25 @@ m2l_tc(TcArgs a) {
                     class_box(oc.cls, L.blo, L.bn, os, ox, oy, oz);
                     obox = (oz * L.bn[1] + oy) * L.bn[0] + ox;
                 }
-                float *dst = L.le + (obox * B + obb) * a.ldk + ph_half * nsum;
+                // 16-byte stores of the whole half row: columns from K up to
+                // Npad hold zeros (the operator images are zero there) and stay
+                // inside the row's padding (Npad <= ldk)
+                float4 *dst = reinterpret_cast<float4 *>(L.le + (obox * B + obb) * a.ldk + ph_half * nsum);
                 if (a.kind == kTcL2L) {
 #pragma unroll
-                    for (int q = 0; q < NS; ++q)
-                        if (q < nsum && ph_half * nsum + q < K) dst[q] += acc[q];
+                    for (int q = 0; q < NS; q += 4)
+                        if (q < nsum) {
+                            float4 v = dst[q / 4];
+                            v.x += acc[q];
+                            v.y += acc[q + 1];
+                            v.z += acc[q + 2];
+                            v.w += acc[q + 3];
+                            dst[q / 4] = v;
+                        }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < NS; ++q)
-                        if (q < nsum && ph_half * nsum + q < K) dst[q] = acc[q];
+                    for (int q = 0; q < NS; q += 4)
+                        if (q < nsum) dst[q / 4] = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
                 }
             }
         }
