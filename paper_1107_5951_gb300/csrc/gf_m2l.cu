@@ -580,7 +580,7 @@ m2l_tc(TcArgs a) {
     __shared__ int abort_flag;
     __shared__ uint32_t omask[6];   // M2L: offsets with at least one source box in this tile
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int K = a.K, B = a.B, Npad = a.Npad, nck = a.nck, NST = a.nst;
+    const int B = a.B, Npad = a.Npad, nck = a.nck, NST = a.nst;
     const int nsum = Npad / 2;
     const uint32_t b_bytes = 2u * (uint32_t)Npad * 64u;
     const uint32_t stage_bytes = tc_stage_bytes(Npad);
