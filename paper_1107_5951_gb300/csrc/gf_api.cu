@@ -394,6 +394,14 @@ gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info) {
         set_error("plan and info must be non-NULL");
         return GF_ERR_INVALID_ARG;
     }
+    if (plan->opt.mode == GF_MODE_FMM && !plan->counts_done) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != plan->device) cudaSetDevice(plan->device);
+        const gf_status rc = fmm_work_counts(plan, plan->arena.stream);
+        if (cur != plan->device) cudaSetDevice(cur);
+        if (rc != GF_OK) return rc;
+    }
     memset(info, 0, sizeof(*info));
     info->mode = plan->opt.mode;
     info->precision = plan->opt.precision;

@@ -929,6 +929,54 @@ gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out) {
     return GF_OK;
 }
 
+// P2M matrices, one per (device, p, leaf size, quadrature rule), cached for
+// the life of the process like the operator tables: plans rebuilt for the
+// same rule (a solve loop, a server) do not rebuild them.
+struct P2MEntry {
+    int device, p, b, nq;
+    double xi[kMaxQuad][3], wn[kMaxQuad];
+    double *pd;
+    float *pf;
+};
+std::mutex g_p2m_mu;
+std::vector<P2MEntry *> g_p2m;
+
+gf_status get_p2m(gf_plan_s *plan, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const QuadRule &q = plan->quad;
+    std::lock_guard<std::mutex> lk(g_p2m_mu);
+    for (P2MEntry *e : g_p2m)
+        if (e->device == plan->device && e->p == F->p && e->b == F->b && e->nq == q.nq &&
+            !memcmp(e->xi, q.xi, sizeof(double) * 3 * q.nq) && !memcmp(e->wn, q.wn, sizeof(double) * q.nq)) {
+            F->p2m_d = e->pd;
+            F->p2m_f = e->pf;
+            return GF_OK;
+        }
+    P2MEntry *e = new P2MEntry();
+    e->device = plan->device;
+    e->p = F->p;
+    e->b = F->b;
+    e->nq = q.nq;
+    memcpy(e->xi, q.xi, sizeof(double) * 3 * q.nq);
+    memcpy(e->wn, q.wn, sizeof(double) * q.nq);
+    const int b3 = F->b * F->b * F->b, K = F->K;
+    if (cudaMalloc(&e->pd, sizeof(double) * b3 * K) != cudaSuccess ||
+        cudaMalloc(&e->pf, sizeof(float) * b3 * K) != cudaSuccess) {
+        cudaGetLastError();
+        delete e;
+        set_error("cannot allocate the P2M matrix");
+        return GF_ERR_OOM;
+    }
+    const size_t shm = sizeof(double) * ((F->p + 1) * (F->p + 2) + K);
+    build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), e->pd, e->pf);
+    GF_KERNEL_DONE();
+    GF_CUDA(cudaStreamSynchronize(st));   // other streams may use the cached matrix next
+    g_p2m.push_back(e);
+    F->p2m_d = e->pd;
+    F->p2m_f = e->pf;
+    return GF_OK;
+}
+
 gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     DeviceArena &A = plan->arena;
@@ -942,8 +990,6 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     }
     const int b3 = F->b * F->b * F->b;
     GF_TRY(A.alloc(&F->mass, (size_t)std::max<int64_t>(F->lev[F->L].ns, 1) * B * b3 * rs));
-    GF_TRY(A.alloc_n(&F->p2m_d, (size_t)b3 * K));
-    GF_TRY(A.alloc_n(&F->p2m_f, (size_t)b3 * K));
     static bool il_ready[64] = {false};
     static std::mutex il_mu;
     {
@@ -956,9 +1002,7 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
         }
     }
     GF_TRY(get_tables(plan->device, F->p, st, &F->tab));
-    const size_t shm = sizeof(double) * ((F->p + 1) * (F->p + 2) + K);
-    build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), F->p2m_d, F->p2m_f);
-    GF_KERNEL_DONE();
+    GF_TRY(get_p2m(plan, st));
     GF_TRY(fmm_adjoint_prepare(plan, st));
     return m2l_tc_prepare(plan);
 }

@@ -86,6 +86,7 @@ struct gf_plan_s {
     int *d_status = nullptr;     // device-side check word
     size_t device_bytes = 0;
     int64_t near_pairs = 0, m2l_pairs = 0;
+    bool counts_done = false;    // FMM work counts computed (on first info request)
     bool timing = false;
     cudaEvent_t ev[GF_NUM_STAGES + 1] = {};
     bool ev_used[GF_NUM_STAGES + 1] = {};
@@ -123,6 +124,7 @@ void fmm_destroy(gf_plan_s *plan);
 // Free a plan whose device work has all completed (no device-wide wait).
 void plan_release(gf_plan_s *plan);
 gf_status fmm_info(const gf_plan_s *plan, gf_plan_info *info);
+gf_status fmm_work_counts(gf_plan_s *plan, cudaStream_t st);
 gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *keys,
                           uint64_t *box_keys, int64_t *ilist, int64_t *near_);
 size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt);

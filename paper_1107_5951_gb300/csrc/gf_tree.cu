@@ -184,7 +184,8 @@ __global__ void count_near(const uint64_t *__restrict__ tkey, const int32_t *__r
         const int64_t sx = x + d % 3 - 1 - slo0, sy = y + (d / 3) % 3 - 1 - slo1, sz = z + d / 9 - 1 - slo2;
         cnt += (sx >= 0 && sy >= 0 && sz >= 0 && sx < sn0 && sy < sn1 && sz < sn2);
     }
-    atomicAdd(out, (unsigned long long)((int64_t)cnt * per_leaf * (beg[t + 1] - beg[t])));
+    const unsigned long long v = (unsigned long long)((int64_t)cnt * per_leaf * (beg[t + 1] - beg[t]));
+    atomicAdd(out, v);
 }
 
 __global__ void count_il(const uint64_t *__restrict__ tkey, int64_t nt, int64_t slo0, int64_t slo1, int64_t slo2,
@@ -424,7 +425,18 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
         item_fill<<<ceil_div(nleaf, 256), 256, 0, st>>>(F->leaf_beg, nleaf, flags, F->items);
         GF_KERNEL_DONE();
     }
-    // ---- work counts
+    return fmm_alloc_workspaces(plan, st);
+}
+
+// Work counts (near-field pairs, interaction-list box pairs): only reported
+// by gf_plan_get_info, so computed on the first request rather than at plan
+// build.
+gf_status fmm_work_counts(gf_plan_s *plan, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    DeviceArena &A = plan->arena;
+    const int L = F->L;
+    const FmmLevel &leaf = F->lev[L];
+    const int64_t nleaf = leaf.nt;
     unsigned long long *d_cntw;
     GF_TRY(A.alloc_n(&d_cntw, 2));
     GF_CUDA(cudaMemsetAsync(d_cntw, 0, 2 * sizeof(unsigned long long), st));
@@ -446,7 +458,8 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     GF_CUDA(cudaStreamSynchronize(st));
     plan->near_pairs = (int64_t)hc[0];
     plan->m2l_pairs = (int64_t)hc[1];
-    return fmm_alloc_workspaces(plan, st);
+    plan->counts_done = true;
+    return GF_OK;
 }
 
 void fmm_destroy(gf_plan_s *plan) {
