@@ -599,8 +599,9 @@ def bench_serving(args, rank, world):
     clk = clocks.stop()
     sat_s = max_over_ranks(sum(pass_s), world, torch.device("cuda", local_rank))
     sat_rate = len(reqs) * args.steps / sat_s
-    # open loop at Poisson arrival times: the stream's own rate (100 requests/s,
-    # light load) and half the saturated rate
+    # open loop at Poisson arrival times: half the saturated rate, and light
+    # load (the stream's own 100 requests/s, or a quarter of the saturated
+    # rate if that is lower)
     def open_loop(rate):
         arr = np.array([r["arrival_s"] for r in reqs]) * (100.0 / rate)   # drawn at 100 requests/s
         t0 = time.perf_counter()
@@ -619,7 +620,8 @@ def bench_serving(args, rank, world):
 
     rate = args.rate if args.rate > 0 else 0.5 * sat_rate
     lat, open_s = open_loop(rate)
-    lat_l, open_l = open_loop(100.0)
+    light = min(100.0, 0.25 * sat_rate)
+    lat_l, open_l = open_loop(light)
     st = srv.stats()
     srv.close()
     # accuracy of a few requests on a station sample, against the FP64 oracle
@@ -658,7 +660,7 @@ def bench_serving(args, rank, world):
                        "l2_flush": "inputs larger than L2 (%.1f GB of densities per pass)" % (h2d / 1e9)},
             "interactions_per_s": units * sat_rate * world / len(reqs),
             "latency_open_loop": lat_summary(rate, lat, open_s),
-            "latency_light_load": lat_summary(100.0, lat_l, open_l),
+            "latency_light_load": lat_summary(light, lat_l, open_l),
             "cold_pass": {"seconds": cold_s, "plans_created": int(st_cold["plans_created"]),
                           "solves_per_s": len(reqs) / cold_s},
             "server": {k: st[k] for k in ("completed", "failed", "plans_created", "plans_evicted",

@@ -937,6 +937,7 @@ struct P2MEntry {
     double xi[kMaxQuad][3], wn[kMaxQuad];
     double *pd;
     float *pf;
+    float *tc = nullptr;   // tensor-core image (built on first use)
 };
 std::mutex g_p2m_mu;
 std::vector<P2MEntry *> g_p2m;
@@ -975,6 +976,28 @@ gf_status get_p2m(gf_plan_s *plan, cudaStream_t st) {
     F->p2m_d = e->pd;
     F->p2m_f = e->pf;
     return GF_OK;
+}
+
+gf_status get_p2m_tc(gf_plan_s *plan, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    std::lock_guard<std::mutex> lk(g_p2m_mu);
+    for (P2MEntry *e : g_p2m) {
+        if (e->pd != F->p2m_d) continue;
+        if (!e->tc) {
+            const int b3 = F->b * F->b * F->b, npad = F->tab->tc_npad;
+            if (cudaMalloc(&e->tc, sizeof(float) * (size_t)(b3 / 16) * 2 * npad * 16) != cudaSuccess) {
+                cudaGetLastError();
+                e->tc = nullptr;
+                set_error("cannot allocate the P2M tensor-core image");
+                return GF_ERR_OOM;
+            }
+            GF_TRY(build_p2m_tc_image(e->pd, F->K, npad, b3, e->tc, st));
+            GF_CUDA(cudaStreamSynchronize(st));
+        }
+        F->p2m_tc = e->tc;
+        return GF_OK;
+    }
+    return GF_OK;   // no cached matrix: the P2M stays on the SIMT path
 }
 
 gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {

@@ -125,6 +125,8 @@ void fmm_destroy(gf_plan_s *plan);
 void plan_release(gf_plan_s *plan);
 gf_status fmm_info(const gf_plan_s *plan, gf_plan_info *info);
 gf_status fmm_work_counts(gf_plan_s *plan, cudaStream_t st);
+// The plan's P2M matrix as a tensor-core image, cached with the matrix.
+gf_status get_p2m_tc(gf_plan_s *plan, cudaStream_t st);
 gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *keys,
                           uint64_t *box_keys, int64_t *ilist, int64_t *near_);
 size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt);

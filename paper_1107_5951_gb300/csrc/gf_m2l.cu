@@ -68,6 +68,12 @@ __global__ void build_tc_images(const double *__restrict__ m2l_d, int K, int Npa
 
 }  // namespace
 
+gf_status build_p2m_tc_image(const double *pd, int K, int npad, int b3, float *img, cudaStream_t st) {
+    build_tc_images<<<1, 256, 0, st>>>(pd, K, npad, b3 / 16, img, 1, b3);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
 gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
     const int npad = (T->K + 15) & ~15;
     if (npad > 256) return GF_OK;  // beyond one MMA's N: SIMT only
@@ -1031,14 +1037,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
             t.le = (float *)lv.me;
             t.cls_off[0] = 0;
             for (int c = 1; c <= 8; ++c) t.cls_off[c] = lv.ns;
-            const int b3 = F->b * F->b * F->b;
-            if (b3 % 16 == 0) {
-                const int nck_in = b3 / 16;
-                GF_TRY(plan->arena.alloc_n(&F->p2m_tc, (size_t)nck_in * 2 * F->tab->tc_npad * 16));
-                build_tc_images<<<1, 256, 0, plan->arena.stream>>>(F->p2m_d, F->K, F->tab->tc_npad, nck_in,
-                                                                   F->p2m_tc, 1, b3);
-                GF_KERNEL_DONE();
-            }
+            if ((F->b * F->b * F->b) % 16 == 0) GF_TRY(get_p2m_tc(plan, plan->arena.stream));
         }
         F->tc_xlate_host.assign(reinterpret_cast<unsigned char *>(h.data()),
                                 reinterpret_cast<unsigned char *>(h.data() + h.size()));

@@ -8,6 +8,8 @@ namespace gf {
 
 gf_status m2l_upload_offsets(const signed char h_il[8][189][3]);
 gf_status m2l_prepare_tables(Tables *T, cudaStream_t st);
+// Tensor-core image of a P2M matrix [b3][K] (b3 a multiple of 16).
+gf_status build_p2m_tc_image(const double *pd, int K, int npad, int b3, float *img, cudaStream_t st);
 
 // LE_l[t] = sum over the interaction list of box t of T_o * ME_l[t + o],
 // for every observer box t of every level (overwrites each LE_l).  Mixed
