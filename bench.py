@@ -38,16 +38,13 @@ FLOPS_PER_PAIR = 20.0            # the paper's count: 5 add, 7 mul, 1 sqrt ~ 20 
 TF32_PER_BF16 = 1.1 / 2.25       # nominal dense TF32 / BF16 tensor rates
 
 
-# DRAM traffic per launch of the dominant kernels, from one ncu capture of
-# the default workload (profiles/m2l_tc_grf_volume128_p12.md,
-# profiles/eval_kernel_grf_volume128_p12.md), with the SHA-1 of the kernel's
-# source file at capture time: once the source changes the figure no longer
-# describes the kernel and the bench reports null.
+# DRAM traffic per launch of the dominant kernel, from one ncu capture of
+# the default workload (profiles/m2l_tc_grf_volume128_p12.md), with the
+# SHA-1 of the kernel's source file at capture time: once the source changes
+# the figure no longer describes the kernel and the bench reports null.
 NCU_TRAFFIC = {
-    ("m2l", "grf_volume_128^3", 12): (212157184, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
-                                      "20b1b232f5a9738c53754da1065d781d527400e3"),
-    ("eval", "grf_volume_128^3", 12): (87542784, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
-                                       "5975c25c0bc551f5a0282e0d1c61db254055f7cb"),
+    ("m2l", "grf_volume_128^3", 12): (213687040, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
+                                      "638a9b64856a39fb2e8ef1b34acda689f318f490"),
 }
 
 
