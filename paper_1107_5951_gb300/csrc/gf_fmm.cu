@@ -623,7 +623,7 @@ struct EvalArgs {
 // leaf's centre, mass times quadrature weight) and every lane sweeps them
 // for its two observers.  Per-leaf partial sums are merged with TwoSum.
 template <class T>
-__global__ void __launch_bounds__(kEvalWarps * 32, sizeof(T) == 4 ? 5 : 1)   // FP32: 5 blocks (20 warps) per SM
+__global__ void __launch_bounds__(kEvalWarps * 32, sizeof(T) == 4 ? 6 : 1)   // FP32: 6 blocks (24 warps) per SM
 eval_kernel(EvalArgs a) {
     extern __shared__ unsigned char shraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
