@@ -451,6 +451,13 @@ gf_status fmm_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B, double
         GF_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * B * plan->nvox, st));
         return GF_OK;
     }
+    FmmPlan *F = plan->fmm;
+    if (!F->adj_ready) {   // adjoint-only structures, built once per plan
+        GF_TRY(fmm_adjoint_prepare(plan, plan->arena.stream));
+        GF_TRY(m2l_tc_prepare_adj(plan));
+        GF_CUDA(cudaStreamSynchronize(plan->arena.stream));
+        F->adj_ready = true;
+    }
     if (plan->fmm->mixed) return run_adjoint<float>(plan, r, ncomp, B, grad, st);
     return run_adjoint<double>(plan, r, ncomp, B, grad, st);
 }

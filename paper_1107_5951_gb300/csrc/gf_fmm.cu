@@ -1026,7 +1026,6 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     }
     GF_TRY(get_tables(plan->device, F->p, st, &F->tab));
     GF_TRY(get_p2m(plan, st));
-    GF_TRY(fmm_adjoint_prepare(plan, st));
     return m2l_tc_prepare(plan);
 }
 

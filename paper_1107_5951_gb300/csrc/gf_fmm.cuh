@@ -85,6 +85,7 @@ struct FmmPlan {
     int64_t mlo[kMaxLevels + 1][3] = {}, mn[kMaxLevels + 1][3] = {};
     int32_t *child[kMaxLevels + 1] = {};
     int64_t scls_off[kMaxLevels + 1][9] = {};
+    bool adj_ready = false;                      // adjoint structures built (on first adjoint)
     void *tc_levels_adj = nullptr;
     std::vector<unsigned char> tc_levels_adj_host;
     float *p2m_tc = nullptr;                     // tensor-core P2M operator image

@@ -966,10 +966,42 @@ m2l_tc(TcArgs a) {
 
 }  // namespace
 
+gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
+    FmmPlan *F = plan->fmm;
+    if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
+    for (int adj = 1; adj < 2; ++adj) {
+        std::vector<TcLevel> h(F->L + 1);
+        memset(h.data(), 0, h.size() * sizeof(TcLevel));
+        for (int l = 2; l <= F->L; ++l) {
+            const FmmLevel &lv = F->lev[l];
+            TcLevel &t = h[l];
+            t.me = (const float *)(adj ? lv.le : lv.me);
+            t.le = (float *)(adj ? lv.me : lv.le);
+            t.order = lv.m2l_order;
+            t.tkey = lv.tkey;
+            t.adj = adj;
+            t.imap = F->imap[l];
+            for (int d = 0; d < 3; ++d) {
+                t.blo[d] = lv.slo[d];
+                t.bn[d] = lv.sn[d];
+                t.mlo[d] = F->mlo[l][d];
+                t.mn[d] = F->mn[l][d];
+            }
+            for (int c = 0; c <= 8; ++c) t.cls_off[c] = adj ? F->scls_off[l][c] : lv.cls_off[c];
+        }
+        std::vector<unsigned char> &hb = adj ? F->tc_levels_adj_host : F->tc_levels_host;
+        void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
+        hb.assign(reinterpret_cast<unsigned char *>(h.data()), reinterpret_cast<unsigned char *>(h.data() + h.size()));
+        GF_TRY(plan->arena.alloc(&dev, hb.size()));
+        GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
+    }
+    return GF_OK;
+}
+
 gf_status m2l_tc_prepare(gf_plan_s *plan) {
     FmmPlan *F = plan->fmm;
     if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
-    for (int adj = 0; adj < 2; ++adj) {
+    for (int adj = 0; adj < 1; ++adj) {
         std::vector<TcLevel> h(F->L + 1);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
         for (int l = 2; l <= F->L; ++l) {

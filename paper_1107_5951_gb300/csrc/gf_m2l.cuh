@@ -34,6 +34,8 @@ gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_
 
 // Plan-time set-up of the tensor-core path (level descriptors on the device).
 gf_status m2l_tc_prepare(gf_plan_s *plan);
+// The adjoint's level tables (built on the plan's first adjoint call).
+gf_status m2l_tc_prepare_adj(gf_plan_s *plan);
 
 // P2M on the tensor cores (mixed precision, leaves of 16k voxels): ME of
 // every leaf = P^T x its leaf-blocked masses.  p2m_tc_ok says whether the

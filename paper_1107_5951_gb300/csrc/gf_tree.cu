@@ -47,7 +47,7 @@ __device__ __forceinline__ void demorton(uint64_t k, int64_t &x, int64_t &y, int
 
 struct Geo {
     double lo[3];
-    double inv_s, h;
+    double inv_s, h, inv_h;
     int L, b;
 };
 
@@ -113,7 +113,10 @@ __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restr
     int64_t c[3];
     demorton(okey[i], c[0], c[1], c[2]);
     for (int a = 0; a < 3; ++a) {
-        const double u = (obs[3 * j + a] - g.lo[a]) / g.h;
+        // voxel units by a multiply (FP64 division is a long sequence on this
+        // GPU); the last-bit difference from dividing stays far below the
+        // coincidence radius
+        const double u = (obs[3 * j + a] - g.lo[a]) * g.inv_h;
         const double loc = u - ((double)c[a] * g.b + 0.5 * g.b);
         if (td) td[3 * i + a] = loc;
         if (tf) tf[3 * i + a] = (float)loc;
@@ -318,6 +321,7 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     for (int a = 0; a < 3; ++a) g.lo[a] = F->lo[a];
     g.inv_s = F->inv_s;
     g.h = F->h;
+    g.inv_h = 1.0 / F->h;
     g.L = L;
     g.b = F->b;
 
