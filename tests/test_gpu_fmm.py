@@ -86,6 +86,33 @@ def test_tree_matches_numpy_octree_bit_for_bit(seed, leaf_vox):
                     assert np.array_equal(gn, wn)
 
 
+@pytest.mark.parametrize("seed,npts,leaf_vox", [(5, 1, 0), (6, 2, 0)])
+def test_work_counts_match_numpy_octree(seed, npts, leaf_vox):
+    """The pair counts the roofline divides by: near-field (observer, source
+    point) pairs and interaction-list (observer box, source box) pairs, equal
+    to the counts over the numpy octree's near and interaction lists."""
+    wk = cube_case(seed, n=20, npts=npts, n_obs=700, pad=6.0, vol_targets=200)
+    with plan_for(wk, leaf_vox=leaf_vox) as plan:
+        info = plan.info
+        L, b = info.L, info.leaf_vox
+        lo = np.array(info.lo[:])
+        off = np.array(info.voxel_offset[:])
+        keys, perm = tree.sort_points(wk.obs, lo, info.inv_leaf_side, L)
+        levels = tree.level_boxes(keys[perm], L)
+        m2l = 0
+        for lev in range(2, L + 1):
+            slo, shi = tree.source_rect(off, wk.grid.n, b, L, lev)
+            for c in tree.deinterleave(levels[lev], L):
+                m2l += len(tree.interaction_list(c, slo, shi))
+        slo, shi = tree.source_rect(off, wk.grid.n, b, L, L)
+        leaf_keys, counts = np.unique(keys[perm], return_counts=True)
+        near = 0
+        for c, n_obs in zip(tree.deinterleave(leaf_keys, L), counts):
+            near += len(tree.near_list(c, slo, shi)) * b ** 3 * len(wk.w) * int(n_obs)
+        assert int(info.m2l_pairs) == m2l
+        assert int(info.near_pairs) == near
+
+
 # ------------------------------------------------------------------ parity
 @pytest.mark.parametrize("seed,npts,leaf_vox,pad", [(11, 1, 0, 3.0), (12, 2, 0, 2.0), (13, 1, 3, 8.0),
                                                       (14, 1, 2, 0.5)])
