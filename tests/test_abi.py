@@ -97,3 +97,61 @@ def test_plan_bytes_grows_with_problem():
     small = gf.gf_plan_bytes(grid, q.c, 1000, opt)
     big = gf.gf_plan_bytes(grid, q.c, 100000, opt)
     assert big > small > 0
+
+
+def test_server_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the serving structs have the C sizes and offsets."""
+    prog = tmp_path / "ss.c"
+    prog.write_text('#include "gf.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
+                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gf_server_options), sizeof(gf_request),'
+                    ' sizeof(gf_server_stats), offsetof(gf_server_options, mem_budget), offsetof(gf_request, rho_host),'
+                    ' offsetof(gf_request, g_host), offsetof(gf_server_stats, p99_ms), offsetof(gf_server_stats, busy_s));'
+                    ' return 0;}')
+    exe = tmp_path / "ss"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out == [ctypes.sizeof(gf.gf_server_options), ctypes.sizeof(gf.gf_request),
+                   ctypes.sizeof(gf.gf_server_stats), gf.gf_server_options.mem_budget.offset,
+                   gf.gf_request.rho_host.offset, gf.gf_request.g_host.offset, gf.gf_server_stats.p99_ms.offset,
+                   gf.gf_server_stats.busy_s.offset]
+
+
+def test_server_arguments_rejected_on_host():
+    """Bad server options and requests fail with GF_ERR_INVALID_ARG before any
+    device call (this also holds on a machine without a GPU)."""
+    lib = pkg.load()
+    o = gf.gf_server_options()
+    o.max_slots = 0
+    o.precision = gf.GF_PREC_MIXED
+    o.p = 12
+    h = ctypes.c_void_p()
+    assert lib.gf_server_create(ctypes.byref(o), ctypes.byref(h)) == gf.GF_ERR_INVALID_ARG
+    o.max_slots = 4
+    o.p = 99
+    assert lib.gf_server_create(ctypes.byref(o), ctypes.byref(h)) == gf.GF_ERR_INVALID_ARG
+    t = ctypes.c_int64()
+    assert lib.gf_server_submit(None, None, ctypes.byref(t)) == gf.GF_ERR_INVALID_ARG
+    assert lib.gf_server_wait(None, 1, 0.0, None) == gf.GF_ERR_INVALID_ARG
+    assert lib.gf_server_destroy(None) == gf.GF_OK
+
+
+def test_no_gpu_means_an_error_not_a_fallback():
+    """Without a usable GPU, creating a plan or a server reports a CUDA error;
+    nothing silently computes on the CPU."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = pkg.load()
+    o = gf.gf_server_options()
+    o.max_slots = 2
+    o.precision = gf.GF_PREC_MIXED
+    o.p = 8
+    h = ctypes.c_void_p()
+    rc = lib.gf_server_create(ctypes.byref(o), ctypes.byref(h))
+    assert rc == gf.GF_ERR_CUDA and not h.value
+    grid, q, opt = _args(mode="direct")
+    obs = np.zeros((3, 3))
+    plan = ctypes.c_void_p()
+    rc = lib.gf_plan_create(ctypes.byref(grid), ctypes.byref(q.c), obs.ctypes.data, 1, ctypes.byref(opt), None,
+                            ctypes.byref(plan))
+    assert rc != gf.GF_OK and not plan.value
