@@ -35,12 +35,20 @@ struct FmmLevel {
 //                                          of the child box
 struct Tables {
     int device = -1, p = 0, K = 0, Kp = 0;   // Kp = K rounded up to 8
-    // Tensor-core operand images of the M2L operators (mixed precision):
-    // for every offset slot and every 32-wide input chunk, the TF32 high
-    // and low parts of T_o[k_out][k_in] as two [Npad][32] FP32 tiles in the
-    // 128-byte-swizzled K-major shared-memory layout, ready for a bulk copy.
-    float *m2l_tc = nullptr;
-    int tc_npad = 0, tc_nck = 0;
+    // Tensor-core operand images (mixed precision), one bulk copy per
+    // pipeline stage, in the 64-byte-swizzled K-major shared-memory layout
+    // (rows of 64 bytes):
+    //   m2l_tc, am2l_tc  [343 slots][tc_nck_h chunks of 32 inputs][hi|lo][Npad][32]
+    //                    FP16 parts of T_o[k_out][k_in] * colscale[k_out]
+    //   m2m_tc, l2l_tc   [8][tc_nck chunks of 16 inputs][hi|lo][Npad][16]
+    //                    TF32 parts of the operator
+    // colscale (m2l_cs / am2l_cs: [Npad] scale, then [Npad] its inverse) is
+    // the power of two that brings each output column's largest entry over
+    // all offsets into (2^13, 2^14], so that both FP16 parts of every entry
+    // that matters are normal numbers.
+    void *m2l_tc = nullptr, *am2l_tc = nullptr;
+    float *m2l_cs = nullptr, *am2l_cs = nullptr;
+    int tc_npad = 0, tc_nck = 0, tc_nck_h = 0;
     double *m2l_d = nullptr;
     float *m2l_f = nullptr;
     double *m2m_d = nullptr, *l2l_d = nullptr;
@@ -50,7 +58,6 @@ struct Tables {
     //   am2m[oct] = (T_M2M,oct)^T,  al2l[oct] = (T_L2L,oct)^T
     double *am2l_d = nullptr, *am2m_d = nullptr, *al2l_d = nullptr;
     float *am2l_f = nullptr, *am2m_f = nullptr, *al2l_f = nullptr;
-    float *am2l_tc = nullptr;
     float *m2m_tc = nullptr, *l2l_tc = nullptr;   // [8] operator images (tensor-core translations)
 };
 
@@ -76,6 +83,14 @@ struct FmmPlan {
     float *p2m_f = nullptr;
     const Tables *tab = nullptr;
     void *tc_levels = nullptr;                  // tensor-core M2L level table
+    // largest |input| of each level's M2L (bits of a non-negative float;
+    // [0, kMaxLevels]: forward, [kMaxLevels + 1, 2 kMaxLevels + 1]: adjoint),
+    // reduced on the device before each tensor-core M2L
+    uint32_t *tc_amax = nullptr;
+    // the M2L inputs of levels 2..L split into scaled FP16 high and low
+    // parts: for every input row and 32-wide chunk, 64 bytes of high parts
+    // then 64 bytes of low parts (the same byte offsets as the FP32 rows)
+    unsigned char *tc_split = nullptr, *tc_split_adj = nullptr;
     std::vector<unsigned char> tc_levels_host;
     // adjoint: per level, observer-box index over the source block widened
     // by 3 boxes (-1 where no observer box), the children of each observer

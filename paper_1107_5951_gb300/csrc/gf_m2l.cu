@@ -7,6 +7,7 @@
 // K x 32 matrix of gathered source expansions ME[t + o], accumulating the
 // K x 32 result in registers.  Sources outside the source block contribute
 // zero columns.  Each output is written once, so the result is deterministic.
+#include <cuda_fp16.h>
 #include <string.h>
 
 #include <algorithm>
@@ -38,7 +39,70 @@ __host__ __device__ __forceinline__ uint32_t swz64(int row, int k) {
     return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((((k >> 2) ^ (row >> 1)) & 3) << 4) + (k & 3) * 4);
 }
 
-// Operator images for the tensor-core M2L: img[off][c][part][Npad*16],
+// Byte offset of FP16 element (row, k), k < 32, in a [rows][32] tile in the
+// same swizzled layout (the swizzle acts on 16-byte chunks, 8 halves each).
+__host__ __device__ __forceinline__ uint32_t swz64h(int row, int k) {
+    return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((((k >> 3) ^ (row >> 1)) & 3) << 4) + (k & 7) * 2);
+}
+
+// Column scales of an M2L operator set (one block per output component n <
+// Npad): s_n = 2^(14 - ceil(log2 max |T_o[n][k]|)), the maximum over the
+// used offset slots and every input k.  cs[n] = s_n, cs[Npad + n] = 1 / s_n
+// (1 for empty columns and n >= K).
+__global__ void m2l_colscale(const double *__restrict__ tab, int K, int Npad, float *__restrict__ cs) {
+    __shared__ double red[256];
+    const int n = blockIdx.x;
+    double mx = 0.0;
+    if (n < K)
+        for (int e = threadIdx.x; e < 343 * K; e += blockDim.x) {
+            const int off = e / K, kin = e - off * K;
+            const int dx = off % 7 - 3, dy = (off / 7) % 7 - 3, dz = off / 49 - 3;
+            if (max(abs(dx), max(abs(dy), abs(dz))) < 2) continue;
+            mx = fmax(mx, fabs(tab[(size_t)off * K * K + (size_t)kin * K + n]));
+        }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int sh = 0;
+        if (red[0] > 0.0) {
+            int e;
+            const double f = frexp(red[0], &e);   // red = f 2^e, f in [0.5, 1)
+            sh = 14 - (f == 0.5 ? e - 1 : e);
+        }
+        cs[n] = ldexpf(1.f, sh);
+        cs[Npad + n] = ldexpf(1.f, -sh);
+    }
+}
+
+// FP16 operator images of the tensor-core M2L: img[off][c][part][Npad][32],
+// part 0 = FP16(T s), part 1 = FP16(T s - part 0), T = T_off[k_out][k_in]
+// for the 32 inputs of chunk c, s = the column scale of k_out.
+__global__ void build_h16_images(const double *__restrict__ tab, int K, int Npad, int nck,
+                                 const float *__restrict__ cs, __half *__restrict__ img) {
+    const int off = blockIdx.x;
+    const int dx = off % 7 - 3, dy = (off / 7) % 7 - 3, dz = off / 49 - 3;
+    const bool used = max(abs(dx), max(abs(dy), abs(dz))) >= 2;
+    const size_t tile = (size_t)Npad * 32;
+    for (int c = 0; c < nck; ++c) {
+        __half *hi = img + ((size_t)off * nck + c) * 2 * tile;
+        __half *lo = hi + tile;
+        for (int e = threadIdx.x; e < Npad * 32; e += blockDim.x) {
+            const int n = e / 32, kk = e % 32, kin = 32 * c + kk;
+            const double v = (used && n < K && kin < K) ? tab[(size_t)off * K * K + (size_t)kin * K + n] * cs[n] : 0.0;
+            const float f = (float)v;
+            const __half h = __float2half_rn(f);
+            const uint32_t o = swz64h(n, kk) / 2;
+            hi[o] = h;
+            lo[o] = __float2half_rn(f - __half2float(h));
+        }
+    }
+}
+
+// Operator images for the tensor-core M2M / L2L / P2M: img[off][c][part][Npad*16],
 // part 0 = TF32(T), part 1 = TF32(T - TF32(T)), T = T_off[k_out][k_in] for
 // the 16 inputs k_in of chunk c.
 // With all_used (M2M / L2L: 8 octant operators) every slot is filled; for the
@@ -79,13 +143,19 @@ gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
     if (npad > 256) return GF_OK;  // beyond one MMA's N: SIMT only
     T->tc_npad = npad;
     T->tc_nck = (T->K + 15) / 16;
-    const size_t n = (size_t)343 * T->tc_nck * 2 * npad * 16;
-    GF_CUDA(cudaMalloc(&T->m2l_tc, n * sizeof(float)));
-    build_tc_images<<<343, 256, 0, st>>>(T->m2l_d, T->K, npad, T->tc_nck, T->m2l_tc);
-    GF_KERNEL_DONE();
-    GF_CUDA(cudaMalloc(&T->am2l_tc, n * sizeof(float)));
-    build_tc_images<<<343, 256, 0, st>>>(T->am2l_d, T->K, npad, T->tc_nck, T->am2l_tc);
-    GF_KERNEL_DONE();
+    T->tc_nck_h = (T->K + 31) / 32;
+    const size_t n = (size_t)343 * T->tc_nck_h * 2 * npad * 32;
+    for (int adj = 0; adj < 2; ++adj) {
+        const double *tab = adj ? T->am2l_d : T->m2l_d;
+        void *&img = adj ? T->am2l_tc : T->m2l_tc;
+        float *&cs = adj ? T->am2l_cs : T->m2l_cs;
+        GF_CUDA(cudaMalloc(&cs, 2 * npad * sizeof(float)));
+        m2l_colscale<<<npad, 256, 0, st>>>(tab, T->K, npad, cs);
+        GF_KERNEL_DONE();
+        GF_CUDA(cudaMalloc(&img, n * sizeof(__half)));
+        build_h16_images<<<343, 256, 0, st>>>(tab, T->K, npad, T->tc_nck_h, cs, (__half *)img);
+        GF_KERNEL_DONE();
+    }
     const size_t n8 = (size_t)8 * T->tc_nck * 2 * npad * 16;
     GF_CUDA(cudaMalloc(&T->m2m_tc, n8 * sizeof(float)));
     build_tc_images<<<8, 256, 0, st>>>(T->m2m_d, T->K, npad, T->tc_nck, T->m2m_tc, 1);
@@ -432,12 +502,21 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 // For the M2L, a CTA owns 128 target columns --
 // (box, batch member) pairs of one parity class of one level -- and, offset
 // by offset, computes D_o[col][k_out] = sum_k_in ME[t + o][k_in] T_o[k_out][k_in]
-// on the tensor cores as 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi).  Inputs
-// come in chunks of 16 through a ring of shared-memory stages (64-byte
-// swizzle), filled by warp-specialised producers:
-//   warps 0-3   A producers: thread r gathers column r's 16 inputs of the
-//               chunk (two chunks in flight in registers), splits them into
-//               TF32 high and low parts and stores them swizzled;
+// on the tensor cores from FP16 parts, A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (K = 16 per MMA), with FP32 accumulation.  Both operands are scaled by
+// powers of two so that every part that matters is a normal FP16 number:
+// the inputs of a level by 2^sh (largest |input| into (2^14, 2^15]), each
+// output column of the operator images by its own factor; the write-back
+// divides both out exactly.  The inputs are split once per level by a small
+// kernel before the M2L; the M2M, L2L and P2M kinds split FP32 inputs into
+// TF32 parts in the kernel (3xTF32, K = 8 per MMA).  Inputs come in chunks
+// (32 FP16 or 16 TF32 inputs) through a ring of shared-memory stages
+// (64-byte swizzle), filled by warp-specialised producers:
+//   warps 0-3   A producers: thread r gathers column r's inputs of the chunk
+//               with 16-byte asynchronous copies -- FP16 parts straight into
+//               the stage, signalled two stages later; FP32 values into a
+//               private ring three chunks ahead, then split into TF32 parts
+//               and stored swizzled;
 //   warp 4      one thread issues the MMAs of a stage and commits them to the
 //               stage's "empty" barrier (and, after an offset's last chunk,
 //               to the bank's "full" barrier);
@@ -475,6 +554,8 @@ struct TcLevel {
     int64_t mlo[3], mn[3];
     int64_t clo[3], cn[3];       // M2M: child source block
     const int32_t *tparent;      // L2L: parent of each observer box
+    const uint32_t *amax;        // M2L: largest |input| of the level (float bits)
+    const unsigned char *split;  // M2L: the level's inputs split into scaled FP16 parts
 };
 
 struct TcArgs {
@@ -485,7 +566,8 @@ struct TcArgs {
     int kind, noff;             // TcKind; offsets per target (189, 8 or 1)
     int ntiles;                 // tiles of the launch (persistent kinds)
     int kin, ldin;              // input coefficients per row and input row stride
-    const float *img;
+    const unsigned char *img;   // operator images, one [hi|lo] tile pair per (slot, chunk)
+    const float *cs;            // M2L: column scales of the image ([Npad] scale, [Npad] inverse)
     int *status;
 };
 
@@ -505,6 +587,26 @@ __device__ __forceinline__ uint64_t umma_desc64(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     // D = FP32, A = B = TF32, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    // D = FP32, A = B = FP16 (format 0), both K-major
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Power-of-two scale sig = 2^sh that brings the largest |input| m of an
+// M2L level into (2^14, 2^15] (the top of the FP16 range, far from its
+// subnormals), from the bits of m: ceil(log2 m) = E + (mantissa != 0) for
+// m = 1.mantissa * 2^E.  sh is clamped to [-126, 126]; m = 0 gives 1.
+__device__ __forceinline__ void input_scale(uint32_t mbits, float &sig, float &inv) {
+    int sh = 0;
+    if (mbits != 0u) {
+        const int eb = (int)(mbits >> 23);   // biased exponent (0: subnormal)
+        const int cl = (eb == 0 ? -126 : eb - 127) + ((mbits & 0x7FFFFFu) != 0u ? 1 : 0);
+        sh = min(126, max(-126, 15 - cl));
+    }
+    sig = __int_as_float((127 + sh) << 23);
+    inv = __int_as_float((127 - sh) << 23);
 }
 
 constexpr long kWaitTries = 1l << 24;
@@ -545,6 +647,11 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
                  "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void commit_to(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -567,15 +674,30 @@ constexpr int kTcMaxStages = 8;
 constexpr uint32_t kTcCols = 512;           // two banks of 256 columns
 constexpr uint32_t kTcA = 2u * 8192u;       // A hi + lo: 128 rows x 64 bytes each
 
+constexpr int kTcRaw = 4;                   // input chunks in flight per producer thread
+
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 64u; }
+// raw FP32 input ring of the producers: [kTcRaw][128 rows][32 or 16 floats]
+__host__ __device__ constexpr uint32_t tc_raw_bytes(bool h16) { return h16 ? 0u : kTcRaw * 128u * 64u; }
+constexpr int kTcLag = 2;   // FP16 inputs: stages copied ahead of their arrival (needs >= 3 stages)
 constexpr size_t kTcSmemBudget = 227 * 1024 - 2048;
-inline int tc_stages(int Npad) {
-    const int n = (int)(kTcSmemBudget / tc_stage_bytes(Npad));
+inline int tc_stages(int Npad, bool h16) {
+    const int n = (int)((kTcSmemBudget - tc_raw_bytes(h16)) / tc_stage_bytes(Npad));
     return n > kTcMaxStages ? kTcMaxStages : n;
 }
-size_t tc_smem_bytes(int Npad) { return (size_t)tc_stages(Npad) * tc_stage_bytes(Npad) + 1024; }
+size_t tc_smem_bytes(int Npad, bool h16) {
+    return (size_t)tc_stages(Npad, h16) * tc_stage_bytes(Npad) + tc_raw_bytes(h16) + 1024;
+}
 
-template <int NS>   // NS >= Npad / 2: FP32 sums held per promoter thread
+// 16-byte asynchronous global -> shared copy; nbytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t nbytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
+}
+
+// NS >= Npad / 2: FP32 sums held per promoter thread.  H16: the M2L with
+// FP16 operands, 32 inputs per stage (K = 16 per MMA); otherwise TF32, 16
+// inputs per stage (K = 8 per MMA).
+template <int NS, bool H16>
 __global__ void __launch_bounds__(kTcThreads, 1)
 m2l_tc(TcArgs a) {
     extern __shared__ unsigned char dsm[];
@@ -643,10 +765,16 @@ m2l_tc(TcArgs a) {
     const int slot = row / B, bb = row - slot * B;
     Ctx pc = ctx_of(0);
     int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
+    int64_t qbn0 = 0, qbn1 = 0, qbn2 = 0;   // the level's source block extent, kept in registers
+    int qadj = 0;
     auto set_target = [&]() {
         tbox = -1;
         tc0 = tc1 = tc2 = 0;
         const TcLevel &L = *pc.L;
+        qbn0 = L.bn[0];
+        qbn1 = L.bn[1];
+        qbn2 = L.bn[2];
+        qadj = L.adj;
         const int64_t sidx = (int64_t)pc.tile * nbox + slot;
         if (warp >= 4 || slot >= nbox || sidx >= pc.ccnt) return;
         if (a.kind == kTcP2M) {
@@ -686,9 +814,9 @@ m2l_tc(TcArgs a) {
         if (a.kind == kTcP2M) return (tbox * B + bb) * a.ldin;
         const int cls = pc.cls;
         const int64_t sx = tc0 + c_il[cls][oi][0], sy = tc1 + c_il[cls][oi][1], sz = tc2 + c_il[cls][oi][2];
-        if (!L.adj) {
-            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < L.bn[0] && sy < L.bn[1] && sz < L.bn[2])
-                return (((sz * L.bn[1] + sy) * L.bn[0] + sx) * B + bb) * a.ldin;
+        if (!qadj) {
+            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < qbn0 && sy < qbn1 && sz < qbn2)
+                return (((sz * qbn1 + sy) * qbn0 + sx) * B + bb) * a.ldin;
             return -1;
         }
         const int64_t wx = sx + L.blo[0] - L.mlo[0], wy = sy + L.blo[1] - L.mlo[1], wz = sz + L.blo[2] - L.mlo[2];
@@ -700,9 +828,12 @@ m2l_tc(TcArgs a) {
     };
     __syncthreads();
     if (!persist && warp < 4) {
-        for (int oi = 0; oi < noff; ++oi) {
-            const unsigned any = __ballot_sync(0xffffffffu, src_row(oi) >= 0);
-            if (lane == 0 && any) atomicOr(&omask[oi >> 5], 1u << (oi & 31));
+        for (int w = 0; w * 32 < noff; ++w) {
+            uint32_t bits = 0;
+            for (int b = 0; b < 32 && 32 * w + b < noff; ++b)
+                if (src_row(32 * w + b) >= 0) bits |= 1u << b;
+            bits = __reduce_or_sync(0xffffffffu, bits);
+            if (lane == 0 && bits) atomicOr(&omask[w], bits);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -741,60 +872,114 @@ m2l_tc(TcArgs a) {
                 qs = (qj < ntl && qo < noff) ? src_row(qo) : -1;
             }
         };
-        const float *me = pc.L->me;   // every tile of a launch reads the same input array
-        auto load = [&](int64_t sr, int cc, float4 *v) {
-            if (sr >= 0) {
-                const float4 *p4 = reinterpret_cast<const float4 *>(me + sr + 16 * cc);
+        if (H16) {
+            // FP16 inputs, scaled and split in advance: each thread copies its
+            // row's 64-byte high and low pieces of a chunk straight into the
+            // stage (16-byte asynchronous copies to the swizzled positions, a
+            // missing source copies zeros) and signals the stage kTcLag
+            // stages later, once its copies have landed.
+            const unsigned char *spl = pc.L->split;   // every tile of a launch reads the same levels
+            int s = 0, sa = 0;
+            uint32_t ph = 0;
+            for (int it = 0; it < iters + kTcLag; ++it) {
+                if (it < iters) {
+                    if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                    int cc;
+                    int64_t sr;
+                    take(cc, sr);
+                    unsigned char *stage = base + (size_t)s * stage_bytes;
+                    const unsigned char *src = sr >= 0 ? spl + (size_t)sr * 4 + (size_t)cc * 128 : spl;
+                    const uint32_t nb = sr >= 0 ? 16u : 0u;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = __ldg(p4 + q);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        };
-        float4 cur[4], nxt[4];
-        int c0;
-        int64_t s0;
-        take(c0, s0);
-        if (iters > 0) load(s0, c0, cur);
-        int s = 0;
-        uint32_t ph = 0;
-        for (int it = 0; it < iters; ++it) {
-            int c1;
-            int64_t s1;
-            take(c1, s1);   // prefetch the next chunk
-            if (it + 1 < iters) load(s1, c1, nxt);
-            if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
-            unsigned char *stage = base + (size_t)s * stage_bytes;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float x4[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
-                uint32_t h[4], l[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int kin = 16 * c0 + 4 * q + j;
-                    const float x = kin < a.kin ? x4[j] : 0.f;
-                    h[j] = to_tf32(x);
-                    l[j] = to_tf32(x - __uint_as_float(h[j]));
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t o = swz64h(row, 8 * q);
+                        cp_async16(smem_u32(stage + o), src + (sr >= 0 ? 16 * q : 0), nb);
+                        cp_async16(smem_u32(stage + 8192 + o), src + (sr >= 0 ? 64 + 16 * q : 0), nb);
+                    }
+                    if (++s == NST) {
+                        s = 0;
+                        ph ^= 1;
+                    }
                 }
-                const uint32_t o = swz64(row, 4 * q);
-                *reinterpret_cast<uint4 *>(stage + o) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4 *>(stage + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                if (it >= kTcLag) {
+                    asm volatile("cp.async.wait_group %0;" ::"n"(kTcLag) : "memory");   // chunk it - kTcLag landed
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(smem_u32(&afull[sa]));
+                    if (++sa == NST) sa = 0;
+                }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(smem_u32(&afull[s]));
+            asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the loop (abort)
+        } else {
+            // TF32 inputs, split here
+            constexpr int kW = 16;     // inputs per stage
+            constexpr int kV = kW / 4; // 16-byte pieces per row and stage
+            const float *me = pc.L->me;   // every tile of a launch reads the same input array
+            // Each thread copies its own row's chunks kTcRaw - 1 stages ahead into
+            // a raw ring (16-byte pieces XOR-swizzled by row, so that a warp's
+            // reads of one piece hit distinct banks); a missing source copies
+            // zeros.  Only the copying thread reads them back.
+            unsigned char *raw = base + (size_t)NST * stage_bytes + (size_t)row * (kW * 4);
+            auto issue = [&](int j) {
+                int cc;
+                int64_t sr;
+                take(cc, sr);
+                const uint32_t d0 = smem_u32(raw + (size_t)(j % kTcRaw) * 128 * (kW * 4));
+                const float *src = sr >= 0 ? me + sr + kW * cc : me;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
-            c0 = c1;
-            if (++s == NST) {
-                s = 0;
-                ph ^= 1;
+                for (int q = 0; q < kV; ++q)
+                    cp_async16(d0 + ((q ^ (row & (kV - 1))) << 4), src + (sr >= 0 ? 4 * q : 0), sr >= 0 ? 16u : 0u);
+            };
+#pragma unroll 1
+            for (int j = 0; j < kTcRaw - 1; ++j) {
+                if (j < iters) issue(j);
+                asm volatile("cp.async.commit_group;" ::: "memory");
             }
+            int s = 0;
+            uint32_t ph = 0;
+            for (int it = 0; it < iters; ++it) {
+                if (it + kTcRaw - 1 < iters) issue(it + kTcRaw - 1);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                asm volatile("cp.async.wait_group %0;" ::"n"(kTcRaw - 1) : "memory");   // chunk `it` has landed
+                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                const int c0 = it % nck;   // every offset runs all nck chunks, in order
+                float4 cur[kV];
+                {
+                    const float4 *rr = reinterpret_cast<const float4 *>(raw + (size_t)(it % kTcRaw) * 128 * (kW * 4));
+#pragma unroll
+                    for (int q = 0; q < kV; ++q) cur[q] = rr[q ^ (row & (kV - 1))];
+                }
+                unsigned char *stage = base + (size_t)s * stage_bytes;
+                {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float x4[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
+                        uint32_t h[4], l[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int kin = 16 * c0 + 4 * q + j;
+                            const float x = kin < a.kin ? x4[j] : 0.f;
+                            h[j] = to_tf32(x);
+                            l[j] = to_tf32(x - __uint_as_float(h[j]));
+                        }
+                        const uint32_t o = swz64(row, 4 * q);
+                        *reinterpret_cast<uint4 *>(stage + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4 *>(stage + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&afull[s]));
+                if (++s == NST) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the loop (abort)
         }
     } else if (warp == 4) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(128, Npad);
+            const uint32_t idesc = H16 ? idesc_f16(128, Npad) : idesc_tf32(128, Npad);
             int s = 0, c = 0, g = 0;
             uint32_t ph = 0;
             int last = -1;
@@ -805,14 +990,21 @@ m2l_tc(TcArgs a) {
                 const unsigned char *stage = base + (size_t)s * stage_bytes;
                 const uint32_t sa = smem_u32(stage), sb = smem_u32(stage + kTcA);
                 const uint32_t d = tmem + (uint32_t)(g & 1) * 256u;
-                const int nk8 = min(2, (a.kin - 16 * c + 7) / 8);
-                for (int ks = 0; ks < nk8; ++ks) {
+                // k-steps of 32 bytes (8 TF32 or 16 FP16 inputs) holding inputs
+                const int nks = H16 ? min(2, (a.kin - 32 * c + 15) / 16) : min(2, (a.kin - 16 * c + 7) / 8);
+                for (int ks = 0; ks < nks; ++ks) {
                     const uint32_t ko = ks * 32;
                     const uint64_t ah = umma_desc64(sa + ko), al = umma_desc64(sa + 8192 + ko);
                     const uint64_t bh = umma_desc64(sb + ko), bl = umma_desc64(sb + (uint32_t)Npad * 64 + ko);
-                    mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_tf32(d, ah, bl, idesc, 1u);
-                    mma_tf32(d, al, bh, idesc, 1u);
+                    if (H16) {
+                        mma_f16(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_f16(d, ah, bl, idesc, 1u);
+                        mma_f16(d, al, bh, idesc, 1u);
+                    } else {
+                        mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_tf32(d, ah, bl, idesc, 1u);
+                        mma_tf32(d, al, bh, idesc, 1u);
+                    }
                 }
                 commit_to(&empty[s]);
                 last = it;
@@ -853,7 +1045,7 @@ m2l_tc(TcArgs a) {
                 unsigned char *stage = base + (size_t)s * stage_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&afull[s])),
                              "r"(b_bytes));
-                const float *srcimg = a.img + ((size_t)slot_off * nck + c) * 2 * (size_t)Npad * 16;
+                const unsigned char *srcimg = a.img + ((size_t)slot_off * nck + c) * b_bytes;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         smem_u32(stage + kTcA)),
@@ -949,6 +1141,18 @@ m2l_tc(TcArgs a) {
                             v.w += acc[q + 3];
                             dst[q / 4] = v;
                         }
+                } else if (H16) {
+                    // undo the column scales of the image and the input scale
+                    float sig, sig_inv;
+                    input_scale(*L.amax, sig, sig_inv);
+                    const float4 *ci = reinterpret_cast<const float4 *>(a.cs + Npad + ph_half * nsum);
+#pragma unroll
+                    for (int q = 0; q < NS; q += 4)
+                        if (q < nsum) {
+                            const float4 c4 = __ldg(ci + q / 4);
+                            dst[q / 4] = make_float4(acc[q] * c4.x * sig_inv, acc[q + 1] * c4.y * sig_inv,
+                                                     acc[q + 2] * c4.z * sig_inv, acc[q + 3] * c4.w * sig_inv);
+                        }
                 } else {
 #pragma unroll
                     for (int q = 0; q < NS; q += 4)
@@ -966,9 +1170,18 @@ m2l_tc(TcArgs a) {
 
 }  // namespace
 
+// Bytes of the split FP16 inputs of levels 2..l-1 (the start of level l in
+// the split buffer), for the plan's largest batch.
+static size_t split_offset(const FmmPlan *F, int adj, int l) {
+    size_t off = 0;
+    for (int k = 2; k < l; ++k) off += (size_t)(adj ? F->lev[k].nt : F->lev[k].ns) * F->B * F->KS * sizeof(float);
+    return off;
+}
+
 gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
     FmmPlan *F = plan->fmm;
     if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
+    GF_TRY(plan->arena.alloc((void **)&F->tc_split_adj, std::max<size_t>(16, split_offset(F, 1, F->L + 1))));
     for (int adj = 1; adj < 2; ++adj) {
         std::vector<TcLevel> h(F->L + 1);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
@@ -988,6 +1201,8 @@ gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
                 t.mn[d] = F->mn[l][d];
             }
             for (int c = 0; c <= 8; ++c) t.cls_off[c] = adj ? F->scls_off[l][c] : lv.cls_off[c];
+            t.amax = F->tc_amax + (adj ? kMaxLevels + 1 : 0) + l;
+            t.split = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l);
         }
         std::vector<unsigned char> &hb = adj ? F->tc_levels_adj_host : F->tc_levels_host;
         void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
@@ -1001,6 +1216,8 @@ gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
 gf_status m2l_tc_prepare(gf_plan_s *plan) {
     FmmPlan *F = plan->fmm;
     if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
+    GF_TRY(plan->arena.alloc((void **)&F->tc_amax, 2 * (kMaxLevels + 1) * sizeof(uint32_t)));
+    GF_TRY(plan->arena.alloc((void **)&F->tc_split, std::max<size_t>(16, split_offset(F, 0, F->L + 1))));
     for (int adj = 0; adj < 1; ++adj) {
         std::vector<TcLevel> h(F->L + 1);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
@@ -1020,6 +1237,8 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
                 t.mn[d] = F->mn[l][d];
             }
             for (int c = 0; c <= 8; ++c) t.cls_off[c] = adj ? F->scls_off[l][c] : lv.cls_off[c];
+            t.amax = F->tc_amax + (adj ? kMaxLevels + 1 : 0) + l;
+            t.split = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l);
         }
         std::vector<unsigned char> &hb = adj ? F->tc_levels_adj_host : F->tc_levels_host;
         void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
@@ -1082,17 +1301,102 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
 
 namespace {
 
+// Largest |x| over the first kin components of every row of each level's
+// M2L input (forward: ME_l; adjoint: the LE_l duals), as the bits of a
+// non-negative float, combined with atomicMax (out[] zeroed before).
+struct AmaxArgs {
+    const float4 *in[kMaxLevels + 1];
+    int64_t rows[kMaxLevels + 1];
+    uint32_t *out;
+    int lmin, ld4, kin;
+};
+
+__global__ void __launch_bounds__(256) input_absmax(AmaxArgs a) {
+    const int l = a.lmin + (int)blockIdx.y;
+    const float4 *p = a.in[l];
+    const int64_t n = a.rows[l] * a.ld4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = i + u * stride < n ? __ldg(p + i + u * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = (int)((i + u * stride) % a.ld4) * 4;
+            if (c < a.kin) m = fmaxf(m, fabsf(v[u].x));
+            if (c + 1 < a.kin) m = fmaxf(m, fabsf(v[u].y));
+            if (c + 2 < a.kin) m = fmaxf(m, fabsf(v[u].z));
+            if (c + 3 < a.kin) m = fmaxf(m, fabsf(v[u].w));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(a.out + l, __float_as_uint(m));
+}
+
+// Split every M2L input row into the FP16 operand parts the tensor-core
+// M2L copies: x s = hi + lo + O(2^-22 |x s|), s = the level's input scale;
+// per row and 32-wide chunk, 64 bytes of hi then 64 bytes of lo (inputs
+// beyond kin are zero).
+struct SplitArgs {
+    unsigned char *out[kMaxLevels + 1];
+};
+
+__global__ void __launch_bounds__(256) input_split(AmaxArgs a, SplitArgs o, int nck) {
+    const int l = a.lmin + (int)blockIdx.y;
+    float sig, sig_inv;
+    input_scale(a.out[l], sig, sig_inv);
+    const int64_t items = a.rows[l] * nck;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / nck;
+        const int c = (int)(i - r * nck);
+        const float4 *src = a.in[l] + r * a.ld4 + 8 * c;
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldg(src + q);
+        uint4 *dst = reinterpret_cast<uint4 *>(o.out[l] + (size_t)i * 128);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float x8[8] = {v[2 * q].x,     v[2 * q].y,     v[2 * q].z,     v[2 * q].w,
+                                 v[2 * q + 1].x, v[2 * q + 1].y, v[2 * q + 1].z, v[2 * q + 1].w};
+            uint32_t h[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int kin = 32 * c + 8 * q + 2 * j;
+                const float x0 = kin < a.kin ? x8[2 * j] * sig : 0.f;
+                const float x1 = kin + 1 < a.kin ? x8[2 * j + 1] * sig : 0.f;
+                const __half2 hh = __floats2half2_rn(x0, x1);
+                const float2 hf = __half22float2(hh);
+                const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+                memcpy(&h[j], &hh, 4);
+                memcpy(&lo[j], &ll, 4);
+            }
+            dst[q] = make_uint4(h[0], h[1], h[2], h[3]);
+            dst[4 + q] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
 gf_status tc_launch(TcArgs &a, int tiles, cudaStream_t st) {
     if (tiles == 0) return GF_OK;
     a.ntiles = tiles;
     // the M2L runs one tile per CTA; the other kinds loop over tiles, one CTA per SM
     const int grid = a.kind == kTcM2L ? tiles : std::min(tiles, 152);
-    const size_t shm = tc_smem_bytes(a.Npad);
+    const bool h16 = a.kind == kTcM2L;
+    const size_t shm = tc_smem_bytes(a.Npad, h16);
+    a.nst = tc_stages(a.Npad, h16);
     const int nsum = a.Npad / 2;
 #define GF_TC_LAUNCH(NS)                                                  \
     do {                                                                  \
-        GF_TRY(ensure_smem(m2l_tc<NS>, shm));                             \
-        m2l_tc<NS><<<grid, kTcThreads, shm, st>>>(a);                     \
+        if (a.kind == kTcM2L) {                                           \
+            GF_TRY((ensure_smem(m2l_tc<NS, true>, shm)));                 \
+            m2l_tc<NS, true><<<grid, kTcThreads, shm, st>>>(a);           \
+        } else {                                                          \
+            GF_TRY((ensure_smem(m2l_tc<NS, false>, shm)));                \
+            m2l_tc<NS, false><<<grid, kTcThreads, shm, st>>>(a);          \
+        }                                                                 \
     } while (0)
     if (nsum <= 32)
         GF_TC_LAUNCH(32);
@@ -1117,7 +1421,6 @@ TcArgs tc_args(gf_plan_s *plan, int B) {
     a.B = B;
     a.Npad = T->tc_npad;
     a.nck = T->tc_nck;
-    a.nst = tc_stages(T->tc_npad);
     a.kin = F->K;
     a.ldin = F->KS;
     a.status = plan->d_status;
@@ -1132,7 +1435,34 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     a.lmin = 2;
     a.kind = kTcM2L;
     a.noff = 189;
-    a.img = adj ? T->am2l_tc : T->m2l_tc;
+    a.nck = T->tc_nck_h;
+    a.img = (const unsigned char *)(adj ? T->am2l_tc : T->m2l_tc);
+    a.cs = adj ? T->am2l_cs : T->m2l_cs;
+    if (F->L < 2) return GF_OK;
+    // the largest |input| of every level, for the FP16 input scales
+    {
+        AmaxArgs m;
+        memset(&m, 0, sizeof(m));
+        m.out = F->tc_amax + (adj ? kMaxLevels + 1 : 0);
+        m.lmin = 2;
+        m.ld4 = F->KS / 4;
+        m.kin = F->K;
+        int64_t most = 0;
+        for (int l = 2; l <= F->L; ++l) {
+            m.in[l] = (const float4 *)(adj ? F->lev[l].le : F->lev[l].me);
+            m.rows[l] = (adj ? F->lev[l].nt : F->lev[l].ns) * B;
+            most = std::max(most, m.rows[l] * m.ld4);
+        }
+        GF_CUDA(cudaMemsetAsync(m.out, 0, (kMaxLevels + 1) * sizeof(uint32_t), st));
+        const int gx = (int)std::min<int64_t>(8 * 152, std::max<int64_t>(1, (most + 1023) / 1024));
+        input_absmax<<<dim3(gx, F->L - 1), 256, 0, st>>>(m);
+        GF_KERNEL_DONE();
+        SplitArgs o;
+        memset(&o, 0, sizeof(o));
+        for (int l = 2; l <= F->L; ++l) o.out[l] = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l);
+        input_split<<<dim3(gx, F->L - 1), 256, 0, st>>>(m, o, T->tc_nck_h);
+        GF_KERNEL_DONE();
+    }
     const int nbox = 128 / B;
     int tiles = 0, e = 0;
     for (int l = 2; l <= F->L; ++l)
@@ -1158,7 +1488,7 @@ gf_status p2m_run_tc_impl(gf_plan_s *plan, int B, cudaStream_t st) {
     a.kin = b3;
     a.ldin = b3;
     a.nck = b3 / 16;
-    a.img = F->p2m_tc;
+    a.img = (const unsigned char *)F->p2m_tc;
     const int nbox = 128 / B;
     const int64_t ns = F->lev[F->L].ns;
     const int tiles = (int)((ns + nbox - 1) / nbox);
@@ -1178,7 +1508,7 @@ gf_status xlate_run_tc(gf_plan_s *plan, int level, int kind, int B, cudaStream_t
     a.lmin = level;
     a.kind = kind == 0 ? kTcM2M : kTcL2L;
     a.noff = kind == 0 ? 8 : 1;
-    a.img = kind == 0 ? T->m2m_tc : T->l2l_tc;
+    a.img = (const unsigned char *)(kind == 0 ? T->m2m_tc : T->l2l_tc);
     const TcLevel &h = reinterpret_cast<const TcLevel *>(F->tc_xlate_host.data())[(kind == 0 ? 0 : F->L + 1) + level];
     const int nbox = 128 / B;
     int tiles = 0;
@@ -1248,7 +1578,7 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st
 bool p2m_tc_ok(const gf_plan_s *plan, int B) {
     const FmmPlan *F = plan->fmm;
     return F && F->mixed && F->p2m_tc && F->tc_xlate && !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
-           tc_stages(F->tab->tc_npad) >= 2;
+           tc_stages(F->tab->tc_npad, false) >= 2;
 }
 
 gf_status p2m_run_tc(gf_plan_s *plan, int B, cudaStream_t st) { return p2m_run_tc_impl(plan, B, st); }
@@ -1258,7 +1588,7 @@ gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_
     FmmPlan *F = plan->fmm;
     // mixed precision: forward M2M / L2L on the tensor cores (3xTF32)
     if (sizeof(Ts) == 4 && sizeof(Tc) == 4 && (kind == 0 || kind == 1) && F->tc_xlate &&
-        !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 && tc_stages(F->tab->tc_npad) >= 2)
+        !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 && tc_stages(F->tab->tc_npad, false) >= 2)
         return xlate_run_tc(plan, level, kind, B, st);
     XArgs a;
     a.K = F->K;
@@ -1356,7 +1686,7 @@ gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     const bool tc = sizeof(T) == 4 && F->tab->m2l_tc && (adj ? F->tc_levels_adj : F->tc_levels) &&
                     !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
-                    tc_smem_bytes(F->tab->tc_npad) <= 227 * 1024;
+                    tc_stages(F->tab->tc_npad, true) >= kTcLag + 1;
     if (tc) return m2l_run_tc(plan, B, adj, st);
     for (int l = 2; l <= F->L; ++l) {
         if (F->lev[l].nt == 0 && !adj) continue;   // the adjoint writes every source box

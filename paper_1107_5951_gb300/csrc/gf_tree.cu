@@ -243,6 +243,8 @@ size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_optio
     const double ntgt = std::min<double>((double)M, nleaf * 4.0) * 8.0 / 7.0 + 64;
     double bytes = (nsrc + ntgt) * K * rs * opt->max_batch;
     bytes += nleaf * b * b * b * rs * opt->max_batch;          // blocked densities
+    if (opt->precision == GF_PREC_MIXED)                         // M2L inputs split into FP16 parts
+        bytes += nsrc * ((K + 31) / 32 * 32) * 4.0 * opt->max_batch;
     bytes += (double)M * (8 + 4 + 4 + 12 + 24) + ntgt * 24;       // keys, perm, locals, box tables
     bytes += (double)M * 32 + 8e6;                                // sort buffers and scratch
     return (size_t)bytes;

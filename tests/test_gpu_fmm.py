@@ -144,8 +144,9 @@ def test_fmm_mixed_matches_oracle(seed, npts):
 
 @pytest.mark.parametrize("p", [4, 8, 12, 14, 15])
 def test_m2l_tensor_cores_match_simt(p):
-    """Mixed precision: the tcgen05 M2L (3xTF32, FP32 accumulation in tensor
-    memory) and the SIMT FP32 M2L agree to FP32-level rounding, and the
+    """Mixed precision: the tcgen05 M2L (three FP16 products of scaled
+    high/low parts, FP32 accumulation in tensor memory) and the SIMT FP32 M2L
+    agree to FP32-level rounding, and the
     tensor-core result meets the oracle at the accuracy its expansion degree
     allows (<= 1e-5 from p = 10 up)."""
     wk = cube_case(81 + p, n=28, vol_targets=400)
