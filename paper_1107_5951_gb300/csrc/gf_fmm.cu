@@ -572,6 +572,11 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
@@ -596,6 +601,7 @@ constexpr int kEvalWarps = 4;
 constexpr int kEvalChunk = 64;
 constexpr int kTPL = 2;            // targets per lane: a work item has <= 64 targets
 constexpr int kSrcTable = 512;     // per-block table of a leaf's source offsets
+constexpr int kMaxLat = 8;         // lattice planes per axis of a leaf (lattice near field)
 
 struct EvalArgs {
     const int4 *items;
@@ -615,6 +621,14 @@ struct EvalArgs {
                                // a source coincident with an observer (else only
                                // the observer's own leaf can)
     double *g, *gz;
+    // Lattice form of a leaf's sources (rules that are tensor products of m
+    // nodes per axis): the b^3 nq sources sit on N1^3 lattice points, N1 =
+    // b m.  lat_c[a][i]: coordinate of lattice plane i along axis a from the
+    // leaf centre (voxel units); lat_q[(ia % m) + m ((ib % m) + m (ic % m))]
+    // is the rule's node at lattice point (ia, ib, ic).
+    int lat_m;
+    float lat_c[3][kMaxLat];
+    int lat_q[kMaxQuad];
 };
 
 // Near field + far field of the observers of one leaf, one warp per work
@@ -622,7 +636,9 @@ struct EvalArgs {
 // shared-memory slice in chunks of 64 (position relative to the target
 // leaf's centre, mass times quadrature weight) and every lane sweeps them
 // for its two observers.  Per-leaf partial sums are merged with TwoSum.
-template <class T>
+// N1 > 0 (FP32, sources on an N1^3 lattice per leaf): the lattice form of
+// the near field below.
+template <class T, int N1>
 __global__ void __launch_bounds__(kEvalWarps * 32, sizeof(T) == 4 ? 6 : 1)   // FP32: 6 blocks (24 warps) per SM
 eval_kernel(EvalArgs a) {
     extern __shared__ unsigned char shraw[];
@@ -647,7 +663,17 @@ eval_kernel(EvalArgs a) {
     const T inv_b = T(1) / T(a.b);
     const T eps2 = (T)a.eps2;
     const bool use_tab = nsrc <= kSrcTable;
-    if (use_tab) {
+    if (N1 > 0) {
+        // lattice point n = i + N1 (j + N1 k): its voxel and the rule's weight
+        const int m = a.lat_m;
+        for (int n = threadIdx.x; n < N1 * N1 * N1; n += blockDim.x) {
+            const int i = n % N1, j = (n / N1) % N1, k = n / (N1 * N1);
+            const int v = i / m + a.b * (j / m + a.b * (k / m));
+            const int q = a.lat_q[i % m + m * (j % m + m * (k % m))];
+            tab[n].w = (T)a.qr->wn[q];
+            tvox[n] = v;
+        }
+    } else if (use_tab) {
         for (int u = threadIdx.x; u < nsrc; u += blockDim.x) {
             const int v = u / a.nq, q = u - v * a.nq;
             Vec4<T> e;
@@ -700,6 +726,89 @@ eval_kernel(EvalArgs a) {
                 const int64_t sl = (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx;
                 const T *ms = mass + (sl * a.B + bb) * b3;
                 const T ox = T(dx * a.b), oy = T(dy * a.b), oz = T(dz * a.b);
+                if constexpr (N1 > 0 && std::is_same<T, float>::value) {
+                    // Lattice form.  With d = t - s and the sources on the planes
+                    // x = X_i, y = Y_j, z = Z_k, the leaf's sum of w d / |d|^3 is
+                    //   (sum_i dx_i Sx_i, sum_j dy_j Sy_j, sum_k dz_k Sz_k),
+                    //   Sx_i = sum_{j,k} w_ijk |d_ijk|^-3  (Sy_j, Sz_k alike),
+                    // so a source costs one add (|d|^2 from the squared plane
+                    // distances), the reciprocal square root, three multiplies and
+                    // three adds; the lane's two observers form one packed pair.
+                    constexpr int N3 = N1 * N1 * N1;
+                    __syncwarp();
+                    float2 *wl = reinterpret_cast<float2 *>(wsh);
+                    for (int n = lane; n < N3; n += 32) {
+                        const float w = tab[n].w * ms[tvox[n]];
+                        wl[n] = make_float2(w, w);
+                    }
+                    __syncwarp();
+                    const uint64_t PX = pk2(tx[0], tx[1]), PY = pk2(ty[0], ty[1]), PZ = pk2(tz[0], tz[1]);
+                    uint64_t X2[N1], Y2[N1], SX[N1], SY[N1];
+#pragma unroll
+                    for (int i = 0; i < N1; ++i) {
+                        const float cx = a.lat_c[0][i] + ox, cy = a.lat_c[1][i] + oy;
+                        const uint64_t ex = sub2(PX, pk2(cx, cx)), ey = sub2(PY, pk2(cy, cy));
+                        X2[i] = mul2(ex, ex);
+                        Y2[i] = mul2(ey, ey);
+                        SX[i] = SY[i] = 0;
+                    }
+                    uint64_t QZ = 0;
+                    // one z-plane of the lattice at a time (Sz_k is a single sum)
+                    auto lattice = [&](auto guarded) {
+                        constexpr bool kGuard = decltype(guarded)::value;
+#pragma unroll 1
+                        for (int k = 0; k < N1; ++k) {
+                            const float cz = a.lat_c[2][k] + oz;
+                            const uint64_t ez = sub2(PZ, pk2(cz, cz));
+                            const uint64_t Z2 = mul2(ez, ez);
+                            const uint64_t *wk = reinterpret_cast<const uint64_t *>(wl + N1 * N1 * k);
+                            uint64_t SZ = 0;
+#pragma unroll
+                            for (int j = 0; j < N1; ++j) {
+                                const uint64_t YZ = add2(Y2[j], Z2);
+#pragma unroll
+                                for (int i = 0; i < N1; ++i) {
+                                    const uint64_t R2 = add2(X2[i], YZ);
+                                    float r0, r1;
+                                    up2(R2, r0, r1);
+                                    float i0 = rsqrt_ftz(r0), i1 = rsqrt_ftz(r1);
+                                    if constexpr (kGuard) {
+                                        i0 = r0 > (float)eps2 ? i0 : 0.f;
+                                        i1 = r1 > (float)eps2 ? i1 : 0.f;
+                                    }
+                                    const uint64_t RI = pk2(i0, i1);
+                                    const uint64_t K3 = mul2(mul2(RI, RI), mul2(RI, wk[i + N1 * j]));
+                                    SX[i] = add2(SX[i], K3);
+                                    SY[j] = add2(SY[j], K3);
+                                    SZ = add2(SZ, K3);
+                                }
+                            }
+                            QZ = fma2(SZ, ez, QZ);
+                        }
+                    };
+                    if (a.guard_all || nb == 13)
+                        lattice(std::true_type{});
+                    else
+                        lattice(std::false_type{});
+                    uint64_t QX = 0, QY = 0;
+#pragma unroll
+                    for (int i = 0; i < N1; ++i) {
+                        const float cx = a.lat_c[0][i] + ox, cy = a.lat_c[1][i] + oy;
+                        QX = fma2(SX[i], sub2(PX, pk2(cx, cx)), QX);
+                        QY = fma2(SY[i], sub2(PY, pk2(cy, cy)), QY);
+                    }
+                    float gx[2], gy[2], gz[2];
+                    up2(QX, gx[0], gx[1]);
+                    up2(QY, gy[0], gy[1]);
+                    up2(QZ, gz[0], gz[1]);
+#pragma unroll
+                    for (int u = 0; u < kTPL; ++u) {
+                        two_sum(hx[u], lx[u], (T)gx[u]);
+                        two_sum(hy[u], ly[u], (T)gy[u]);
+                        two_sum(hz[u], lz[u], (T)gz[u]);
+                    }
+                    continue;
+                }
                 T px[kTPL], py[kTPL], pz[kTPL];
 #pragma unroll
                 for (int u = 0; u < kTPL; ++u) px[u] = py[u] = pz[u] = T(0);
@@ -1032,6 +1141,44 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
 // ---------------------------------------------------------------- forward
 namespace {
 
+// Lattice form of a leaf's sources for the near field: when the rule is a
+// tensor product of m nodes per axis (the same nodes on every axis), the
+// b^3 nq sources of a leaf sit on an N1^3 lattice, N1 = b m.  Fills the
+// plane coordinates and the node map of `a` and returns N1, or 0 when the
+// rule is not such a product or N1 is not the size the kernel handles (4).
+static int lattice_of(const QuadRule &qr, int b, EvalArgs &a) {
+    double nodes[kMaxQuad];
+    int m = 0;
+    for (int q = 0; q < qr.nq; ++q) {   // distinct x-nodes, ascending
+        const double x = qr.xi[q][0];
+        bool seen = false;
+        for (int t = 0; t < m; ++t) seen = seen || nodes[t] == x;
+        if (!seen) nodes[m++] = x;
+    }
+    std::sort(nodes, nodes + m);
+    if (m * m * m != qr.nq || b * m != 4 || b * m > kMaxLat) return 0;
+    int seen[kMaxQuad];
+    for (int t = 0; t < qr.nq; ++t) seen[t] = 0;
+    for (int q = 0; q < qr.nq; ++q) {
+        int idx[3];
+        for (int d = 0; d < 3; ++d) {
+            idx[d] = -1;
+            for (int t = 0; t < m; ++t)
+                if (qr.xi[q][d] == nodes[t]) idx[d] = t;
+            if (idx[d] < 0) return 0;
+        }
+        const int c = idx[0] + m * (idx[1] + m * idx[2]);
+        if (seen[c]++) return 0;
+        a.lat_q[c] = q;
+    }
+    a.lat_m = m;
+    const float half_b = 0.5f * (float)b;
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < b * m; ++i)
+            a.lat_c[d][i] = ((float)(i / m) + (float)(0.5 + 0.5 * nodes[i % m])) - half_b;
+    return b * m;
+}
+
 template <class T>
 gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, double *g, double *gz,
                       cudaStream_t st) {
@@ -1145,11 +1292,17 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
                 if (fabs(plan->quad.xi[q][d]) >= 1.0) a.guard_all = 1;
         a.g = g;
         a.gz = gz;
+        const int n1 = sizeof(T) == 4 ? lattice_of(plan->quad, F->b, a) : 0;
         const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
                            sizeof(T) * kEvalWarps * ((4 * kEvalChunk + 3 * F->p * F->p + 7) & ~7);
         const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
-        GF_TRY(ensure_smem(eval_kernel<T>, shm));
-        eval_kernel<T><<<grid, kEvalWarps * 32, shm, st>>>(a);
+        if (sizeof(T) == 4 && n1 == 4) {
+            GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
+            eval_kernel<float, 4><<<grid, kEvalWarps * 32, shm, st>>>(a);
+        } else {
+            GF_TRY((ensure_smem(eval_kernel<T, 0>, shm)));
+            eval_kernel<T, 0><<<grid, kEvalWarps * 32, shm, st>>>(a);
+        }
         GF_KERNEL_DONE();
     }
     stage_mark(plan, 6, st);
