@@ -597,11 +597,79 @@ __device__ __forceinline__ void two_sum(T &hi, T &lo, T x) {
     hi = s;
 }
 
+// Coefficients of the regular-harmonic recursion of the L2P sums (the
+// recursion of fmm_math.cuh), for m < n < kMaxP at t = n (n + 1) / 2 + m:
+//   c_ra[t] = (2n - 1) / sqrt((n + m)(n - m)),
+//   c_rb[t] = sqrt((n - 1 + m)(n - 1 - m)) / sqrt((n + m)(n - m))  (0 for n = m + 1),
+// and c_rf[m] = -sqrt((2m - 1) / (2m)) for the sectoral step, so that the
+// FP32 evaluation needs no square roots or divisions.
+__constant__ float c_ra[kMaxP * (kMaxP + 1) / 2], c_rb[kMaxP * (kMaxP + 1) / 2], c_rf[kMaxP];
+
+// sum_{n<p, m} D_n^m conj(R_n^m(X)) for the gradient expansions of
+// l2p_sum (fmm_math.cuh), for two points at once (packed pairs X, Y, Z).
+// D holds each coefficient as a duplicated pair {d, d}, with the factor 2
+// of the m > 0 terms folded in.
+__device__ __forceinline__ void l2p_sum2(int p, const float2 *Dx, const float2 *Dy, const float2 *Dz, uint64_t X,
+                                         uint64_t Y, uint64_t Z, uint64_t &gx, uint64_t &gy, uint64_t &gz) {
+    const uint64_t r2 = fma2(Z, Z, fma2(Y, Y, mul2(X, X)));
+    uint64_t sr = pk2(1.f, 1.f), si = 0;
+    uint64_t ax = 0, ay = 0, az = 0;
+    auto ld = [](const float2 *d, int k) { return *reinterpret_cast<const uint64_t *>(d + k); };
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) {
+            const float f = c_rf[m];
+            const uint64_t XF = mul2(X, pk2(f, f)), YF = mul2(Y, pk2(f, f)), YN = mul2(Y, pk2(-f, -f));
+            const uint64_t nr = fma2(XF, sr, mul2(YN, si));
+            const uint64_t ni = fma2(XF, si, mul2(YF, sr));
+            sr = nr;
+            si = ni;
+        }
+        uint64_t r1 = sr, i1 = si, r0 = 0, i0 = 0;
+        for (int n = m; n < p; ++n) {
+            uint64_t cr = sr, ci = si;
+            if (n > m) {
+                const int t = n * (n + 1) / 2 + m;
+                const float av = c_ra[t], bv = c_rb[t];
+                const uint64_t AZ = mul2(Z, pk2(av, av)), BN = mul2(r2, pk2(-bv, -bv));
+                cr = fma2(AZ, r1, mul2(BN, r0));
+                ci = fma2(AZ, i1, mul2(BN, i0));
+                r0 = r1;
+                i0 = i1;
+                r1 = cr;
+                i1 = ci;
+            }
+            if (m == 0) {
+                const int k = n * n;
+                ax = fma2(ld(Dx, k), cr, ax);
+                ay = fma2(ld(Dy, k), cr, ay);
+                az = fma2(ld(Dz, k), cr, az);
+            } else {
+                const int k = n * n + 2 * m - 1;
+                ax = fma2(ld(Dx, k), cr, fma2(ld(Dx, k + 1), ci, ax));
+                ay = fma2(ld(Dy, k), cr, fma2(ld(Dy, k + 1), ci, ay));
+                az = fma2(ld(Dz, k), cr, fma2(ld(Dz, k + 1), ci, az));
+            }
+        }
+    }
+    gx = ax;
+    gy = ay;
+    gz = az;
+}
+
 constexpr int kEvalWarps = 4;
 constexpr int kEvalChunk = 64;
 constexpr int kTPL = 2;            // targets per lane: a work item has <= 64 targets
 constexpr int kSrcTable = 512;     // per-block table of a leaf's source offsets
 constexpr int kMaxLat = 8;         // lattice planes per axis of a leaf (lattice near field)
+
+// Elements of one warp's shared-memory slice of the evaluation kernel
+// (a multiple of 8): 4 kEvalChunk staged source values, three gradient
+// expansions of P2 coefficients (FP32: duplicated pairs) and 27
+// neighbour-leaf indices (int64).
+inline __host__ __device__ int eval_slice(int P2, int tsize) {
+    const int dmul = tsize == 4 ? 2 : 1;
+    return (4 * kEvalChunk + 3 * dmul * P2 + 27 * 8 / tsize + 7) & ~7;
+}
 
 struct EvalArgs {
     const int4 *items;
@@ -651,11 +719,14 @@ eval_kernel(EvalArgs a) {
     Vec4<T> *tab = reinterpret_cast<Vec4<T> *>(shraw);
     int *tvox = reinterpret_cast<int *>(tab + kSrcTable);
     // per-warp slice, a multiple of 8 elements so every slice keeps the
-    // alignment of the vector type
-    const int wstride = (4 * kEvalChunk + 3 * P2 + 7) & ~7;
+    // alignment of the vector type: staged sources, the gradient expansions
+    // (FP32: duplicated pairs), the item's neighbour leaves
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    const int wstride = eval_slice(P2, sizeof(T));
     T *wsh = reinterpret_cast<T *>(tvox + kSrcTable) + (size_t)warp * wstride;
     Vec4<T> *src = reinterpret_cast<Vec4<T> *>(wsh);
-    T *Dx = wsh + 4 * kEvalChunk, *Dy = Dx + P2, *Dz = Dy + P2;
+    T *Dx = wsh + 4 * kEvalChunk, *Dy = Dx + (kF32 ? 2 : 1) * P2, *Dz = Dy + (kF32 ? 2 : 1) * P2;
+    int64_t *nbl = reinterpret_cast<int64_t *>(Dz + (kF32 ? 2 : 1) * P2);
     const T *tloc = reinterpret_cast<const T *>(a.tloc);
     const T *mass = reinterpret_cast<const T *>(a.mass);
     const T *le = reinterpret_cast<const T *>(a.le);
@@ -686,6 +757,15 @@ eval_kernel(EvalArgs a) {
         }
     }
     __syncthreads();
+    // lattice form: this lane's two lattice points (weight, voxel)
+    float lw0 = 0.f, lw1 = 0.f;
+    int lv0 = 0, lv1 = 0;
+    if (N1 > 0) {
+        lw0 = (float)tab[lane].w;
+        lw1 = (float)tab[lane + 32].w;
+        lv0 = tvox[lane];
+        lv1 = tvox[lane + 32];
+    }
     for (int64_t it = (int64_t)blockIdx.x * kEvalWarps + warp; it < a.n_items;
          it += (int64_t)gridDim.x * kEvalWarps) {
         const int4 item = a.items[it];
@@ -712,18 +792,24 @@ eval_kernel(EvalArgs a) {
             ty[u] = tloc[3 * i + 1];
             tz[u] = tloc[3 * i + 2];
         }
+        // the item's neighbour leaves: source-block index, or -1 outside the block
+        __syncwarp();
+        if (lane < 27) {
+            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1], sz = lc[2] + dz - a.blk.lo[2];
+            const bool in = sx >= 0 && sy >= 0 && sz >= 0 && sx < a.blk.n[0] && sy < a.blk.n[1] && sz < a.blk.n[2];
+            nbl[lane] = in ? (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx : -1;
+        }
+        __syncwarp();
         for (int bb = 0; bb < a.B; ++bb) {
             T hx[kTPL], hy[kTPL], hz[kTPL], lx[kTPL], ly[kTPL], lz[kTPL];
 #pragma unroll
             for (int u = 0; u < kTPL; ++u) hx[u] = hy[u] = hz[u] = lx[u] = ly[u] = lz[u] = T(0);
             // ---- near field: the leaf itself and its nearest neighbours
             for (int nb = 0; nb < 27; ++nb) {
+                const int64_t sl = nbl[nb];
+                if (sl < 0) continue;
                 const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
-                const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1],
-                              sz = lc[2] + dz - a.blk.lo[2];
-                if (sx < 0 || sy < 0 || sz < 0 || sx >= a.blk.n[0] || sy >= a.blk.n[1] || sz >= a.blk.n[2])
-                    continue;
-                const int64_t sl = (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx;
                 const T *ms = mass + (sl * a.B + bb) * b3;
                 const T ox = T(dx * a.b), oy = T(dy * a.b), oz = T(dz * a.b);
                 if constexpr (N1 > 0 && std::is_same<T, float>::value) {
@@ -737,9 +823,11 @@ eval_kernel(EvalArgs a) {
                     constexpr int N3 = N1 * N1 * N1;
                     __syncwarp();
                     float2 *wl = reinterpret_cast<float2 *>(wsh);
-                    for (int n = lane; n < N3; n += 32) {
-                        const float w = tab[n].w * ms[tvox[n]];
-                        wl[n] = make_float2(w, w);
+                    static_assert(N3 == 64, "two lattice points per lane");
+                    {
+                        const float w0 = lw0 * ms[lv0], w1 = lw1 * ms[lv1];
+                        wl[lane] = make_float2(w0, w0);
+                        wl[lane + 32] = make_float2(w1, w1);
                     }
                     __syncwarp();
                     const uint64_t PX = pk2(tx[0], tx[1]), PY = pk2(ty[0], ty[1]), PZ = pk2(tz[0], tz[1]);
@@ -942,14 +1030,48 @@ eval_kernel(EvalArgs a) {
             // ---- far field: gradient of the leaf's local expansion
             __syncwarp();
             const T *L = le + ((int64_t)leaf * a.B + bb) * a.ldk;
-            for (int e = lane; e < P2; e += 32) grad_coeff<T>(L, e, Dx[e], Dy[e], Dz[e]);
-            __syncwarp();
+            T fxa[kTPL], fya[kTPL], fza[kTPL];
+            if constexpr (kF32) {
+                // duplicated pairs, the factor 2 of the m > 0 terms folded in;
+                // both observers of the lane in one packed sum
+                float2 *Dx2 = reinterpret_cast<float2 *>(Dx), *Dy2 = reinterpret_cast<float2 *>(Dy),
+                       *Dz2 = reinterpret_cast<float2 *>(Dz);
+                for (int e = lane; e < P2; e += 32) {
+                    float vx, vy, vz;
+                    grad_coeff<float>(reinterpret_cast<const float *>(L), e, vx, vy, vz);
+                    int n = 0;
+                    while ((n + 1) * (n + 1) <= e) ++n;
+                    const float f2 = e == n * n ? 1.f : 2.f;
+                    Dx2[e] = make_float2(f2 * vx, f2 * vx);
+                    Dy2[e] = make_float2(f2 * vy, f2 * vy);
+                    Dz2[e] = make_float2(f2 * vz, f2 * vz);
+                }
+                __syncwarp();
+                uint64_t FX, FY, FZ;
+                l2p_sum2(a.p, Dx2, Dy2, Dz2, pk2(tx[0] * inv_b, tx[1] * inv_b), pk2(ty[0] * inv_b, ty[1] * inv_b),
+                         pk2(tz[0] * inv_b, tz[1] * inv_b), FX, FY, FZ);
+                float f0, f1;
+                up2(FX, f0, f1);
+                fxa[0] = f0;
+                fxa[1] = f1;
+                up2(FY, f0, f1);
+                fya[0] = f0;
+                fya[1] = f1;
+                up2(FZ, f0, f1);
+                fza[0] = f0;
+                fza[1] = f1;
+            } else {
+                for (int e = lane; e < P2; e += 32) grad_coeff<T>(L, e, Dx[e], Dy[e], Dz[e]);
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < kTPL; ++u)
+                    l2p_sum<T>(a.p, Dx, Dy, Dz, tx[u] * inv_b, ty[u] * inv_b, tz[u] * inv_b, fxa[u], fya[u], fza[u]);
+            }
+            const double far_s = -1.0 / ((double)a.b * (double)a.b);
 #pragma unroll
             for (int u = 0; u < kTPL; ++u) {
                 if (tid[u] < 0) continue;
-                T fx, fy, fz;
-                l2p_sum<T>(a.p, Dx, Dy, Dz, tx[u] * inv_b, ty[u] * inv_b, tz[u] * inv_b, fx, fy, fz);
-                const double far_s = -1.0 / ((double)a.b * (double)a.b);
+                const T fx = fxa[u], fy = fya[u], fz = fza[u];
                 const double gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
                 const double gy = ((double)hy[u] + (double)ly[u] + far_s * (double)fy) * a.scale;
                 const double gzv = ((double)hz[u] + (double)lz[u] + far_s * (double)fz) * a.scale;
@@ -989,6 +1111,24 @@ __global__ void transpose_ops(const double *__restrict__ fwd, double *__restrict
 // ---------------------------------------------------------------- tables
 std::mutex g_tab_mu;
 std::vector<Tables *> g_tabs;
+
+// The recursion coefficients of l2p_sum2 for the current device.
+gf_status upload_l2p_coefs() {
+    constexpr int NT = kMaxP * (kMaxP + 1) / 2;
+    float ra[NT] = {}, rb[NT] = {}, rf[kMaxP] = {};
+    for (int n = 1; n < kMaxP; ++n)
+        for (int m = 0; m < n; ++m) {
+            const int t = n * (n + 1) / 2 + m;
+            const double inv = 1.0 / std::sqrt((double)((n + m) * (n - m)));
+            ra[t] = (float)((2 * n - 1) * inv);
+            rb[t] = n - 1 > m ? (float)(std::sqrt((double)((n - 1 + m) * (n - 1 - m))) * inv) : 0.f;
+        }
+    for (int m = 1; m < kMaxP; ++m) rf[m] = (float)-std::sqrt((2.0 * m - 1.0) / (2.0 * m));
+    GF_CUDA(cudaMemcpyToSymbol(c_ra, ra, sizeof(ra)));
+    GF_CUDA(cudaMemcpyToSymbol(c_rb, rb, sizeof(rb)));
+    GF_CUDA(cudaMemcpyToSymbol(c_rf, rf, sizeof(rf)));
+    return GF_OK;
+}
 
 }  // namespace
 
@@ -1032,6 +1172,7 @@ gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out) {
     transpose_ops<<<8, 256, 0, st>>>(T->l2l_d, T->al2l_d, T->al2l_f, T->K, 8, 0);
     GF_KERNEL_DONE();
     GF_TRY(m2l_prepare_tables(T, st));
+    GF_TRY(upload_l2p_coefs());
     GF_CUDA(cudaStreamSynchronize(st));
     g_tabs.push_back(T);
     *out = T;
@@ -1294,7 +1435,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         a.gz = gz;
         const int n1 = sizeof(T) == 4 ? lattice_of(plan->quad, F->b, a) : 0;
         const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
-                           sizeof(T) * kEvalWarps * ((4 * kEvalChunk + 3 * F->p * F->p + 7) & ~7);
+                           sizeof(T) * kEvalWarps * eval_slice(F->p * F->p, (int)sizeof(T));
         const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
         if (sizeof(T) == 4 && n1 == 4) {
             GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
