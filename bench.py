@@ -35,7 +35,7 @@ N_SM = 152
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM per clock
 FP64_TFLOPS_NOMINAL = 1.25       # GB300 FP64 (vector and tensor) rate
 FLOPS_PER_PAIR = 20.0            # the paper's count: 5 add, 7 mul, 1 sqrt ~ 20 mul-equivalents
-TF32_PER_BF16 = 1.1 / 2.25       # nominal dense TF32 / BF16 tensor rates
+F16_PER_BF16 = 1.0               # nominal dense FP16 / BF16 tensor rates
 
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture of
@@ -219,12 +219,13 @@ def fmm_roofline(stages, info, args, peaks, workload):
     tensor = args.precision == "mixed" and args.p <= 15 and args.m2l != "simt"
     work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P)"),
             "m2l": ("tensor" if tensor else "alu", 2.0 * K * K * float(info.m2l_pairs),
-                    "m2l_tc (tcgen05 3xTF32, all levels)" if tensor else "m2l_simt (all levels)")}
+                    "m2l_tc (tcgen05 FP16 parts, 3 products, all levels; with the input split)" if tensor
+                    else "m2l_simt (all levels)")}
     dom = max(("eval", "m2l"), key=lambda k: stages.get(k, 0.0))
     bound, flops, kern = work[dom]
     if bound == "tensor":
-        peak = peaks.get("bf16_tflops", 1870.7) * TF32_PER_BF16
-        note = ("TF32 dense = measured BF16 burst x nominal TF32/BF16 (1.1/2.25); the 3xTF32 split "
+        peak = peaks.get("bf16_tflops", 1870.7) * F16_PER_BF16
+        note = ("FP16 dense = measured BF16 burst x nominal FP16/BF16 (1); the high/low split "
                 "executes 3 MMAs per algorithmic flop")
     elif args.precision == "mixed":
         peak, note = fp32_peak_tflops(peaks), "FP32 SIMT: 152 SM x 128 lanes x 2 x sm_max_mhz"

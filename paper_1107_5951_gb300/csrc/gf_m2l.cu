@@ -679,14 +679,16 @@ constexpr int kTcRaw = 4;                   // input chunks in flight per produc
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 64u; }
 // raw FP32 input ring of the producers: [kTcRaw][128 rows][32 or 16 floats]
 __host__ __device__ constexpr uint32_t tc_raw_bytes(bool h16) { return h16 ? 0u : kTcRaw * 128u * 64u; }
-constexpr int kTcLag = 2;   // FP16 inputs: stages copied ahead of their arrival (needs >= 3 stages)
+// Chunks per pipeline stage: the FP16 M2L moves two 32-input chunks per
+// stage (12 MMAs per barrier wait), the TF32 kinds one 16-input chunk.
+__host__ __device__ constexpr int tc_chunks_per_stage(bool h16) { return h16 ? 2 : 1; }
 constexpr size_t kTcSmemBudget = 227 * 1024 - 2048;
 inline int tc_stages(int Npad, bool h16) {
-    const int n = (int)((kTcSmemBudget - tc_raw_bytes(h16)) / tc_stage_bytes(Npad));
+    const int n = (int)((kTcSmemBudget - tc_raw_bytes(h16)) / (tc_chunks_per_stage(h16) * tc_stage_bytes(Npad)));
     return n > kTcMaxStages ? kTcMaxStages : n;
 }
 size_t tc_smem_bytes(int Npad, bool h16) {
-    return (size_t)tc_stages(Npad, h16) * tc_stage_bytes(Npad) + tc_raw_bytes(h16) + 1024;
+    return (size_t)tc_stages(Npad, h16) * tc_chunks_per_stage(h16) * tc_stage_bytes(Npad) + tc_raw_bytes(h16) + 1024;
 }
 
 // 16-byte asynchronous global -> shared copy; nbytes = 0 fills zeros.
@@ -711,7 +713,8 @@ m2l_tc(TcArgs a) {
     const int B = a.B, Npad = a.Npad, nck = a.nck, NST = a.nst;
     const int nsum = Npad / 2;
     const uint32_t b_bytes = 2u * (uint32_t)Npad * 64u;
-    const uint32_t stage_bytes = tc_stage_bytes(Npad);
+    constexpr int S = tc_chunks_per_stage(H16);   // chunks per stage
+    const uint32_t stage_bytes = S * tc_stage_bytes(Npad);   // [A: S x (hi, lo)][B: S x (hi, lo)]
     volatile int *abortp = &abort_flag;
     const int nbox = 128 / B;
     const int noff = a.noff;
@@ -846,7 +849,8 @@ m2l_tc(TcArgs a) {
         for (int w = 0; w < 6; ++w) G += __popc(omask[w]);
     }
     const int offs = G * ntl;        // offsets run by this CTA
-    const int iters = offs * nck;    // stages run by this CTA
+    const int nsp = (nck + S - 1) / S;   // stages per offset
+    const int iters = offs * nsp;    // stages run by this CTA
     // the next offset to run after oi within a tile (noff when none is left)
     auto next_off = [&](int oi) -> int {
         for (++oi; oi < noff; ++oi)
@@ -873,40 +877,48 @@ m2l_tc(TcArgs a) {
             }
         };
         if (H16) {
-            // FP16 inputs, scaled and split in advance: each thread copies its
-            // row's 64-byte high and low pieces of a chunk straight into the
-            // stage (16-byte asynchronous copies to the swizzled positions, a
-            // missing source copies zeros) and signals the stage kTcLag
-            // stages later, once its copies have landed.
+            // FP16 inputs, scaled and split in advance: once a stage is free,
+            // each thread copies its row's 64-byte high and low pieces of the
+            // stage's chunks straight into it (16-byte asynchronous copies to
+            // the swizzled positions; a missing source copies zeros), waits for
+            // them and signals the stage.  The copies overlap the MMAs of the
+            // previous stage.
             const unsigned char *spl = pc.L->split;   // every tile of a launch reads the same levels
-            int s = 0, sa = 0;
+            int s = 0;
             uint32_t ph = 0;
-            for (int it = 0; it < iters + kTcLag; ++it) {
-                if (it < iters) {
-                    if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+            for (int it = 0; it < iters; ++it) {
+                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                unsigned char *stage = base + (size_t)s * stage_bytes;
+                int c0 = 0;
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    if (q > 0 && c0 + q >= nck) break;   // the offset's last stage may hold fewer chunks
                     int cc;
                     int64_t sr;
                     take(cc, sr);
-                    unsigned char *stage = base + (size_t)s * stage_bytes;
-                    const unsigned char *src = sr >= 0 ? spl + (size_t)sr * 4 + (size_t)cc * 128 : spl;
-                    const uint32_t nb = sr >= 0 ? 16u : 0u;
+                    if (q == 0) c0 = cc;
+                    // the warp's 32 rows in 8 passes of 4: eight lanes copy one
+                    // row's 128 contiguous bytes (pieces 0-3 high, 4-7 low)
+                    const uint32_t sub = smem_u32(stage + q * kTcA);
+                    const int k = lane & 7;
+                    const uint32_t kpart = k < 4 ? 0u : 8192u;
+                    const int kk = 8 * (k & 3);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t o = swz64h(row, 8 * q);
-                        cp_async16(smem_u32(stage + o), src + (sr >= 0 ? 16 * q : 0), nb);
-                        cp_async16(smem_u32(stage + 8192 + o), src + (sr >= 0 ? 64 + 16 * q : 0), nb);
-                    }
-                    if (++s == NST) {
-                        s = 0;
-                        ph ^= 1;
+                    for (int pp = 0; pp < 8; ++pp) {
+                        const int rl = 4 * pp + (lane >> 3);
+                        const int64_t srp = __shfl_sync(0xffffffffu, (long long)sr, rl);
+                        const int r = (row & ~31) + rl;
+                        const unsigned char *src = srp >= 0 ? spl + (size_t)srp * 4 + (size_t)cc * 128 + 16 * k : spl;
+                        cp_async16(sub + kpart + swz64h(r, kk), src, srp >= 0 ? 16u : 0u);
                     }
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
-                if (it >= kTcLag) {
-                    asm volatile("cp.async.wait_group %0;" ::"n"(kTcLag) : "memory");   // chunk it - kTcLag landed
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_arrive(smem_u32(&afull[sa]));
-                    if (++sa == NST) sa = 0;
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&afull[s]));
+                if (++s == NST) {
+                    s = 0;
+                    ph ^= 1;
                 }
             }
             asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the loop (abort)
@@ -980,37 +992,43 @@ m2l_tc(TcArgs a) {
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = H16 ? idesc_f16(128, Npad) : idesc_tf32(128, Npad);
-            int s = 0, c = 0, g = 0;
+            int s = 0, c0 = 0, g = 0;
             uint32_t ph = 0;
             int last = -1;
             for (int it = 0; it < iters; ++it) {
                 if (!mbar_wait_ab(smem_u32(&afull[s]), ph, abortp)) break;
-                if (c == 0 && g >= 2 && !mbar_wait_ab(smem_u32(&bank_empty[g & 1]), ((g - 2) >> 1) & 1, abortp)) break;
+                if (c0 == 0 && g >= 2 && !mbar_wait_ab(smem_u32(&bank_empty[g & 1]), ((g - 2) >> 1) & 1, abortp)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const unsigned char *stage = base + (size_t)s * stage_bytes;
-                const uint32_t sa = smem_u32(stage), sb = smem_u32(stage + kTcA);
                 const uint32_t d = tmem + (uint32_t)(g & 1) * 256u;
-                // k-steps of 32 bytes (8 TF32 or 16 FP16 inputs) holding inputs
-                const int nks = H16 ? min(2, (a.kin - 32 * c + 15) / 16) : min(2, (a.kin - 16 * c + 7) / 8);
-                for (int ks = 0; ks < nks; ++ks) {
-                    const uint32_t ko = ks * 32;
-                    const uint64_t ah = umma_desc64(sa + ko), al = umma_desc64(sa + 8192 + ko);
-                    const uint64_t bh = umma_desc64(sb + ko), bl = umma_desc64(sb + (uint32_t)Npad * 64 + ko);
-                    if (H16) {
-                        mma_f16(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_f16(d, ah, bl, idesc, 1u);
-                        mma_f16(d, al, bh, idesc, 1u);
-                    } else {
-                        mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_tf32(d, ah, bl, idesc, 1u);
-                        mma_tf32(d, al, bh, idesc, 1u);
+                const int nc = min(S, nck - c0);
+                for (int q = 0; q < nc; ++q) {
+                    const int c = c0 + q;
+                    const uint32_t sa = smem_u32(stage + q * kTcA);
+                    const uint32_t sb = smem_u32(stage + S * kTcA + q * b_bytes);
+                    // k-steps of 32 bytes (8 TF32 or 16 FP16 inputs) holding inputs
+                    const int nks = H16 ? min(2, (a.kin - 32 * c + 15) / 16) : min(2, (a.kin - 16 * c + 7) / 8);
+                    for (int ks = 0; ks < nks; ++ks) {
+                        const uint32_t ko = ks * 32;
+                        const uint64_t ah = umma_desc64(sa + ko), al = umma_desc64(sa + 8192 + ko);
+                        const uint64_t bh = umma_desc64(sb + ko), bl = umma_desc64(sb + (uint32_t)Npad * 64 + ko);
+                        if (H16) {
+                            mma_f16(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                            mma_f16(d, ah, bl, idesc, 1u);
+                            mma_f16(d, al, bh, idesc, 1u);
+                        } else {
+                            mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                            mma_tf32(d, ah, bl, idesc, 1u);
+                            mma_tf32(d, al, bh, idesc, 1u);
+                        }
                     }
                 }
                 commit_to(&empty[s]);
                 last = it;
-                if (++c == nck) {
+                c0 += S;
+                if (c0 >= nck) {
                     commit_to(&bank_full[g & 1]);
-                    c = 0;
+                    c0 = 0;
                     ++g;
                 }
                 if (++s == NST) {
@@ -1024,7 +1042,7 @@ m2l_tc(TcArgs a) {
     } else if (warp == 5) {
         // ---------------- operator images
         if (lane == 0) {
-            int s = 0, c = 0, bj = 0;
+            int s = 0, c0 = 0, bj = 0;
             int oi = next_off(-1);
             int bcls = pc.cls;
             uint32_t ph = 0;
@@ -1043,17 +1061,20 @@ m2l_tc(TcArgs a) {
                     slot_off = 0;
                 }
                 unsigned char *stage = base + (size_t)s * stage_bytes;
+                // the stage's chunks of the operator image are contiguous
+                const uint32_t nbytes = (uint32_t)min(S, nck - c0) * b_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&afull[s])),
-                             "r"(b_bytes));
-                const unsigned char *srcimg = a.img + ((size_t)slot_off * nck + c) * b_bytes;
+                             "r"(nbytes));
+                const unsigned char *srcimg = a.img + ((size_t)slot_off * nck + c0) * b_bytes;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(stage + kTcA)),
-                    "l"(srcimg), "r"(b_bytes), "r"(smem_u32(&afull[s]))
+                        smem_u32(stage + S * kTcA)),
+                    "l"(srcimg), "r"(nbytes), "r"(smem_u32(&afull[s]))
                     : "memory");
                 last = it;
-                if (++c == nck) {
-                    c = 0;
+                c0 += S;
+                if (c0 >= nck) {
+                    c0 = 0;
                     oi = next_off(oi);
                     if (oi >= noff && ++bj < ntl) {
                         bcls = ctx_of(bj).cls;
@@ -1686,7 +1707,7 @@ gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     const bool tc = sizeof(T) == 4 && F->tab->m2l_tc && (adj ? F->tc_levels_adj : F->tc_levels) &&
                     !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
-                    tc_stages(F->tab->tc_npad, true) >= kTcLag + 1;
+                    tc_stages(F->tab->tc_npad, true) >= 2;
     if (tc) return m2l_run_tc(plan, B, adj, st);
     for (int l = 2; l <= F->L; ++l) {
         if (F->lev[l].nt == 0 && !adj) continue;   // the adjoint writes every source box
