@@ -160,45 +160,51 @@ radix_scatter(const uint64_t *__restrict__ keys, const int32_t *__restrict__ val
 }
 
 // -------------------------------------------------------------- bbox
-__global__ void bbox_partial(const double *__restrict__ p, int64_t n, double *__restrict__ part) {
-    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+// Bounding box on the integer units: a double's bits map to an unsigned key
+// with the same order (negative values: all bits flipped; others: the sign
+// bit set), so min/max are integer operations (FP64 is slow on this GPU)
+// and the blocks combine with 64-bit atomics.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void bbox_keys(const double *__restrict__ p, int64_t n, unsigned long long *__restrict__ out) {
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double v = p[3 * i + a];
-            mn[a] = fmin(mn[a], v);
-            mx[a] = fmax(mx[a], v);
+            const unsigned long long k = order_key(p[3 * i + a]);
+            mn[a] = k < mn[a] ? k : mn[a];
+            mx[a] = k > mx[a] ? k : mx[a];
         }
     }
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
         for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn[a], o), y = __shfl_xor_sync(0xffffffffu, mx[a], o);
+            mn[a] = x < mn[a] ? x : mn[a];
+            mx[a] = y > mx[a] ? y : mx[a];
         }
     }
-    __shared__ double s[32][6];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
+    if ((threadIdx.x & 31) == 0)
         for (int a = 0; a < 3; ++a) {
-            s[warp][a] = mn[a];
-            s[warp][3 + a] = mx[a];
+            atomicMin(out + a, mn[a]);
+            atomicMax(out + 3 + a, mx[a]);
         }
-    __syncthreads();
+}
+
+// keys back to doubles
+__global__ void bbox_decode(const unsigned long long *__restrict__ k, double *__restrict__ out) {
     if (threadIdx.x < 6) {
-        double r = threadIdx.x < 3 ? DBL_MAX : -DBL_MAX;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            r = threadIdx.x < 3 ? fmin(r, s[w][threadIdx.x]) : fmax(r, s[w][threadIdx.x]);
-        part[blockIdx.x * 6 + threadIdx.x] = r;
+        const unsigned long long u = k[threadIdx.x];
+        out[threadIdx.x] = __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
     }
 }
 
-__global__ void bbox_final(const double *__restrict__ part, int nb, double *__restrict__ out) {
-    if (threadIdx.x < 6) {
-        double r = threadIdx.x < 3 ? DBL_MAX : -DBL_MAX;
-        for (int b = 0; b < nb; ++b)
-            r = threadIdx.x < 3 ? fmin(r, part[b * 6 + threadIdx.x]) : fmax(r, part[b * 6 + threadIdx.x]);
-        out[threadIdx.x] = r;
-    }
+__global__ void bbox_init(unsigned long long *__restrict__ k) {
+    if (threadIdx.x < 6) k[threadIdx.x] = threadIdx.x < 3 ? ~0ull : 0ull;
 }
 
 }  // namespace
@@ -256,12 +262,15 @@ gf_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int3
 }
 
 gf_status bbox3(const double *pts, int64_t n, double *out, cudaStream_t st) {
-    // out must have room for 6 + 6*256 doubles: the partials follow the result
-    const int nb = (int)std::min<int64_t>(256, (n + 255) / 256);
+    // out must have room for 12 doubles: the integer keys follow the result
     if (n <= 0) return GF_OK;
-    bbox_partial<<<nb, 256, 0, st>>>(pts, n, out + 6);
+    unsigned long long *k = reinterpret_cast<unsigned long long *>(out + 6);
+    bbox_init<<<1, 32, 0, st>>>(k);
     GF_KERNEL_DONE();
-    bbox_final<<<1, 32, 0, st>>>(out + 6, nb, out);
+    const int nb = (int)std::min<int64_t>(4 * 152, (n + 255) / 256);
+    bbox_keys<<<nb, 256, 0, st>>>(pts, n, k);
+    GF_KERNEL_DONE();
+    bbox_decode<<<1, 32, 0, st>>>(k, out);
     GF_KERNEL_DONE();
     return GF_OK;
 }

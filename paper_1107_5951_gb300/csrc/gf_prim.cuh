@@ -21,7 +21,7 @@ gf_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int3
                          int64_t n, int bits, void *scratch, cudaStream_t st);
 
 // min/max of the three coordinates of n points [n][3] (FP64) into out[6]
-// (min x,y,z, max x,y,z); out must hold 6 doubles.
+// (min x,y,z, max x,y,z); out must hold 12 doubles (6 of scratch).
 gf_status bbox3(const double *pts, int64_t n, double *out, cudaStream_t st);
 
 }  // namespace gf

@@ -57,32 +57,50 @@ __global__ void obs_keys(const double *__restrict__ obs, int64_t M, Geo g, uint6
                          int32_t *__restrict__ vals, int *__restrict__ status) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
-    const double top = (double)((1ll << g.L) - 1);
+    const float top = (float)((1ll << g.L) - 1);
     int64_t c[3];
     for (int a = 0; a < 3; ++a) {
         const double x = obs[3 * j + a];
         if (!isfinite(x)) atomicOr(status + 2, 1);
-        double q = floor(__dmul_rn(__dsub_rn(x, g.lo[a]), g.inv_s));
-        q = fmin(fmax(q, 0.0), top);
-        c[a] = (int64_t)q;
+        // The box index is floor((x - lo) / s) evaluated in FP64 (the rounding
+        // the tree is defined with).  FP32 gets it right unless the value is
+        // within a few FP32 roundings of an integer, and FP64 arithmetic is
+        // slow on this GPU, so FP64 is used only there.
+        const float xf = __double2float_rn(x), lof = (float)g.lo[a], isf = (float)g.inv_s;
+        const float qf = (xf - lof) * isf;
+        float fl = floorf(qf);
+        const float dist = fminf(qf - fl, fl + 1.f - qf);
+        const float tol = ((fabsf(xf) + fabsf(lof)) * fabsf(isf) + fabsf(qf) + 1.f) * 1e-6f;
+        if (!(dist > tol)) fl = (float)fmin(fmax(floor(__dmul_rn(__dsub_rn(x, g.lo[a]), g.inv_s)), -1.0), (double)top + 1.0);
+        fl = fminf(fmaxf(fl, 0.f), top);
+        c[a] = (int64_t)fl;
     }
     keys[j] = morton(c[0], c[1], c[2]);
     vals[j] = (int32_t)j;
 }
 
-__global__ void mark_new(const uint64_t *__restrict__ keys, int64_t n, int shift, int64_t *__restrict__ flags) {
+// The tree is built without host round trips: counts stay on the device
+// (d_n; nullptr: the host count n), kernels run over an upper bound ub and
+// treat indices past the count as absent.
+__device__ __forceinline__ int64_t dev_count(const int64_t *d_n, int64_t n) { return d_n ? *d_n : n; }
+
+__global__ void mark_new(const uint64_t *__restrict__ keys, const int64_t *d_n, int64_t n, int64_t ub, int shift,
+                         int64_t *__restrict__ flags) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    flags[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+    if (i >= ub) return;
+    const int64_t cnt = dev_count(d_n, n);
+    flags[i] = (i < cnt && (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift))) ? 1 : 0;
 }
 
 // After an exclusive scan of the flags: write the unique (shifted) keys, the
 // first index of each run, and the run index of every element.
-__global__ void compact_runs(const uint64_t *__restrict__ keys, int64_t n, int shift,
+// (also: the number of runs, excl[ub], into *runs)
+__global__ void compact_runs(const uint64_t *__restrict__ keys, const int64_t *d_n, int64_t n, int64_t ub, int shift,
                              const int64_t *__restrict__ excl, uint64_t *__restrict__ ukeys,
-                             int32_t *__restrict__ beg, int32_t *__restrict__ run_of) {
+                             int32_t *__restrict__ beg, int32_t *__restrict__ run_of, int64_t *__restrict__ runs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i == 0) *runs = excl[ub];
+    if (i >= dev_count(d_n, n)) return;
     const bool nw = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift));
     const int64_t e = excl[i];
     if (nw) {
@@ -92,16 +110,19 @@ __global__ void compact_runs(const uint64_t *__restrict__ keys, int64_t n, int s
     if (run_of) run_of[i] = (int32_t)(nw ? e : e - 1);
 }
 
-__global__ void set_last(int32_t *__restrict__ a, int64_t idx, int32_t v) { a[idx] = v; }
+__global__ void set_last(int32_t *__restrict__ a, const int64_t *d_idx, int32_t v) { a[*d_idx] = v; }
 
-__global__ void class_keys(const uint64_t *__restrict__ tkey, int64_t n, uint64_t *__restrict__ ck,
-                           int32_t *__restrict__ idx, int *__restrict__ cnt) {
+// Parity class of every observer box (8 for the slots past the count, so
+// that they sort last) and the boxes per class.
+__global__ void class_keys(const uint64_t *__restrict__ tkey, const int64_t *d_n, int64_t ub,
+                           uint64_t *__restrict__ ck, int32_t *__restrict__ idx, int *__restrict__ cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = (int)(tkey[i] & 7);
+    if (i >= ub) return;
+    const bool in = i < *d_n;
+    const int c = in ? (int)(tkey[i] & 7) : 8;
     ck[i] = (uint64_t)c;
     idx[i] = (int32_t)i;
-    atomicAdd(cnt + c, 1);
+    if (in) atomicAdd(cnt + c, 1);
 }
 
 __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restrict__ perm,
@@ -125,17 +146,20 @@ __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restr
 
 constexpr int kItemTargets = 64;   // targets per evaluation work item (2 per lane)
 
-__global__ void item_counts(const int32_t *__restrict__ beg, int64_t nleaf, int64_t *__restrict__ cnt) {
+__global__ void item_counts(const int32_t *__restrict__ beg, const int64_t *d_nleaf, int64_t ub,
+                            int64_t *__restrict__ cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nleaf) return;
-    const int64_t n = beg[i + 1] - beg[i];
+    if (i >= ub) return;
+    const int64_t n = i < *d_nleaf ? beg[i + 1] - beg[i] : 0;
     cnt[i] = (n + kItemTargets - 1) / kItemTargets;
 }
 
-__global__ void item_fill(const int32_t *__restrict__ beg, int64_t nleaf, const int64_t *__restrict__ off,
-                          int4 *__restrict__ items) {
+// (also: the number of items, off[ub], into *nitems)
+__global__ void item_fill(const int32_t *__restrict__ beg, const int64_t *d_nleaf, int64_t ub,
+                          const int64_t *__restrict__ off, int4 *__restrict__ items, int64_t *__restrict__ nitems) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nleaf) return;
+    if (i == 0) *nitems = off[ub];
+    if (i >= *d_nleaf) return;
     const int b0 = beg[i], b1 = beg[i + 1];
     int64_t o = off[i];
     for (int f = b0; f < b1; f += kItemTargets) items[o++] = make_int4((int)i, f, min(kItemTargets, b1 - f), 0);
@@ -347,65 +371,63 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
         GF_TRY(radix_sort_u64(keys, F->perm, keys2, vals2, M, 3 * L, scratch, st));
     }
 
-    // ---- leaves and their ancestors
+    // ---- leaves and their ancestors.  Counts stay on the device (d_cnt:
+    // observer boxes per level, then the evaluation items, then boxes per
+    // parity class and level) and arrays are sized by upper bounds, so the
+    // whole build is one stream of launches with one read-back at the end.
     FmmLevel &leaf = F->lev[L];
-    int64_t nleaf = 0;
+    int64_t ub[kMaxLevels + 1];
+    {
+        int64_t cap = std::max<int64_t>(M, 1);
+        for (int l = L; l >= 0; --l) {
+            const int64_t full = (int64_t)1 << std::min(62, 3 * l);
+            cap = std::min(cap, full);
+            ub[l] = cap;
+        }
+    }
+    int64_t *d_cnt;   // [0, L]: boxes per level, [kMaxLevels + 1]: items
+    int *d_ccnt;      // [8 (kMaxLevels + 1)]: boxes per parity class and level
+    GF_TRY(A.alloc_n(&d_cnt, kMaxLevels + 2));
+    GF_TRY(A.alloc_n(&d_ccnt, 8 * (kMaxLevels + 1)));
+    GF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * (kMaxLevels + 2), st));
+    GF_CUDA(cudaMemsetAsync(d_ccnt, 0, sizeof(int) * 8 * (kMaxLevels + 1), st));
+    GF_TRY(A.alloc_n(&leaf.tkey, ub[L]));
+    GF_TRY(A.alloc_n(&F->leaf_beg, ub[L] + 1));
     if (M > 0) {
-        mark_new<<<ceil_div(M, 256), 256, 0, st>>>(keys, M, 0, flags);
+        mark_new<<<ceil_div(M, 256), 256, 0, st>>>(keys, nullptr, M, M, 0, flags);
         GF_KERNEL_DONE();
         GF_TRY(exclusive_scan_i64(flags, flags, M, scratch, st));
-        GF_CUDA(cudaMemcpyAsync(&nleaf, flags + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        GF_CUDA(cudaStreamSynchronize(st));
-    }
-    leaf.nt = nleaf;
-    GF_TRY(A.alloc_n(&leaf.tkey, std::max<int64_t>(nleaf, 1)));
-    GF_TRY(A.alloc_n(&F->leaf_beg, nleaf + 1));
-    if (M > 0) {
-        compact_runs<<<ceil_div(M, 256), 256, 0, st>>>(keys, M, 0, flags, leaf.tkey, F->leaf_beg, nullptr);
+        compact_runs<<<ceil_div(M, 256), 256, 0, st>>>(keys, nullptr, M, M, 0, flags, leaf.tkey, F->leaf_beg,
+                                                      nullptr, d_cnt + L);
         GF_KERNEL_DONE();
     }
-    set_last<<<1, 1, 0, st>>>(F->leaf_beg, nleaf, (int32_t)M);
+    set_last<<<1, 1, 0, st>>>(F->leaf_beg, d_cnt + L, (int32_t)M);
     GF_KERNEL_DONE();
     for (int l = L - 1; l >= 1; --l) {
         FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
-        GF_TRY(A.alloc_n(&ch.tparent, std::max<int64_t>(ch.nt, 1)));
-        int64_t np = 0;
-        if (ch.nt > 0) {
-            mark_new<<<ceil_div(ch.nt, 256), 256, 0, st>>>(ch.tkey, ch.nt, 3, flags);
+        GF_TRY(A.alloc_n(&ch.tparent, ub[l + 1]));
+        GF_TRY(A.alloc_n(&pa.tkey, ub[l]));
+        if (M > 0) {
+            const int64_t u = ub[l + 1];
+            mark_new<<<ceil_div(u, 256), 256, 0, st>>>(ch.tkey, d_cnt + l + 1, 0, u, 3, flags);
             GF_KERNEL_DONE();
-            GF_TRY(exclusive_scan_i64(flags, flags, ch.nt, scratch, st));
-            GF_CUDA(cudaMemcpyAsync(&np, flags + ch.nt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            GF_CUDA(cudaStreamSynchronize(st));
-        }
-        pa.nt = np;
-        GF_TRY(A.alloc_n(&pa.tkey, std::max<int64_t>(np, 1)));
-        if (ch.nt > 0) {
-            compact_runs<<<ceil_div(ch.nt, 256), 256, 0, st>>>(ch.tkey, ch.nt, 3, flags, pa.tkey, nullptr,
-                                                             ch.tparent);
+            GF_TRY(exclusive_scan_i64(flags, flags, u, scratch, st));
+            compact_runs<<<ceil_div(u, 256), 256, 0, st>>>(ch.tkey, d_cnt + l + 1, 0, u, 3, flags, pa.tkey, nullptr,
+                                                          ch.tparent, d_cnt + l);
             GF_KERNEL_DONE();
         }
     }
 
     // ---- per level: observer boxes grouped by parity class (M2L order)
-    int *d_cnt;
-    GF_TRY(A.alloc_n(&d_cnt, 8 * (kMaxLevels + 1)));
-    GF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int) * 8 * (kMaxLevels + 1), st));
     for (int l = 2; l <= L; ++l) {
         FmmLevel &lv = F->lev[l];
-        GF_TRY(A.alloc_n(&lv.m2l_order, std::max<int64_t>(lv.nt, 1)));
-        if (lv.nt == 0) continue;
-        class_keys<<<ceil_div(lv.nt, 256), 256, 0, st>>>(lv.tkey, lv.nt, keys2, lv.m2l_order, d_cnt + 8 * l);
+        GF_TRY(A.alloc_n(&lv.m2l_order, ub[l]));
+        if (M == 0) continue;
+        class_keys<<<ceil_div(ub[l], 256), 256, 0, st>>>(lv.tkey, d_cnt + l, ub[l], keys2, lv.m2l_order,
+                                                         d_ccnt + 8 * l);
         GF_KERNEL_DONE();
-        GF_TRY(radix_sort_u64(keys2, lv.m2l_order, reinterpret_cast<uint64_t *>(flags), vals2, lv.nt, 3,
+        GF_TRY(radix_sort_u64(keys2, lv.m2l_order, reinterpret_cast<uint64_t *>(flags), vals2, ub[l], 4,
                               scratch, st));
-    }
-    int cnt[8 * (kMaxLevels + 1)];
-    GF_CUDA(cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
-    GF_CUDA(cudaStreamSynchronize(st));
-    for (int l = 2; l <= L; ++l) {
-        FmmLevel &lv = F->lev[l];
-        lv.cls_off[0] = 0;
-        for (int c = 0; c < 8; ++c) lv.cls_off[c + 1] = lv.cls_off[c] + cnt[8 * l + c];
     }
 
     // ---- observer offsets from their leaf centres, evaluation work list
@@ -417,19 +439,30 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
         obs_local<<<ceil_div(M, 256), 256, 0, st>>>(obs, F->perm, keys, M, g, F->tloc_f, F->tloc_d);
         GF_KERNEL_DONE();
     }
-    int64_t nitems = 0;
-    if (nleaf > 0) {
-        item_counts<<<ceil_div(nleaf, 256), 256, 0, st>>>(F->leaf_beg, nleaf, flags);
+    // items: at most one per leaf plus one per kItemTargets observers
+    const int64_t item_ub = ub[L] + M / kItemTargets + 1;
+    GF_TRY(A.alloc_n(&F->items, item_ub));
+    if (M > 0) {
+        item_counts<<<ceil_div(ub[L], 256), 256, 0, st>>>(F->leaf_beg, d_cnt + L, ub[L], flags);
         GF_KERNEL_DONE();
-        GF_TRY(exclusive_scan_i64(flags, flags, nleaf, scratch, st));
-        GF_CUDA(cudaMemcpyAsync(&nitems, flags + nleaf, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        GF_CUDA(cudaStreamSynchronize(st));
+        GF_TRY(exclusive_scan_i64(flags, flags, ub[L], scratch, st));
+        item_fill<<<ceil_div(ub[L], 256), 256, 0, st>>>(F->leaf_beg, d_cnt + L, ub[L], flags, F->items,
+                                                        d_cnt + kMaxLevels + 1);
+        GF_KERNEL_DONE();
     }
-    F->n_items = nitems;
-    GF_TRY(A.alloc_n(&F->items, std::max<int64_t>(nitems, 1)));
-    if (nleaf > 0) {
-        item_fill<<<ceil_div(nleaf, 256), 256, 0, st>>>(F->leaf_beg, nleaf, flags, F->items);
-        GF_KERNEL_DONE();
+
+    // ---- the one read-back: box counts, items, class counts
+    int64_t hcnt[kMaxLevels + 2];
+    int ccnt[8 * (kMaxLevels + 1)];
+    GF_CUDA(cudaMemcpyAsync(hcnt, d_cnt, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
+    GF_CUDA(cudaMemcpyAsync(ccnt, d_ccnt, sizeof(ccnt), cudaMemcpyDeviceToHost, st));
+    GF_CUDA(cudaStreamSynchronize(st));
+    for (int l = 1; l <= L; ++l) F->lev[l].nt = M > 0 ? hcnt[l] : 0;
+    F->n_items = M > 0 ? hcnt[kMaxLevels + 1] : 0;
+    for (int l = 2; l <= L; ++l) {
+        FmmLevel &lv = F->lev[l];
+        lv.cls_off[0] = 0;
+        for (int c = 0; c < 8; ++c) lv.cls_off[c + 1] = lv.cls_off[c] + ccnt[8 * l + c];
     }
     return fmm_alloc_workspaces(plan, st);
 }
