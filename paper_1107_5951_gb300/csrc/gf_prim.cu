@@ -70,10 +70,46 @@ __global__ void write_total(int64_t *__restrict__ out, int64_t n, const int64_t 
     out[n] = offs[nb - 1] + sums[nb - 1];
 }
 
+// Whole scan in one block (n <= kSmallScan): rounds of 1024 consecutive
+// items, one per thread (coalesced), each round a block-wide scan plus the
+// running total of the rounds before; also the total into out[n] when asked.
+constexpr int kSmallThreads = 1024;
+constexpr int64_t kSmallScan = 32 * kSmallThreads;
+
+__global__ void __launch_bounds__(kSmallThreads)
+scan_small(const int64_t *__restrict__ in, int64_t *__restrict__ out, int64_t n, int write_tot) {
+    __shared__ int64_t warp_tot[kSmallThreads / 32 + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t carry = 0;
+    for (int64_t r0 = 0; r0 < n; r0 += kSmallThreads) {
+        const int64_t i = r0 + threadIdx.x;
+        const int64_t v = i < n ? in[i] : 0;
+        const int64_t incl = warp_incl_scan(v);
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int64_t w = warp_tot[lane];
+            const int64_t wi = warp_incl_scan(w);
+            warp_tot[lane] = wi - w;
+            if (lane == 31) warp_tot[32] = wi;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + warp_tot[warp] + incl - v;
+        carry += warp_tot[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && write_tot) out[n] = carry;
+}
+
 gf_status scan_rec(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch, cudaStream_t st,
                    bool write_tot) {
     if (n <= 0) {
         if (write_tot) GF_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        return GF_OK;
+    }
+    if (n <= kSmallScan) {
+        scan_small<<<1, kSmallThreads, 0, st>>>(in, out, n, write_tot ? 1 : 0);
+        GF_KERNEL_DONE();
         return GF_OK;
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
