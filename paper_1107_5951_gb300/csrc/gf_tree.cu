@@ -49,7 +49,51 @@ struct Geo {
     double lo[3];
     double inv_s, h, inv_h;
     int L, b;
+    // FP32 copies for the fast paths (FP64 arithmetic and conversions are
+    // slow on this GPU): lo, 1/s; and the fixed-point form of the leaf
+    // centres, k fractional bits (k < 0: not used), lo and half a leaf side
+    // in those units, 2^-k / h
+    float lof[3], isf;
+    int fixk;
+    long long lofix[3], halfleaf_fix;
+    float fix_to_vox;
 };
+
+// Sign, exponent and the top 23 mantissa bits of a double repacked as a
+// float (truncation: relative error below 2^-23), integer operations only;
+// false when the value is outside the normal FP32 range (zero excepted).
+__device__ __forceinline__ bool trunc_f32(double x, float &f) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -126 || e > 127) {
+        f = 0.f;
+        return (b << 1) == 0;
+    }
+    f = __uint_as_float((unsigned)((b >> 32) & 0x80000000ull) | ((unsigned)(e + 127) << 23) |
+                        (unsigned)((b >> 29) & 0x7fffffull));
+    return true;
+}
+
+// trunc(x 2^k) for |x 2^k| < 2^62, integer operations only.
+__device__ __forceinline__ long long to_fix(double x, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = e - 1075 + k;
+    const long long v = sh >= 0 ? (long long)(m << sh) : (sh > -64 ? (long long)(m >> -sh) : 0);
+    return (b >> 63) ? -v : v;
+}
+
+// |v| < 2^63 as a float, truncating, integer operations only.
+__device__ __forceinline__ float fix_to_f32(long long v) {
+    if (v == 0) return 0.f;
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    const unsigned long long n = a << lz;   // leading one at bit 63
+    return __uint_as_float((v < 0 ? 0x80000000u : 0u) | ((unsigned)(63 - lz + 127) << 23) |
+                           (unsigned)((n >> 40) & 0x7fffffull));
+}
 
 // Leaf key of every observer: floor((x - lo) * inv_s) with one rounded
 // subtraction and one rounded multiplication, clamped to the root.
@@ -61,17 +105,19 @@ __global__ void obs_keys(const double *__restrict__ obs, int64_t M, Geo g, uint6
     int64_t c[3];
     for (int a = 0; a < 3; ++a) {
         const double x = obs[3 * j + a];
-        if (!isfinite(x)) atomicOr(status + 2, 1);
+        if ((((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff) atomicOr(status + 2, 1);
         // The box index is floor((x - lo) / s) evaluated in FP64 (the rounding
         // the tree is defined with).  FP32 gets it right unless the value is
-        // within a few FP32 roundings of an integer, and FP64 arithmetic is
-        // slow on this GPU, so FP64 is used only there.
-        const float xf = __double2float_rn(x), lof = (float)g.lo[a], isf = (float)g.inv_s;
-        const float qf = (xf - lof) * isf;
+        // within a few FP32 roundings of an integer, and FP64 is slow on this
+        // GPU, so FP64 is used only there.
+        float xf;
+        const bool fin = trunc_f32(x, xf);
+        const float qf = (xf - g.lof[a]) * g.isf;
         float fl = floorf(qf);
         const float dist = fminf(qf - fl, fl + 1.f - qf);
-        const float tol = ((fabsf(xf) + fabsf(lof)) * fabsf(isf) + fabsf(qf) + 1.f) * 1e-6f;
-        if (!(dist > tol)) fl = (float)fmin(fmax(floor(__dmul_rn(__dsub_rn(x, g.lo[a]), g.inv_s)), -1.0), (double)top + 1.0);
+        const float tol = ((fabsf(xf) + fabsf(g.lof[a])) * fabsf(g.isf) + fabsf(qf) + 1.f) * 2e-6f;
+        if (!fin || !(dist > tol))
+            fl = (float)fmin(fmax(floor(__dmul_rn(__dsub_rn(x, g.lo[a]), g.inv_s)), -1.0), (double)top + 1.0);
         fl = fminf(fmaxf(fl, 0.f), top);
         c[a] = (int64_t)fl;
     }
@@ -134,6 +180,13 @@ __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restr
     int64_t c[3];
     demorton(okey[i], c[0], c[1], c[2]);
     for (int a = 0; a < 3; ++a) {
+        if (tf && g.fixk >= 0) {
+            // FP32 output: the offset from the leaf centre in fixed point (an
+            // exact integer difference), then scaled to voxel units in FP32
+            const long long d = to_fix(obs[3 * j + a], g.fixk) - (g.lofix[a] + (2 * c[a] + 1) * g.halfleaf_fix);
+            tf[3 * i + a] = fix_to_f32(d) * g.fix_to_vox;
+            continue;
+        }
         // voxel units by a multiply (FP64 division is a long sequence on this
         // GPU); the last-bit difference from dividing stays far below the
         // coincidence radius
@@ -350,6 +403,26 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     g.inv_h = 1.0 / F->h;
     g.L = L;
     g.b = F->b;
+    for (int a = 0; a < 3; ++a) g.lof[a] = (float)F->lo[a];
+    g.isf = (float)F->inv_s;
+    {
+        // fixed point with k fractional bits such that every coordinate of the
+        // observers and of the root box stays below 2^61 in magnitude
+        double xmax = 0.0;
+        for (int a = 0; a < 3; ++a)
+            xmax = std::max({xmax, std::fabs(bb[a]), std::fabs(bb[3 + a]), std::fabs(F->lo[a]),
+                             std::fabs(F->lo[a] + std::ldexp(F->s_leaf, L))});
+        int ex = 0;
+        std::frexp(std::max(xmax, 1e-300), &ex);   // xmax < 2^ex
+        const int k = std::min(80, 61 - ex);
+        g.fixk = k >= 0 ? k : -1;
+        if (g.fixk >= 0) {
+            const double hl = 0.5 * F->b * F->h;
+            for (int a = 0; a < 3; ++a) g.lofix[a] = (long long)std::llround(std::ldexp(F->lo[a], k));
+            g.halfleaf_fix = (long long)std::llround(std::ldexp(hl, k));
+            g.fix_to_vox = (float)(std::ldexp(1.0, -k) / F->h);
+        }
+    }
 
     // ---- observer keys and stable sort by (key, index)
     const int64_t Mx = std::max<int64_t>(M, 1);
