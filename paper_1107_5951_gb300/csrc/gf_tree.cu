@@ -158,19 +158,6 @@ __global__ void compact_runs(const uint64_t *__restrict__ keys, const int64_t *d
 
 __global__ void set_last(int32_t *__restrict__ a, const int64_t *d_idx, int32_t v) { a[*d_idx] = v; }
 
-// Parity class of every observer box (8 for the slots past the count, so
-// that they sort last) and the boxes per class.
-__global__ void class_keys(const uint64_t *__restrict__ tkey, const int64_t *d_n, int64_t ub,
-                           uint64_t *__restrict__ ck, int32_t *__restrict__ idx, int *__restrict__ cnt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ub) return;
-    const bool in = i < *d_n;
-    const int c = in ? (int)(tkey[i] & 7) : 8;
-    ck[i] = (uint64_t)c;
-    idx[i] = (int32_t)i;
-    if (in) atomicAdd(cnt + c, 1);
-}
-
 __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restrict__ perm,
                           const uint64_t *__restrict__ okey, int64_t M, Geo g, float *__restrict__ tf,
                           double *__restrict__ td) {
@@ -198,6 +185,77 @@ __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restr
 }
 
 constexpr int kItemTargets = 64;   // targets per evaluation work item (2 per lane)
+
+// ---- observer boxes of every level 2..L grouped by parity class (the M2L
+// order; stable: ascending box index within a class), three launches for
+// all levels: per-block class counts, one scan, a stable scatter.  Blocks
+// of 1024 boxes; the counts are laid out [level][class][block] so that the
+// scan gives each (level, class, block) its first position, measured from
+// the level's first entry.
+constexpr int kClsBlock = 1024;
+struct ClsArgs {
+    const uint64_t *tkey[kMaxLevels + 1];
+    int32_t *order[kMaxLevels + 1];
+    const int64_t *cnt;               // boxes per level (device)
+    int64_t first_block[kMaxLevels + 2];   // blocks of levels 2..L, prefix
+    int64_t nblk[kMaxLevels + 1];
+    int64_t entry0[kMaxLevels + 2];   // first count entry of each level
+    int lmin, lmax;
+    int64_t *bc;                      // [entries + 1] counts, then their scan
+    int *ccnt;                        // [8 l + c] boxes per class
+};
+
+__device__ __forceinline__ void cls_locate(const ClsArgs &a, int &l, int64_t &blk) {
+    l = a.lmin;
+    while (l < a.lmax && (int64_t)blockIdx.x >= a.first_block[l + 1]) ++l;
+    blk = (int64_t)blockIdx.x - a.first_block[l];
+}
+
+__global__ void __launch_bounds__(kClsBlock) cls_count(ClsArgs a) {
+    __shared__ int c8[8];
+    int l;
+    int64_t blk;
+    cls_locate(a, l, blk);
+    if (threadIdx.x < 8) c8[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = blk * kClsBlock + threadIdx.x;
+    if (i < a.cnt[l]) atomicAdd(&c8[(int)(a.tkey[l][i] & 7)], 1);
+    __syncthreads();
+    if (threadIdx.x < 8) a.bc[a.entry0[l] + threadIdx.x * a.nblk[l] + blk] = c8[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kClsBlock) cls_scatter(ClsArgs a) {
+    __shared__ int wc[kClsBlock / 32][8];
+    int l;
+    int64_t blk;
+    cls_locate(a, l, blk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = blk * kClsBlock + threadIdx.x;
+    const bool in = i < a.cnt[l];
+    const int c = in ? (int)(a.tkey[l][i] & 7) : 8;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (threadIdx.x < kClsBlock / 32 * 8) wc[threadIdx.x >> 3][threadIdx.x & 7] = 0;
+    __syncthreads();
+    if (in && rank == 0) wc[warp][c] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < 8) {   // exclusive prefix over the warps, per class
+        int acc = 0;
+        for (int w = 0; w < kClsBlock / 32; ++w) {
+            const int t = wc[w][threadIdx.x];
+            wc[w][threadIdx.x] = acc;
+            acc += t;
+        }
+    }
+    __syncthreads();
+    const int64_t base = a.bc[a.entry0[l]];
+    if (in) a.order[l][a.bc[a.entry0[l] + c * a.nblk[l] + blk] - base + wc[warp][c] + rank] = (int32_t)i;
+    if (blk == 0 && threadIdx.x < 8) {
+        const int64_t e = a.entry0[l] + threadIdx.x * a.nblk[l];
+        const int64_t next = threadIdx.x < 7 ? e + a.nblk[l] : a.entry0[l + 1];
+        a.ccnt[8 * l + threadIdx.x] = (int)(a.bc[next] - a.bc[e]);
+    }
+}
 
 __global__ void item_counts(const int32_t *__restrict__ beg, const int64_t *d_nleaf, int64_t ub,
                             int64_t *__restrict__ cnt) {
@@ -492,15 +550,33 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     }
 
     // ---- per level: observer boxes grouped by parity class (M2L order)
-    for (int l = 2; l <= L; ++l) {
-        FmmLevel &lv = F->lev[l];
-        GF_TRY(A.alloc_n(&lv.m2l_order, ub[l]));
-        if (M == 0) continue;
-        class_keys<<<ceil_div(ub[l], 256), 256, 0, st>>>(lv.tkey, d_cnt + l, ub[l], keys2, lv.m2l_order,
-                                                         d_ccnt + 8 * l);
+    for (int l = 2; l <= L; ++l) GF_TRY(A.alloc_n(&F->lev[l].m2l_order, ub[l]));
+    if (M > 0 && L >= 2) {
+        ClsArgs ca;
+        memset(&ca, 0, sizeof(ca));
+        ca.lmin = 2;
+        ca.lmax = L;
+        int64_t blocks = 0, entries = 0;
+        for (int l = 2; l <= L; ++l) {
+            ca.tkey[l] = F->lev[l].tkey;
+            ca.order[l] = F->lev[l].m2l_order;
+            ca.nblk[l] = (ub[l] + kClsBlock - 1) / kClsBlock;
+            ca.first_block[l] = blocks;
+            ca.entry0[l] = entries;
+            blocks += ca.nblk[l];
+            entries += 8 * ca.nblk[l];
+        }
+        ca.first_block[L + 1] = blocks;
+        ca.entry0[L + 1] = entries;
+        ca.cnt = d_cnt;
+        ca.ccnt = d_ccnt;
+        ca.bc = flags;   // entries <= 8 (ub[L] / 1024 + levels) fit in the M + 1 flags
+        if (entries + 1 > Mx + 1) GF_TRY(A.alloc_n(&ca.bc, entries + 1));
+        cls_count<<<(unsigned)blocks, kClsBlock, 0, st>>>(ca);
         GF_KERNEL_DONE();
-        GF_TRY(radix_sort_u64(keys2, lv.m2l_order, reinterpret_cast<uint64_t *>(flags), vals2, ub[l], 4,
-                              scratch, st));
+        GF_TRY(exclusive_scan_i64(ca.bc, ca.bc, entries, scratch, st));
+        cls_scatter<<<(unsigned)blocks, kClsBlock, 0, st>>>(ca);
+        GF_KERNEL_DONE();
     }
 
     // ---- observer offsets from their leaf centres, evaluation work list
