@@ -39,12 +39,14 @@ F16_PER_BF16 = 1.0               # nominal dense FP16 / BF16 tensor rates
 
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture of
-# the default workload (profiles/m2l_tc_grf_volume128_p12.md), with the
+# the default workload (the ncu summaries under profiles/), with the
 # SHA-1 of the kernel's source file at capture time: once the source changes
 # the figure no longer describes the kernel and the bench reports null.
 NCU_TRAFFIC = {
-    ("m2l", "grf_volume_128^3", 12): (213687040, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
-                                      "638a9b64856a39fb2e8ef1b34acda689f318f490"),
+    ("m2l", "grf_volume_128^3", 12): (105652992 + 18162944, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
+                                      "c767075d1316cf226e843179731a70be155465c2"),
+    ("eval", "grf_volume_128^3", 12): (72217088 + 21319936, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
+                                       "ea302cbb475dec0b9fc07303574739ad674056e5"),
 }
 
 

@@ -70,35 +70,45 @@ __global__ void write_total(int64_t *__restrict__ out, int64_t n, const int64_t 
     out[n] = offs[nb - 1] + sums[nb - 1];
 }
 
-// Whole scan in one block (n <= kSmallScan): rounds of 1024 consecutive
-// items, one per thread (coalesced), each round a block-wide scan plus the
-// running total of the rounds before; also the total into out[n] when asked.
+// Whole scan in one block (n <= kSmallScan): thread t takes the run of up
+// to 32 consecutive items starting at t * ceil(n / 1024); a first sweep sums
+// the run (independent, unrolled loads), one block-wide scan of the run
+// totals gives every run its offset, and a second sweep writes the run.
+// Also the total into out[n] when asked.  (`in` may alias `out`: the
+// second sweep reads each item before writing it.)
 constexpr int kSmallThreads = 1024;
-constexpr int64_t kSmallScan = 32 * kSmallThreads;
+constexpr int kSmallItems = 32;
+constexpr int64_t kSmallScan = (int64_t)kSmallItems * kSmallThreads;
 
 __global__ void __launch_bounds__(kSmallThreads)
-scan_small(const int64_t *__restrict__ in, int64_t *__restrict__ out, int64_t n, int write_tot) {
+scan_small(const int64_t *in, int64_t *out, int64_t n, int write_tot) {
     __shared__ int64_t warp_tot[kSmallThreads / 32 + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t carry = 0;
-    for (int64_t r0 = 0; r0 < n; r0 += kSmallThreads) {
-        const int64_t i = r0 + threadIdx.x;
-        const int64_t v = i < n ? in[i] : 0;
-        const int64_t incl = warp_incl_scan(v);
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int64_t w = warp_tot[lane];
-            const int64_t wi = warp_incl_scan(w);
-            warp_tot[lane] = wi - w;
-            if (lane == 31) warp_tot[32] = wi;
-        }
-        __syncthreads();
-        if (i < n) out[i] = carry + warp_tot[warp] + incl - v;
-        carry += warp_tot[32];
-        __syncthreads();
+    const int per = (int)((n + kSmallThreads - 1) / kSmallThreads);
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    int64_t loc = 0;
+#pragma unroll
+    for (int i = 0; i < kSmallItems; ++i)
+        if (i < per && b0 + i < n) loc += in[b0 + i];
+    const int64_t incl = warp_incl_scan(loc);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t w = warp_tot[lane];
+        const int64_t wi = warp_incl_scan(w);
+        warp_tot[lane] = wi - w;
+        if (lane == 31) warp_tot[32] = wi;
     }
-    if (threadIdx.x == 0 && write_tot) out[n] = carry;
+    __syncthreads();
+    int64_t run = warp_tot[warp] + incl - loc;
+#pragma unroll 8
+    for (int i = 0; i < kSmallItems; ++i)
+        if (i < per && b0 + i < n) {
+            const int64_t v = in[b0 + i];
+            out[b0 + i] = run;
+            run += v;
+        }
+    if (threadIdx.x == 0 && write_tot) out[n] = warp_tot[32];
 }
 
 gf_status scan_rec(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch, cudaStream_t st,
