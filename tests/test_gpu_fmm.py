@@ -161,6 +161,34 @@ def test_m2l_tensor_cores_match_simt(p):
     assert rel_l2(g_tc, ref) <= 1e-5 or p < 10
 
 
+@pytest.mark.parametrize("kind", ["scaled_up", "scaled_down", "zero_mean", "one_heavy_voxel"])
+def test_mixed_power_of_two_scaling_is_scale_free(kind):
+    """The FP16 operands of the tensor-core M2L are scaled by powers of two
+    chosen from the data (each level's largest |input|), so the mixed result
+    meets the bar for densities far from unit size, of either sign, and with
+    a dynamic range of 1e8 between voxels; scaling the densities by 2^k
+    scales the result exactly."""
+    wk = cube_case(71, n=28, vol_targets=400)
+    rho = np.asarray(wk.rho, dtype=np.float64)
+    if kind == "scaled_up":
+        rho = rho * 2.0 ** 80
+    elif kind == "scaled_down":
+        rho = rho * 2.0 ** -80
+    elif kind == "zero_mean":
+        rho = rho - rho.mean()
+    else:
+        rho = rho * 1e-8
+        rho[(14, 12, 10)] = 3000.0
+    ref = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, rho, wk.obs, wk.G)
+    g, _, _ = run(wk, "mixed", p=12, rho=rho)
+    assert np.all(np.isfinite(g))
+    assert rel_l2(g, ref) <= 1e-5
+    if kind.startswith("scaled"):
+        k = 80 if kind == "scaled_up" else -80
+        g1, _, _ = run(wk, "mixed", p=12, rho=np.asarray(wk.rho, dtype=np.float64))
+        assert np.array_equal(g * 2.0 ** -k, g1)
+
+
 def test_m2l_tensor_cores_batched():
     wk = cube_case(91, n=20, B=5, vol_targets=200)
     g5, _, _ = run(wk, "mixed", p=10)
