@@ -45,8 +45,9 @@ F16_PER_BF16 = 1.0               # nominal dense FP16 / BF16 tensor rates
 NCU_TRAFFIC = {
     ("m2l", "grf_volume_128^3", 12): (105652992 + 18162944, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
                                       "c767075d1316cf226e843179731a70be155465c2"),
-    ("eval", "grf_volume_128^3", 12): (72217088 + 21319936, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
-                                       "ea302cbb475dec0b9fc07303574739ad674056e5"),
+    # (dram__bytes.sum.per_second x gpu__time_duration.sum of the capture)
+    ("eval", "grf_volume_128^3", 12): (93877005, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
+                                       "9615a4796a37aa84873a8207e2012a3531bae912"),
 }
 
 

@@ -77,8 +77,9 @@ enum { GF_MODE_DIRECT = 0, GF_MODE_FMM = 1 };
 /* GF_PREC_FP64: every stage in FP64.  GF_PREC_MIXED: FP32 near field with
  * compensated accumulation; tensor-core M2L on FP16 high/low parts of
  * power-of-two-scaled operands (three products, FP32 accumulation) and
- * split-TF32 P2M/M2M/L2L; FP64 for the top-level translations; FP32 near+far
- * sum.  Results stay within a relative L2 error of about 1e-5 (p >= 10). */
+ * split-TF32 P2M/M2M/L2L; FP64 for the top-level translations and the final
+ * near+far sum.  Results stay within a relative L2 error of about 1e-5
+ * (p >= 10). */
 enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1 };
 enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
 enum { GF_FLAG_M2L_SIMT = 1 };

@@ -757,9 +757,8 @@ eval_kernel(EvalArgs a) {
         }
     }
     __syncthreads();
-    // far-field scale of the L2P gradient (voxel units) and the output scale
+    // far-field scale of the L2P gradient (voxel units)
     const double far_s = -1.0 / ((double)a.b * (double)a.b);
-    const float far_sf = -1.f / ((float)a.b * (float)a.b), scale_f = (float)a.scale;
     // lattice form: this lane's two lattice points (weight, voxel)
     float lw0 = 0.f, lw1 = 0.f;
     int lv0 = 0, lv1 = 0;
@@ -1074,19 +1073,10 @@ eval_kernel(EvalArgs a) {
             for (int u = 0; u < kTPL; ++u) {
                 if (tid[u] < 0) continue;
                 const T fx = fxa[u], fy = fya[u], fz = fza[u];
-                double gx, gy, gzv;
-                if constexpr (kF32) {
-                    // near (hi + lo) + far, scaled, in FP32: the result is good
-                    // to a few units of FP32 rounding, far inside the mixed
-                    // precision's error bar, without FP64 arithmetic (slow here)
-                    gx = (double)((hx[u] + (lx[u] + far_sf * fx)) * scale_f);
-                    gy = (double)((hy[u] + (ly[u] + far_sf * fy)) * scale_f);
-                    gzv = (double)((hz[u] + (lz[u] + far_sf * fz)) * scale_f);
-                } else {
-                    gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
-                    gy = ((double)hy[u] + (double)ly[u] + far_s * (double)fy) * a.scale;
-                    gzv = ((double)hz[u] + (double)lz[u] + far_s * (double)fz) * a.scale;
-                }
+                // near (hi + lo) + far and the scale in FP64, in both precisions
+                const double gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
+                const double gy = ((double)hy[u] + (double)ly[u] + far_s * (double)fy) * a.scale;
+                const double gzv = ((double)hz[u] + (double)lz[u] + far_s * (double)fz) * a.scale;
                 const int64_t j = a.perm[tid[u]];
                 if (a.g) {
                     double *o = a.g + ((int64_t)bb * a.M + j) * 3;
