@@ -44,10 +44,10 @@ F16_PER_BF16 = 1.0               # nominal dense FP16 / BF16 tensor rates
 # the figure no longer describes the kernel and the bench reports null.
 NCU_TRAFFIC = {
     ("m2l", "grf_volume_128^3", 12): (105652992 + 18162944, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
-                                      "c767075d1316cf226e843179731a70be155465c2"),
+                                      "76e737871ad62083f36c560515e8864aa520efad"),
     # (dram__bytes.sum.per_second x gpu__time_duration.sum of the capture)
-    ("eval", "grf_volume_128^3", 12): (93878272, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
-                                       "9615a4796a37aa84873a8207e2012a3531bae912"),
+    ("eval", "grf_volume_128^3", 12): (94665033, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
+                                       "87b53e13c240d3512b21aa833b348f6d07156677"),
 }
 
 

@@ -825,7 +825,7 @@ eval_kernel(EvalArgs a) {
                     constexpr int N3 = N1 * N1 * N1;
                     __syncwarp();
                     float2 *wl = reinterpret_cast<float2 *>(wsh);
-                    static_assert(N3 == 64, "two lattice points per lane");
+                    static_assert(N1 == 4, "two lattice points per lane, rows of four");
                     {
                         const float w0 = lw0 * ms[lv0], w1 = lw1 * ms[lv1];
                         wl[lane] = make_float2(w0, w0);
@@ -856,6 +856,9 @@ eval_kernel(EvalArgs a) {
 #pragma unroll
                             for (int j = 0; j < N1; ++j) {
                                 const uint64_t YZ = add2(Y2[j], Z2);
+                                // the row's four terms: each into its Sx_i, their
+                                // pairwise sum once into Sy_j and Sz (short chains)
+                                uint64_t K3v[N1];
 #pragma unroll
                                 for (int i = 0; i < N1; ++i) {
                                     const uint64_t R2 = add2(X2[i], YZ);
@@ -867,11 +870,12 @@ eval_kernel(EvalArgs a) {
                                         i1 = r1 > (float)eps2 ? i1 : 0.f;
                                     }
                                     const uint64_t RI = pk2(i0, i1);
-                                    const uint64_t K3 = mul2(mul2(RI, RI), mul2(RI, wk[i + N1 * j]));
-                                    SX[i] = add2(SX[i], K3);
-                                    SY[j] = add2(SY[j], K3);
-                                    SZ = add2(SZ, K3);
+                                    K3v[i] = mul2(mul2(RI, RI), mul2(RI, wk[i + N1 * j]));
+                                    SX[i] = add2(SX[i], K3v[i]);
                                 }
+                                const uint64_t tj = add2(add2(K3v[0], K3v[1]), add2(K3v[2], K3v[3]));
+                                SY[j] = add2(SY[j], tj);
+                                SZ = add2(SZ, tj);
                             }
                             QZ = fma2(SZ, ez, QZ);
                         }

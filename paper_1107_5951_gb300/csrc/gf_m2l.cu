@@ -510,13 +510,15 @@ gf_status launch_simt(const M2LArgs &a, int64_t max_tiles, cudaStream_t st) {
 // divides both out exactly.  The inputs are split once per level by a small
 // kernel before the M2L; the M2M, L2L and P2M kinds split FP32 inputs into
 // TF32 parts in the kernel (3xTF32, K = 8 per MMA).  Inputs come in chunks
-// (32 FP16 or 16 TF32 inputs) through a ring of shared-memory stages
-// (64-byte swizzle), filled by warp-specialised producers:
-//   warps 0-3   A producers: thread r gathers column r's inputs of the chunk
-//               with 16-byte asynchronous copies -- FP16 parts straight into
-//               the stage, signalled two stages later; FP32 values into a
-//               private ring three chunks ahead, then split into TF32 parts
-//               and stored swizzled;
+// (32 FP16 or 16 TF32 inputs; an FP16 stage holds two chunks) through a ring
+// of shared-memory stages (64-byte swizzle), filled by warp-specialised
+// producers:
+//   warps 0-3   A producers, with 16-byte asynchronous copies: FP16 parts go
+//               straight into the stage (eight lanes per row's 128 contiguous
+//               bytes), and the stage is signalled once they have landed;
+//               FP32 values (thread r: column r) go into a private ring three
+//               chunks ahead, then are split into TF32 parts and stored
+//               swizzled;
 //   warp 4      one thread issues the MMAs of a stage and commits them to the
 //               stage's "empty" barrier (and, after an offset's last chunk,
 //               to the bank's "full" barrier);
