@@ -412,7 +412,7 @@ def bench_gf(args, rank, world):
         obs_e = torch.empty_like(obs_d)
         rho_e = torch.empty_like(rho_d)
         e_ev = []
-        for k in range(args.steps):
+        for k in range(args.warmup + args.steps):   # warm-up passes first, as for the device leg
             flush.fill_(float(k))
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -427,7 +427,8 @@ def bench_gf(args, rank, world):
                 g_h.copy_(g_d, non_blocking=True)
                 pl.close()
             b.record(stream)
-            e_ev.append((a, b))
+            if k >= args.warmup:
+                e_ev.append((a, b))
         torch.cuda.synchronize()
         e_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in e_ev])), world, dev)
         e2e = {"value": job_rate(units, world, e_ms * 1e-3), "unit": "interactions/s",
