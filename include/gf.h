@@ -126,7 +126,10 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad,
  * Enqueues on `stream` and returns; allocates nothing, so it may be captured
  * in a CUDA graph.  Direct mode sums every pair (Sec. 2.1); FMM mode runs
  * P2M, M2M, M2L, L2L, L2P and the near-field P2P (Sec. 2.3, Fig. 3) and adds
- * near and far parts (Eq. 10).
+ * near and far parts (Eq. 10).  The plan's workspaces (expansions, the M2L's
+ * split inputs) serve all its calls: calls on one plan whose device work
+ * overlaps (different streams) race, so serialise them or use one plan per
+ * stream.
  */
 gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype,
                      int32_t B, double *g_dev, double *gz_dev, void *stream);
