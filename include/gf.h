@@ -59,7 +59,7 @@ typedef enum {
 /* Voxel brick of Sec. 2.1: voxel (i,j,k) spans origin + [i,i+1)*h along each
  * axis; density arrays are [nz][ny][nx] with x fastest. */
 typedef struct {
-    int64_t n[3];       /* nx, ny, nz >= 1                                 */
+    int64_t n[3];       /* nx, ny, nz in [1, 2^22], nx*ny*nz <= 2^40       */
     double origin[3];   /* lower corner of voxel (0,0,0), metres           */
     double h[3];        /* voxel edge lengths, metres, > 0                 */
 } gf_grid;

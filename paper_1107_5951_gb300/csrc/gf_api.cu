@@ -91,7 +91,7 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
         return GF_ERR_INVALID_ARG;
     }
     for (int a = 0; a < 3; ++a) {
-        if (grid->n[a] < 1 || grid->n[a] > (int64_t(1) << 22)) {
+        if (grid->n[a] < 1 || grid->n[a] > kMaxAxis) {
             set_error("grid.n[%d] = %lld out of range [1, 2^22]", a, (long long)grid->n[a]);
             return GF_ERR_INVALID_ARG;
         }
@@ -99,6 +99,12 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
             set_error("grid.h[%d] must be finite and positive, origin finite", a);
             return GF_ERR_INVALID_ARG;
         }
+    }
+    // each axis is below 2^22, so the first product cannot overflow
+    if (grid->n[0] * grid->n[1] > kMaxVoxels / grid->n[2]) {
+        set_error("grid of %lld x %lld x %lld voxels exceeds 2^40 voxels", (long long)grid->n[0],
+                  (long long)grid->n[1], (long long)grid->n[2]);
+        return GF_ERR_INVALID_ARG;
     }
     if (quad->nq < 1 || quad->nq > kMaxQuad || !quad->xi || !quad->w) {
         set_error("quad.nq = %d must be in [1, %d] with non-NULL xi and w", quad->nq, kMaxQuad);

@@ -392,11 +392,15 @@ extern "C" gf_status gf_direct_forward_static(const gf_grid *grid, const gf_quad
         return GF_ERR_INVALID_ARG;
     }
     for (int a = 0; a < 3; ++a) {
-        if (grid->n[a] < 1 || grid->n[a] > (int64_t(1) << 22) || !(grid->h[a] > 0.0) || !isfinite(grid->h[a]) ||
+        if (grid->n[a] < 1 || grid->n[a] > kMaxAxis || !(grid->h[a] > 0.0) || !isfinite(grid->h[a]) ||
             !isfinite(grid->origin[a])) {
             set_error("grid axis %d: need 1 <= n <= 2^22, finite h > 0 and finite origin", a);
             return GF_ERR_INVALID_ARG;
         }
+    }
+    if (grid->n[0] * grid->n[1] > kMaxVoxels / grid->n[2]) {
+        set_error("grid exceeds 2^40 voxels");
+        return GF_ERR_INVALID_ARG;
     }
     if (quad->nq < 1 || quad->nq > kMaxQuad || !quad->xi || !quad->w) {
         set_error("quad.nq = %d must be in [1, %d] with non-NULL xi and w", quad->nq, kMaxQuad);

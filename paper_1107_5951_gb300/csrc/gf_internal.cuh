@@ -36,6 +36,8 @@ const char *get_error();
 constexpr int kMaxQuad = 64;
 constexpr int kMaxLevels = 21;      // Morton keys use 3 bits per level in a u64
 constexpr int kMaxP = 16;
+constexpr int64_t kMaxAxis = int64_t(1) << 22;     // voxels along one grid axis
+constexpr int64_t kMaxVoxels = int64_t(1) << 40;   // voxels in a grid (no int64 overflow)
 constexpr int kNumM2LOffsets = 316; // 7^3 - 3^3 interaction-list offsets
 
 // Quadrature rule as the kernels see it (Sec. 2.1): node offsets from the

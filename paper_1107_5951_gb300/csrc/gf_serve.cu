@@ -18,6 +18,7 @@
 #include <list>
 #include <mutex>
 #include <new>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -340,7 +341,10 @@ gf_status gf_server_create(const gf_server_options *opt, gf_server_t *out) {
     }
     GF_CUDA(cudaSetDevice(opt->device));
     gf_server_s *s = new (std::nothrow) gf_server_s();
-    if (!s) return GF_ERR_OOM;
+    if (!s) {
+        set_error("host allocation failed");
+        return GF_ERR_OOM;
+    }
     s->opt = *opt;
     if (s->opt.mem_budget == 0) {
         size_t fr = 0, tot = 0;
@@ -358,8 +362,21 @@ gf_status gf_server_create(const gf_server_options *opt, gf_server_t *out) {
         s->streams.push_back(st);
         s->free_slots.push_back(opt->max_slots - 1 - i);
     }
-    cudaStreamCreateWithFlags(&s->house, cudaStreamNonBlocking);
-    s->worker = std::thread(scheduler, s);
+    if (cudaStreamCreateWithFlags(&s->house, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("stream creation failed");
+        for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+        delete s;
+        return GF_ERR_CUDA;
+    }
+    try {
+        s->worker = std::thread(scheduler, s);
+    } catch (const std::system_error &) {
+        set_error("cannot start the scheduler thread");
+        for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+        cudaStreamDestroy(s->house);
+        delete s;
+        return GF_ERR_CUDA;
+    }
     *out = s;
     return GF_OK;
 }
@@ -375,32 +392,40 @@ gf_status gf_server_submit(gf_server_t s, const gf_request *req, int64_t *ticket
         set_error("request: need densities, an output, observers, a quadrature rule and a valid dtype");
         return GF_ERR_INVALID_ARG;
     }
+    // footprint for admission: the plan plus its resident input and outputs;
+    // gf_plan_bytes also validates the grid, the rule and M before anything
+    // is copied
+    const gf_options o = plan_options(s->opt);
+    size_t b = 0;
+    const gf_status rc = gf_plan_bytes(&req->grid, &req->quad, req->M, &o, &b);
+    if (rc != GF_OK) return rc;
+    const int64_t nvox = req->grid.n[0] * req->grid.n[1] * req->grid.n[2];
+    const size_t need = b + dtype_size(req->rho_dtype) * nvox + 4 * sizeof(double) * req->M;
+    if (need > s->opt.mem_budget) {
+        set_error("request needs %zu device bytes, more than the server's budget of %zu", need,
+                  s->opt.mem_budget);
+        return GF_ERR_BUSY;
+    }
     Ticket *t = new (std::nothrow) Ticket();
-    if (!t) return GF_ERR_OOM;
+    if (!t) {
+        set_error("host allocation failed");
+        return GF_ERR_OOM;
+    }
+    try {
+        t->xi.assign(req->quad.xi, req->quad.xi + 3 * req->quad.nq);
+        t->w.assign(req->quad.w, req->quad.w + req->quad.nq);
+        t->obs.assign(req->obs_host, req->obs_host + 3 * req->M);
+    } catch (const std::bad_alloc &) {
+        delete t;
+        set_error("host allocation of the request's copies failed");
+        return GF_ERR_OOM;
+    }
     t->req = *req;
-    t->xi.assign(req->quad.xi, req->quad.xi + 3 * req->quad.nq);
-    t->w.assign(req->quad.w, req->quad.w + req->quad.nq);
-    t->obs.assign(req->obs_host, req->obs_host + 3 * req->M);
     t->req.quad.xi = t->xi.data();
     t->req.quad.w = t->w.data();
     t->req.obs_host = t->obs.data();
     t->srv = s;
-    // footprint for admission: the plan plus its resident input and outputs
-    const gf_options o = plan_options(s->opt);
-    size_t b = 0;
-    const gf_status rc = gf_plan_bytes(&t->req.grid, &t->req.quad, t->req.M, &o, &b);
-    if (rc != GF_OK) {
-        delete t;
-        return rc;
-    }
-    const int64_t nvox = req->grid.n[0] * req->grid.n[1] * req->grid.n[2];
-    t->need = b + dtype_size(req->rho_dtype) * nvox + 4 * sizeof(double) * req->M;
-    if (t->need > s->opt.mem_budget) {
-        set_error("request needs %zu device bytes, more than the server's budget of %zu", t->need,
-                  s->opt.mem_budget);
-        delete t;
-        return GF_ERR_BUSY;
-    }
+    t->need = need;
     t->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -85,6 +85,23 @@ def test_invalid_grid_and_quadrature_rejected():
     assert e.value.status == gf.GF_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("n,ok", [((1 << 22,) * 3, False), ((1 << 14,) * 3, False),
+                                  ((1 << 13,) * 3, True), ((1 << 22, 1 << 18, 1), True)])
+def test_total_voxel_count_is_bounded(n, ok):
+    """Grids above 2^40 voxels are rejected before any index product could
+    overflow; each axis may still reach 2^22."""
+    grid, q, opt = _args(mode="direct")
+    for a in range(3):
+        grid.n[a] = n[a]
+    if ok:
+        assert gf.gf_plan_bytes(grid, q.c, 10, opt) > 0
+    else:
+        with pytest.raises(gf.GfError) as e:
+            gf.gf_plan_bytes(grid, q.c, 10, opt)
+        assert e.value.status == gf.GF_ERR_INVALID_ARG
+        assert "2^40" in gf.gf_last_error()
+
+
 def test_null_plan_and_null_outputs_rejected():
     lib = pkg.load()
     assert lib.gf_forward(None, None, 0, 1, None, None, None) == gf.GF_ERR_INVALID_ARG
