@@ -298,6 +298,38 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def _check_tensor(t, name, numel, device=None, dtypes=None):
+    """Reject a tensor the kernels would read or write out of bounds: it must
+    be contiguous, hold `numel` elements of one of `dtypes` (default float64)
+    and live on `device` (a CUDA device; None means host memory)."""
+    import torch
+    dtypes = dtypes or (torch.float64,)
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if device is None:
+        if t.is_cuda:
+            raise TypeError("%s must be in host memory" % name)
+    elif not (t.is_cuda and t.device == device):
+        raise TypeError("%s must be a CUDA tensor on %s (got %s)" % (name, device, t.device))
+    if t.dtype not in dtypes:
+        raise TypeError("%s must have dtype %s (got %s)" % (name, " or ".join(map(str, dtypes)), t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() != numel:
+        raise ValueError("%s must hold %d elements (got %d)" % (name, numel, t.numel()))
+
+
+def _check_array(a, name, numel):
+    """Host output arrays of a serving request: C-contiguous float64 with
+    `numel` elements."""
+    if not isinstance(a, np.ndarray):
+        raise TypeError("%s must be a numpy array" % name)
+    if a.dtype != np.float64 or not a.flags.c_contiguous or not a.flags.writeable:
+        raise TypeError("%s must be a writeable C-contiguous float64 array" % name)
+    if a.size != numel:
+        raise ValueError("%s must hold %d elements (got %d)" % (name, numel, a.size))
+
+
 class Plan:
     """A forward-model plan for one voxel grid, quadrature rule and
     observer set (see ``gf_plan_create``).
@@ -328,29 +360,36 @@ class Plan:
         return gf_plan_get_info(self.handle)
 
     def forward(self, rho, g=None, gz=None, want_g=True, want_gz=False, stream=None):
-        """rho: CUDA tensor (nz, ny, nx) or (B, nz, ny, nx), float32/float64.
-        Returns (g, gz) with g (B?, M, 3) and gz (B?, M) float64 (None for
-        an output not requested)."""
+        """rho: CUDA tensor (nz, ny, nx) or (B, nz, ny, nx), float32/float64,
+        on the plan's device.  Returns (g, gz) with g (B?, M, 3) and gz
+        (B?, M) float64 (None for an output not requested).  Outputs passed
+        in must be contiguous float64 CUDA tensors of B*M*3 (g) or B*M (gz)
+        elements on the same device; they are filled and returned as given."""
         import torch
-        single = rho.dim() == 3
         nx, ny, nz = self.shape
+        if not isinstance(rho, torch.Tensor) or rho.dim() not in (3, 4) or tuple(rho.shape[-3:]) != (nz, ny, nx):
+            raise ValueError("rho must be a tensor of shape (nz, ny, nx) or (B, nz, ny, nx) = (B?, %d, %d, %d)"
+                             % (nz, ny, nx))
+        single = rho.dim() == 3
         rho = rho.contiguous().reshape(-1, nz, ny, nx)
         B = int(rho.shape[0])
-        if rho.dtype == torch.float64:
-            dt = GF_DTYPE_F64
-        elif rho.dtype == torch.float32:
-            dt = GF_DTYPE_F32
-        else:
-            raise TypeError("rho must be float32 or float64")
+        _check_tensor(rho, "rho", B * nz * ny * nx, self.device, (torch.float32, torch.float64))
+        dt = GF_DTYPE_F64 if rho.dtype == torch.float64 else GF_DTYPE_F32
+        own_g, own_gz = g is None, gz is None
         if want_g and g is None:
             g = torch.empty((B, self.M, 3), dtype=torch.float64, device=rho.device)
         if want_gz and gz is None:
             gz = torch.empty((B, self.M), dtype=torch.float64, device=rho.device)
-        gf_forward(self.handle, rho.data_ptr(), dt, B, g.data_ptr() if g is not None else 0,
-                   gz.data_ptr() if gz is not None else 0, _stream_handle(stream))
+        if g is not None:
+            _check_tensor(g, "g", B * self.M * 3, self.device)
+        if gz is not None:
+            _check_tensor(gz, "gz", B * self.M, self.device)
+        with torch.cuda.device(self.device):
+            gf_forward(self.handle, rho.data_ptr(), dt, B, g.data_ptr() if g is not None else 0,
+                       gz.data_ptr() if gz is not None else 0, _stream_handle(stream))
         if single:
-            g = g[0] if g is not None else None
-            gz = gz[0] if gz is not None else None
+            g = g[0] if (g is not None and own_g) else g
+            gz = gz[0] if (gz is not None and own_gz) else gz
         return g, gz
 
     def adjoint(self, r, ncomp=1, grad=None, stream=None):
@@ -358,13 +397,25 @@ class Plan:
         Returns grad (B?, nz, ny, nx) float64."""
         import torch
         nx, ny, nz = self.shape
+        if ncomp not in (1, 3):
+            raise ValueError("ncomp must be 1 (weights on g_z) or 3 (weights on g)")
+        if not (isinstance(r, torch.Tensor) and r.is_cuda and r.device == self.device):
+            raise TypeError("r must be a CUDA tensor on %s" % self.device)
         single = r.dim() == (1 if ncomp == 1 else 2)
-        r = r.to(torch.float64).contiguous().reshape(-1, self.M, ncomp)
-        B = int(r.shape[0])
+        r = r.to(torch.float64).contiguous()
+        if self.M == 0:
+            B = 1 if single else int(r.shape[0])
+        elif r.numel() % (self.M * ncomp) == 0 and r.numel() > 0:
+            B = r.numel() // (self.M * ncomp)
+        else:
+            raise ValueError("r must have shape (B?, M) for ncomp = 1 or (B?, M, 3) for ncomp = 3")
+        own = grad is None
         if grad is None:
             grad = torch.empty((B, nz, ny, nx), dtype=torch.float64, device=r.device)
-        gf_adjoint(self.handle, r.data_ptr(), ncomp, B, grad.data_ptr(), _stream_handle(stream))
-        return grad[0] if single else grad
+        _check_tensor(grad, "grad", B * nz * ny * nx, self.device)
+        with torch.cuda.device(self.device):
+            gf_adjoint(self.handle, r.data_ptr(), ncomp, B, grad.data_ptr(), _stream_handle(stream))
+        return grad[0] if (single and own) else grad
 
     def set_timing(self, enable=True):
         gf_plan_set_timing(self.handle, enable)
@@ -432,6 +483,7 @@ class Server:
         o.G = float(G)
         self._geoms = {}
         self._pending = {}
+        self._device_index = int(device)
         self.handle = None
         self.handle = gf_server_create(o)
 
@@ -444,32 +496,46 @@ class Server:
     def submit(self, gid, rho, gz=None, g=None, want_gz=True, want_g=False) -> int:
         """Queue a forward of densities `rho` (nz, ny, nx) on geometry `gid`.
         rho and the outputs are host arrays (numpy, or CPU tensors; pinned
-        ones make the copies asynchronous) or all CUDA tensors.  Returns a
-        ticket for :meth:`wait`."""
+        ones make the copies asynchronous) or all CUDA tensors on the
+        server's device; outputs passed in are contiguous float64 with M
+        (gz) or 3M (g) elements.  Returns a ticket for :meth:`wait`."""
         import torch
         grid, quad, obs, shape = self._geoms[int(gid)]
         M = obs.shape[0]
+        if not isinstance(rho, torch.Tensor):
+            rho = np.ascontiguousarray(rho)
+        if tuple(rho.shape) != (shape[2], shape[1], shape[0]):
+            raise ValueError("rho must have shape (nz, ny, nx) = %r" % ((shape[2], shape[1], shape[0]),))
         if isinstance(rho, torch.Tensor):
             on_device = rho.is_cuda
+            dev = torch.device("cuda", self._device_index) if on_device else None
             pin = (not on_device) and rho.is_pinned()
             rho = rho.contiguous()
-            rdt = {torch.float64: GF_DTYPE_F64, torch.float32: GF_DTYPE_F32}[rho.dtype]
+            _check_tensor(rho, "rho", rho.numel(), dev, (torch.float32, torch.float64))
+            rdt = GF_DTYPE_F64 if rho.dtype == torch.float64 else GF_DTYPE_F32
             if want_gz and gz is None:
                 gz = torch.empty(M, dtype=torch.float64, device=rho.device, pin_memory=pin)
             if want_g and g is None:
                 g = torch.empty((M, 3), dtype=torch.float64, device=rho.device, pin_memory=pin)
+            if gz is not None:
+                _check_tensor(gz, "gz", M, dev)
+            if g is not None:
+                _check_tensor(g, "g", 3 * M, dev)
             ptr = lambda a: a.data_ptr()  # noqa: E731
         else:
             on_device = False
-            rho = np.ascontiguousarray(rho)
-            rdt = {np.dtype(np.float64): GF_DTYPE_F64, np.dtype(np.float32): GF_DTYPE_F32}[rho.dtype]
+            if rho.dtype not in (np.dtype(np.float64), np.dtype(np.float32)):
+                raise TypeError("rho must be float32 or float64")
+            rdt = GF_DTYPE_F64 if rho.dtype == np.float64 else GF_DTYPE_F32
             if want_gz and gz is None:
                 gz = np.empty(M, dtype=np.float64)
             if want_g and g is None:
                 g = np.empty((M, 3), dtype=np.float64)
+            if gz is not None:
+                _check_array(gz, "gz", M)
+            if g is not None:
+                _check_array(g, "g", 3 * M)
             ptr = lambda a: a.ctypes.data  # noqa: E731
-        if tuple(rho.shape) != (shape[2], shape[1], shape[0]):
-            raise ValueError("rho must have shape (nz, ny, nx) = %r" % ((shape[2], shape[1], shape[0]),))
         r = gf_request()
         r.grid = grid
         r.quad = quad.c
