@@ -269,6 +269,21 @@ def test_linearity_and_mirror_symmetry():
     assert np.allclose(g2[:, 1:], g1[:, 1:], atol=1e-13 * sc)
 
 
+def test_translation_invariance():
+    """Moving the grid and the observers by the same vector leaves g
+    unchanged: Eq. 1 depends on r - x only.  The shift is a multiple of
+    the voxel size, so only the rounding of the coordinates differs."""
+    wk = wl.random_small(51, n=(5, 4, 3), npts=2, n_obs=29, h=(0.5, 0.5, 0.5), origin=(0.0, 0.0, 0.0))
+    t = np.array([64.0, -32.0, 128.0])
+    g0 = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs, 1.0)
+    g1 = direct.forward(wk.grid.n, tuple(np.array(wk.grid.origin) + t), wk.grid.h, wk.xi, wk.w, wk.rho,
+                        wk.obs + t, 1.0)
+    assert np.max(np.abs(g1 - g0)) <= 1e-11 * np.max(np.abs(g0))
+    g2 = direct.forward(wk.grid.n, tuple(np.array(wk.grid.origin) + t), wk.grid.h, wk.xi, wk.w, wk.rho,
+                        wk.obs, 1.0)
+    assert np.max(np.abs(g2 - g0)) > 1e-3 * np.max(np.abs(g0))
+
+
 def test_adjoint_subset_matches_full_transpose():
     """The sampled transpose sum returns exactly the full transpose sum's
     values at the sampled voxels (same arithmetic, same order)."""
