@@ -58,6 +58,10 @@ def _load():
             lib.gfo_prism_norms.argtypes = [_dp, _dp, dbl, dbl, _dp, _dp, i64, i64,
                                             i32, _dp, _dp, _dp, i32]
             lib.gfo_prism_norms.restype = None
+            lib.gfo_prism_g_many.argtypes = [_dp, _dp, dbl, dbl, _dp, i64, _dp, i32]
+            lib.gfo_prism_g_many.restype = None
+            lib.gfo_forward_analytic.argtypes = [i64, i64, i64, _dp, _dp, _dp, i32, _dp, i64, dbl, _dp, i32]
+            lib.gfo_forward_analytic.restype = i32
             lib.gfo_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -169,6 +173,35 @@ def prism_gz(lo, hi, rho, G, pts, nthreads: int = 0) -> np.ndarray:
     _load().gfo_prism_gz_many(_p(_c(lo)), _p(_c(hi)), float(rho), float(G),
                               _p(pts), pts.shape[0], _p(out), int(nthreads))
     return out
+
+
+def prism_g(lo, hi, rho, G, pts, nthreads: int = 0) -> np.ndarray:
+    """Closed-form field g (all three components) of the prism [lo, hi]
+    with density rho at pts (n, 3); returns (n, 3)."""
+    pts = _c(pts).reshape(-1, 3)
+    out = np.zeros((pts.shape[0], 3), dtype=np.float64)
+    _load().gfo_prism_g_many(_p(_c(lo)), _p(_c(hi)), float(rho), float(G),
+                             _p(pts), pts.shape[0], _p(out), int(nthreads))
+    return out
+
+
+def forward_analytic(shape, origin, h, rho, obs, G, nthreads: int = 0) -> np.ndarray:
+    """SUM-AN: the exact field of the piecewise-constant density, each voxel
+    integrated in closed form.  Same shapes as :func:`forward` (no
+    quadrature rule)."""
+    nx, ny, nz = (int(s) for s in shape)
+    rho = _c(rho)
+    single = rho.ndim == 3
+    rho = rho.reshape(-1, nz, ny, nx)
+    B = rho.shape[0]
+    obs = _c(obs).reshape(-1, 3)
+    M = obs.shape[0]
+    out = np.zeros((B, M, 3), dtype=np.float64)
+    rc = _load().gfo_forward_analytic(nx, ny, nz, _p(_c(origin)), _p(_c(h)), _p(rho), B,
+                                      _p(obs), M, float(G), _p(out), int(nthreads))
+    if rc != 0:
+        raise ValueError("gfo_forward_analytic: bad arguments")
+    return out[0] if single else out
 
 
 def prism_norms(plo, phi, rho, G, dlo, dhi, Mbar, m, ngauss=4, nthreads=0):

@@ -28,10 +28,11 @@
  * zero-mean random densities whose terms cancel heavily.  Build with
  * -ffp-contract=off so that no fused multiply-add changes the rounding.
  *
- * Also here: the adjoint (transpose) sum, the closed-form vertical field of a
+ * Also here: the adjoint (transpose) sum, the closed-form field of a
  * constant-density rectangular prism (the SUM-AN reference of Sec. 2.1, whose
  * formula the paper cites but does not print -- restated here from the
- * mathematics), and the Appendix A norm quadrature of that field.
+ * mathematics), the SUM-AN sum over a voxel grid built from it, and the
+ * Appendix A norm quadrature of the prism's vertical field.
  */
 #include <math.h>
 #include <stdint.h>
@@ -301,6 +302,93 @@ double gfo_prism_gz(const double *lo, const double *hi, double rho, double G,
                 acc += s * prism_corner(u, v, w);
             }
     return G * rho * acc;
+}
+
+/*
+ * All three components of the prism field.  Relabelling the axes in the
+ * derivation above gives g_x and g_y: the corner function keeps its form
+ * with the component's own axis in the third (arctangent) slot,
+ *
+ *   g_x = G rho sum s [ v ln(w+R) + w ln(v+R) - u atan(v w / (u R)) ]
+ *   g_y = G rho sum s [ w ln(u+R) + u ln(w+R) - v atan(w u / (v R)) ]
+ *
+ * with the same corner signs s.  g[2] equals gfo_prism_gz bit for bit.
+ */
+void gfo_prism_g(const double *lo, const double *hi, double rho, double G,
+                 const double *r, double *g) {
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                const double u = (a ? hi[0] : lo[0]) - r[0];
+                const double v = (b ? hi[1] : lo[1]) - r[1];
+                const double w = (c ? hi[2] : lo[2]) - r[2];
+                const double s = ((a + b + c) & 1) ? 1.0 : -1.0;
+                ax += s * prism_corner(v, w, u);
+                ay += s * prism_corner(w, u, v);
+                az += s * prism_corner(u, v, w);
+            }
+    g[0] = G * rho * ax;
+    g[1] = G * rho * ay;
+    g[2] = G * rho * az;
+}
+
+void gfo_prism_g_many(const double *lo, const double *hi, double rho, double G,
+                      const double *pts, long n, double *out, int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) gfo_prism_g(lo, hi, rho, G, pts + 3 * i, out + 3 * i);
+}
+
+/*
+ * SUM-AN (Sec. 2.1): the field of the piecewise-constant density itself,
+ * every voxel integrated in closed form,
+ *
+ *   g(r) = sum_v  prism field of voxel v = origin + [i, i+1) x [j, j+1) x
+ *                 [k, k+1) * h  with density rho_v,
+ *
+ * with one Neumaier sum per observer, component and model.  No quadrature
+ * and no coincidence rule: the closed form is finite everywhere, on voxel
+ * faces, edges and corners included.
+ *   rho : [B][nz][ny][nx],  obs : [M][3],  g : [B][M][3]
+ */
+int gfo_forward_analytic(long nx, long ny, long nz, const double *origin,
+                         const double *h, const double *rho, int B,
+                         const double *obs, long M, double G, double *g,
+                         int nthreads) {
+    if (nx < 0 || ny < 0 || nz < 0 || B <= 0 || M < 0) return -1;
+    set_threads(nthreads);
+    const long nvox = nx * ny * nz;
+#pragma omp parallel
+    {
+        nsum *acc = (nsum *)malloc(sizeof(nsum) * 3 * (size_t)B);
+#pragma omp for schedule(dynamic, 4)
+        for (long s = 0; s < M; ++s) {
+            memset(acc, 0, sizeof(nsum) * 3 * (size_t)B);
+            for (long k = 0; k < nz; ++k)
+                for (long j = 0; j < ny; ++j)
+                    for (long i = 0; i < nx; ++i) {
+                        const long v = (k * ny + j) * nx + i;
+                        const double lo[3] = {origin[0] + (double)i * h[0],
+                                              origin[1] + (double)j * h[1],
+                                              origin[2] + (double)k * h[2]};
+                        const double hi[3] = {origin[0] + (double)(i + 1) * h[0],
+                                              origin[1] + (double)(j + 1) * h[1],
+                                              origin[2] + (double)(k + 1) * h[2]};
+                        double f[3];
+                        gfo_prism_g(lo, hi, 1.0, 1.0, obs + 3 * s, f);
+                        for (int b = 0; b < B; ++b) {
+                            const double d = rho[(long)b * nvox + v];
+                            for (int a = 0; a < 3; ++a) nsum_add(&acc[3 * b + a], d * f[a]);
+                        }
+                    }
+            for (int b = 0; b < B; ++b)
+                for (int a = 0; a < 3; ++a)
+                    g[((long)b * M + s) * 3 + a] = G * nsum_val(&acc[3 * b + a]);
+        }
+        free(acc);
+    }
+    return 0;
 }
 
 /* Vectorised prism field at n points. */
