@@ -604,9 +604,9 @@ def bench_serving(args, rank, world):
     clk = clocks.stop()
     sat_s = max_over_ranks(sum(pass_s), world, torch.device("cuda", local_rank))
     sat_rate = len(reqs) * args.steps / sat_s
-    # open loop at Poisson arrival times: half the saturated rate, and light
-    # load (the stream's own 100 requests/s, or a quarter of the saturated
-    # rate if that is lower)
+    # open loop at Poisson arrival times: half and 80% of the saturated rate,
+    # and light load (the stream's own 100 requests/s, or a quarter of the
+    # saturated rate if that is lower)
     def open_loop(rate):
         arr = np.array([r["arrival_s"] for r in reqs]) * (100.0 / rate)   # drawn at 100 requests/s
         t0 = time.perf_counter()
@@ -625,6 +625,7 @@ def bench_serving(args, rank, world):
 
     rate = args.rate if args.rate > 0 else 0.5 * sat_rate
     lat, open_s = open_loop(rate)
+    lat_h, open_h = open_loop(0.8 * sat_rate)
     light = min(100.0, 0.25 * sat_rate)
     lat_l, open_l = open_loop(light)
     st = srv.stats()
@@ -665,6 +666,7 @@ def bench_serving(args, rank, world):
                        "l2_flush": "inputs larger than L2 (%.1f GB of densities per pass)" % (h2d / 1e9)},
             "interactions_per_s": units * sat_rate * world / len(reqs),
             "latency_open_loop": lat_summary(rate, lat, open_s),
+            "latency_open_loop_80pct": lat_summary(0.8 * sat_rate, lat_h, open_h),
             "latency_light_load": lat_summary(light, lat_l, open_l),
             "cold_pass": {"seconds": cold_s, "plans_created": int(st_cold["plans_created"]),
                           "solves_per_s": len(reqs) / cold_s},
