@@ -9,7 +9,8 @@
 // three logarithms, three arctangents, one square root) and s(v, c) = +1
 // when c is reached from v's lower corner by an odd number of upper limits,
 // -1 otherwise.  The same voxels are also summed with n^3-point Gauss rules
-// (n = 2, 3, 4) for comparison.  Each voxel is assigned to a shell by its
+// (n = 2, 3, 4), and with the midpoint rule plus the l = 4 (hexadecapole)
+// term of a uniform cube, for comparison.  Each voxel is assigned to a shell by its
 // Chebyshev distance, in voxels, from the voxel holding the observer, and
 // every method is evaluated shell by shell so the caller can see where each
 // is accurate enough.
@@ -19,7 +20,8 @@
 //            (i, j, k) spans [i, i+1) x [j, j+1) x [k, k+1) (h = 1), G = 1
 //   out.bin: doubles  g[method][shell][M][3] for methods
 //            0 lattice FP64, 1 lattice FP32, 2 Gauss 2^3 FP32,
-//            3 Gauss 3^3 FP32, 4 Gauss 4^3 FP32, and shells 0..kShells-1
+//            3 Gauss 3^3 FP32, 4 Gauss 4^3 FP32, 5 midpoint + cube
+//            hexadecapole FP32, and shells 0..kShells-1
 //            (the last shell holds every voxel at distance >= kShells-1)
 #include <algorithm>
 #include <cmath>
@@ -28,7 +30,7 @@
 #include <vector>
 
 static constexpr int kShells = 6;
-static constexpr int kMethods = 5;
+static constexpr int kMethods = 6;
 
 // ln(a + R) with R = sqrt(a^2 + q), q = the other two squares; the form
 // without cancellation when a < 0
@@ -151,6 +153,29 @@ int main(int argc, char **argv) {
                             for (int a = 0; a < 3; ++a) gg[a] += acc[a];
                         }
             }
+            // midpoint + hexadecapole of the unit cube: with R = r - c,
+            // Phi = G m [1/R - (7/192) (sum R_i^4 - 3/5 R^4) / R^9] up to
+            // l = 6 (a cube has no quadrupole), g = -grad Phi
+            double *gm = at(5, s, j);
+            for (int k = 0; k < nb; ++k)
+                for (int jj = 0; jj < nb; ++jj)
+                    for (int i = 0; i < nb; ++i) {
+                        if (shell(i, jj, k) != s) continue;
+                        const float m = (float)rho[((size_t)k * nb + jj) * nb + i];
+                        const float R[3] = {(float)ox - (float)(i + 0.5), (float)oy - (float)(jj + 0.5),
+                                            (float)oz - (float)(k + 0.5)};
+                        const float r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+                        if (r2 == 0.f) continue;
+                        const float ri = 1.0f / std::sqrt(r2), ri2 = ri * ri;
+                        const float ri3 = ri * ri2, ri9 = ri3 * ri3 * ri3, ri11 = ri9 * ri2;
+                        const float S4 = R[0] * R[0] * R[0] * R[0] + R[1] * R[1] * R[1] * R[1] +
+                                         R[2] * R[2] * R[2] * R[2];
+                        const float q = 9.f * (S4 - 0.6f * r2 * r2) * ri11;
+                        for (int a = 0; a < 3; ++a) {
+                            const float t = (4.f * R[a] * R[a] - 2.4f * r2) * R[a] * ri9 - q * R[a];
+                            gm[a] += (double)(m * (R[a] * ri3 + (7.f / 192.f) * t));
+                        }
+                    }
         }
     }
     FILE *fo = fopen(argv[2], "wb");

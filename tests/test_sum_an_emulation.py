@@ -10,7 +10,12 @@ observer's voxel) over the 12^3 voxels of a leaf's 27 neighbour leaves
 * the closed form in FP32 stays within 1e-5 of the total field on the
   shells 0..2, its cancellation growing like (d/h)^3 beyond;
 * Gauss rules fail near the observer (the integrand is singular in its own
-  voxel) and reach the FP32 floor from shell 3 with 3^3 points.
+  voxel) and reach the FP32 floor from shell 3 with 3^3 points;
+* one point per voxel suffices from shell 3 once the l = 4 (hexadecapole)
+  term of a uniform cube, -(7/192) G m h^4 (sum R_i^4 - 3/5 R^4) / R^9 in
+  the potential, is added (a cube has no quadrupole), so the design --
+  closed form on shells 0..2, corrected midpoint beyond -- stays within the
+  mixed-precision bar of 1e-5.
 """
 import os
 import shutil
@@ -23,7 +28,7 @@ from oracle import direct
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 NB, SHELLS = 12, 6
-LAT64, LAT32, G2, G3, G4 = range(5)
+LAT64, LAT32, G2, G3, G4, MIDHEX = range(6)
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +48,7 @@ def _run(emu, rho, obs):
     inp, out = str(d / "in.bin"), str(d / "out.bin")
     np.concatenate([[NB, len(obs)], rho.ravel(), obs.ravel()]).astype(np.float64).tofile(inp)
     subprocess.run([exe, inp, out], check=True)
-    return np.fromfile(out).reshape(5, SHELLS, len(obs), 3)
+    return np.fromfile(out).reshape(6, SHELLS, len(obs), 3)
 
 
 def _oracle_by_shell(rho, obs):
@@ -76,3 +81,8 @@ def test_corner_lattice_design(emu, kind):
     assert err[LAT32, 5] > err[LAT32, 0]              # cancellation grows with distance
     assert err[G2, 0] > 0.1 and err[G4, 1] > 1e-2     # quadrature fails next to the observer
     assert err[G3, 3:].max() <= 2e-6
+    # the midpoint rule plus a cube's l = 4 term: error falls like (h/d)^6
+    assert err[MIDHEX, 3:].max() <= 5e-6 and err[MIDHEX, 4:].max() <= 1e-6
+    # the design: closed form on shells 0..2, corrected midpoint beyond
+    design = g[LAT32, :3].sum(0) + g[MIDHEX, 3:].sum(0)
+    assert (np.linalg.norm(design - ref.sum(0), axis=1) / scale).max() <= 1e-5
