@@ -107,9 +107,10 @@ typedef struct gf_plan_s *gf_plan_t;
  *   opt        : mode, precision, expansion degree, batch capacity, G
  * In FMM mode this builds the Morton-sorted octree of Sec. 2.3 on the
  * device: observer keys and their stable sort, the occupied boxes of every
- * level, the near lists and the interaction lists ("cells of the same level
- * that are not nearest neighbours but are children of the nearest neighbours
- * of the parent", starting at level 2), and the translation operators.
+ * level, the near lists and the interaction lists (for each box: the boxes
+ * one level down from its parent's neighbourhood, i.e. children of boxes
+ * within Chebyshev distance 1 of the parent, minus the box's own neighbours;
+ * from level 2 on), and the translation operators.
  * Waits for the device.  On success *plan receives the new plan.
  */
 gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad,

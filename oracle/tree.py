@@ -9,9 +9,9 @@ Sec. 2.3 ("Hierarchical space decomposition", "Overview of the algorithm"):
 * a box's near domain is itself plus its nearest neighbours, i.e. the boxes
   of the same level whose integer coordinates differ by at most one on every
   axis (Chebyshev distance <= 1);
-* a box's interaction list holds the boxes of the same level that are not
-  nearest neighbours but are children of the nearest neighbours of its
-  parent; lists start at level 2.
+* a box's interaction list: take the children of every box within
+  Chebyshev distance 1 of its parent and drop those within Chebyshev
+  distance 1 of the box itself; lists start at level 2.
 
 Conventions the CUDA path must reproduce exactly (they are choices, not
 paper facts): the point-to-leaf map is ``floor((x - lo) * inv_s)`` evaluated
