@@ -10,7 +10,8 @@ Contents
 ``direct``  -- ctypes wrapper of ``gf_oracle.c``: the discretised Eq. 1 sum
                (Sec. 2.1 quadrature, Eq. 7 N-body form), its transpose, the
                closed-form prism field (all three components), the SUM-AN
-               sum over a voxel grid built from it, and the Appendix A norms.
+               sum over a voxel grid built from it and its transpose, and the
+               Appendix A norms.
 ``tree``    -- numpy octree: Morton keys, box tables, near lists and
                interaction lists (Sec. 2.3 "Overview of the algorithm") and the
                surface-to-volume work model of Eqs. 14-19.

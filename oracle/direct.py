@@ -62,6 +62,8 @@ def _load():
             lib.gfo_prism_g_many.restype = None
             lib.gfo_forward_analytic.argtypes = [i64, i64, i64, _dp, _dp, _dp, i32, _dp, i64, dbl, _dp, i32]
             lib.gfo_forward_analytic.restype = i32
+            lib.gfo_adjoint_analytic.argtypes = [i64, i64, i64, _dp, _dp, _dp, i64, _dp, i32, i32, dbl, _dp, i32]
+            lib.gfo_adjoint_analytic.restype = i32
             lib.gfo_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -201,6 +203,29 @@ def forward_analytic(shape, origin, h, rho, obs, G, nthreads: int = 0) -> np.nda
                                       _p(obs), M, float(G), _p(out), int(nthreads))
     if rc != 0:
         raise ValueError("gfo_forward_analytic: bad arguments")
+    return out[0] if single else out
+
+
+def adjoint_analytic(shape, origin, h, obs, r, G, ncomp: int = 1, nthreads: int = 0) -> np.ndarray:
+    """Transpose of :func:`forward_analytic`; same shapes as :func:`adjoint`."""
+    nx, ny, nz = (int(s) for s in shape)
+    obs = _c(obs).reshape(-1, 3)
+    M = obs.shape[0]
+    r = _c(r)
+    if ncomp == 1:
+        single = r.ndim == 1
+        r = r.reshape(-1, M)
+    elif ncomp == 3:
+        single = r.ndim == 2
+        r = r.reshape(-1, M, 3)
+    else:
+        raise ValueError("ncomp must be 1 or 3")
+    B = r.shape[0]
+    out = np.zeros((B, nz, ny, nx), dtype=np.float64)
+    rc = _load().gfo_adjoint_analytic(nx, ny, nz, _p(_c(origin)), _p(_c(h)), _p(obs), M, _p(_c(r)), ncomp, B,
+                                      float(G), _p(out), int(nthreads))
+    if rc != 0:
+        raise ValueError("gfo_adjoint_analytic: bad arguments")
     return out[0] if single else out
 
 

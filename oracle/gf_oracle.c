@@ -391,6 +391,51 @@ int gfo_forward_analytic(long nx, long ny, long nz, const double *origin,
     return 0;
 }
 
+/*
+ * Transpose of gfo_forward_analytic: for weights r on the outputs (ncomp = 1:
+ * on g_z only, r [B][M]; ncomp = 3: on g, r [B][M][3]),
+ *
+ *   grad_v = G sum_j r_j . (prism field of voxel v, unit density, at obs_j),
+ *
+ * one Neumaier sum per voxel and model.  grad : [B][nz][ny][nx].
+ */
+int gfo_adjoint_analytic(long nx, long ny, long nz, const double *origin,
+                         const double *h, const double *obs, long M,
+                         const double *r, int ncomp, int B, double G,
+                         double *grad, int nthreads) {
+    if (nx < 0 || ny < 0 || nz < 0 || B <= 0 || M < 0 || (ncomp != 1 && ncomp != 3)) return -1;
+    set_threads(nthreads);
+    const long nvox = nx * ny * nz;
+#pragma omp parallel
+    {
+        nsum *acc = (nsum *)malloc(sizeof(nsum) * (size_t)B);
+#pragma omp for schedule(dynamic, 4)
+        for (long v = 0; v < nvox; ++v) {
+            const long i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+            const double lo[3] = {origin[0] + (double)i * h[0], origin[1] + (double)j * h[1],
+                                  origin[2] + (double)k * h[2]};
+            const double hi[3] = {origin[0] + (double)(i + 1) * h[0], origin[1] + (double)(j + 1) * h[1],
+                                  origin[2] + (double)(k + 1) * h[2]};
+            memset(acc, 0, sizeof(nsum) * (size_t)B);
+            for (long s = 0; s < M; ++s) {
+                double f[3];
+                gfo_prism_g(lo, hi, 1.0, 1.0, obs + 3 * s, f);
+                for (int b = 0; b < B; ++b) {
+                    if (ncomp == 1) {
+                        nsum_add(&acc[b], r[(long)b * M + s] * f[2]);
+                    } else {
+                        const double *rb = r + ((long)b * M + s) * 3;
+                        for (int a = 0; a < 3; ++a) nsum_add(&acc[b], rb[a] * f[a]);
+                    }
+                }
+            }
+            for (int b = 0; b < B; ++b) grad[(long)b * nvox + v] = G * nsum_val(&acc[b]);
+        }
+        free(acc);
+    }
+    return 0;
+}
+
 /* Vectorised prism field at n points. */
 void gfo_prism_gz_many(const double *lo, const double *hi, double rho,
                        double G, const double *pts, long n, double *out,

@@ -3,7 +3,8 @@ its SUM-AN grid sum (Sec. 2.1: each constant-density voxel integrated in
 closed form), against facts other than the formulas themselves: the vertical
 component that Table 10 pins, the axis symmetry of Eq. 1, the point-mass
 limit, Gauss's law (Eq. 2) outside and inside the body, fourth-order
-convergence of the Gauss sums, and additivity of the integral over voxels.
+convergence of the Gauss sums, additivity of the integral over voxels, and
+the dot-product identity between the SUM-AN sum and its transpose.
 """
 import numpy as np
 import pytest
@@ -151,3 +152,20 @@ def test_sum_an_is_linear_and_tends_to_the_midpoint_sum():
         errs.append(np.max(np.abs(an - mid)) / np.max(np.abs(an)))
     ratios = np.array(errs[:-1]) / np.array(errs[1:])
     assert np.all((ratios > 13.0) & (ratios < 19.0)), ratios
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_sum_an_adjoint_dot_product(ncomp):
+    """<A x, y> = <x, A^T y> for the SUM-AN sum and its transpose (the sum is
+    linear in rho), observers inside and outside the grid."""
+    n, origin, h = (4, 3, 2), (-1.0, 0.5, -2.0), (0.5, 0.75, 1.0)
+    rho = RNG.normal(size=(2, 2, 3, 4))
+    obs = np.concatenate([RNG.uniform(-3.0, 3.0, size=(9, 3)), RNG.uniform((-1.0, 0.5, -2.0), (1.0, 2.75, 0.0),
+                                                                            size=(4, 3))])
+    g = direct.forward_analytic(n, origin, h, rho, obs, 0.3)
+    y = RNG.normal(size=(2, len(obs)) if ncomp == 1 else (2, len(obs), 3))
+    at = direct.adjoint_analytic(n, origin, h, obs, y, 0.3, ncomp=ncomp)
+    for b in range(2):
+        lhs = np.sum((g[b, :, 2] if ncomp == 1 else g[b]) * y[b])
+        rhs = np.sum(rho[b] * at[b])
+        assert lhs == pytest.approx(rhs, rel=1e-12)
