@@ -82,7 +82,15 @@ enum { GF_MODE_DIRECT = 0, GF_MODE_FMM = 1 };
  * (p >= 10). */
 enum { GF_PREC_FP64 = 0, GF_PREC_MIXED = 1 };
 enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
-enum { GF_FLAG_M2L_SIMT = 1 };
+/* Option flags (gf_options.reserved0):
+ *   GF_FLAG_M2L_SIMT  FMM, mixed precision: the M2L on the SIMT cores
+ *                     instead of the tensor cores.
+ *   GF_FLAG_SUM_AN    direct mode, FP64 only: every voxel integrated in
+ *                     closed form (SUM-AN of Sec. 2.1, the exact field of
+ *                     the piecewise-constant density, finite on voxel faces,
+ *                     edges and corners) instead of sampled by the quadrature
+ *                     rule; the rule is then ignored. */
+enum { GF_FLAG_M2L_SIMT = 1, GF_FLAG_SUM_AN = 2 };
 
 typedef struct {
     int32_t mode;        /* GF_MODE_DIRECT or GF_MODE_FMM                  */
@@ -92,8 +100,7 @@ typedef struct {
     int32_t leaf_vox;    /* FMM leaf edge in voxels (leaf = leaf_vox^3     */
                          /* voxels), 0 = library default                   */
     int32_t max_batch;   /* largest B passed to gf_forward/gf_adjoint, >=1 */
-    int32_t reserved0;   /* flags: GF_FLAG_M2L_SIMT runs the mixed-precision */
-                         /* M2L on the SIMT cores instead of the tensor cores */
+    int32_t reserved0;   /* GF_FLAG_* option flags, 0 = none               */
     double G;            /* gravitational constant; 0 = 6.67428e-11        */
 } gf_options;
 

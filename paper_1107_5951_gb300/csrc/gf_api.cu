@@ -141,6 +141,14 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
         set_error("opt.G must be finite and >= 0 (0 selects 6.67428e-11)");
         return GF_ERR_INVALID_ARG;
     }
+    if (opt->reserved0 & ~(GF_FLAG_M2L_SIMT | GF_FLAG_SUM_AN)) {
+        set_error("opt.reserved0 = %d holds unknown flags", opt->reserved0);
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((opt->reserved0 & GF_FLAG_SUM_AN) && (opt->mode != GF_MODE_DIRECT || opt->precision != GF_PREC_FP64)) {
+        set_error("GF_FLAG_SUM_AN (closed-form voxels) is implemented in direct mode, FP64 only");
+        return GF_ERR_UNSUPPORTED;
+    }
     if (opt->mode == GF_MODE_FMM) {
         if (opt->p < 1 || opt->p > kMaxP) {
             set_error("opt.p = %d out of range [1, %d]", opt->p, kMaxP);
@@ -181,6 +189,7 @@ gf_status gf_plan_bytes(const gf_grid *grid, const gf_quad *quad, int64_t M,
     if (opt->mode == GF_MODE_DIRECT) {
         b += (size_t)M * 3 * sizeof(double) + 512;
         if (opt->precision == GF_PREC_MIXED) b += (size_t)M * 6 * sizeof(float) + 512;
+        if (opt->reserved0 & GF_FLAG_SUM_AN) b += sum_an_bytes(grid, opt->max_batch);
     } else {
         b += fmm_bytes_estimate(grid, quad->nq, M, opt);
     }
@@ -241,7 +250,8 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
     if (s == GF_OK) {
         if (opt->mode == GF_MODE_DIRECT) {
             s = direct_prepare(p, obs_dev, st);
-            p->near_pairs = p->M * p->nvox * quad->nq;
+            if (s == GF_OK && (opt->reserved0 & GF_FLAG_SUM_AN)) s = sum_an_prepare(p);
+            p->near_pairs = p->M * p->nvox * ((opt->reserved0 & GF_FLAG_SUM_AN) ? 1 : quad->nq);
         }
         else
             s = fmm_create(p, obs_dev, st);
@@ -291,7 +301,10 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int
     for (int i = 0; i <= GF_NUM_STAGES; ++i) plan->ev_used[i] = false;
     stage_mark(plan, 0, st);
     if (plan->opt.mode == GF_MODE_DIRECT) {
-        GF_TRY(direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
+        if (plan->opt.reserved0 & GF_FLAG_SUM_AN)
+            GF_TRY(sum_an_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
+        else
+            GF_TRY(direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
         stage_mark(plan, 6, st);
         return GF_OK;
     }
@@ -317,8 +330,10 @@ gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp, int32_t
         return GF_ERR_INVALID_ARG;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (plan->opt.mode == GF_MODE_DIRECT)
+    if (plan->opt.mode == GF_MODE_DIRECT) {
+        if (plan->opt.reserved0 & GF_FLAG_SUM_AN) return sum_an_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
         return direct_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
+    }
     return fmm_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
 }
 

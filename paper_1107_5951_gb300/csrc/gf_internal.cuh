@@ -84,6 +84,7 @@ struct gf_plan_s {
     double *d_obs = nullptr;     // [M][3] FP64
     int32_t *d_obs_ivox = nullptr;   // [M][3] floor of voxel coordinates (mixed)
     float *d_obs_fvox = nullptr;     // [M][3] fractional voxel coordinates (mixed)
+    double *d_corner = nullptr;      // closed-form voxels: [max_batch][corners] weights
     gf::FmmPlan *fmm = nullptr;
     int *d_status = nullptr;     // device-side check word
     size_t device_bytes = 0;
@@ -114,6 +115,14 @@ gf_status direct_prepare(gf_plan_s *plan, const double *obs_dev, cudaStream_t st
 gf_status direct_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
                          double *g, double *gz, cudaStream_t st);
 gf_status direct_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B,
+                         double *grad, cudaStream_t st);
+
+// Closed-form voxels, SUM-AN (gf_sum_an.cu; direct mode, FP64)
+size_t sum_an_bytes(const gf_grid *grid, int max_batch);
+gf_status sum_an_prepare(gf_plan_s *plan);
+gf_status sum_an_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
+                         double *g, double *gz, cudaStream_t st);
+gf_status sum_an_adjoint(gf_plan_s *plan, const double *r, int ncomp, int B,
                          double *grad, cudaStream_t st);
 
 // FMM (gf_fmm.cu)

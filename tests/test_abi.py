@@ -102,6 +102,25 @@ def test_total_voxel_count_is_bounded(n, ok):
         assert "2^40" in gf.gf_last_error()
 
 
+def test_closed_form_voxels_only_in_direct_fp64():
+    """GF_FLAG_SUM_AN is accepted in direct mode in FP64 (the plan then holds
+    the corner-lattice weights) and refused elsewhere; unknown flag bits are
+    invalid arguments."""
+    grid, q, opt = _args(mode="direct")
+    plain = gf.gf_plan_bytes(grid, q.c, 10, opt)
+    opt.reserved0 = gf.GF_FLAG_SUM_AN
+    assert gf.gf_plan_bytes(grid, q.c, 10, opt) >= plain + 5 ** 3 * 8
+    for bad in (dict(mode="fmm", p=6), dict(mode="direct", precision="mixed")):
+        grid, q, opt = _args(flags=gf.GF_FLAG_SUM_AN, **bad)
+        with pytest.raises(gf.GfError) as e:
+            gf.gf_plan_bytes(grid, q.c, 10, opt)
+        assert e.value.status == gf.GF_ERR_UNSUPPORTED
+    grid, q, opt = _args(mode="direct", flags=8)
+    with pytest.raises(gf.GfError) as e:
+        gf.gf_plan_bytes(grid, q.c, 10, opt)
+    assert e.value.status == gf.GF_ERR_INVALID_ARG
+
+
 def test_null_plan_and_null_outputs_rejected():
     lib = pkg.load()
     assert lib.gf_forward(None, None, 0, 1, None, None, None) == gf.GF_ERR_INVALID_ARG
