@@ -97,10 +97,11 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "scale", "serving", "adjoint"],
+    ap.add_argument("--workload", default="volume", choices=["volume", "scale", "serving", "adjoint", "sum_an"],
                     help="volume: 128^3 random field, stations + voxel centres; scale: 464^3 layered "
                          "model, 1024^2 stations; serving: a stream of uneven requests; adjoint: misfit "
-                         "gradients of 16 models at 256^2 stations")
+                         "gradients of 16 models at 256^2 stations; sum_an: the 16^3 prism model with "
+                         "every voxel integrated in closed form (direct, FP64)")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests on the device at once")
     ap.add_argument("--rate", type=float, default=0.0,
@@ -543,6 +544,81 @@ def bench_adjoint(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ SUM-AN
+def bench_sum_an(args, rank, world):
+    """SUM-AN in direct mode (FP64): every voxel of the 16^3 prism-plus-noise
+    model (1 km voxels) integrated in closed form at the 64^2 stations 100 m
+    above it.  One step = one forward (corner-lattice weights + the sum over
+    the corner lattice).  Unit of work: a (voxel, observer) pair."""
+    import torch
+
+    import paper_1107_5951_gb300 as pkg
+    from oracle import direct
+    from paper_1107_5951_gb300 import workloads as wl
+
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wk = wl.fp64_prism_noise(1)
+    nvox, M = int(np.prod(wk.grid.n)), wk.n_obs
+    stream = torch.cuda.Stream(device=dev)
+    obs_d = torch.tensor(wk.obs, dtype=torch.float64, device=dev)
+    rho_d = torch.tensor(wk.rho, dtype=torch.float64, device=dev)
+    g_d = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    plan = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode="direct", precision="fp64",
+                    G=wk.G, stream=stream, voxels="closed_form")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        with torch.cuda.stream(stream):
+            plan.forward(rho_d, g=g_d, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local_rank, not args.no_clocks)
+    launches0 = pkg.gf_launch_count()
+    ev = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    launches = pkg.gf_launch_count() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+    units = float(nvox) * M
+    err, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(29)
+        idx = np.sort(rng.choice(M, 256, replace=False))
+        t1 = time.perf_counter()
+        want = direct.forward_analytic(wk.grid.n, wk.grid.origin, wk.grid.h, wk.rho, wk.obs[idx], wk.G)
+        dt = time.perf_counter() - t1
+        got = g_d.cpu().numpy()[idx]
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        cpu = {"value": nvox * len(idx) / dt, "unit": "interactions/s", "cores": direct.max_threads(),
+               "kind": "oracle", "sample": "256 seeded stations of %d x all %d voxels (%.1f s)" % (M, nvox, dt)}
+    plan.close()
+    if rank != 0:
+        return
+    line = {"metric": "effective interactions/s (SUM-AN, closed-form voxels)",
+            "value": job_rate(units, world, ms * 1e-3), "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wk.name + "_sum_an", "voxels": nvox, "M_observers": M,
+                       "l2_flush": "256 MiB buffer written between timed steps",
+                       "step": "corner-lattice weights + closed-form sum over the corner lattice"},
+            "rel_err_vs_oracle_sample": err, "roofline": None, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 def bench_serving(args, rank, world):
     """Serving stream: `--requests` forward solves, grid side n log-uniform
@@ -694,6 +770,8 @@ def main():
             bench_serving(args, rank, world)
         elif args.workload == "adjoint":
             bench_adjoint(args, rank, world)
+        elif args.workload == "sum_an":
+            bench_sum_an(args, rank, world)
         else:
             bench_gf(args, rank, world)
     finally:
