@@ -83,12 +83,13 @@ __device__ __forceinline__ double an_plane(double o, double h, int64_t I) {
 }
 
 // ln(a + R) with R = sqrt(a^2 + q), q > 0.
-__device__ __forceinline__ double an_log(double a, double q, double R) {
+__host__ __device__ __forceinline__ double an_log(double a, double q, double R) {
     return a >= 0.0 ? log(a + R) : log(q / (R - a));
 }
 
-// All three components of the corner function at (u, v, w).
-__device__ __forceinline__ void an_corner(double u, double v, double w, double &fx, double &fy, double &fz) {
+// All three components of the corner function at (u, v, w).  Host-callable
+// too: a CPU test checks it against the oracle's prism field.
+__host__ __device__ __forceinline__ void an_corner(double u, double v, double w, double &fx, double &fy, double &fz) {
     const double u2 = u * u, v2 = v * v, w2 = w * w;
     const double R = sqrt(u2 + v2 + w2);
     fx = fy = fz = 0.0;
@@ -103,7 +104,7 @@ __device__ __forceinline__ void an_corner(double u, double v, double w, double &
 }
 
 // The vertical component alone (two logarithms, one arctangent).
-__device__ __forceinline__ double an_corner_z(double u, double v, double w) {
+__host__ __device__ __forceinline__ double an_corner_z(double u, double v, double w) {
     const double u2 = u * u, v2 = v * v, w2 = w * w;
     const double R = sqrt(u2 + v2 + w2);
     if (R == 0.0) return 0.0;
