@@ -3,7 +3,7 @@
 // sampled by a quadrature rule.  FP64, direct mode, and its transpose.
 //
 // The field of voxel v (density rho_v) at r is G rho_v sum_c s(v, c) F(c - r)
-// over its eight corners c, F the corner function below and s(v, c) = +1 at
+// over its eight corners c, F the corner function (gf_sum_an.cuh) and s(v, c) = +1 at
 // the corners reached from the voxel's lower corner through an odd number of
 // upper limits, -1 at the others.  A lattice corner is shared by up to eight
 // voxels, so the sum over voxels is regrouped onto the corner lattice,
@@ -15,15 +15,7 @@
 // are skipped.  The transpose is regrouped the same way: per corner
 // E_c = sum_j r_j . F(c - x'_j), then grad_v = G sum_{c of v} s(v, c) E_c.
 //
-// Corner function, with (u, v, w) = corner minus observer and R = |(u,v,w)|,
-// from Eq. 1 by integrating along one axis and then over the other two:
-//   F_x = v ln(w + R) + w ln(v + R) - u atan(v w / (u R))
-//   F_y = w ln(u + R) + u ln(w + R) - v atan(w u / (v R))
-//   F_z = u ln(v + R) + v ln(u + R) - w atan(u v / (w R))
-// A logarithm ln(a + R) whose argument would cancel (a < 0) is evaluated as
-// ln(q / (R - a)), q = R^2 - a^2 formed as the sum of the other two squares;
-// terms whose coefficient is zero are dropped, so F is finite everywhere
-// (observers on faces, edges and corners included).
+// The corner function F and its evaluation are in gf_sum_an.cuh.
 //
 // Layout: corners are numbered I + (nx + 1) (J + (ny + 1) K) and sit at
 // origin + (I, J, K) h, rounded as origin + I h.  One thread per observer
@@ -35,6 +27,7 @@
 #include <algorithm>
 
 #include "gf_internal.cuh"
+#include "gf_sum_an.cuh"
 
 namespace gf {
 namespace {
@@ -82,38 +75,6 @@ __device__ __forceinline__ double an_plane(double o, double h, int64_t I) {
     return __dadd_rn(o, __dmul_rn((double)I, h));
 }
 
-// ln(a + R) with R = sqrt(a^2 + q), q > 0.
-__host__ __device__ __forceinline__ double an_log(double a, double q, double R) {
-    return a >= 0.0 ? log(a + R) : log(q / (R - a));
-}
-
-// All three components of the corner function at (u, v, w).  Host-callable
-// too: a CPU test checks it against the oracle's prism field.
-__host__ __device__ __forceinline__ void an_corner(double u, double v, double w, double &fx, double &fy, double &fz) {
-    const double u2 = u * u, v2 = v * v, w2 = w * w;
-    const double R = sqrt(u2 + v2 + w2);
-    fx = fy = fz = 0.0;
-    if (R == 0.0) return;
-    const double qu = v2 + w2, qv = u2 + w2, qw = u2 + v2;
-    const double Lu = qu > 0.0 ? an_log(u, qu, R) : 0.0;
-    const double Lv = qv > 0.0 ? an_log(v, qv, R) : 0.0;
-    const double Lw = qw > 0.0 ? an_log(w, qw, R) : 0.0;
-    fx = v * Lw + w * Lv - (u != 0.0 ? u * atan((v * w) / (u * R)) : 0.0);
-    fy = w * Lu + u * Lw - (v != 0.0 ? v * atan((w * u) / (v * R)) : 0.0);
-    fz = u * Lv + v * Lu - (w != 0.0 ? w * atan((u * v) / (w * R)) : 0.0);
-}
-
-// The vertical component alone (two logarithms, one arctangent).
-__host__ __device__ __forceinline__ double an_corner_z(double u, double v, double w) {
-    const double u2 = u * u, v2 = v * v, w2 = w * w;
-    const double R = sqrt(u2 + v2 + w2);
-    if (R == 0.0) return 0.0;
-    const double qu = v2 + w2, qv = u2 + w2;
-    const double Lu = qu > 0.0 ? an_log(u, qu, R) : 0.0;
-    const double Lv = qv > 0.0 ? an_log(v, qv, R) : 0.0;
-    return u * Lv + v * Lu - (w != 0.0 ? w * atan((u * v) / (w * R)) : 0.0);
-}
-
 // D[b][c]: signed sum of the densities of the voxels sharing corner c.
 __global__ void an_corner_weights(const void *__restrict__ rho, int rho_f32, AnGrid g,
                                   double *__restrict__ D) {
@@ -159,7 +120,7 @@ an_forward(const double *__restrict__ obs, int64_t M, const double *__restrict__
             const double d = sd[u];   // the same for every thread: a uniform branch
             if (d != 0.0) {
                 double fx, fy, fz;
-                an_corner(an_plane(g.ox, g.hx, I) - rx, an_plane(g.oy, g.hy, J) - ry,
+                an_corner<double>(an_plane(g.ox, g.hx, I) - rx, an_plane(g.oy, g.hy, J) - ry,
                           an_plane(g.oz, g.hz, K) - rz, fx, fy, fz);
                 px = fma(d, fx, px);
                 py = fma(d, fy, py);
@@ -222,11 +183,11 @@ an_adjoint_corners(const double *__restrict__ obs, int64_t M, const double *__re
         if (ncomp == 3) {
             for (int u = 0; u < cnt; ++u) {
                 double fx, fy, fz;
-                an_corner(X - ox[u], Y - oy[u], Z - oz[u], fx, fy, fz);
+                an_corner<double>(X - ox[u], Y - oy[u], Z - oz[u], fx, fy, fz);
                 p = fma(w0[u], fx, fma(w1[u], fy, fma(w2[u], fz, p)));
             }
         } else {
-            for (int u = 0; u < cnt; ++u) p = fma(w2[u], an_corner_z(X - ox[u], Y - oy[u], Z - oz[u]), p);
+            for (int u = 0; u < cnt; ++u) p = fma(w2[u], an_corner_z<double>(X - ox[u], Y - oy[u], Z - oz[u]), p);
         }
         an_neumaier(s, sc, p);
     }

@@ -7,6 +7,12 @@
 //   usage: sum_an_corner_host in.bin out.bin
 //   in.bin : doubles  n, then n records lo[3] hi[3] r[3]
 //   out.bin: doubles  n records gx gy gz gz'
+//
+// and of the FMM form's near field (gf_sum_an.cuh: an_near_block) in FP32
+// and FP64:
+//   usage: sum_an_corner_host in.bin out.bin near
+//   in.bin : doubles  nb, M, rho[nb^3] (x fastest), t[M][3] (voxel units)
+//   out.bin: doubles  M records g32[3] g64[3]
 #include <cstdarg>
 #include <cstdio>
 #include <vector>
@@ -23,8 +29,38 @@ gf_status DeviceArena::alloc(void **p, size_t) {
 }
 }  // namespace gf
 
+static int near_mode(const char *in, const char *outp) {
+    FILE *fi = fopen(in, "rb");
+    if (!fi) return 3;
+    double hdr[2];
+    if (fread(hdr, sizeof(double), 2, fi) != 2) return 4;
+    const int nb = (int)hdr[0];
+    const long M = (long)hdr[1];
+    std::vector<double> rho((size_t)nb * nb * nb), t(3 * (size_t)M), out(6 * (size_t)M);
+    if (fread(rho.data(), sizeof(double), rho.size(), fi) != rho.size()) return 5;
+    if (fread(t.data(), sizeof(double), t.size(), fi) != t.size()) return 6;
+    fclose(fi);
+    std::vector<float> rf(rho.begin(), rho.end());
+    for (long j = 0; j < M; ++j) {
+        float g32[3];
+        double g64[3];
+        gf::an_near_block<float>(rf.data(), nb, (float)t[3 * j], (float)t[3 * j + 1], (float)t[3 * j + 2], g32);
+        gf::an_near_block<double>(rho.data(), nb, t[3 * j], t[3 * j + 1], t[3 * j + 2], g64);
+        for (int a = 0; a < 3; ++a) {
+            out[6 * j + a] = g32[a];
+            out[6 * j + 3 + a] = g64[a];
+        }
+    }
+    FILE *fo = fopen(outp, "wb");
+    if (!fo) return 7;
+    fwrite(out.data(), sizeof(double), out.size(), fo);
+    fclose(fo);
+    return 0;
+}
+
 int main(int argc, char **argv) {
     if (argc < 3) return 2;
+    if (argc > 3) return near_mode(argv[1], argv[2]);
     FILE *fi = fopen(argv[1], "rb");
     if (!fi) return 3;
     double nd;
@@ -42,11 +78,11 @@ int main(int argc, char **argv) {
             const double u = (a ? hi[0] : lo[0]) - r[0], v = (b ? hi[1] : lo[1]) - r[1],
                          w = (e ? hi[2] : lo[2]) - r[2];
             double fx, fy, fz;
-            gf::an_corner(u, v, w, fx, fy, fz);
+            gf::an_corner<double>(u, v, w, fx, fy, fz);
             g[0] += s * fx;
             g[1] += s * fy;
             g[2] += s * fz;
-            gz2 += s * gf::an_corner_z(u, v, w);
+            gz2 += s * gf::an_corner_z<double>(u, v, w);
         }
         out[4 * t + 0] = g[0];
         out[4 * t + 1] = g[1];

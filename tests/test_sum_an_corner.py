@@ -1,9 +1,15 @@
-"""The SUM-AN kernels' corner function (gf_sum_an.cu: an_corner, an_corner_z),
-compiled for the host by nvcc into tests/emu/sum_an_corner_host.cu, against
-the oracle's closed-form prism field: summed with the corner signs over a
-prism's eight corners it gives the prism's field.  Observers inside and on
-faces, edges and corners agree to rounding; outside, the eight-term sum
-cancels like (d / size)^3, so the bar grows with distance."""
+"""The closed-form (SUM-AN) arithmetic of gf_sum_an.cuh, compiled for the host
+by nvcc into tests/emu/sum_an_corner_host.cu, against the oracle:
+
+* the corner function (an_corner, an_corner_z), summed with the corner signs
+  over a prism's eight corners, gives the prism's closed-form field;
+  observers inside and on faces, edges and corners agree to rounding,
+  outside the eight-term sum cancels like (d / size)^3;
+* the FMM form's near field (an_near_block: closed form on the 5^3 voxels
+  around the observer's voxel, midpoint plus a cube's l = 4 term beyond)
+  over the 12^3 voxels of a leaf's 27 neighbours (leaves of 4^3 voxels)
+  meets the mixed-precision bar against the oracle's SUM-AN sum of the
+  same voxels, in FP32 and in FP64."""
 import os
 import shutil
 import subprocess
@@ -52,3 +58,21 @@ def test_corner_function_matches_the_oracle_prism_field(harness):
     assert err[inside].max() <= 1e-14
     assert np.all(err[~inside] <= 1e-13 * np.maximum(dist[~inside], 1.0) ** 3)
     assert np.all(np.abs(out[:, 3] - ref[:, 2]) <= 1e-13 * np.maximum(dist, 1.0) ** 3 * scale)
+
+
+@pytest.mark.parametrize("kind", ["positive", "zero_mean"])
+def test_near_block_meets_the_mixed_bar(harness, kind):
+    exe, d = harness
+    nb = 12
+    rng = np.random.default_rng(17 if kind == "positive" else 18)
+    rho = rng.uniform(1.0, 3.0, size=(nb,) * 3) if kind == "positive" else rng.normal(size=(nb,) * 3)
+    t = rng.uniform(4.0, 8.0, size=(64, 3))        # observers in the central leaf
+    t[0] = [6.0, 6.0, 6.0]                          # a corner shared by eight voxels
+    t[1] = [5.5, 6.0, 6.25]                         # on a face
+    t[2] = [4.0, 7.999, 5.0]                        # on the leaf's boundary
+    np.concatenate([[nb, len(t)], rho.ravel(), t.ravel()]).tofile(str(d / "near_in.bin"))
+    subprocess.run([exe, str(d / "near_in.bin"), str(d / "near_out.bin"), "near"], check=True)
+    out = np.fromfile(str(d / "near_out.bin")).reshape(-1, 6)
+    ref = direct.forward_analytic((nb,) * 3, (0.0,) * 3, (1.0,) * 3, rho, t, 1.0)
+    for g in (out[:, :3], out[:, 3:]):
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 5e-6
