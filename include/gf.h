@@ -278,7 +278,8 @@ typedef struct {
     int64_t n_target_boxes[24];       /* occupied observer boxes per level */
     int64_t src_lo[24][3];            /* source boxes per level: inclusive */
     int64_t src_hi[24][3];            /* integer bounds of the dense block */
-    int64_t M, n_sources;
+    int64_t M, n_sources;             /* observers; quadrature points (or  */
+                                      /* voxels, with GF_FLAG_SUM_AN)      */
     int64_t near_pairs;               /* (observer, source) pairs summed   */
                                       /* directly in the near field        */
     int64_t m2l_pairs;                /* (observer box, source box) pairs  */

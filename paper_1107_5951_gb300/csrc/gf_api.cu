@@ -427,7 +427,7 @@ gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info) {
     info->mode = plan->opt.mode;
     info->precision = plan->opt.precision;
     info->M = plan->M;
-    info->n_sources = plan->nvox * plan->quad.nq;
+    info->n_sources = plan->nvox * ((plan->opt.reserved0 & GF_FLAG_SUM_AN) ? 1 : plan->quad.nq);
     info->device_bytes = plan->arena.bytes;
     info->near_pairs = plan->near_pairs;
     info->m2l_pairs = plan->m2l_pairs;
