@@ -130,7 +130,8 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad,
  *   rho_dev   : [B][nz][ny][nx] densities, FP64 or FP32 per rho_dtype
  *   B         : 1..opt.max_batch
  *   g_dev     : [B][M][3] FP64 output, observers in caller order, or NULL
- *   gz_dev    : [B][M] FP64 vertical component, or NULL (not both NULL)
+ *   gz_dev    : [B][M] FP64 vertical component, or NULL (not both NULL
+ *               unless M = 0)
  * Enqueues on `stream` and returns; allocates nothing, so it may be captured
  * in a CUDA graph.  Direct mode sums every pair (Sec. 2.1); FMM mode runs
  * P2M, M2M, M2L, L2L, L2P and the near-field P2P (Sec. 2.3, Fig. 3) and adds

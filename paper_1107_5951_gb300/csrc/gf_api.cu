@@ -285,7 +285,7 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int
         set_error("plan is NULL");
         return GF_ERR_INVALID_ARG;
     }
-    if (!rho_dev || (!g_dev && !gz_dev)) {
+    if (!rho_dev || (!g_dev && !gz_dev && plan->M > 0)) {
         set_error("rho_dev must be non-NULL and at least one of g_dev, gz_dev given");
         return GF_ERR_INVALID_ARG;
     }
