@@ -79,8 +79,9 @@ struct AnSum {
 // Near field (without the factor G h) at one observer of the voxels of an
 // nb^3 block, in voxel units (h = 1): rho[(k nb + j) nb + i] is the density
 // of voxel [i, i+1) x [j, j+1) x [k, k+1), t the observer's position in the
-// block.  Voxels within Chebyshev distance 2 of the observer's voxel are
-// integrated in closed form, on their corner lattice (6^3 corners, each
+// block.  Voxels within Chebyshev distance rad (2 in FP32) of the
+// observer's voxel are integrated in closed form, on their corner lattice
+// ((2 rad + 2)^3 corners, each
 // weighted by the signed sum of the densities of the included voxels that
 // share it); the others take the midpoint rule plus the l = 4 term of a
 // uniform cube, whose potential is m [1/R - (7/192)(sum R_i^4 - 3/5 R^4)/R^9]
@@ -90,7 +91,7 @@ struct AnSum {
 // why it stops at distance 2).  Rows of the block are summed plainly and
 // merged into compensated totals.
 template <class T>
-__host__ __device__ inline void an_near_block(const T *rho, int nb, T tx, T ty, T tz, T g[3]) {
+__host__ __device__ inline void an_near_block(const T *rho, int nb, T tx, T ty, T tz, T g[3], int rad = 2) {
     const int vi = (int)an_floor(tx), vj = (int)an_floor(ty), vk = (int)an_floor(tz);
     AnSum<T> Sx, Sy, Sz;
     for (int k = 0; k < nb; ++k)
@@ -100,7 +101,7 @@ __host__ __device__ inline void an_near_block(const T *rho, int nb, T tx, T ty, 
                 const int di = i - vi, dj = j - vj, dk = k - vk;
                 const int sh = an_imax(an_imax(di < 0 ? -di : di, dj < 0 ? -dj : dj), dk < 0 ? -dk : dk);
                 const T m = rho[(k * nb + j) * nb + i];
-                if (sh <= 2 || m == T(0)) continue;
+                if (sh <= rad || m == T(0)) continue;
                 const T Rx = tx - (T(i) + T(0.5)), Ry = ty - (T(j) + T(0.5)), Rz = tz - (T(k) + T(0.5));
                 const T r2 = Rx * Rx + Ry * Ry + Rz * Rz;
                 const T ri = T(1) / an_sqrt(r2), ri2 = ri * ri;
@@ -117,9 +118,9 @@ __host__ __device__ inline void an_near_block(const T *rho, int nb, T tx, T ty, 
             Sz.add(gz);
         }
     // closed form: voxels [lo, hi] (clipped to the block) around the observer's voxel
-    const int ilo = an_imax(vi - 2, 0), ihi = an_imin(vi + 2, nb - 1);
-    const int jlo = an_imax(vj - 2, 0), jhi = an_imin(vj + 2, nb - 1);
-    const int klo = an_imax(vk - 2, 0), khi = an_imin(vk + 2, nb - 1);
+    const int ilo = an_imax(vi - rad, 0), ihi = an_imin(vi + rad, nb - 1);
+    const int jlo = an_imax(vj - rad, 0), jhi = an_imin(vj + rad, nb - 1);
+    const int klo = an_imax(vk - rad, 0), khi = an_imin(vk + rad, nb - 1);
     for (int K = klo; K <= khi + 1; ++K)
         for (int J = jlo; J <= jhi + 1; ++J) {
             T gx = T(0), gy = T(0), gz = T(0);

@@ -45,7 +45,7 @@ static int near_mode(const char *in, const char *outp) {
         float g32[3];
         double g64[3];
         gf::an_near_block<float>(rf.data(), nb, (float)t[3 * j], (float)t[3 * j + 1], (float)t[3 * j + 2], g32);
-        gf::an_near_block<double>(rho.data(), nb, t[3 * j], t[3 * j + 1], t[3 * j + 2], g64);
+        gf::an_near_block<double>(rho.data(), nb, t[3 * j], t[3 * j + 1], t[3 * j + 2], g64, 3);
         for (int a = 0; a < 3; ++a) {
             out[6 * j + a] = g32[a];
             out[6 * j + 3 + a] = g64[a];

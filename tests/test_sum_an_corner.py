@@ -5,11 +5,12 @@ by nvcc into tests/emu/sum_an_corner_host.cu, against the oracle:
   over a prism's eight corners, gives the prism's closed-form field;
   observers inside and on faces, edges and corners agree to rounding,
   outside the eight-term sum cancels like (d / size)^3;
-* the FMM form's near field (an_near_block: closed form on the 5^3 voxels
-  around the observer's voxel, midpoint plus a cube's l = 4 term beyond)
-  over the 12^3 voxels of a leaf's 27 neighbours (leaves of 4^3 voxels)
-  meets the mixed-precision bar against the oracle's SUM-AN sum of the
-  same voxels, in FP32 and in FP64."""
+* the FMM form's near field (an_near_block: closed form on the voxels
+  within Chebyshev distance 2 (FP32) or 3 (FP64) of the observer's voxel,
+  midpoint plus a cube's l = 4 term beyond) over the 12^3 voxels of a
+  leaf's 27 neighbours (leaves of 4^3 voxels) against the oracle's SUM-AN
+  sum of the same voxels: the mixed-precision bar in FP32, the FP64 FMM
+  bar in FP64."""
 import os
 import shutil
 import subprocess
@@ -74,5 +75,5 @@ def test_near_block_meets_the_mixed_bar(harness, kind):
     subprocess.run([exe, str(d / "near_in.bin"), str(d / "near_out.bin"), "near"], check=True)
     out = np.fromfile(str(d / "near_out.bin")).reshape(-1, 6)
     ref = direct.forward_analytic((nb,) * 3, (0.0,) * 3, (1.0,) * 3, rho, t, 1.0)
-    for g in (out[:, :3], out[:, 3:]):
-        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 5e-6
+    assert np.linalg.norm(out[:, :3] - ref) / np.linalg.norm(ref) <= 5e-6
+    assert np.linalg.norm(out[:, 3:] - ref) / np.linalg.norm(ref) <= 5e-7
