@@ -1,0 +1,118 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake in
+a copy of oracle/gf_oracle.c (a flipped sign, a dropped normalisation, a
+transposed index, a wrong axis, a wrong corner sign, a wrong special axis),
+builds the copy, and checks that a pin which the real oracle passes fails
+on it: the exact-arithmetic brute force, the closed-form prism field the
+quadrature sums must converge to, Table 10's vertical formula, or the axis
+relabelling of that formula."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import direct
+from paper_1107_5951_gb300 import workloads as wl
+from test_oracle_pins import _exact_sum
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "gf_oracle.c")
+_dp = ctypes.POINTER(ctypes.c_double)
+
+MUTATIONS = {
+    "separation_sign": ("const double d0 = r0 - x[0], d1 = r1 - x[1],", "const double d0 = x[0] - r0, d1 = r1 - x[1],"),
+    "weight_not_normalised": ("                            const double wq = w[q] / wsum;",
+                              "                            const double wq = w[q];"),
+    "density_index_transposed": ("const long v = (k * ny + j) * nx + i;\n                        for (int q",
+                                 "const long v = (k * ny + i) * nx + j;\n                        for (int q"),
+    "node_offset_wrong_axis": ("x[0] = c0 + 0.5 * h[0] * xi_q[0];", "x[0] = c0 + 0.5 * h[1] * xi_q[0];"),
+    "prism_corner_sign": ("const double s = ((a + b + c) & 1) ? 1.0 : -1.0;\n                acc += s * prism_corner(u, v, w);",
+                          "const double s = ((a + b) & 1) ? 1.0 : -1.0;\n                acc += s * prism_corner(u, v, w);"),
+    "gx_wrong_special_axis": ("ax += s * prism_corner(v, w, u);", "ax += s * prism_corner(u, w, v);"),
+}
+
+
+def _build(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / (name + ".c")
+    path.write_text(src.replace(old, new))
+    lib = tmp_path / (name + ".so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", str(path),
+                    "-o", str(lib), "-lm"], check=True)
+    L = ctypes.CDLL(str(lib))
+    i64, i32, dbl = ctypes.c_long, ctypes.c_int, ctypes.c_double
+    L.gfo_forward.argtypes = [i64, i64, i64, _dp, _dp, i32, _dp, _dp, _dp, i32, _dp, i64, dbl, _dp, i32]
+    L.gfo_prism_gz_many.argtypes = [_dp, _dp, dbl, dbl, _dp, i64, _dp, i32]
+    L.gfo_prism_g_many.argtypes = [_dp, _dp, dbl, dbl, _dp, i64, _dp, i32]
+    return L
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _forward(L, shape, origin, h, xi, w, rho, obs):
+    nx, ny, nz = shape
+    rho, obs, xi, w = _c(rho), _c(obs).reshape(-1, 3), _c(xi).reshape(-1, 3), _c(w)
+    out = np.zeros((1, obs.shape[0], 3))
+    L.gfo_forward(nx, ny, nz, _p(_c(origin)), _p(_c(h)), xi.shape[0], _p(xi), _p(w), _p(rho), 1, _p(obs),
+                  obs.shape[0], 1.0, _p(out), 1)
+    return out[0]
+
+
+def _pins_fail(L):
+    """True when at least one pin rejects the library L."""
+    # (1) a 2x2x2-Gauss sum over a refined uniform prism must approach the
+    # closed form of the real oracle (fourth order): 8^3 cells, 1e-5
+    lo, hi = np.array([0.0, 0.0, -1.0]), np.array([1.0, 1.0, 0.0])
+    obs = np.array([[1.7, 1.3, 0.8], [-0.6, 0.4, 0.9]])
+    xi, w = wl.gauss_rule(2)
+    s = 8
+    g = _forward(L, (s, s, s), lo, (1.0 / s,) * 3, xi, w, np.ones((s, s, s)), obs)
+    exact = direct.prism_g(lo, hi, 1.0, 1.0, obs)
+    if np.max(np.abs(g - exact)) > 1e-5 * np.max(np.abs(exact)):
+        return True
+    # (2) random densities on an anisotropic grid against the exact-arithmetic
+    # brute force (to a few ulp of the sum of magnitudes)
+    wk = wl.random_small(4, n=(2, 2, 2), npts=2, n_obs=6, h=(0.75, 1.25, 1.0), origin=(-1.0, 0.5, -2.0))
+    g = _forward(L, wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs)
+    exact, mag = _exact_sum(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs)
+    if np.any(np.abs(g - exact) > 4e-16 * mag + 1e-300):
+        return True
+    # (3) the closed-form prism field: its g_z against the Table-10-pinned
+    # formula of the real oracle, g_x against g_z of the relabelled prism
+    a, b = np.array([-0.5, 0.2, -1.0]), np.array([0.7, 1.1, 0.3])
+    pts = np.array([[1.5, 0.4, 2.0], [-2.0, 1.0, -0.5], [0.1, 0.5, -0.2]])
+    gz = np.zeros(3)
+    L.gfo_prism_gz_many(_p(_c(a)), _p(_c(b)), 1.0, 1.0, _p(_c(pts)), 3, _p(gz), 1)
+    if np.max(np.abs(gz - direct.prism_gz(a, b, 1.0, 1.0, pts))) > 1e-13:
+        return True
+    gv = np.zeros((3, 3))
+    L.gfo_prism_g_many(_p(_c(a)), _p(_c(b)), 1.0, 1.0, _p(_c(pts)), 3, _p(gv), 1)
+    perm = [1, 2, 0]
+    gx_rot = direct.prism_gz(a[perm], b[perm], 1.0, 1.0, pts[:, perm])
+    return np.max(np.abs(gv[:, 0] - gx_rot)) > 1e-13
+
+
+@pytest.fixture(scope="module")
+def gcc():
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+
+
+def test_the_real_oracle_passes(gcc, tmp_path):
+    same = MUTATIONS["separation_sign"][0]
+    L = _build(tmp_path, "unchanged", same, same)
+    assert not _pins_fail(L)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_a_planted_mistake_fails_a_pin(gcc, tmp_path, name):
+    old, new = MUTATIONS[name]
+    assert _pins_fail(_build(tmp_path, name, old, new)), name
