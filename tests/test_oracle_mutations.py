@@ -57,12 +57,14 @@ def _p(a):
     return a.ctypes.data_as(_dp)
 
 
+# nthreads = 0 everywhere: the copies share the process's OpenMP runtime, and
+# setting a thread count there would also slow the real oracle in later tests
 def _forward(L, shape, origin, h, xi, w, rho, obs):
     nx, ny, nz = shape
     rho, obs, xi, w = _c(rho), _c(obs).reshape(-1, 3), _c(xi).reshape(-1, 3), _c(w)
     out = np.zeros((1, obs.shape[0], 3))
     L.gfo_forward(nx, ny, nz, _p(_c(origin)), _p(_c(h)), xi.shape[0], _p(xi), _p(w), _p(rho), 1, _p(obs),
-                  obs.shape[0], 1.0, _p(out), 1)
+                  obs.shape[0], 1.0, _p(out), 0)
     return out[0]
 
 
@@ -90,11 +92,11 @@ def _pins_fail(L):
     a, b = np.array([-0.5, 0.2, -1.0]), np.array([0.7, 1.1, 0.3])
     pts = np.array([[1.5, 0.4, 2.0], [-2.0, 1.0, -0.5], [0.1, 0.5, -0.2]])
     gz = np.zeros(3)
-    L.gfo_prism_gz_many(_p(_c(a)), _p(_c(b)), 1.0, 1.0, _p(_c(pts)), 3, _p(gz), 1)
+    L.gfo_prism_gz_many(_p(_c(a)), _p(_c(b)), 1.0, 1.0, _p(_c(pts)), 3, _p(gz), 0)
     if np.max(np.abs(gz - direct.prism_gz(a, b, 1.0, 1.0, pts))) > 1e-13:
         return True
     gv = np.zeros((3, 3))
-    L.gfo_prism_g_many(_p(_c(a)), _p(_c(b)), 1.0, 1.0, _p(_c(pts)), 3, _p(gv), 1)
+    L.gfo_prism_g_many(_p(_c(a)), _p(_c(b)), 1.0, 1.0, _p(_c(pts)), 3, _p(gv), 0)
     perm = [1, 2, 0]
     gx_rot = direct.prism_gz(a[perm], b[perm], 1.0, 1.0, pts[:, perm])
     return np.max(np.abs(gv[:, 0] - gx_rot)) > 1e-13
