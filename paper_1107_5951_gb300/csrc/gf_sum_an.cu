@@ -3,10 +3,11 @@
 // sampled by a quadrature rule.  FP64, direct mode, and its transpose.
 //
 // The field of voxel v (density rho_v) at r is G rho_v sum_c s(v, c) F(c - r)
-// over its eight corners c, F the corner function (gf_sum_an.cuh) and s(v, c) = +1 at
-// the corners reached from the voxel's lower corner through an odd number of
-// upper limits, -1 at the others.  A lattice corner is shared by up to eight
-// voxels, so the sum over voxels is regrouped onto the corner lattice,
+// over its eight corners c, F the corner function of gf_sum_an.cuh and
+// s(v, c) = +1 at the corners reached from the voxel's lower corner through
+// an odd number of upper limits, -1 at the others.  A lattice corner is
+// shared by up to eight voxels, so the sum over voxels is regrouped onto the
+// corner lattice,
 //
 //   g(r) = G sum_c D_c F(c - r),   D_c = sum_{v sharing c} s(v, c) rho_v,
 //
@@ -14,8 +15,6 @@
 // voxel; D_c vanishes inside regions of constant density, and those corners
 // are skipped.  The transpose is regrouped the same way: per corner
 // E_c = sum_j r_j . F(c - x'_j), then grad_v = G sum_{c of v} s(v, c) E_c.
-//
-// The corner function F and its evaluation are in gf_sum_an.cuh.
 //
 // Layout: corners are numbered I + (nx + 1) (J + (ny + 1) K) and sit at
 // origin + (I, J, K) h, rounded as origin + I h.  One thread per observer
