@@ -611,6 +611,10 @@ __device__ __forceinline__ void input_scale(uint32_t mbits, float &sig, float &i
     inv = __int_as_float((127 - sh) << 23);
 }
 
+// Input chunk that an offset processes at step j of its nck steps: the
+// highest chunk first (see the MMA issue order).
+__host__ __device__ __forceinline__ int chunk_of(int nck, int j) { return nck - 1 - j; }
+
 constexpr long kWaitTries = 1l << 24;
 
 __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
@@ -891,17 +895,23 @@ m2l_tc(TcArgs a) {
             for (int it = 0; it < iters; ++it) {
                 if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
                 unsigned char *stage = base + (size_t)s * stage_bytes;
-                int c0 = 0;
+                int c0 = 0, nc = S;
 #pragma unroll
                 for (int q = 0; q < S; ++q) {
                     if (q > 0 && c0 + q >= nck) break;   // the offset's last stage may hold fewer chunks
                     int cc;
                     int64_t sr;
                     take(cc, sr);
-                    if (q == 0) c0 = cc;
+                    if (q == 0) {
+                        c0 = cc;
+                        nc = min(S, nck - c0);
+                    }
+                    // chunks run from the highest inputs down (chunk_of), and the
+                    // stage keeps its chunks in ascending order
+                    const int pc = chunk_of(nck, cc);
                     // the warp's 32 rows in 8 passes of 4: eight lanes copy one
                     // row's 128 contiguous bytes (pieces 0-3 high, 4-7 low)
-                    const uint32_t sub = smem_u32(stage + q * kTcA);
+                    const uint32_t sub = smem_u32(stage + (nc - 1 - q) * kTcA);
                     const int k = lane & 7;
                     const uint32_t kpart = k < 4 ? 0u : 8192u;
                     const int kk = 8 * (k & 3);
@@ -910,7 +920,7 @@ m2l_tc(TcArgs a) {
                         const int rl = 4 * pp + (lane >> 3);
                         const int64_t srp = __shfl_sync(0xffffffffu, (long long)sr, rl);
                         const int r = (row & ~31) + rl;
-                        const unsigned char *src = srp >= 0 ? spl + (size_t)srp * 4 + (size_t)cc * 128 + 16 * k : spl;
+                        const unsigned char *src = srp >= 0 ? spl + (size_t)srp * 4 + (size_t)pc * 128 + 16 * k : spl;
                         cp_async16(sub + kpart + swz64h(r, kk), src, srp >= 0 ? 16u : 0u);
                     }
                 }
@@ -939,7 +949,7 @@ m2l_tc(TcArgs a) {
                 int64_t sr;
                 take(cc, sr);
                 const uint32_t d0 = smem_u32(raw + (size_t)(j % kTcRaw) * 128 * (kW * 4));
-                const float *src = sr >= 0 ? me + sr + kW * cc : me;
+                const float *src = sr >= 0 ? me + sr + kW * chunk_of(nck, cc) : me;
 #pragma unroll
                 for (int q = 0; q < kV; ++q)
                     cp_async16(d0 + ((q ^ (row & (kV - 1))) << 4), src + (sr >= 0 ? 4 * q : 0), sr >= 0 ? 16u : 0u);
@@ -956,7 +966,7 @@ m2l_tc(TcArgs a) {
                 asm volatile("cp.async.commit_group;" ::: "memory");
                 asm volatile("cp.async.wait_group %0;" ::"n"(kTcRaw - 1) : "memory");   // chunk `it` has landed
                 if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
-                const int c0 = it % nck;   // every offset runs all nck chunks, in order
+                const int c0 = chunk_of(nck, it % nck);   // every offset runs all nck chunks, in order
                 float4 cur[kV];
                 {
                     const float4 *rr = reinterpret_cast<const float4 *>(raw + (size_t)(it % kTcRaw) * 128 * (kW * 4));
@@ -1004,24 +1014,33 @@ m2l_tc(TcArgs a) {
                 const unsigned char *stage = base + (size_t)s * stage_bytes;
                 const uint32_t d = tmem + (uint32_t)(g & 1) * 256u;
                 const int nc = min(S, nck - c0);
+                // Inputs in descending order: the stage's chunks from the last
+                // slot down, each chunk's k-steps from the last down, and in each
+                // k-step the two small cross products before the main one.  The
+                // accumulator adds of the tensor cores truncate, so every add made
+                // once the sum has its full size costs up to an ulp of it, all of
+                // the same sign; leading with the small high-order terms leaves
+                // only the last few adds at full size.
                 for (int q = 0; q < nc; ++q) {
-                    const int c = c0 + q;
-                    const uint32_t sa = smem_u32(stage + q * kTcA);
-                    const uint32_t sb = smem_u32(stage + S * kTcA + q * b_bytes);
+                    const int sl = nc - 1 - q;
+                    const int c = chunk_of(nck, c0 + nc - 1) + sl;   // the input chunk in slot sl
+                    const uint32_t sa = smem_u32(stage + sl * kTcA);
+                    const uint32_t sb = smem_u32(stage + S * kTcA + sl * b_bytes);
                     // k-steps of 32 bytes (8 TF32 or 16 FP16 inputs) holding inputs
                     const int nks = H16 ? min(2, (a.kin - 32 * c + 15) / 16) : min(2, (a.kin - 16 * c + 7) / 8);
-                    for (int ks = 0; ks < nks; ++ks) {
+                    for (int ks = nks - 1; ks >= 0; --ks) {
                         const uint32_t ko = ks * 32;
                         const uint64_t ah = umma_desc64(sa + ko), al = umma_desc64(sa + 8192 + ko);
                         const uint64_t bh = umma_desc64(sb + ko), bl = umma_desc64(sb + (uint32_t)Npad * 64 + ko);
+                        const uint32_t acc = (c0 > 0 || q > 0 || ks < nks - 1) ? 1u : 0u;
                         if (H16) {
-                            mma_f16(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                            mma_f16(d, ah, bl, idesc, 1u);
+                            mma_f16(d, ah, bl, idesc, acc);
                             mma_f16(d, al, bh, idesc, 1u);
+                            mma_f16(d, ah, bh, idesc, 1u);
                         } else {
-                            mma_tf32(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                            mma_tf32(d, ah, bl, idesc, 1u);
+                            mma_tf32(d, ah, bl, idesc, acc);
                             mma_tf32(d, al, bh, idesc, 1u);
+                            mma_tf32(d, ah, bh, idesc, 1u);
                         }
                     }
                 }
@@ -1064,10 +1083,12 @@ m2l_tc(TcArgs a) {
                 }
                 unsigned char *stage = base + (size_t)s * stage_bytes;
                 // the stage's chunks of the operator image are contiguous
-                const uint32_t nbytes = (uint32_t)min(S, nck - c0) * b_bytes;
+                // (ascending, the lowest being that of the stage's last chunk)
+                const int ncs = min(S, nck - c0);
+                const uint32_t nbytes = (uint32_t)ncs * b_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&afull[s])),
                              "r"(nbytes));
-                const unsigned char *srcimg = a.img + ((size_t)slot_off * nck + c0) * b_bytes;
+                const unsigned char *srcimg = a.img + ((size_t)slot_off * nck + chunk_of(nck, c0 + ncs - 1)) * b_bytes;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         smem_u32(stage + S * kTcA)),
