@@ -1,15 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the voxel-gravity forward model on one GB300 (or N replicas).
 
-Default workload: 128^3 voxels of 250 m with an exponential-covariance random
-density (correlation length 2 km, sigma 150 kg/m^3), midpoint rule
-(2,097,152 sources), observers = 512^2 surface stations plus every voxel
-centre (2,359,296).  A timed step is one whole pass of the path on resident
-inputs: the plan build (observer Morton keys, sort, box tables, lists) and
-the forward solve (sources, upward sweep, M2L, downward sweep, evaluation,
-near field, near+far combine), then the plan's release.
+Default workload: 464^3 = 99,897,344 voxels of 100 m (FP32 densities), a
+layered 2600/2700/2900 kg/m^3 background with three seeded +-400 kg/m^3
+ellipsoids, midpoint rule, 1024^2 surface stations -- the largest workload of
+the paper's scale (about 1e8 voxels).  A timed step is one whole pass of the
+path on resident inputs: the plan build (observer Morton keys, sort, box
+tables, lists) and the forward solve (sources, upward sweep, M2L, downward
+sweep, evaluation, near field, near+far combine), then the plan's release.
+The mixed-precision FMM runs at a degree whose error against the FP64 oracle
+stays below 1e-6 (relative L2 on a seeded observer sample); the plain FP64 FMM
+and lower degrees are timed beside it on the same GPU.
 
-Metric: effective interactions/s = N_sources * M_observers / step time.
+Metric: effective interactions/s = N_sources * M_observers / step time, and
+ms/solve of the forward with the plan built.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores on a bounded sample of the same workload.
@@ -37,6 +41,12 @@ FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM per clock
 FP64_TFLOPS_NOMINAL = 1.25       # GB300 FP64 (vector and tensor) rate
 FLOPS_PER_PAIR = 20.0            # the paper's count: 5 add, 7 mul, 1 sqrt ~ 20 mul-equivalents
 F16_PER_BF16 = 1.0               # nominal dense FP16 / BF16 tensor rates
+SFU_RSQRT_PER_SM = 16            # reciprocal square roots per SM per clock
+# Throughput probes on a GB300 of this machine (FMA chains and MUFU rsqrt chains,
+# 152 x 8 blocks of 256 threads, CUDA events): the denominators of the
+# near field's secondary fractions.
+FP32_TFLOPS_PROBE = 69.6
+MUFU_RSQRT_PROBE = 4.63e12
 
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture of
@@ -89,7 +99,7 @@ def parse_args():
     ap.add_argument("--stations", type=int, default=0, help="stations per axis (0: the workload's own)")
     ap.add_argument("--mode", default="auto", choices=["auto", "fmm", "direct"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--p", type=int, default=12)
+    ap.add_argument("--p", type=int, default=0, help="expansion degree (0: the workload's default)")
     ap.add_argument("--leaf-vox", type=int, default=0)
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt"])
     ap.add_argument("--sample-obs", type=int, default=8192,
@@ -97,9 +107,11 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "scale", "serving", "adjoint", "sum_an"],
-                    help="volume: 128^3 random field, stations + voxel centres; scale: 464^3 layered "
-                         "model, 1024^2 stations; serving: a stream of uneven requests; adjoint: misfit "
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64 FMM and the lower-degree runs beside the headline")
+    ap.add_argument("--workload", default="scale", choices=["volume", "scale", "serving", "adjoint", "sum_an"],
+                    help="scale (default): 464^3 layered model, 1024^2 stations; volume: 128^3 random "
+                         "field, stations + voxel centres; serving: a stream of uneven requests; adjoint: misfit "
                          "gradients of 16 models at 256^2 stations; sum_an: the 16^3 prism model with "
                          "every voxel integrated in closed form (direct, FP64)")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
@@ -189,11 +201,31 @@ def job_rate(units_per_rank, world, seconds):
 
 
 # ------------------------------------------------------------------ workload
+# Expansion degree per workload: the headline runs the mixed-precision FMM at
+# a degree whose sampled error stays below the metric's 1e-6 with margin, and
+# the plain FP64 FMM beside it at the smallest degree that meets 1e-6.
+DEFAULT_P = {"scale": 11, "volume": 12}
+FP64_P = {"scale": 10, "volume": 14}
+SWEEP_P = (4, 6, 8)
+REL_ERR_BAR = 1e-6
+
+
 def make_workload(args):
     from paper_1107_5951_gb300 import workloads as wl
     if args.workload == "scale":
         return wl.layered_scale(n=args.side or 464, stations=args.stations or 1024)
     return wl.grf_volume(n=args.side or 128, stations=args.stations or 512)
+
+
+def workload_p(args):
+    return args.p if args.p else DEFAULT_P.get(args.workload, 12)
+
+
+def workload_config(wk, world):
+    """The workload as both arms name it (identical dicts)."""
+    return {"workload": wk.name, "N_sources": int(wk.n_sources), "M_observers": int(wk.n_obs),
+            "rel_err_bar": REL_ERR_BAR, "parallelism": "replicas" if world > 1 else "single",
+            "l2_flush": "GPU arm: a 256 MiB buffer is written between timed steps; host arm: n/a"}
 
 
 ORACLE_SAMPLE_PAIRS = 2.0e10     # bounds the oracle's sample to ~15 s on 16 cores
@@ -209,7 +241,8 @@ def oracle_sample(wk, args, seed=17):
 def run_cpu_oracle(wk, idx):
     from oracle import direct
     t0 = time.perf_counter()
-    g = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs[idx], wk.G)
+    rho = np.asarray(wk.rho, dtype=np.float64)
+    g = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, rho, wk.obs[idx], wk.G)
     dt = time.perf_counter() - t0
     return g, dt, direct.max_threads()
 
@@ -218,33 +251,77 @@ def fp32_peak_tflops(peaks):
     return N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def fmm_roofline(stages, info, args, peaks, workload):
-    """Roofline of the stage that dominates the forward: the near-field
-    evaluation (ALU: 20 flops per pair, the paper's count) or the M2L
-    (2 K^2 flops per interaction-list box pair)."""
+def sfu_peak_per_s(peaks):
+    """Reciprocal square roots per second: 16 per SM per clock (SFU)."""
+    return N_SM * SFU_RSQRT_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
+
+
+def level_boxes(info, l):
+    n = 1
+    for a in range(3):
+        n *= int(info.src_hi[l][a]) - int(info.src_lo[l][a]) + 1
+    return n
+
+
+def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4):
+    """Roofline of the kernel that dominates the forward: the near-field
+    evaluation (ALU: 20 flops per pair, the paper's count; its SFU share
+    beside it), the M2L (tensor: 2 K^2 flops per interaction-list box pair),
+    or the HBM-bound P2M / M2M (densities read once and expansions written
+    once; each child expansion read once and each parent written once)."""
     K = int(info.K)
-    tensor = args.precision == "mixed" and args.p <= 15 and args.m2l != "simt"
-    work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P)"),
+    p = workload_p(args)
+    tensor = args.precision == "mixed" and p <= 15 and args.m2l != "simt"
+    fbytes = 4 if args.precision == "mixed" else 8
+    L = int(getattr(info, "L", 0))
+    work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P + combine)"),
             "m2l": ("tensor" if tensor else "alu", 2.0 * K * K * float(info.m2l_pairs),
-                    "m2l_tc (tcgen05 FP16 parts, 3 products, all levels; with the input split)" if tensor
+                    "m2l_tc (tcgen05 FP16 parts, 3 products, all levels)" if tensor
                     else "m2l_simt (all levels)")}
-    dom = max(("eval", "m2l"), key=lambda k: stages.get(k, 0.0))
-    bound, flops, kern = work[dom]
+    if nvox is not None and L >= 2:
+        ns = {l: level_boxes(info, l) for l in range(2, L + 1)}
+        work["p2m"] = ("hbm", float(nvox * rho_bytes + ns[L] * K * fbytes),
+                       "block_rows + m2l_tc P2M kind" if tensor else "p2m_fused")
+        work["m2m"] = ("hbm", float(sum(ns[l] * K * fbytes for l in range(3, L + 1))
+                                    + sum(ns[l] * K * fbytes for l in range(2, L))),
+                       "m2l_tc M2M kind + m2m_kernel (FP64 into level 2)" if tensor else "xlate_simt")
+    dom = max(work, key=lambda k: stages.get(k, 0.0))
+    bound, amount, kern = work[dom]
+    extra = {}
     if bound == "tensor":
-        peak = peaks.get("bf16_tflops", 1870.7) * F16_PER_BF16
+        peak, unit = peaks.get("bf16_tflops", 1870.7) * F16_PER_BF16, "TFLOP/s"
         note = ("FP16 dense = measured BF16 burst x nominal FP16/BF16 (1); the high/low split "
                 "executes 3 MMAs per algorithmic flop")
+        achieved = amount / (stages[dom] * 1e-3) / 1e12
+    elif bound == "hbm":
+        peak, unit = peaks.get("hbm_gbs", 6774.6), "GB/s"
+        note = "measured HBM copy bandwidth"
+        achieved = amount / (stages[dom] * 1e-3) / 1e9
     elif args.precision == "mixed":
-        peak, note = fp32_peak_tflops(peaks), "FP32 SIMT: 152 SM x 128 lanes x 2 x sm_max_mhz"
+        peak, unit = fp32_peak_tflops(peaks), "TFLOP/s"
+        note = "FP32 SIMT: 152 SM x 128 lanes x 2 x sm_max_mhz"
+        achieved = amount / (stages[dom] * 1e-3) / 1e12
+        if dom == "eval":
+            rate = float(info.near_pairs) / (stages[dom] * 1e-3)
+            extra = {"sfu_frac": rate / sfu_peak_per_s(peaks),
+                     "sfu_frac_of_probe": rate / MUFU_RSQRT_PROBE,
+                     "frac_of_fp32_probe": achieved / FP32_TFLOPS_PROBE,
+                     "sfu_source": "one reciprocal square root per pair: 152 SM x 16 per clock x sm_max_mhz; "
+                                   "probe = measured MUFU rsqrt throughput on this GPU (%.3g/s)"
+                                   % MUFU_RSQRT_PROBE}
     else:
-        peak, note = FP64_TFLOPS_NOMINAL, "FP64 nominal 1.25 TFLOP/s"
-    achieved = flops / (stages[dom] * 1e-3) / 1e12
-    traffic = ncu_traffic(dom, workload, args.p, args.precision, args.m2l)
-    return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_source": note,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture "
-                              "(profiles/), per launch" if traffic else None,
-            "algorithmic": "%.4g flops per launch set" % flops, "stage_ms": stages[dom]}
+        peak, unit = FP64_TFLOPS_NOMINAL, "TFLOP/s"
+        note = "FP64 nominal 1.25 TFLOP/s"
+        achieved = amount / (stages[dom] * 1e-3) / 1e12
+    traffic = ncu_traffic(dom, workload, p, args.precision, args.m2l)
+    r = {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
+         "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_source": note,
+         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture "
+                           "(profiles/), per launch set" if traffic else None,
+         "algorithmic": "%.4g %s per launch set" % (amount, "bytes" if bound == "hbm" else "flops"),
+         "stage_ms": stages[dom]}
+    r.update(extra)
+    return r
 
 
 # ------------------------------------------------------------------ reference arm
@@ -255,10 +332,11 @@ def bench_reference(args, rank, world):
     n_src = wk.n_sources
     idx_all = oracle_sample(wk, args)
     # each step evaluates a bounded sample of observers against every source
-    per_step = max(64, len(idx_all) // 4)
+    # (about 2 s of host work per step)
+    per_step = int(max(8, min(len(idx_all), 3.0e9 / n_src)))
     times = []
     for s in range(args.warmup + args.steps):
-        idx = idx_all[(s * per_step) % len(idx_all):][:per_step]
+        idx = np.resize(np.roll(idx_all, -s * per_step), per_step)
         _, dt, cores = run_cpu_oracle(wk, idx)
         if s >= args.warmup:
             times.append((dt, len(idx)))
@@ -270,8 +348,8 @@ def bench_reference(args, rank, world):
             "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wk.name, "N_sources": n_src, "M_observers": wk.n_obs,
-                       "parallelism": "replicas", "l2_flush": "n/a (host)"},
+            "config": workload_config(wk, world),
+            "method": {"impl": "FP64 direct sum on the host cores (the oracle)"},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
@@ -280,6 +358,23 @@ def bench_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+def timed_forwards(plan, rho_d, g_d, stream, flush, reps):
+    """Mean CUDA-event time of `reps` warm forwards on `stream`, L2 flushed
+    before each."""
+    import torch
+    ev = []
+    for k in range(reps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.forward(rho_d, g=g_d, stream=stream)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
 def bench_gf(args, rank, world):
     import torch
 
@@ -292,6 +387,7 @@ def bench_gf(args, rank, world):
     wk = make_workload(args)
     N, M = wk.n_sources, wk.n_obs
     units = float(N) * float(M)
+    p = workload_p(args)
 
     mode = args.mode
     if mode == "auto":
@@ -302,9 +398,9 @@ def bench_gf(args, rank, world):
     rho_d = torch.tensor(wk.rho, dtype=rho_dtype, device=dev)
     g_d = torch.empty((M, 3), dtype=torch.float64, device=dev)
 
-    def make_plan():
-        return pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode=mode,
-                        precision=args.precision, p=args.p, leaf_vox=args.leaf_vox, G=wk.G,
+    def make_plan(precision=args.precision, pp=p, obs=obs_d):
+        return pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs, mode=mode,
+                        precision=precision, p=pp, leaf_vox=args.leaf_vox, G=wk.G,
                         stream=stream, m2l=args.m2l)
 
     try:
@@ -349,47 +445,10 @@ def bench_gf(args, rank, world):
     tot_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     value = job_rate(units * args.steps, world, tot_ms * 1e-3)
 
-    # warm forward with the plan built, and the dominant kernel's duration
+    # warm forward with the plan built; per-stage device times
     plan = make_plan()
-    fwd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        fwd_ev[k][0].record(stream)
-        plan.forward(rho_d, g=g_d, stream=stream)
-        fwd_ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b in fwd_ev]))
-
-    # accuracy on the oracle's sample (rank 0 only)
-    idx = oracle_sample(wk, args)
-    g_host = g_d.cpu().numpy()
-    cpu = None
-    rel_err = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ref, dt, cores = run_cpu_oracle(wk, idx)
-        rel_err = float(np.linalg.norm(g_host[idx] - ref) / np.linalg.norm(ref))
-        cpu = {"value": N * len(idx) / dt, "unit": "interactions/s", "cores": cores, "kind": "oracle",
-               "sample": "%d seeded observers of %d x all %d sources (%.1f s)" % (len(idx), M, N, dt)}
-
-    # roofline of the dominant kernel
-    if mode == "direct":
-        flops = FLOPS_PER_PAIR * units
-        if args.precision == "mixed":
-            peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            peak_note = "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % peaks["_source"]
-        else:
-            peak = FP64_TFLOPS_NOMINAL
-            peak_note = "FP64 nominal 1.25 TFLOP/s"
-        achieved = flops / (fwd_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "direct_fwd_%s" % ("mixed" if args.precision == "mixed" else "f64"),
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_note,
-                "algorithmic": "%.0f flops/pair x N*M pairs" % FLOPS_PER_PAIR}
-    else:
-        roof = None
-    # per-stage device times (CUDA events on the forward's stream)
+    fwd_ms = timed_forwards(plan, rho_d, g_d, stream, flush, args.steps)
+    g_main = g_d.cpu().numpy()
     plan.set_timing(True)
     stage_runs = []
     for k in range(args.steps):
@@ -400,9 +459,62 @@ def bench_gf(args, rank, world):
     plan.set_timing(False)
     stages = {k: float(np.mean([r[k] for r in stage_runs])) for k in stage_runs[0]}
     info = plan.info
-    if mode == "fmm":
-        roof = fmm_roofline(stages, info, args, peaks, wk.name)
     plan.close()
+
+    # the plain FP64 FMM on the same GPU, and the mixed form at lower degrees
+    compare = {}
+    sampled = {}
+    if mode == "fmm" and not args.no_compare:
+        rho64 = rho_d.double() if args.precision == "mixed" else rho_d
+        pf = FP64_P.get(args.workload, 14)
+        with make_plan("fp64", pf) as pl:
+            pl.forward(rho64, g=g_d, stream=stream)
+            ms = timed_forwards(pl, rho64, g_d, stream, flush, 2)
+            sampled["fp64_fmm"] = g_d.cpu().numpy()
+        compare["fp64_fmm"] = {"precision": "fp64", "p": pf, "ms_per_solve": ms,
+                               "value": units / (ms * 1e-3), "unit": "interactions/s"}
+        del rho64
+        if args.precision == "mixed":
+            for ps in SWEEP_P:
+                with make_plan("mixed", ps) as pl:
+                    pl.forward(rho_d, g=g_d, stream=stream)
+                    ms = timed_forwards(pl, rho_d, g_d, stream, flush, max(3, args.steps // 4))
+                    sampled["p%d" % ps] = g_d.cpu().numpy()
+                compare["mixed_p%d" % ps] = {"precision": "mixed", "p": ps, "ms_per_solve": ms,
+                                             "value": units / (ms * 1e-3), "unit": "interactions/s"}
+        compare["mixed_over_fp64"] = compare["fp64_fmm"]["ms_per_solve"] / fwd_ms
+
+    # accuracy on the oracle's sample (rank 0 only)
+    idx = oracle_sample(wk, args)
+    cpu = None
+    rel_err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ref, dt, cores = run_cpu_oracle(wk, idx)
+        nref = np.linalg.norm(ref)
+        rel_err = float(np.linalg.norm(g_main[idx] - ref) / nref)
+        for key, gs in sampled.items():
+            ck = "fp64_fmm" if key == "fp64_fmm" else "mixed_" + key
+            compare[ck]["rel_err_vs_oracle_sample"] = float(np.linalg.norm(gs[idx] - ref) / nref)
+        cpu = {"value": N * len(idx) / dt, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+               "sample": "%d seeded observers of %d x all %d sources (%.1f s)" % (len(idx), M, N, dt)}
+
+    # roofline of the dominant kernel
+    if mode == "direct":
+        flops = FLOPS_PER_PAIR * units
+        if args.precision == "mixed":
+            peak = fp32_peak_tflops(peaks)
+            peak_note = "FP32 SIMT: 152 SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % peaks["_source"]
+        else:
+            peak = FP64_TFLOPS_NOMINAL
+            peak_note = "FP64 nominal 1.25 TFLOP/s"
+        achieved = flops / (fwd_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "direct_fwd_%s" % ("mixed" if args.precision == "mixed" else "f64"),
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_note,
+                "algorithmic": "%.0f flops/pair x N*M pairs" % FLOPS_PER_PAIR}
+    else:
+        roof = fmm_roofline(stages, info, args, peaks, wk.name, nvox=wk.grid.nvox,
+                            rho_bytes=4 if args.precision == "mixed" else 8)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -421,9 +533,7 @@ def bench_gf(args, rank, world):
             with torch.cuda.stream(stream):
                 obs_e.copy_(obs_h, non_blocking=True)
                 rho_e.copy_(rho_h, non_blocking=True)
-                pl = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_e, mode=mode,
-                              precision=args.precision, p=args.p, leaf_vox=args.leaf_vox, G=wk.G,
-                              stream=stream, m2l=args.m2l)
+                pl = make_plan(obs=obs_e)
                 pl.forward(rho_e, g=g_d, stream=stream)
                 g_h.copy_(g_d, non_blocking=True)
                 pl.close()
@@ -443,14 +553,17 @@ def bench_gf(args, rank, world):
             "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": wk.name, "mode": mode, "precision": args.precision,
-                       "p": args.p if mode == "fmm" else None, "m2l": args.m2l,
+            "config": workload_config(wk, world),
+            "method": {"mode": mode, "precision": args.precision, "p": p if mode == "fmm" else None,
+                       "m2l": args.m2l,
                        "leaf_vox": int(plan_info.leaf_vox) if mode == "fmm" else None,
-                       "N_sources": N, "M_observers": M, "parallelism": "replicas" if world > 1 else "single",
-                       "l2_flush": "256 MiB buffer written between timed steps",
+                       "levels": int(plan_info.L) if mode == "fmm" else None,
                        "step": "plan build + forward + release"},
-            "ms_per_solve": fwd_ms, "rel_err_vs_oracle_sample": rel_err, "stages_ms": stages,
+            "ms_per_solve": fwd_ms, "rel_err_vs_oracle_sample": rel_err,
+            "meets_rel_err_bar": None if rel_err is None else bool(rel_err <= REL_ERR_BAR),
+            "stages_ms": stages,
             "work": {"near_pairs": int(info.near_pairs), "m2l_box_pairs": int(info.m2l_pairs)},
+            "compare": compare or None,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
@@ -480,7 +593,7 @@ def bench_adjoint(args, rank, world):
     rdt = torch.float32 if args.precision == "mixed" else torch.float64
     models = torch.tensor(wk.rho, dtype=rdt, device=dev)
     plan = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode="fmm",
-                    precision=args.precision, p=args.p, max_batch=B, G=wk.G, stream=stream)
+                    precision=args.precision, p=workload_p(args), max_batch=B, G=wk.G, stream=stream)
     hidden = torch.tensor(wk.extra["hidden"], dtype=rdt, device=dev)
     _, d = plan.forward(hidden, want_g=False, want_gz=True, stream=stream)
     gz = torch.empty((B, M), dtype=torch.float64, device=dev)
@@ -535,7 +648,7 @@ def bench_adjoint(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": wk.name, "precision": args.precision, "p": args.p, "batch": B,
+            "config": {"workload": wk.name, "precision": args.precision, "p": workload_p(args), "batch": B,
                        "N_sources": N, "M_observers": M,
                        "l2_flush": "256 MiB buffer written between timed steps",
                        "step": "forward of 16 models + residual + adjoint of 16 residuals"},
@@ -647,7 +760,7 @@ def bench_serving(args, rank, world):
         pool_np[offs[i]:offs[i + 1]] = wl.serving_density(r, field).ravel()
     M = reqs[0]["obs"].shape[0]
     gz_pool = torch.empty((len(reqs), M), dtype=torch.float64, pin_memory=True)
-    srv = pkg.Server(slots=args.slots, precision=args.precision, p=args.p, use_graphs=True,
+    srv = pkg.Server(slots=args.slots, precision=args.precision, p=workload_p(args), use_graphs=True,
                      device=local_rank)
     xi, w = wl.gauss_rule(1)
     for r in reqs:
@@ -737,7 +850,7 @@ def bench_serving(args, rank, world):
             "ms_per_step": 1e3 * sum(pass_s) / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": "serving_stream_%d_req_n32-%d_256^2_stations" % (len(reqs), nmax),
-                       "precision": args.precision, "p": args.p, "slots": args.slots,
+                       "precision": args.precision, "p": workload_p(args), "slots": args.slots,
                        "step": "one pass of the whole stream, submitted at once",
                        "l2_flush": "inputs larger than L2 (%.1f GB of densities per pass)" % (h2d / 1e9)},
             "interactions_per_s": units * sat_rate * world / len(reqs),

@@ -314,11 +314,13 @@ gf_status gf_plan_export_tree(gf_plan_t plan, int32_t level, int32_t *perm_host,
  * gf_forward records CUDA events between its stages on its stream;
  * gf_plan_stage_times waits for the last forward and returns the device
  * time of each stage in milliseconds:
- *   [0] leaf-blocked densities  [1] P2M  [2] M2M  [3] M2L  [4] L2L
- *   [5] evaluation (near field + L2P + combine)  [6] whole forward
- * (direct mode: only [5] and [6]).  Timing must be off while a forward is
+ *   [0] leaf-blocked densities  [1] P2M  [2] M2M
+ *   [3] M2L input split (mixed precision: scaled FP16 parts of every level's
+ *       multipole expansions)  [4] M2L  [5] L2L
+ *   [6] evaluation (near field + L2P + combine)  [7] whole forward
+ * (direct mode: only [6] and [7]).  Timing must be off while a forward is
  * captured in a CUDA graph. */
-#define GF_NUM_STAGES 7
+#define GF_NUM_STAGES 8
 gf_status gf_plan_set_timing(gf_plan_t plan, int32_t enable);
 gf_status gf_plan_stage_times(gf_plan_t plan, double *ms);
 

@@ -305,7 +305,7 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int
             GF_TRY(sum_an_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
         else
             GF_TRY(direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
-        stage_mark(plan, 6, st);
+        stage_mark(plan, 7, st);
         return GF_OK;
     }
     return fmm_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st);

@@ -1391,8 +1391,8 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     stage_mark(plan, 3, st);
     // a5/a6: M2L at every level (each overwrites its level's LE), then the
     // L2L chain from level 3 down, which adds each finished parent LE.
-    GF_TRY(m2l_run<T>(plan, B, false, st));
-    stage_mark(plan, 4, st);
+    GF_TRY(m2l_run<T>(plan, B, false, st));   // marks the end of the input split (4)
+    stage_mark(plan, 5, st);
     for (int l = 3; l <= L; ++l) {
         const FmmLevel &lv = F->lev[l];
         if (lv.nt == 0) continue;
@@ -1411,7 +1411,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
             GF_TRY((translate_run<T, T>(plan, l, 1, B, st)));
         }
     }
-    stage_mark(plan, 5, st);
+    stage_mark(plan, 6, st);
     // a7-a9: near field + L2P + combine + scatter
     if (F->n_items > 0) {
         EvalArgs a;
@@ -1452,7 +1452,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         }
         GF_KERNEL_DONE();
     }
-    stage_mark(plan, 6, st);
+    stage_mark(plan, 7, st);
     return GF_OK;
 }
 

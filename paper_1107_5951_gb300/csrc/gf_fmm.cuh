@@ -23,6 +23,10 @@ struct FmmLevel {
     int32_t *tparent = nullptr;   // [nt] index of the parent box at level-1
     int32_t *m2l_order = nullptr; // [nt] observer boxes grouped by parity class
     int64_t cls_off[9] = {0};     // class c: m2l_order[cls_off[c] .. cls_off[c+1])
+    // z-slabs [m2l_z0, m2l_z1] of the source block (relative to slo[2]) that
+    // an interaction list of this level's observer boxes can reach: the
+    // only multipole expansions the forward M2L reads (empty when z0 > z1)
+    int64_t m2l_z0 = 0, m2l_z1 = -1;
     void *me = nullptr;           // [ns][B][KS]
     void *le = nullptr;           // [nt][B][KS]
 };

@@ -1492,9 +1492,20 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
         m.ld4 = F->KS / 4;
         m.kin = F->K;
         int64_t most = 0;
+        // forward: only the z-slabs of each level's source block that an
+        // interaction list reaches (rows run x fastest, then y, then z)
+        int64_t row0[kMaxLevels + 1] = {};
         for (int l = 2; l <= F->L; ++l) {
-            m.in[l] = (const float4 *)(adj ? F->lev[l].le : F->lev[l].me);
-            m.rows[l] = (adj ? F->lev[l].nt : F->lev[l].ns) * B;
+            const FmmLevel &lv = F->lev[l];
+            int64_t r0 = 0, nr = (adj ? lv.nt : lv.ns) * B;
+            if (!adj) {
+                const int64_t slab = lv.sn[0] * lv.sn[1] * B;
+                r0 = lv.m2l_z1 >= lv.m2l_z0 ? lv.m2l_z0 * slab : 0;
+                nr = lv.m2l_z1 >= lv.m2l_z0 ? (lv.m2l_z1 - lv.m2l_z0 + 1) * slab : 0;
+            }
+            row0[l] = r0;
+            m.in[l] = (const float4 *)(adj ? lv.le : lv.me) + r0 * m.ld4;
+            m.rows[l] = nr;
             most = std::max(most, m.rows[l] * m.ld4);
         }
         GF_CUDA(cudaMemsetAsync(m.out, 0, (kMaxLevels + 1) * sizeof(uint32_t), st));
@@ -1503,10 +1514,12 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
         GF_KERNEL_DONE();
         SplitArgs o;
         memset(&o, 0, sizeof(o));
-        for (int l = 2; l <= F->L; ++l) o.out[l] = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l);
+        for (int l = 2; l <= F->L; ++l)
+            o.out[l] = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l) + (size_t)row0[l] * F->KS * 4;
         input_split<<<dim3(gx, F->L - 1), 256, 0, st>>>(m, o, T->tc_nck_h);
         GF_KERNEL_DONE();
     }
+    if (!adj) stage_mark(plan, 4, st);
     const int nbox = 128 / B;
     int tiles = 0, e = 0;
     for (int l = 2; l <= F->L; ++l)
@@ -1732,6 +1745,7 @@ gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
                     !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
                     tc_stages(F->tab->tc_npad, true) >= 2;
     if (tc) return m2l_run_tc(plan, B, adj, st);
+    if (!adj) stage_mark(plan, 4, st);   // no input split on this path
     for (int l = 2; l <= F->L; ++l) {
         if (F->lev[l].nt == 0 && !adj) continue;   // the adjoint writes every source box
         GF_TRY(m2l_level<T>(plan, l, B, adj, st));

@@ -405,6 +405,7 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
 
     // ---- root geometry: observers' bounding box joined with the grid
     double bb[6];
+    double obs_zlo = 0.0, obs_zhi = 0.0;
     for (int a = 0; a < 3; ++a) {
         bb[a] = gr.origin[a];
         bb[3 + a] = gr.origin[a] + gr.n[a] * F->h;
@@ -424,6 +425,8 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
             bb[a] = std::min(bb[a], ob[a]);
             bb[3 + a] = std::max(bb[3 + a], ob[3 + a]);
         }
+        obs_zlo = ob[2];
+        obs_zhi = ob[5];
     }
     int64_t need = 1;
     for (int a = 0; a < 3; ++a) {
@@ -432,6 +435,11 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
         F->lo[a] = gr.origin[a] - (double)F->voff[a] * F->h;
         const double ext = ceil((bb[3 + a] - F->lo[a]) / F->h);
         need = std::max<int64_t>(need, std::max<int64_t>(F->voff[a] + gr.n[a], (int64_t)ext));
+    }
+    double oz[2] = {bb[2], bb[5]};   // observers' z extent (the grid's when M = 0)
+    if (M > 0) {
+        oz[0] = obs_zlo;
+        oz[1] = obs_zhi;
     }
     int L = 2;
     while (((int64_t)F->b << L) < need) ++L;
@@ -452,6 +460,20 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
             lv.slo[a] = lo;
             lv.sn[a] = hi - lo + 1;
             lv.ns *= lv.sn[a];
+        }
+    }
+    {
+        // Source z-slabs the M2L of each level reads: observer boxes lie in
+        // the leaf z-range of the observers' extent (widened by one leaf
+        // against rounding at box faces), and interaction-list offsets reach
+        // three boxes along each axis.
+        const int64_t top = ((int64_t)1 << L) - 1;
+        const int64_t iz0 = std::max<int64_t>(0, (int64_t)floor((oz[0] - F->lo[2]) * F->inv_s) - 1);
+        const int64_t iz1 = std::min<int64_t>(top, (int64_t)floor((oz[1] - F->lo[2]) * F->inv_s) + 1);
+        for (int l = 2; l <= L; ++l) {
+            FmmLevel &lv = F->lev[l];
+            lv.m2l_z0 = std::max<int64_t>(0, (iz0 >> (L - l)) - 3 - lv.slo[2]);
+            lv.m2l_z1 = std::min<int64_t>(lv.sn[2] - 1, (iz1 >> (L - l)) + 3 - lv.slo[2]);
         }
     }
     Geo g;

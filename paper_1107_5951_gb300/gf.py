@@ -84,8 +84,8 @@ class gf_server_stats(ctypes.Structure):
                 ("mean_ms", ctypes.c_double), ("busy_s", ctypes.c_double)]
 
 
-GF_NUM_STAGES = 7
-STAGE_NAMES = ("densities", "p2m", "m2m", "m2l", "l2l", "eval", "forward")
+GF_NUM_STAGES = 8
+STAGE_NAMES = ("densities", "p2m", "m2m", "m2l_split", "m2l", "l2l", "eval", "forward")
 
 
 _lib = None

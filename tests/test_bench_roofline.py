@@ -63,6 +63,46 @@ def test_traffic_dropped_when_the_source_changes(monkeypatch):
     assert bench.fmm_roofline({"eval": 1.3, "m2l": 1.0}, INFO, args(), PEAKS, WORKLOAD)["traffic"] is None
 
 
+def test_evaluation_reports_its_sfu_share():
+    """One reciprocal square root per near pair: the SFU fraction against
+    152 SMs x 16 per clock, and against the measured MUFU probe."""
+    r = bench.fmm_roofline({"eval": 1.30, "m2l": 1.25}, INFO, args(), PEAKS, WORKLOAD)
+    rate = INFO.near_pairs / 1.30e-3
+    assert r["sfu_frac"] == pytest.approx(rate / (152 * 16 * 2070e6))
+    assert r["sfu_frac_of_probe"] == pytest.approx(rate / bench.MUFU_RSQRT_PROBE)
+
+
+def scale_info():
+    """A 7-level tree over a 116^3 block of leaves (464^3 voxels, 4^3 per
+    leaf): the source block of level l spans ceil(116 / 2^(7-l)) boxes."""
+    L = 7
+    lo = [[0, 0, 0] for _ in range(24)]
+    hi = [[0, 0, 0] for _ in range(24)]
+    for l in range(2, L + 1):
+        n = -(-116 // (1 << (L - l)))
+        hi[l] = [n - 1] * 3
+    return SimpleNamespace(K=144, L=L, near_pairs=596922624, m2l_pairs=1125279, src_lo=lo, src_hi=hi)
+
+
+def test_hbm_bound_upward_sweep_dominant():
+    """When the P2M (or M2M) stage dominates, the roofline is HBM-bound:
+    densities read once plus leaf expansions written once (children read once
+    plus parents written once), in GB/s against the measured copy rate."""
+    info = scale_info()
+    peaks = dict(PEAKS, hbm_gbs=6700.0)
+    r = bench.fmm_roofline({"eval": 0.4, "m2l": 0.5, "p2m": 0.8, "m2m": 0.7}, info, args(p=11), peaks,
+                           "layered_scale_464^3", nvox=464 ** 3, rho_bytes=4)
+    assert r["stage"] == "p2m" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    want = 464 ** 3 * 4 + 116 ** 3 * 144 * 4
+    assert r["achieved"] == pytest.approx(want / 0.8e-3 / 1e9)
+    assert r["peak"] == 6700.0 and r["frac"] == pytest.approx(r["achieved"] / 6700.0)
+    r = bench.fmm_roofline({"eval": 0.4, "m2l": 0.5, "p2m": 0.6, "m2m": 0.7}, info, args(p=11), peaks,
+                           "layered_scale_464^3", nvox=464 ** 3, rho_bytes=4)
+    ns = {l: (-(-116 // (1 << (7 - l)))) ** 3 for l in range(2, 8)}
+    want = sum(ns[l] for l in range(3, 8)) * 144 * 4 + sum(ns[l] for l in range(2, 7)) * 144 * 4
+    assert r["stage"] == "m2m" and r["achieved"] == pytest.approx(want / 0.7e-3 / 1e9)
+
+
 def test_plain_fp64_path_against_the_fp64_rate():
     r = bench.fmm_roofline({"eval": 20.0, "m2l": 989.0}, INFO, args("fp64", 14, "auto"), PEAKS, WORKLOAD)
     assert r["stage"] == "m2l" and r["bound"] == "alu"
