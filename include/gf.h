@@ -89,8 +89,17 @@ enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
  *                     closed form (SUM-AN of Sec. 2.1, the exact field of
  *                     the piecewise-constant density, finite on voxel faces,
  *                     edges and corners) instead of sampled by the quadrature
- *                     rule; the rule is then ignored. */
-enum { GF_FLAG_M2L_SIMT = 1, GF_FLAG_SUM_AN = 2 };
+ *                     rule; the rule is then ignored.
+ *   GF_FLAG_TEST_WAIT_TIMEOUT
+ *                     testing aid for the failure path of the bounded device
+ *                     waits (FMM, mixed precision, tensor-core M2L): the
+ *                     M2L's MMA issuer first waits, with a short bound, on a
+ *                     barrier that nothing completes; the wait runs out, the
+ *                     kernel's roles stop, wait for their copies in flight,
+ *                     free their tensor memory and return, and the next
+ *                     gf_plan_check reports GF_ERR_DEVICE_CHECK (the
+ *                     forward's output is then not valid). */
+enum { GF_FLAG_M2L_SIMT = 1, GF_FLAG_SUM_AN = 2, GF_FLAG_TEST_WAIT_TIMEOUT = 4 };
 
 typedef struct {
     int32_t mode;        /* GF_MODE_DIRECT or GF_MODE_FMM                  */

@@ -141,7 +141,7 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
         set_error("opt.G must be finite and >= 0 (0 selects 6.67428e-11)");
         return GF_ERR_INVALID_ARG;
     }
-    if (opt->reserved0 & ~(GF_FLAG_M2L_SIMT | GF_FLAG_SUM_AN)) {
+    if (opt->reserved0 & ~(GF_FLAG_M2L_SIMT | GF_FLAG_SUM_AN | GF_FLAG_TEST_WAIT_TIMEOUT)) {
         set_error("opt.reserved0 = %d holds unknown flags", opt->reserved0);
         return GF_ERR_INVALID_ARG;
     }

@@ -10,6 +10,7 @@
 // decisions (r == x) are exact.  Mixed path: coordinates are carried as
 // integer voxel index plus an FP32 fraction, so the separation of near pairs
 // is formed to FP32 relative accuracy whatever the size of the domain.
+#include <cuda.h>
 #include <math.h>
 #include <string.h>
 
@@ -66,7 +67,7 @@ __device__ __forceinline__ double node_coord(double o, double h, int64_t i, doub
 __global__ void __launch_bounds__(kTile)
 direct_fwd_f64(const double *__restrict__ obs, int64_t M, const void *__restrict__ rho,
                int rho_f32, GridArgs ga, const QuadRule *__restrict__ qr, double G,
-               double *__restrict__ g, double *__restrict__ gz) {
+               double *__restrict__ g, double *__restrict__ gz, int *__restrict__ status) {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
     const int b = blockIdx.y;
     const int64_t j = (int64_t)blockIdx.x * kTile + threadIdx.x;
@@ -79,6 +80,7 @@ direct_fwd_f64(const double *__restrict__ obs, int64_t M, const void *__restrict
     const void *rho_b = rho_f32 ? (const void *)((const float *)rho + b * ga.nvox)
                                 : (const void *)((const double *)rho + b * ga.nvox);
     double s0 = 0, c0 = 0, s1 = 0, c1 = 0, s2 = 0, c2 = 0;
+    bool bad = false;   // a non-finite density (reported through status[0])
     for (int64_t t0 = 0; t0 < N; t0 += kTile) {
         const int64_t s = t0 + threadIdx.x;
         __syncthreads();
@@ -89,7 +91,9 @@ direct_fwd_f64(const double *__restrict__ obs, int64_t M, const void *__restrict
             sx[threadIdx.x] = node_coord(ga.ox, ga.hx, i, qr->xi[q][0]);
             sy[threadIdx.x] = node_coord(ga.oy, ga.hy, jj, qr->xi[q][1]);
             sz[threadIdx.x] = node_coord(ga.oz, ga.hz, k, qr->xi[q][2]);
-            sm[threadIdx.x] = __dmul_rn(__dmul_rn(load_rho(rho_b, rho_f32, v), ga.vol), qr->wn[q]);
+            const double rv = load_rho(rho_b, rho_f32, v);
+            bad |= !isfinite(rv);
+            sm[threadIdx.x] = __dmul_rn(__dmul_rn(rv, ga.vol), qr->wn[q]);
         } else {
             sx[threadIdx.x] = 0.0;
             sy[threadIdx.x] = 0.0;
@@ -113,6 +117,7 @@ direct_fwd_f64(const double *__restrict__ obs, int64_t M, const void *__restrict
         neumaier(s1, c1, py);
         neumaier(s2, c2, pz);
     }
+    if (bad && status && blockIdx.x == 0) atomicOr(status, 1);
     if (active) {
         const double vx = G * (s0 + c0), vy = G * (s1 + c1), vz = G * (s2 + c2);
         if (g) {
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(kTile)
 direct_fwd_mixed(const float *__restrict__ obs_i, const float *__restrict__ obs_f, int64_t M,
                  const void *__restrict__ rho, int rho_f32, GridArgs ga,
                  const QuadRule *__restrict__ qr, double G, double *__restrict__ g,
-                 double *__restrict__ gz) {
+                 double *__restrict__ gz, int *__restrict__ status) {
     __shared__ float si[kTile][3], sf[kTile][3], sm[kTile];
     const int b = blockIdx.y;
     const int64_t j = (int64_t)blockIdx.x * kTile + threadIdx.x;
@@ -150,6 +155,7 @@ direct_fwd_mixed(const float *__restrict__ obs_i, const float *__restrict__ obs_
     const void *rho_b = rho_f32 ? (const void *)((const float *)rho + b * ga.nvox)
                                 : (const void *)((const double *)rho + b * ga.nvox);
     double ax = 0, ay = 0, az = 0;
+    bool bad = false;   // a non-finite density (reported through status[0])
     for (int64_t t0 = 0; t0 < N; t0 += kTile) {
         const int64_t s = t0 + threadIdx.x;
         __syncthreads();
@@ -162,7 +168,9 @@ direct_fwd_mixed(const float *__restrict__ obs_i, const float *__restrict__ obs_
             sf[threadIdx.x][0] = qr->offf[q][0];
             sf[threadIdx.x][1] = qr->offf[q][1];
             sf[threadIdx.x][2] = qr->offf[q][2];
-            sm[threadIdx.x] = (float)(load_rho(rho_b, rho_f32, v) * ga.vol * qr->wn[q]);
+            const double rv = load_rho(rho_b, rho_f32, v);
+            bad |= !isfinite(rv);
+            sm[threadIdx.x] = (float)(rv * ga.vol * qr->wn[q]);
         } else {
             si[threadIdx.x][0] = si[threadIdx.x][1] = si[threadIdx.x][2] = 0.f;
             sf[threadIdx.x][0] = sf[threadIdx.x][1] = sf[threadIdx.x][2] = 0.f;
@@ -187,6 +195,7 @@ direct_fwd_mixed(const float *__restrict__ obs_i, const float *__restrict__ obs_
         ay += (double)py;
         az += (double)pz;
     }
+    if (bad && status && blockIdx.x == 0) atomicOr(status, 1);
     if (active) {
         const double vx = G * ax, vy = G * ay, vz = G * az;
         if (g) {
@@ -303,11 +312,11 @@ gf_status direct_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
     const int f32 = rho_dtype == GF_DTYPE_F32;
     if (plan->opt.precision == GF_PREC_FP64) {
         direct_fwd_f64<<<grid, kTile, 0, st>>>(plan->d_obs, M, rho, f32, ga, quad_device(plan),
-                                               plan->G, g, gz);
+                                               plan->G, g, gz, plan->d_status);
     } else {
         direct_fwd_mixed<<<grid, kTile, 0, st>>>(reinterpret_cast<const float *>(plan->d_obs_ivox),
                                                  plan->d_obs_fvox, M, rho, f32, ga,
-                                                 quad_device(plan), plan->G, g, gz);
+                                                 quad_device(plan), plan->G, g, gz, plan->d_status);
     }
     GF_KERNEL_DONE();
     return GF_OK;
@@ -350,10 +359,12 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 std::mutex g_static_mu;
 void *g_static_addr[256] = {};
+CUcontext g_static_ctx[256] = {};
 
 // Device address of the scratch array on the current device.  The host
 // symbol is only a stand-in, so the address is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached with the context it belongs to; a
+// new context on the device (after cudaDeviceReset, say) looks it up again.
 gf_status static_scratch_address(void **out) {
     int dev = 0;
     GF_CUDA(cudaGetDevice(&dev));
@@ -362,17 +373,42 @@ gf_status static_scratch_address(void **out) {
         return GF_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
+    // the driver's cuCtxGetCurrent, found through the runtime (the library
+    // does not link the driver library)
+    typedef CUresult (*CtxGetCurrent)(CUcontext *);
+    static CtxGetCurrent ctx_get = nullptr;
+    if (!ctx_get) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            set_error("cannot find the driver's cuCtxGetCurrent");
+            return GF_ERR_CUDA;
+        }
+        ctx_get = reinterpret_cast<CtxGetCurrent>(fn);
+    }
+    CUcontext ctx = nullptr;
+    if (ctx_get(&ctx) != CUDA_SUCCESS) ctx = nullptr;   // none yet: the lookup makes one
+    if (!ctx || !g_static_addr[dev] || g_static_ctx[dev] != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
             set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
             return GF_ERR_CUDA;
         }
+        if (ctx_get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
         g_static_addr[dev] = p;
+        g_static_ctx[dev] = ctx;
     }
     *out = g_static_addr[dev];
     return GF_OK;
+}
+
+// Writes the quadrature rule, passed by value, into the scratch array.
+__global__ void store_quad_rule(QuadRule qr, QuadRule *__restrict__ dst) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&qr);
+    uint32_t *out = reinterpret_cast<uint32_t *>(dst);
+    for (size_t i = threadIdx.x; i < sizeof(QuadRule) / 4; i += blockDim.x) out[i] = src[i];
 }
 
 }  // namespace
@@ -463,13 +499,16 @@ extern "C" gf_status gf_direct_forward_static(const gf_grid *grid, const gf_quad
     ga.hz = grid->h[2];
     ga.vol = ga.hx * ga.hy * ga.hz;
     // every byte the kernels read is rewritten here, so nothing left by an
-    // earlier call is used and nothing needs clearing
-    GF_CUDA(cudaMemcpyAsync(d_qr, &qr, sizeof(QuadRule), cudaMemcpyHostToDevice, st));
+    // earlier call is used and nothing needs clearing; the rule travels as a
+    // kernel argument (no host memory is read once this call returns)
+    store_quad_rule<<<1, 256, 0, st>>>(qr, d_qr);
+    GF_KERNEL_DONE();
     split_voxel_coords<<<ceil_div(M, 256), 256, 0, st>>>(obs_dev, M, ga, oi, of);
     GF_KERNEL_DONE();
     direct_fwd_mixed<<<dim3(ceil_div(M, kTile), B), kTile, 0, st>>>(oi, of, M, rho_dev,
                                                                      rho_dtype == GF_DTYPE_F32, ga, d_qr,
-                                                                     G > 0.0 ? G : 6.67428e-11, g_dev, gz_dev);
+                                                                     G > 0.0 ? G : 6.67428e-11, g_dev, gz_dev,
+                                                                     nullptr);
     GF_KERNEL_DONE();
     return GF_OK;
 }

@@ -118,6 +118,22 @@ __global__ void build_p2m(int p, int K, int b, const QuadRule *__restrict__ qr, 
     }
 }
 
+// P2M into the parent level: Q[o][v][k] = sum_i P[v][i] T_o[i][k] for the
+// 8 child positions o (T_o the M2M operator, input component major), i.e.
+// the parent expansion contributed by unit mass at voxel v of child o.
+// Grid (8, b3), one thread per output component.
+__global__ void compose_p2m_up(const double *__restrict__ P, const double *__restrict__ m2m, int K, int b3,
+                               double *__restrict__ Q) {
+    const int o = blockIdx.x, v = blockIdx.y;
+    const double *pv = P + (size_t)v * K;
+    const double *T = m2m + (size_t)o * K * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < K; ++i) s += pv[i] * T[(size_t)i * K + k];
+        Q[((size_t)o * b3 + v) * K + k] = s;
+    }
+}
+
 // ---------------------------------------------------------------- sources
 struct Block3 {
     int64_t lo[3], n[3];
@@ -354,14 +370,14 @@ gf_status launch_p2m_fused_b(gf_plan_s *plan, const void *rho, int rho_f32, int 
 template <class T, int BV>
 __global__ void __launch_bounds__(128)
 block_rows(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, int64_t nz, int64_t vx, int64_t vy,
-           int64_t vz, Block3 blk, int B, T *__restrict__ mass, int *__restrict__ status) {
+           int64_t vz, Block3 blk, int64_t lz0, int64_t nlz, int B, T *__restrict__ mass, int *__restrict__ status) {
     constexpr int b3 = BV * BV * BV;
     const int64_t lx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (lx >= blk.n[0]) return;
     const int yv = blockIdx.y;
     const int64_t zb = blockIdx.z;
-    const int64_t nzv = blk.n[2] * BV;
-    const int zv = (int)(zb % nzv);
+    const int64_t nzv = nlz * BV;
+    const int zv = (int)(lz0 * BV + zb % nzv);   // voxel layer within the block
     const int bb = (int)(zb / nzv);
     const int64_t j = blk.lo[1] * BV + yv - vy, k = blk.lo[2] * BV + zv - vz;
     const int64_t i0 = (blk.lo[0] + lx) * BV - vx;
@@ -393,17 +409,19 @@ block_rows(const void *__restrict__ rho, int rho_f32, int64_t nx, int64_t ny, in
 }
 
 template <class T, int BV>
-gf_status launch_blocking(gf_plan_s *plan, const void *rho, int rho_f32, int B, cudaStream_t st) {
+gf_status launch_blocking(gf_plan_s *plan, const void *rho, int rho_f32, int B, int64_t lz0, int64_t nlz,
+                          cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     const Block3 blk = block_of(F->lev[F->L]);
-    const int64_t gz = blk.n[2] * BV * B;
+    if (nlz <= 0) return GF_OK;
+    const int64_t gz = nlz * BV * B;
     if (blk.n[1] * BV > 65535 || gz > 65535) {
         set_error("leaf block too large for the density re-blocking grid");
         return GF_ERR_UNSUPPORTED;
     }
     const dim3 grid(ceil_div(blk.n[0], 128), (unsigned)(blk.n[1] * BV), (unsigned)gz);
     block_rows<T, BV><<<grid, 128, 0, st>>>(rho, rho_f32, plan->grid.n[0], plan->grid.n[1], plan->grid.n[2],
-                                            F->voff[0], F->voff[1], F->voff[2], blk, B, (T *)F->mass,
+                                            F->voff[0], F->voff[1], F->voff[2], blk, lz0, nlz, B, (T *)F->mass,
                                             plan->d_status);
     GF_KERNEL_DONE();
     return GF_OK;
@@ -1194,6 +1212,7 @@ struct P2MEntry {
     double *pd;
     float *pf;
     float *tc = nullptr;   // tensor-core image (built on first use)
+    float *up_tc = nullptr;   // tensor-core image of the P2M into the parent level
 };
 std::mutex g_p2m_mu;
 std::vector<P2MEntry *> g_p2m;
@@ -1250,7 +1269,25 @@ gf_status get_p2m_tc(gf_plan_s *plan, cudaStream_t st) {
             GF_TRY(build_p2m_tc_image(e->pd, F->K, npad, b3, e->tc, st));
             GF_CUDA(cudaStreamSynchronize(st));
         }
+        if (!e->up_tc) {
+            const int b3 = F->b * F->b * F->b, npad = F->tab->tc_npad;
+            double *q = nullptr;
+            if (cudaMalloc(&q, sizeof(double) * 8 * (size_t)b3 * F->K) != cudaSuccess ||
+                cudaMalloc(&e->up_tc, sizeof(float) * 8 * (size_t)(b3 / 16) * 2 * npad * 16) != cudaSuccess) {
+                cudaGetLastError();
+                if (q) cudaFree(q);
+                e->up_tc = nullptr;
+                set_error("cannot allocate the tensor-core image of the P2M into the parent level");
+                return GF_ERR_OOM;
+            }
+            compose_p2m_up<<<dim3(8, b3), 128, 0, st>>>(e->pd, F->tab->m2m_d, F->K, b3, q);
+            GF_KERNEL_DONE();
+            GF_TRY(build_p2m_up_tc_image(q, F->K, npad, b3, e->up_tc, st));
+            GF_CUDA(cudaStreamSynchronize(st));
+            cudaFree(q);
+        }
         F->p2m_tc = e->tc;
+        F->p2m_up_tc = e->up_tc;
         return GF_OK;
     }
     return GF_OK;   // no cached matrix: the P2M stays on the SIMT path
@@ -1334,6 +1371,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     const int b3 = F->b * F->b * F->b;
     const Tables *tab = F->tab;
     const bool fused = p2m_fused_ok<T>(F);
+    bool up = false;   // level L-1 expansions made straight from the leaf masses
     if (fused) {
         // a0 + a3: leaf-blocked densities and P2M (timed as P2M): on the
         // tensor cores for 4^3-voxel leaves in mixed precision, else fused
@@ -1341,8 +1379,18 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         const Block3 lb = block_of(F->lev[F->L]);
         if (sizeof(T) == 4 && F->b == 4 && p2m_tc_ok(plan, B) && lb.n[1] * 4 <= 65535 &&
             lb.n[2] * 4 * B <= 65535) {
-            GF_TRY((launch_blocking<T, 4>(plan, rho, rho_dtype == GF_DTYPE_F32, B, st)));
-            GF_TRY(p2m_run_tc(plan, B, st));
+            // Leaf-blocked masses (read by the near field and the leaf P2M)
+            // of every leaf, or -- when the expansions of level L-1 come
+            // straight from the density grid -- of the z-slabs that the leaf
+            // level's M2L (and so the near field) reaches.
+            up = p2m_up_ok(plan, B);
+            const bool from_grid = up && p2m_up_grid_ok(plan, rho, rho_dtype);
+            const FmmLevel &lf = F->lev[L];
+            const int64_t z0 = from_grid ? lf.m2l_z0 : 0;
+            const int64_t nz = from_grid ? std::max<int64_t>(0, lf.m2l_z1 - lf.m2l_z0 + 1) : lb.n[2];
+            GF_TRY((launch_blocking<T, 4>(plan, rho, rho_dtype == GF_DTYPE_F32, B, z0, nz, st)));
+            GF_TRY(p2m_run_tc(plan, B, st));   // every leaf, or only the slabs the M2L reads
+            if (up) GF_TRY(p2m_up_run_tc(plan, B, from_grid ? (const float *)rho : nullptr, st));
         } else {
             GF_TRY(launch_p2m_fused<T>(plan, rho, rho_dtype == GF_DTYPE_F32, B, st));
         }
@@ -1372,7 +1420,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     // a4: M2M up to level 2.  In mixed precision the translation into the
     // top level (2) is done in FP64 on the per-box kernel; the deeper levels
     // run in the batched kernel in the plan's precision.
-    for (int l = L - 1; l >= 2; --l) {
+    for (int l = up ? L - 2 : L - 1; l >= 2; --l) {
         const FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
         if (sizeof(T) == 4 && l <= 2) {
             const int nbc = top_batch_chunk(8, B, K);

@@ -108,6 +108,11 @@ struct FmmPlan {
     void *tc_levels_adj = nullptr;
     std::vector<unsigned char> tc_levels_adj_host;
     float *p2m_tc = nullptr;                     // tensor-core P2M operator image
+    // tensor-core image of the P2M into level L-1: for each child position
+    // o of a parent, Q_o[v][k] = sum_i P[v][i] M2M_o[i][k] (the leaf P2M
+    // followed by the M2M to the parent), so a parent's expansion comes
+    // straight from the masses of its 8 child leaves
+    float *p2m_up_tc = nullptr;
     void *tc_xlate = nullptr;                    // tensor-core M2M / L2L / P2M level tables
     std::vector<unsigned char> tc_xlate_host;
 };

@@ -138,6 +138,12 @@ gf_status build_p2m_tc_image(const double *pd, int K, int npad, int b3, float *i
     return GF_OK;
 }
 
+gf_status build_p2m_up_tc_image(const double *q, int K, int npad, int b3, float *img, cudaStream_t st) {
+    build_tc_images<<<8, 256, 0, st>>>(q, K, npad, b3 / 16, img, 1, b3);
+    GF_KERNEL_DONE();
+    return GF_OK;
+}
+
 gf_status m2l_prepare_tables(Tables *T, cudaStream_t st) {
     const int npad = (T->K + 15) & ~15;
     if (npad > 256) return GF_OK;  // beyond one MMA's N: SIMT only
@@ -558,6 +564,12 @@ struct TcLevel {
     const int32_t *tparent;      // L2L: parent of each observer box
     const uint32_t *amax;        // M2L: largest |input| of the level (float bits)
     const unsigned char *split;  // M2L: the level's inputs split into scaled FP16 parts
+    int64_t tfirst;              // P2M: index of the first leaf of the targets
+    // P2M into level L-1 reading the density grid itself (TcArgs::grid): grid
+    // voxel (i, j, k) of leaf (x, y, z) is i = gb x - goff[0] + (voxel in the
+    // leaf), likewise j, k; leaves lie wholly inside or outside the grid
+    int64_t goff[3], gn[3], gnvox;
+    int gb;
 };
 
 struct TcArgs {
@@ -571,6 +583,14 @@ struct TcArgs {
     const unsigned char *img;   // operator images, one [hi|lo] tile pair per (slot, chunk)
     const float *cs;            // M2L: column scales of the image ([Npad] scale, [Npad] inverse)
     int *status;
+    long wait_tries;            // bound of every barrier wait (kWaitTries)
+    int test_stall;             // testing aid: the MMA issuer first waits on a barrier that
+                                // nothing completes, so the bounded-wait failure path runs
+    // M2M kind over leaf masses taken straight from the FP32 density grid:
+    // the grid, and the element steps of its y and z rows (an input chunk is
+    // one z-layer of a leaf, four rows of four voxels)
+    const float *grid;
+    int64_t gstep[2];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -616,6 +636,7 @@ __device__ __forceinline__ void input_scale(uint32_t mbits, float &sig, float &i
 __host__ __device__ __forceinline__ int chunk_of(int nck, int j) { return nck - 1 - j; }
 
 constexpr long kWaitTries = 1l << 24;
+constexpr long kTestWaitTries = 1l << 12;   // wait bound under GF_FLAG_TEST_WAIT_TIMEOUT
 
 __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
     uint32_t ok;
@@ -628,8 +649,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
 
 // Bounded wait on phase `parity` of an mbarrier that also gives up when
 // another role has set the abort flag; a timeout sets the flag.
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t addr, uint32_t parity, volatile int *abort_flag) {
-    for (long it = 0; it < kWaitTries; ++it) {
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t addr, uint32_t parity, volatile int *abort_flag,
+                                             long tries) {
+    for (long it = 0; it < tries; ++it) {
         if (mbar_try(addr, parity)) return true;
         if ((it & 255) == 255 && *abort_flag) return false;
     }
@@ -638,8 +660,8 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t addr, uint32_t parity, vol
 }
 
 // Bounded wait that ignores the abort flag (used to drain in-flight work).
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    for (long it = 0; it < kWaitTries; ++it)
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long tries) {
+    for (long it = 0; it < tries; ++it)
         if (mbar_try(addr, parity)) return true;
     return false;
 }
@@ -710,7 +732,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 m2l_tc(TcArgs a) {
     extern __shared__ unsigned char dsm[];
     unsigned char *base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);
-    __shared__ __align__(8) uint64_t afull[kTcMaxStages], empty[kTcMaxStages];
+    // afull: the stage's A operand has landed (128 producer arrivals); bfull:
+    // its operator image has landed (the copy's own transaction count, so the
+    // copying thread can always wait for its copies, whatever the producers do)
+    __shared__ __align__(8) uint64_t afull[kTcMaxStages], bfull[kTcMaxStages], empty[kTcMaxStages];
+    __shared__ __align__(8) uint64_t stall_bar;
     __shared__ __align__(8) uint64_t bank_full[2], bank_empty[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
@@ -756,14 +782,16 @@ m2l_tc(TcArgs a) {
     }
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
-            // 128 producer threads + the operator copy's expect-tx arrival
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(129));
+            // 128 producer threads; the operator copy's expect-tx arrival
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[i])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
         }
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bank_full[i])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bank_empty[i])), "r"(8));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&stall_bar)), "r"(1));
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -787,7 +815,7 @@ m2l_tc(TcArgs a) {
         const int64_t sidx = (int64_t)pc.tile * nbox + slot;
         if (warp >= 4 || slot >= nbox || sidx >= pc.ccnt) return;
         if (a.kind == kTcP2M) {
-            tbox = sidx;
+            tbox = L.tfirst + sidx;
         } else if (a.kind == kTcM2M) {
             tbox = sidx;
             tc0 = sidx % L.bn[0];
@@ -815,8 +843,15 @@ m2l_tc(TcArgs a) {
             const int64_t cx = 2 * (tc0 + L.blo[0]) + (oi & 1) - L.clo[0],
                           cy = 2 * (tc1 + L.blo[1]) + ((oi >> 1) & 1) - L.clo[1],
                           cz = 2 * (tc2 + L.blo[2]) + ((oi >> 2) & 1) - L.clo[2];
-            if (cx >= 0 && cy >= 0 && cz >= 0 && cx < L.cn[0] && cy < L.cn[1] && cz < L.cn[2])
+            if (cx >= 0 && cy >= 0 && cz >= 0 && cx < L.cn[0] && cy < L.cn[1] && cz < L.cn[2]) {
+                if (a.grid) {   // the child leaf's first voxel in the density grid
+                    const int64_t i0 = (L.clo[0] + cx) * L.gb - L.goff[0], j0 = (L.clo[1] + cy) * L.gb - L.goff[1],
+                                  k0 = (L.clo[2] + cz) * L.gb - L.goff[2];
+                    if (i0 < 0 || j0 < 0 || k0 < 0 || i0 >= L.gn[0] || j0 >= L.gn[1] || k0 >= L.gn[2]) return -1;
+                    return bb * L.gnvox + (k0 * L.gn[1] + j0) * L.gn[0] + i0;
+                }
                 return (((cz * L.cn[1] + cy) * L.cn[0] + cx) * B + bb) * a.ldin;
+            }
             return -1;
         }
         if (a.kind == kTcL2L) return ((int64_t)L.tparent[tbox] * B + bb) * a.ldin;
@@ -893,7 +928,7 @@ m2l_tc(TcArgs a) {
             int s = 0;
             uint32_t ph = 0;
             for (int it = 0; it < iters; ++it) {
-                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp, a.wait_tries)) break;
                 unsigned char *stage = base + (size_t)s * stage_bytes;
                 int c0 = 0, nc = S;
 #pragma unroll
@@ -938,7 +973,7 @@ m2l_tc(TcArgs a) {
             // TF32 inputs, split here
             constexpr int kW = 16;     // inputs per stage
             constexpr int kV = kW / 4; // 16-byte pieces per row and stage
-            const float *me = pc.L->me;   // every tile of a launch reads the same input array
+            const float *me = a.grid ? a.grid : pc.L->me;   // every tile of a launch reads the same input array
             // Each thread copies its own row's chunks kTcRaw - 1 stages ahead into
             // a raw ring (16-byte pieces XOR-swizzled by row, so that a warp's
             // reads of one piece hit distinct banks); a missing source copies
@@ -949,10 +984,14 @@ m2l_tc(TcArgs a) {
                 int64_t sr;
                 take(cc, sr);
                 const uint32_t d0 = smem_u32(raw + (size_t)(j % kTcRaw) * 128 * (kW * 4));
-                const float *src = sr >= 0 ? me + sr + kW * chunk_of(nck, cc) : me;
+                // a chunk is 16 contiguous inputs, or (density grid) the leaf's
+                // z-layer: four rows of four voxels a y-step apart
+                const int ck = chunk_of(nck, cc);
+                const float *src = sr < 0 ? me : (a.grid ? me + sr + ck * a.gstep[1] : me + sr + kW * ck);
+                const int64_t qs = sr < 0 ? 0 : (a.grid ? a.gstep[0] : 4);
 #pragma unroll
                 for (int q = 0; q < kV; ++q)
-                    cp_async16(d0 + ((q ^ (row & (kV - 1))) << 4), src + (sr >= 0 ? 4 * q : 0), sr >= 0 ? 16u : 0u);
+                    cp_async16(d0 + ((q ^ (row & (kV - 1))) << 4), src + q * qs, sr >= 0 ? 16u : 0u);
             };
 #pragma unroll 1
             for (int j = 0; j < kTcRaw - 1; ++j) {
@@ -961,11 +1000,12 @@ m2l_tc(TcArgs a) {
             }
             int s = 0;
             uint32_t ph = 0;
+            bool bad = false;   // a non-finite input (densities read from the grid)
             for (int it = 0; it < iters; ++it) {
                 if (it + kTcRaw - 1 < iters) issue(it + kTcRaw - 1);
                 asm volatile("cp.async.commit_group;" ::: "memory");
                 asm volatile("cp.async.wait_group %0;" ::"n"(kTcRaw - 1) : "memory");   // chunk `it` has landed
-                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp, a.wait_tries)) break;
                 const int c0 = chunk_of(nck, it % nck);   // every offset runs all nck chunks, in order
                 float4 cur[kV];
                 {
@@ -983,6 +1023,7 @@ m2l_tc(TcArgs a) {
                         for (int j = 0; j < 4; ++j) {
                             const int kin = 16 * c0 + 4 * q + j;
                             const float x = kin < a.kin ? x4[j] : 0.f;
+                            bad |= !isfinite(x);
                             h[j] = to_tf32(x);
                             l[j] = to_tf32(x - __uint_as_float(h[j]));
                         }
@@ -999,6 +1040,7 @@ m2l_tc(TcArgs a) {
                 }
             }
             asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the loop (abort)
+            if (bad && a.grid) atomicOr(a.status, 1);
         }
     } else if (warp == 4) {
         // ---------------- MMA issuer
@@ -1007,9 +1049,15 @@ m2l_tc(TcArgs a) {
             int s = 0, c0 = 0, g = 0;
             uint32_t ph = 0;
             int last = -1;
-            for (int it = 0; it < iters; ++it) {
-                if (!mbar_wait_ab(smem_u32(&afull[s]), ph, abortp)) break;
-                if (c0 == 0 && g >= 2 && !mbar_wait_ab(smem_u32(&bank_empty[g & 1]), ((g - 2) >> 1) & 1, abortp)) break;
+            // testing aid: a wait that nothing completes runs out, sets the abort
+            // flag, and every role stops, drains and reports through status[1]
+            const bool stalled = a.test_stall && !mbar_wait_ab(smem_u32(&stall_bar), 0, abortp, a.wait_tries);
+            for (int it = 0; it < (stalled ? 0 : iters); ++it) {
+                if (!mbar_wait_ab(smem_u32(&afull[s]), ph, abortp, a.wait_tries)) break;
+                if (!mbar_wait_ab(smem_u32(&bfull[s]), ph, abortp, a.wait_tries)) break;
+                if (c0 == 0 && g >= 2 &&
+                    !mbar_wait_ab(smem_u32(&bank_empty[g & 1]), ((g - 2) >> 1) & 1, abortp, a.wait_tries))
+                    break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const unsigned char *stage = base + (size_t)s * stage_bytes;
                 const uint32_t d = tmem + (uint32_t)(g & 1) * 256u;
@@ -1058,7 +1106,7 @@ m2l_tc(TcArgs a) {
                 }
             }
             // drain: the last commit covers every MMA issued
-            if (last >= 0) mbar_wait(smem_u32(&empty[last % NST]), (uint32_t)((last / NST) & 1));
+            if (last >= 0) mbar_wait(smem_u32(&empty[last % NST]), (uint32_t)((last / NST) & 1), a.wait_tries);
         }
     } else if (warp == 5) {
         // ---------------- operator images
@@ -1069,7 +1117,7 @@ m2l_tc(TcArgs a) {
             uint32_t ph = 0;
             int last = -1;
             for (int it = 0; it < iters; ++it) {
-                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp)) break;
+                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp, a.wait_tries)) break;
                 int slot_off;
                 if (a.kind == kTcM2L) {
                     const int dx = c_il[bcls][oi][0], dy = c_il[bcls][oi][1], dz = c_il[bcls][oi][2];
@@ -1086,13 +1134,13 @@ m2l_tc(TcArgs a) {
                 // (ascending, the lowest being that of the stage's last chunk)
                 const int ncs = min(S, nck - c0);
                 const uint32_t nbytes = (uint32_t)ncs * b_bytes;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&afull[s])),
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bfull[s])),
                              "r"(nbytes));
                 const unsigned char *srcimg = a.img + ((size_t)slot_off * nck + chunk_of(nck, c0 + ncs - 1)) * b_bytes;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         smem_u32(stage + S * kTcA)),
-                    "l"(srcimg), "r"(nbytes), "r"(smem_u32(&afull[s]))
+                    "l"(srcimg), "r"(nbytes), "r"(smem_u32(&bfull[s]))
                     : "memory");
                 last = it;
                 c0 += S;
@@ -1109,11 +1157,12 @@ m2l_tc(TcArgs a) {
                     ph ^= 1;
                 }
             }
-            // drain: every copy issued must have landed before the CTA exits (the
-            // stage completes once its copy has landed and the producers have
-            // arrived; after an abort, producers that stopped never arrive and
-            // the drain waits out its bound, long after the copy landed)
-            if (last >= 0) mbar_wait(smem_u32(&afull[last % NST]), (uint32_t)((last / NST) & 1));
+            // drain: every copy issued must have landed before the CTA exits;
+            // the last NST stages may still have copies in flight (earlier ones
+            // were consumed by MMAs before their stage was reused), and each
+            // stage's copy completes its own barrier
+            for (int j = last - NST + 1 > 0 ? last - NST + 1 : 0; j <= last; ++j)
+                mbar_wait(smem_u32(&bfull[j % NST]), (uint32_t)((j / NST) & 1), a.wait_tries);
         }
     }
     // ---------------- promoters (warps 6-13) and the write-back of each tile
@@ -1127,7 +1176,7 @@ m2l_tc(TcArgs a) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) acc[q] = 0.f;
             for (int g = 0; g < G; ++g, ++gg) {
-                bool w_ok = mbar_wait_ab(smem_u32(&bank_full[gg & 1]), (gg >> 1) & 1, abortp);
+                bool w_ok = mbar_wait_ab(smem_u32(&bank_full[gg & 1]), (gg >> 1) & 1, abortp, a.wait_tries);
                 w_ok = __all_sync(0xffffffffu, w_ok);   // tcgen05.ld is warp-collective
                 if (!w_ok) {
                     ok = false;
@@ -1161,8 +1210,10 @@ m2l_tc(TcArgs a) {
             const int64_t os = (int64_t)oc.tile * nbox + oslot;
             if (oslot < nbox && os < oc.ccnt) {
                 int64_t obox;
-                if (a.kind == kTcM2M || a.kind == kTcP2M) {   // dense targets
+                if (a.kind == kTcM2M) {   // dense targets
                     obox = os;
+                } else if (a.kind == kTcP2M) {
+                    obox = L.tfirst + os;
                 } else if (!L.adj) {
                     obox = L.order[oc.cbeg + os];
                 } else {
@@ -1290,10 +1341,12 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
         GF_TRY(plan->arena.alloc(&dev, hb.size()));
         GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
     }
-    // M2M into level l (entries [0, L]), L2L into level l (entries [L+1, 2L+1])
-    // and the P2M (entry 2L+2)
+    // M2M into level l (entries [0, L]), L2L into level l (entries [L+1, 2L+1]),
+    // the P2M of every leaf (entry 2L+2), the P2M into level L-1 straight
+    // from the leaf masses (entry 2L+3) and the P2M of the leaves in the
+    // z-slabs the leaf level's M2L reads (entry 2L+4)
     if (F->tab->m2m_tc && F->tab->l2l_tc) {
-        std::vector<TcLevel> h(2 * (F->L + 1) + 1);
+        std::vector<TcLevel> h(2 * (F->L + 1) + 3);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
         for (int l = 2; l <= F->L; ++l) {
             if (l < F->L) {
@@ -1333,6 +1386,32 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
             t.cls_off[0] = 0;
             for (int c = 1; c <= 8; ++c) t.cls_off[c] = lv.ns;
             if ((F->b * F->b * F->b) % 16 == 0) GF_TRY(get_p2m_tc(plan, plan->arena.stream));
+            TcLevel &r = h[2 * (F->L + 1) + 2];
+            r = t;
+            const int64_t slab = lv.sn[0] * lv.sn[1];
+            const int64_t nz = lv.m2l_z1 >= lv.m2l_z0 ? lv.m2l_z1 - lv.m2l_z0 + 1 : 0;
+            r.tfirst = nz > 0 ? lv.m2l_z0 * slab : 0;
+            for (int c = 1; c <= 8; ++c) r.cls_off[c] = nz * slab;
+        }
+        if (F->L - 1 > 2) {
+            const FmmLevel &pa = F->lev[F->L - 1], &ch = F->lev[F->L];
+            TcLevel &t = h[2 * (F->L + 1) + 1];
+            t.me = (const float *)F->mass;
+            t.le = (float *)pa.me;
+            for (int d = 0; d < 3; ++d) {
+                t.blo[d] = pa.slo[d];
+                t.bn[d] = pa.sn[d];
+                t.clo[d] = ch.slo[d];
+                t.cn[d] = ch.sn[d];
+            }
+            t.cls_off[0] = 0;
+            for (int c = 1; c <= 8; ++c) t.cls_off[c] = pa.ns;
+            t.gb = F->b;
+            t.gnvox = plan->nvox;
+            for (int d = 0; d < 3; ++d) {
+                t.goff[d] = F->voff[d];
+                t.gn[d] = plan->grid.n[d];
+            }
         }
         F->tc_xlate_host.assign(reinterpret_cast<unsigned char *>(h.data()),
                                 reinterpret_cast<unsigned char *>(h.data() + h.size()));
@@ -1468,6 +1547,7 @@ TcArgs tc_args(gf_plan_s *plan, int B) {
     a.kin = F->K;
     a.ldin = F->KS;
     a.status = plan->d_status;
+    a.wait_tries = kWaitTries;
     return a;
 }
 
@@ -1482,6 +1562,10 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     a.nck = T->tc_nck_h;
     a.img = (const unsigned char *)(adj ? T->am2l_tc : T->m2l_tc);
     a.cs = adj ? T->am2l_cs : T->m2l_cs;
+    if (plan->opt.reserved0 & GF_FLAG_TEST_WAIT_TIMEOUT) {
+        a.test_stall = 1;
+        a.wait_tries = kTestWaitTries;
+    }
     if (F->L < 2) return GF_OK;
     // the largest |input| of every level, for the FP16 input scales
     {
@@ -1534,11 +1618,12 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     return tc_launch(a, tiles, st);
 }
 
-gf_status p2m_run_tc_impl(gf_plan_s *plan, int B, cudaStream_t st) {
+gf_status p2m_run_tc_impl(gf_plan_s *plan, int B, bool slabs, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     TcArgs a = tc_args(plan, B);
     const int b3 = F->b * F->b * F->b;
-    a.lv = reinterpret_cast<const TcLevel *>(F->tc_xlate) + 2 * (F->L + 1);
+    const int entry = 2 * (F->L + 1) + (slabs ? 2 : 0);
+    a.lv = reinterpret_cast<const TcLevel *>(F->tc_xlate) + entry;
     a.lmin = 0;
     a.kind = kTcP2M;
     a.noff = 1;
@@ -1547,8 +1632,37 @@ gf_status p2m_run_tc_impl(gf_plan_s *plan, int B, cudaStream_t st) {
     a.nck = b3 / 16;
     a.img = (const unsigned char *)F->p2m_tc;
     const int nbox = 128 / B;
-    const int64_t ns = F->lev[F->L].ns;
+    const int64_t ns = reinterpret_cast<const TcLevel *>(F->tc_xlate_host.data())[entry].cls_off[1];
     const int tiles = (int)((ns + nbox - 1) / nbox);
+    a.tile_begin[0] = 0;
+    for (int c = 1; c <= 8; ++c) a.tile_begin[c] = tiles;
+    a.nent = 8;
+    return tc_launch(a, tiles, st);
+}
+
+// P2M into level L-1: the M2M kind over the leaf masses (8 child positions,
+// b^3 inputs each) with the composite operators Q_o.
+gf_status p2m_up_run_tc_impl(gf_plan_s *plan, int B, const float *grid, cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    TcArgs a = tc_args(plan, B);
+    if (grid) {
+        a.grid = grid;
+        a.gstep[0] = plan->grid.n[0];
+        a.gstep[1] = plan->grid.n[0] * plan->grid.n[1];
+    }
+    const int b3 = F->b * F->b * F->b;
+    const int entry = 2 * (F->L + 1) + 1;
+    a.lv = reinterpret_cast<const TcLevel *>(F->tc_xlate) + entry;
+    a.lmin = 0;
+    a.kind = kTcM2M;
+    a.noff = 8;
+    a.kin = b3;
+    a.ldin = b3;
+    a.nck = b3 / 16;
+    a.img = (const unsigned char *)F->p2m_up_tc;
+    const int nbox = 128 / B;
+    const int64_t np = F->lev[F->L - 1].ns;
+    const int tiles = (int)((np + nbox - 1) / nbox);
     a.tile_begin[0] = 0;
     for (int c = 1; c <= 8; ++c) a.tile_begin[c] = tiles;
     a.nent = 8;
@@ -1638,7 +1752,26 @@ bool p2m_tc_ok(const gf_plan_s *plan, int B) {
            tc_stages(F->tab->tc_npad, false) >= 2;
 }
 
-gf_status p2m_run_tc(gf_plan_s *plan, int B, cudaStream_t st) { return p2m_run_tc_impl(plan, B, st); }
+bool p2m_up_ok(const gf_plan_s *plan, int B) {
+    const FmmPlan *F = plan->fmm;
+    return p2m_tc_ok(plan, B) && F->p2m_up_tc && F->L - 1 > 2 && F->b * F->b * F->b == 64;
+}
+
+gf_status p2m_run_tc(gf_plan_s *plan, int B, cudaStream_t st) {
+    return p2m_run_tc_impl(plan, B, p2m_up_ok(plan, B), st);
+}
+
+bool p2m_up_grid_ok(const gf_plan_s *plan, const void *rho, int rho_dtype) {
+    const FmmPlan *F = plan->fmm;
+    if (rho_dtype != GF_DTYPE_F32 || ((uintptr_t)rho & 15) != 0 || F->b != 4) return false;
+    for (int d = 0; d < 3; ++d)
+        if (plan->grid.n[d] % 4 != 0 || F->voff[d] % 4 != 0) return false;
+    return true;
+}
+
+gf_status p2m_up_run_tc(gf_plan_s *plan, int B, const float *grid, cudaStream_t st) {
+    return p2m_up_run_tc_impl(plan, B, grid, st);
+}
 
 template <class Ts, class Tc>
 gf_status translate_run(gf_plan_s *plan, int level, int kind, int B, cudaStream_t st) {

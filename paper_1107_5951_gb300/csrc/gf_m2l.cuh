@@ -10,6 +10,8 @@ gf_status m2l_upload_offsets(const signed char h_il[8][189][3]);
 gf_status m2l_prepare_tables(Tables *T, cudaStream_t st);
 // Tensor-core image of a P2M matrix [b3][K] (b3 a multiple of 16).
 gf_status build_p2m_tc_image(const double *pd, int K, int npad, int b3, float *img, cudaStream_t st);
+// Tensor-core image of the P2M into the parent level (8 operators [b3][K]).
+gf_status build_p2m_up_tc_image(const double *q, int K, int npad, int b3, float *img, cudaStream_t st);
 
 // LE_l[t] = sum over the interaction list of box t of T_o * ME_l[t + o],
 // for every observer box t of every level (overwrites each LE_l).  Mixed
@@ -42,5 +44,17 @@ gf_status m2l_tc_prepare_adj(gf_plan_s *plan);
 // plan and batch size allow it.
 bool p2m_tc_ok(const gf_plan_s *plan, int B);
 gf_status p2m_run_tc(gf_plan_s *plan, int B, cudaStream_t st);
+// Whether the parent level's expansions can come straight from the leaf
+// masses (p2m_up_run_tc) instead of P2M at every leaf and the M2M out of the
+// leaf level: mixed precision on the tensor cores, L - 1 > 2 (level 2 keeps
+// its FP64 M2M).  The leaf expansions are then computed only for the z-slabs
+// that the leaf level's M2L reads.
+bool p2m_up_ok(const gf_plan_s *plan, int B);
+// Whether the P2M into level L-1 can read the densities straight from the
+// caller's grid (FP32, 16-byte aligned, every axis and the grid's place in
+// the tree multiples of the 4-voxel leaf edge); grid NULL: the leaf-blocked
+// masses of every leaf.
+bool p2m_up_grid_ok(const gf_plan_s *plan, const void *rho, int rho_dtype);
+gf_status p2m_up_run_tc(gf_plan_s *plan, int B, const float *grid, cudaStream_t st);
 
 }  // namespace gf

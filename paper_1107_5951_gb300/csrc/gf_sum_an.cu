@@ -75,21 +75,25 @@ __device__ __forceinline__ double an_plane(double o, double h, int64_t I) {
 }
 
 // D[b][c]: signed sum of the densities of the voxels sharing corner c.
+// Flags a non-finite density in status[0].
 __global__ void an_corner_weights(const void *__restrict__ rho, int rho_f32, AnGrid g,
-                                  double *__restrict__ D) {
+                                  double *__restrict__ D, int *__restrict__ status) {
     const int b = blockIdx.y;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.nc) return;
     const int64_t I = c % g.ncx, J = (c / g.ncx) % g.ncy, K = c / (g.ncx * g.ncy);
     double s = 0.0;
+    bool bad = false;
     for (int e = 0; e < 2; ++e)
         for (int f = 0; f < 2; ++f)
             for (int a = 0; a < 2; ++a) {
                 const int64_t i = I - a, j = J - f, k = K - e;
                 if (i < 0 || j < 0 || k < 0 || i >= g.nx || j >= g.ny || k >= g.nz) continue;
                 const double r = an_rho(rho, rho_f32, (int64_t)b * g.nvox + (k * g.ny + j) * g.nx + i);
+                bad |= !isfinite(r);
                 s += ((a + f + e) & 1) ? r : -r;
             }
+    if (bad) atomicOr(status, 1);
     D[(int64_t)b * g.nc + c] = s;
 }
 
@@ -231,7 +235,7 @@ gf_status sum_an_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B,
                          cudaStream_t st) {
     const AnGrid ga = an_grid(plan);
     an_corner_weights<<<dim3(ceil_div(ga.nc, 256), B), 256, 0, st>>>(rho, rho_dtype == GF_DTYPE_F32, ga,
-                                                                     plan->d_corner);
+                                                                     plan->d_corner, plan->d_status);
     GF_KERNEL_DONE();
     if (plan->M == 0) return GF_OK;
     an_forward<<<dim3(ceil_div(plan->M, kAnTile), B), kAnTile, 0, st>>>(plan->d_obs, plan->M, plan->d_corner, ga,

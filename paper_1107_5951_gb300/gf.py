@@ -277,6 +277,7 @@ class _Quad:
 
 GF_FLAG_M2L_SIMT = 1
 GF_FLAG_SUM_AN = 2
+GF_FLAG_TEST_WAIT_TIMEOUT = 4
 
 
 def make_options(mode="fmm", precision="fp64", p=8, leaf_vox=0, max_batch=1, G=0.0, flags=0) -> gf_options:
@@ -338,10 +339,11 @@ class Plan:
     obs must be a CUDA float64 tensor of shape (M, 3).  m2l="simt" runs the
     mixed-precision M2L on the SIMT cores; voxels="closed_form" integrates
     every voxel exactly (SUM-AN; direct mode, FP64) instead of sampling it
-    with the rule (xi, w)."""
+    with the rule (xi, w).  flags: further GF_FLAG_* bits (testing aids)."""
 
     def __init__(self, shape, origin, h, xi, w, obs, mode="fmm", precision="fp64", p=8,
-                 leaf_vox=0, max_batch=1, G=0.0, stream=None, m2l="auto", voxels="quadrature"):
+                 leaf_vox=0, max_batch=1, G=0.0, stream=None, m2l="auto", voxels="quadrature",
+                 flags=0):
         import torch
         if not (isinstance(obs, torch.Tensor) and obs.is_cuda):
             raise TypeError("obs must be a CUDA tensor")
@@ -356,7 +358,7 @@ class Plan:
             raise ValueError("m2l must be 'auto' or 'simt', voxels 'quadrature' or 'closed_form'")
         self._opt = make_options(mode, precision, p, leaf_vox, max_batch, G,
                                  (GF_FLAG_M2L_SIMT if m2l == "simt" else 0)
-                                 | (GF_FLAG_SUM_AN if voxels == "closed_form" else 0))
+                                 | (GF_FLAG_SUM_AN if voxels == "closed_form" else 0) | int(flags))
         self.handle = None
         with torch.cuda.device(self.device):
             self.handle = gf_plan_create(self._grid, self._quad.c, obs.data_ptr(), self.M, self._opt,

@@ -134,3 +134,34 @@ def test_device_and_pinned_buffers_give_the_same_bits():
     assert np.array_equal(gz_host, gz_pin.numpy()) and np.array_equal(gz_host, gz_dev.cpu().numpy())
     assert np.array_equal(g_host, g_pin.numpy()) and np.array_equal(g_host, g_dev.cpu().numpy())
     assert np.array_equal(g_host[:, 2], gz_host)
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-6)])
+def test_serving_sides_up_to_256(precision, tol):
+    """Requests of the serving workload's full size range (32^3 to 256^3
+    voxels of 250 m, 256^2 stations), queued together on four slots: each
+    meets the oracle on sampled stations and equals the plain plan API bit
+    for bit."""
+    p = 12 if precision == "mixed" else 14
+    sides = (32, 91, 160, 256)
+    dtype = np.float32 if precision == "mixed" else np.float64
+    geo, rhos = {}, {}
+    with pkg.Server(slots=4, precision=precision, p=p) as srv:
+        for gid, n in enumerate(sides):
+            grid, xi, w, obs = geometry(n, stations=256)
+            srv.register(100 + gid, grid.n, grid.origin, grid.h, xi, w, obs)
+            geo[gid] = (grid, xi, w, obs)
+            rhos[gid] = wl.periodic_grf(n, H, 2000.0, 150.0, 77 + gid, dtype=dtype)
+        tickets = {gid: srv.submit(100 + gid, rhos[gid]) for gid in geo}
+        got = {gid: srv.wait(t)[0] for gid, t in tickets.items()}
+    rng = np.random.default_rng(19)
+    for gid, (grid, xi, w, obs) in geo.items():
+        idx = np.sort(rng.choice(len(obs), 48, replace=False))
+        ref = direct.forward(grid.n, grid.origin, grid.h, xi, w, rhos[gid].astype(np.float64), obs[idx],
+                             wl.G_PAPER)[:, 2]
+        assert rel_l2(got[gid][idx], ref) <= tol, sides[gid]
+        with pkg.Plan(grid.n, grid.origin, grid.h, xi, w, torch.tensor(obs, dtype=torch.float64, device="cuda:0"),
+                      mode="fmm", precision=precision, p=p, G=wl.G_PAPER) as plan:
+            _, gz = plan.forward(torch.tensor(rhos[gid], device="cuda:0"), want_g=False, want_gz=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(gz.cpu().numpy(), got[gid]), sides[gid]

@@ -63,6 +63,29 @@ def test_static_forward_matches_plan_on_two_calls_in_a_row():
         assert _rel(z, q) <= TOL
 
 
+def test_static_forward_allocates_no_device_memory():
+    """What the entry point exists for: once the library's module is loaded
+    (a first call), a call changes neither the device's free memory nor
+    torch's reserved memory."""
+    wk = wl.random_small(74, n=(11, 9, 7), npts=2, n_obs=5000, B=1)
+    rho = torch.tensor(wk.rho[None], dtype=torch.float32, device=DEV)
+    _static_result(wk, rho)          # loads the kernels (and the static array) if not yet loaded
+    obs = torch.tensor(wk.obs, dtype=torch.float64, device=DEV)
+    g = torch.empty((1, wk.n_obs, 3), dtype=torch.float64, device=DEV)
+    quad = gf._Quad(wk.xi, wk.w)
+    grid = gf.make_grid(wk.grid.n, wk.grid.origin, wk.grid.h)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        gf.gf_direct_forward_static(grid, quad.c, obs.data_ptr(), wk.n_obs, rho.data_ptr(), gf.GF_DTYPE_F32, 1,
+                                    wk.G, g.data_ptr(), 0, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+
+
 def test_static_forward_rejects_too_many_observers():
     wk = wl.random_small(73, n=(2, 2, 2), npts=1, n_obs=4)
     obs = torch.zeros((65537, 3), dtype=torch.float64, device=DEV)
