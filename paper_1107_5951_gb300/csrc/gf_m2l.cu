@@ -702,7 +702,7 @@ constexpr int kTcMaxStages = 8;
 constexpr uint32_t kTcCols = 512;           // two banks of 256 columns
 constexpr uint32_t kTcA = 2u * 8192u;       // A hi + lo: 128 rows x 64 bytes each
 
-constexpr int kTcRaw = 4;                   // input chunks in flight per producer thread
+constexpr int kTcRaw = 8;                   // input chunks in flight per producer thread
 
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 64u; }
 // raw FP32 input ring of the producers: [kTcRaw][128 rows][32 or 16 floats]

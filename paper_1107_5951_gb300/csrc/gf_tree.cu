@@ -158,6 +158,64 @@ __global__ void compact_runs(const uint64_t *__restrict__ keys, const int64_t *d
 
 __global__ void set_last(int32_t *__restrict__ a, const int64_t *d_idx, int32_t v) { a[*d_idx] = v; }
 
+// Every ancestor level of the leaves in one block: for l = L-1 down to 1 the
+// occupied boxes of level l are the distinct keys (child key >> 3) of the
+// sorted boxes of level l+1, in order; each child records its parent's
+// index.  1024 children per round, a ballot-based block scan of the "new
+// parent" flags.  Used when the leaves are few (one block keeps up).
+struct AncArgs {
+    uint64_t *tkey[kMaxLevels + 1];
+    int32_t *tparent[kMaxLevels + 1];
+};
+
+constexpr int kAncThreads = 1024;
+constexpr int64_t kAncMaxLeaves = 65536;
+
+__global__ void __launch_bounds__(kAncThreads) ancestors_small(AncArgs a, int L, int64_t *__restrict__ cnt) {
+    __shared__ int warp_excl[kAncThreads / 32];
+    __shared__ int64_t s_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = cnt[L];
+    for (int l = L - 1; l >= 1; --l) {
+        const uint64_t *ck = a.tkey[l + 1];
+        uint64_t *pk = a.tkey[l];
+        int32_t *par = a.tparent[l + 1];
+        if (tid == 0) s_base = 0;
+        __syncthreads();
+        for (int64_t c0 = 0; c0 < n; c0 += kAncThreads) {
+            const int64_t i = c0 + tid;
+            const bool in = i < n;
+            const uint64_t key = in ? ck[i] >> 3 : 0;
+            const bool nw = in && (i == 0 || (ck[i - 1] >> 3) != key);
+            const unsigned bal = __ballot_sync(0xffffffffu, nw);
+            const int wpre = __popc(bal & ((1u << lane) - 1u));
+            if (lane == 0) warp_excl[warp] = __popc(bal);
+            __syncthreads();
+            if (warp == 0) {
+                const int t = warp_excl[lane];
+                int incl = t;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                warp_excl[lane] = incl - t;
+            }
+            __syncthreads();
+            const int64_t base = s_base;
+            const int64_t e = base + warp_excl[warp] + wpre;   // parents before this child's run start
+            if (nw) pk[e] = key;
+            if (in) par[i] = (int32_t)(nw ? e : e - 1);
+            __syncthreads();
+            if (tid == kAncThreads - 1) s_base = e + (nw ? 1 : 0);
+            __syncthreads();
+        }
+        n = s_base;
+        if (tid == 0) cnt[l] = n;
+        __syncthreads();
+    }
+}
+
 __global__ void obs_local(const double *__restrict__ obs, const int32_t *__restrict__ perm,
                           const uint64_t *__restrict__ okey, int64_t M, Geo g, float *__restrict__ tf,
                           double *__restrict__ td) {
@@ -405,7 +463,7 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
 
     // ---- root geometry: observers' bounding box joined with the grid
     double bb[6];
-    double obs_zlo = 0.0, obs_zhi = 0.0;
+    double obs_zlo = 0.0, obs_zhi = 0.0, obs_lo[3] = {0.0, 0.0, 0.0}, obs_hi[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 3; ++a) {
         bb[a] = gr.origin[a];
         bb[3 + a] = gr.origin[a] + gr.n[a] * F->h;
@@ -427,6 +485,10 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
         }
         obs_zlo = ob[2];
         obs_zhi = ob[5];
+        for (int a = 0; a < 3; ++a) {
+            obs_lo[a] = ob[a];
+            obs_hi[a] = ob[3 + a];
+        }
     }
     int64_t need = 1;
     for (int a = 0; a < 3; ++a) {
@@ -531,10 +593,23 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     FmmLevel &leaf = F->lev[L];
     int64_t ub[kMaxLevels + 1];
     {
+        // boxes of level l that can hold observers: at most M, 8^l, and the
+        // boxes covering the observers' bounding box (leaf indices of its
+        // corners, widened by one against rounding at box faces)
+        int64_t lo_i[3] = {0, 0, 0}, hi_i[3] = {0, 0, 0};
+        const int64_t top = ((int64_t)1 << L) - 1;
+        for (int a = 0; a < 3; ++a) {
+            const double u0 = M > 0 ? floor((obs_lo[a] - F->lo[a]) * F->inv_s) : 0.0;
+            const double u1 = M > 0 ? floor((obs_hi[a] - F->lo[a]) * F->inv_s) : 0.0;
+            lo_i[a] = std::min<int64_t>(top, std::max<int64_t>(0, (int64_t)std::max(-1.0, u0) - 1));
+            hi_i[a] = std::min<int64_t>(top, std::max<int64_t>(0, (int64_t)std::min((double)top + 1.0, u1) + 1));
+        }
         int64_t cap = std::max<int64_t>(M, 1);
         for (int l = L; l >= 0; --l) {
             const int64_t full = (int64_t)1 << std::min(62, 3 * l);
-            cap = std::min(cap, full);
+            int64_t box = 1;
+            for (int a = 0; a < 3; ++a) box *= (hi_i[a] >> (L - l)) - (lo_i[a] >> (L - l)) + 1;
+            cap = std::min(cap, std::min(full, box));
             ub[l] = cap;
         }
     }
@@ -556,11 +631,12 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     }
     set_last<<<1, 1, 0, st>>>(F->leaf_beg, d_cnt + L, (int32_t)M);
     GF_KERNEL_DONE();
+    const bool anc_small = ub[L] <= kAncMaxLeaves;
     for (int l = L - 1; l >= 1; --l) {
         FmmLevel &ch = F->lev[l + 1], &pa = F->lev[l];
         GF_TRY(A.alloc_n(&ch.tparent, ub[l + 1]));
         GF_TRY(A.alloc_n(&pa.tkey, ub[l]));
-        if (M > 0) {
+        if (M > 0 && !anc_small) {
             const int64_t u = ub[l + 1];
             mark_new<<<ceil_div(u, 256), 256, 0, st>>>(ch.tkey, d_cnt + l + 1, 0, u, 3, flags);
             GF_KERNEL_DONE();
@@ -569,6 +645,16 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
                                                           ch.tparent, d_cnt + l);
             GF_KERNEL_DONE();
         }
+    }
+    if (M > 0 && anc_small && L >= 2) {
+        AncArgs aa;
+        memset(&aa, 0, sizeof(aa));
+        for (int l = 1; l <= L; ++l) {
+            aa.tkey[l] = F->lev[l].tkey;
+            aa.tparent[l] = F->lev[l].tparent;
+        }
+        ancestors_small<<<1, kAncThreads, 0, st>>>(aa, L, d_cnt);
+        GF_KERNEL_DONE();
     }
 
     // ---- per level: observer boxes grouped by parity class (M2L order)
