@@ -49,16 +49,21 @@ FP32_TFLOPS_PROBE = 69.6
 MUFU_RSQRT_PROBE = 4.63e12
 
 
-# DRAM traffic per launch of the dominant kernel, from one ncu capture of
-# the default workload (the ncu summaries under profiles/), with the
-# SHA-1 of the kernel's source file at capture time: once the source changes
-# the figure no longer describes the kernel and the bench reports null.
+# DRAM traffic per launch of the dominant kernel, from one ncu capture (the
+# ncu summaries under profiles/), with the SHA-1 of the kernel's source file
+# at capture time: once the source changes the figure no longer describes
+# the kernel and the bench reports null.  The 464^3 figures are captures of
+# the same recipe at 320^3 (the full size holds too much device memory for a
+# multi-pass capture) scaled by the work units of a launch: near pairs for
+# the evaluation (the traffic grows in proportion: a full-size list of the
+# same kernel read 29.4 MB), interaction-list box pairs for the M2L.
 NCU_TRAFFIC = {
-    ("m2l", "grf_volume_128^3", 12): (105652992 + 18162944, "paper_1107_5951_gb300/csrc/gf_m2l.cu",
-                                      "76e737871ad62083f36c560515e8864aa520efad"),
-    # (dram__bytes.sum.per_second x gpu__time_duration.sum of the capture)
-    ("eval", "grf_volume_128^3", 12): (94665216, "paper_1107_5951_gb300/csrc/gf_fmm.cu",
-                                       "87b53e13c240d3512b21aa833b348f6d07156677"),
+    ("eval", "layered_scale_464^3", 11): (round(13978624 * 596922624 / 280629504),
+                                          "paper_1107_5951_gb300/csrc/gf_fmm.cu",
+                                          "5cedea733d9acbcc59b824709d6afedfd0051c94"),
+    ("m2l", "layered_scale_464^3", 11): (round((25330432 + 8960) * 1125279 / 510295),
+                                         "paper_1107_5951_gb300/csrc/gf_m2l.cu",
+                                         "1c1dcde692396f46cbf2eacedf368f8727af01d2"),
 }
 
 
@@ -280,10 +285,17 @@ def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4):
                     else "m2l_simt (all levels)")}
     if nvox is not None and L >= 2:
         ns = {l: level_boxes(info, l) for l in range(2, L + 1)}
-        work["p2m"] = ("hbm", float(nvox * rho_bytes + ns[L] * K * fbytes),
-                       "block_rows + m2l_tc P2M kind" if tensor else "p2m_fused")
-        work["m2m"] = ("hbm", float(sum(ns[l] * K * fbytes for l in range(3, L + 1))
-                                    + sum(ns[l] * K * fbytes for l in range(2, L))),
+        # mixed precision on the tensor cores with L - 1 > 2: the P2M stage
+        # makes level L-1 straight from the densities (its essential traffic:
+        # the densities once, those expansions once) and the M2M stage starts
+        # from level L-1
+        up = tensor and L - 1 > 2
+        top = L - 1 if up else L
+        work["p2m"] = ("hbm", float(nvox * rho_bytes + ns[top] * K * fbytes),
+                       "block_rows + m2l_tc P2M kinds (into level L-1 from the grid)" if up
+                       else ("block_rows + m2l_tc P2M kind" if tensor else "p2m_fused"))
+        work["m2m"] = ("hbm", float(sum(ns[l] * K * fbytes for l in range(3, top + 1))
+                                    + sum(ns[l] * K * fbytes for l in range(2, top))),
                        "m2l_tc M2M kind + m2m_kernel (FP64 into level 2)" if tensor else "xlate_simt")
     dom = max(work, key=lambda k: stages.get(k, 0.0))
     bound, amount, kern = work[dom]

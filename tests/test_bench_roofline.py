@@ -15,12 +15,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-INFO = SimpleNamespace(K=169, near_pairs=3691610112, m2l_pairs=6039504)
+INFO = SimpleNamespace(K=144, near_pairs=596922624, m2l_pairs=1125279)
 PEAKS = {"bf16_tflops": 1870.7, "sm_max_mhz": 2070.0}
-WORKLOAD = "grf_volume_128^3"
+WORKLOAD = "layered_scale_464^3"
 
 
-def args(precision="mixed", p=12, m2l="auto"):
+def args(precision="mixed", p=11, m2l="auto"):
     return argparse.Namespace(precision=precision, p=p, m2l=m2l)
 
 
@@ -28,7 +28,7 @@ def captured(stage):
     """The table's traffic while the kernel's source still has the captured
     SHA-1, else None."""
     import hashlib
-    nbytes, src, sha = bench.NCU_TRAFFIC[(stage, WORKLOAD, 12)]
+    nbytes, src, sha = bench.NCU_TRAFFIC[(stage, WORKLOAD, 11)]
     with open(os.path.join(ROOT, src), "rb") as f:
         return nbytes if hashlib.sha1(f.read()).hexdigest() == sha else None
 
@@ -46,7 +46,7 @@ def test_tensor_core_m2l_dominant():
     r = bench.fmm_roofline({"eval": 1.0, "m2l": 1.25}, INFO, args(), PEAKS, WORKLOAD)
     assert r["stage"] == "m2l" and r["bound"] == "tensor"
     assert r["peak"] == pytest.approx(1870.7 * bench.F16_PER_BF16)
-    assert r["achieved"] == pytest.approx(2.0 * 169 * 169 * INFO.m2l_pairs / 1.25e-3 / 1e12)
+    assert r["achieved"] == pytest.approx(2.0 * 144 * 144 * INFO.m2l_pairs / 1.25e-3 / 1e12)
     assert r["traffic"] == captured("m2l")
 
 
@@ -57,7 +57,7 @@ def test_traffic_only_for_the_captured_configuration():
 
 
 def test_traffic_dropped_when_the_source_changes(monkeypatch):
-    key = ("eval", WORKLOAD, 12)
+    key = ("eval", WORKLOAD, 11)
     nbytes, src, _ = bench.NCU_TRAFFIC[key]
     monkeypatch.setitem(bench.NCU_TRAFFIC, key, (nbytes, src, "0" * 40))
     assert bench.fmm_roofline({"eval": 1.3, "m2l": 1.0}, INFO, args(), PEAKS, WORKLOAD)["traffic"] is None
@@ -86,20 +86,21 @@ def scale_info():
 
 def test_hbm_bound_upward_sweep_dominant():
     """When the P2M (or M2M) stage dominates, the roofline is HBM-bound:
-    densities read once plus leaf expansions written once (children read once
-    plus parents written once), in GB/s against the measured copy rate."""
+    densities read once plus the level L-1 expansions (made straight from
+    them) written once; children read once plus parents written once from
+    level L-1 up; in GB/s against the measured copy rate."""
     info = scale_info()
     peaks = dict(PEAKS, hbm_gbs=6700.0)
     r = bench.fmm_roofline({"eval": 0.4, "m2l": 0.5, "p2m": 0.8, "m2m": 0.7}, info, args(p=11), peaks,
                            "layered_scale_464^3", nvox=464 ** 3, rho_bytes=4)
     assert r["stage"] == "p2m" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    want = 464 ** 3 * 4 + 116 ** 3 * 144 * 4
+    want = 464 ** 3 * 4 + 58 ** 3 * 144 * 4      # densities once, level-6 expansions once
     assert r["achieved"] == pytest.approx(want / 0.8e-3 / 1e9)
     assert r["peak"] == 6700.0 and r["frac"] == pytest.approx(r["achieved"] / 6700.0)
     r = bench.fmm_roofline({"eval": 0.4, "m2l": 0.5, "p2m": 0.6, "m2m": 0.7}, info, args(p=11), peaks,
                            "layered_scale_464^3", nvox=464 ** 3, rho_bytes=4)
     ns = {l: (-(-116 // (1 << (7 - l)))) ** 3 for l in range(2, 8)}
-    want = sum(ns[l] for l in range(3, 8)) * 144 * 4 + sum(ns[l] for l in range(2, 7)) * 144 * 4
+    want = sum(ns[l] for l in range(3, 7)) * 144 * 4 + sum(ns[l] for l in range(2, 6)) * 144 * 4
     assert r["stage"] == "m2m" and r["achieved"] == pytest.approx(want / 0.7e-3 / 1e9)
 
 

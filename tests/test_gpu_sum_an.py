@@ -2,7 +2,8 @@
 form, Sec. 2.1) against the FP64 CPU oracle's per-voxel closed-form sum and
 its transpose, element by element, and against the prism formula that
 Table 10 pins.  The kernels regroup the voxels' corners onto the corner
-lattice, so agreement is to rounding, not bit for bit: bar 1e-11."""
+lattice, so agreement is to rounding, not bit for bit: bar 1e-12 (the
+direct-mode FP64 bar; measured 1e-15 to 9e-14)."""
 import numpy as np
 import pytest
 
@@ -14,7 +15,7 @@ from oracle import direct  # noqa: E402
 from paper_1107_5951_gb300 import workloads as wl  # noqa: E402
 
 DEV = "cuda:0"
-TOL = 1e-11
+TOL = 1e-12
 
 
 def rel_l2(a, b):
@@ -47,6 +48,7 @@ def test_sum_an_forward_matches_oracle(n, n_obs, B):
         torch.cuda.synchronize()
         plan.check()
         g, gz = g.cpu().numpy(), gz.cpu().numpy()
+    print("SUM-AN forward %s rel L2 %.3e" % (n, rel_l2(g, ref)))
     assert rel_l2(g, ref) <= TOL
     assert np.array_equal(gz, g[..., 2])
 
@@ -60,6 +62,7 @@ def test_sum_an_adjoint_matches_oracle(ncomp):
     ref = direct.adjoint_analytic(n, origin, h, obs, r, 0.3, ncomp=ncomp)
     with _plan(n, origin, h, obs, 2) as plan:
         grad = plan.adjoint(torch.tensor(r, device=DEV), ncomp=ncomp).cpu().numpy()
+    print("SUM-AN transpose ncomp=%d rel L2 %.3e" % (ncomp, rel_l2(grad, ref)))
     assert rel_l2(grad, ref) <= TOL
 
 
@@ -79,4 +82,5 @@ def test_sum_an_prism_model_is_the_closed_form():
     with _plan(n, origin, h, obs, 1) as plan:
         _, gz = plan.forward(torch.tensor(rho, device=DEV), want_g=False, want_gz=True)
         gz = gz.cpu().numpy()
-    assert rel_l2(gz, ref) <= 1e-10
+    print("SUM-AN prism model rel L2 %.3e" % rel_l2(gz, ref))
+    assert rel_l2(gz, ref) <= 1e-12
