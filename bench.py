@@ -110,6 +110,9 @@ def parse_args():
     ap.add_argument("--sample-obs", type=int, default=8192,
                     help="observers in the oracle's bounded sample")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--parallel", default="replicas", choices=["replicas", "sources"],
+                    help="N > 1: independent replicas (weak scaling), or one solve with the sources "
+                         "split over the ranks and one sum all-reduce of the field (strong scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -199,6 +202,15 @@ def barrier(world):
         torch.distributed.barrier()
 
 
+def sum_over_ranks(t, world):
+    """Sum a tensor over the ranks in place (the one exchange of a
+    source-partitioned solve: each rank holds its sources' field)."""
+    if world > 1:
+        import torch
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return t
+
+
 def job_rate(units_per_rank, world, seconds):
     """Whole-job throughput: every rank processed units_per_rank in at most
     `seconds` (replicas, weak scaling)."""
@@ -226,10 +238,11 @@ def workload_p(args):
     return args.p if args.p else DEFAULT_P.get(args.workload, 12)
 
 
-def workload_config(wk, world):
+def workload_config(wk, world, parallel="replicas"):
     """The workload as both arms name it (identical dicts)."""
+    par = "single" if world <= 1 else ("replicas" if parallel == "replicas" else "source_parts")
     return {"workload": wk.name, "N_sources": int(wk.n_sources), "M_observers": int(wk.n_obs),
-            "rel_err_bar": REL_ERR_BAR, "parallelism": "replicas" if world > 1 else "single",
+            "rel_err_bar": REL_ERR_BAR, "parallelism": par,
             "l2_flush": "GPU arm: a 256 MiB buffer is written between timed steps; host arm: n/a"}
 
 
@@ -360,7 +373,7 @@ def bench_reference(args, rank, world):
             "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wk, world),
+            "config": workload_config(wk, world, args.parallel),
             "method": {"impl": "FP64 direct sum on the host cores (the oracle)"},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -410,10 +423,15 @@ def bench_gf(args, rank, world):
     rho_d = torch.tensor(wk.rho, dtype=rho_dtype, device=dev)
     g_d = torch.empty((M, 3), dtype=torch.float64, device=dev)
 
+    parts = world > 1 and args.parallel == "sources"
+
     def make_plan(precision=args.precision, pp=p, obs=obs_d):
-        return pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs, mode=mode,
-                        precision=precision, p=pp, leaf_vox=args.leaf_vox, G=wk.G,
-                        stream=stream, m2l=args.m2l)
+        pl = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs, mode=mode,
+                      precision=precision, p=pp, leaf_vox=args.leaf_vox, G=wk.G,
+                      stream=stream, m2l=args.m2l)
+        if parts:
+            pl.set_source_part(rank, world)
+        return pl
 
     try:
         probe = make_plan()
@@ -432,6 +450,8 @@ def bench_gf(args, rank, world):
         with torch.cuda.stream(stream):
             plan = make_plan()
             plan.forward(rho_d, g=g_d, stream=stream)
+            if parts:
+                sum_over_ranks(g_d, world)   # NCCL on the forward's stream
             plan.close()
 
     for _ in range(args.warmup):
@@ -455,11 +475,17 @@ def bench_gf(args, rank, world):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     torch.cuda.synchronize()
     tot_ms = max_over_ranks(float(sum(step_ms)), world, dev)
-    value = job_rate(units * args.steps, world, tot_ms * 1e-3)
+    # replicas: every rank solves the whole problem; source parts: the ranks
+    # share one problem
+    value = job_rate(units * args.steps, 1 if parts else world, tot_ms * 1e-3)
 
     # warm forward with the plan built; per-stage device times
     plan = make_plan()
     fwd_ms = timed_forwards(plan, rho_d, g_d, stream, flush, args.steps)
+    if parts:
+        with torch.cuda.stream(stream):
+            sum_over_ranks(g_d, world)
+        torch.cuda.synchronize()
     g_main = g_d.cpu().numpy()
     plan.set_timing(True)
     stage_runs = []
@@ -476,7 +502,7 @@ def bench_gf(args, rank, world):
     # the plain FP64 FMM on the same GPU, and the mixed form at lower degrees
     compare = {}
     sampled = {}
-    if mode == "fmm" and not args.no_compare:
+    if mode == "fmm" and not args.no_compare and not parts:
         rho64 = rho_d.double() if args.precision == "mixed" else rho_d
         pf = FP64_P.get(args.workload, 14)
         with make_plan("fp64", pf) as pl:
@@ -500,7 +526,7 @@ def bench_gf(args, rank, world):
     idx = oracle_sample(wk, args)
     cpu = None
     rel_err = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and (world == 1 or parts) and not args.no_cpu_baseline:
         ref, dt, cores = run_cpu_oracle(wk, idx)
         nref = np.linalg.norm(ref)
         rel_err = float(np.linalg.norm(g_main[idx] - ref) / nref)
@@ -547,6 +573,8 @@ def bench_gf(args, rank, world):
                 rho_e.copy_(rho_h, non_blocking=True)
                 pl = make_plan(obs=obs_e)
                 pl.forward(rho_e, g=g_d, stream=stream)
+                if parts:
+                    sum_over_ranks(g_d, world)
                 g_h.copy_(g_d, non_blocking=True)
                 pl.close()
             b.record(stream)
@@ -554,7 +582,7 @@ def bench_gf(args, rank, world):
                 e_ev.append((a, b))
         torch.cuda.synchronize()
         e_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in e_ev])), world, dev)
-        e2e = {"value": job_rate(units, world, e_ms * 1e-3), "unit": "interactions/s",
+        e2e = {"value": job_rate(units, 1 if parts else world, e_ms * 1e-3), "unit": "interactions/s",
                "h2d_bytes_per_step": int(obs_h.numel() * 8 + rho_h.numel() * rho_h.element_size()),
                "d2h_bytes_per_step": int(g_h.numel() * 8), "ms_per_step": e_ms}
 
@@ -562,10 +590,11 @@ def bench_gf(args, rank, world):
         return
     line = {"metric": "effective interactions/s", "value": value, "unit": "interactions/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if parts else "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": workload_config(wk, world),
+            "config": workload_config(wk, world, args.parallel),
             "method": {"mode": mode, "precision": args.precision, "p": p if mode == "fmm" else None,
                        "m2l": args.m2l,
                        "leaf_vox": int(plan_info.leaf_vox) if mode == "fmm" else None,

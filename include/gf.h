@@ -259,6 +259,28 @@ gf_status gf_server_stats_get(gf_server_t server, gf_server_stats *stats);
 /* Wait for all requests, then release every resident plan and stream. */
 gf_status gf_server_destroy(gf_server_t server);
 
+/*
+ * gf_plan_set_source_part -- restrict a FMM plan's forward to one part of
+ * its sources, for a source-partitioned solve over several devices.  Eq. 1
+ * is linear in the sources, so the field is the sum over parts of each
+ * part's field, as the summation method of Sec. 2.1 splits the voxels over
+ * processes and sums the station vector; one sum all-reduce of the outputs
+ * of the nparts plans (one per device, each with its own part) gives the
+ * whole field.
+ *   part, nparts : 0 <= part < nparts <= 64; nparts = 1 restores all sources
+ *   code_lo, code_hi : if not NULL, receive the part as a range [lo, hi) of
+ *                  Morton codes (x -> bit 0, y -> bit 1, z -> bit 2 per level)
+ *                  of the 64 boxes of octree level 2
+ * A part is a range of level-2 boxes (every box of level 2 and deeper lies
+ * under exactly one of them), cut so that the parts hold nearly equal
+ * numbers of grid voxels.  The plan's near field and M2L then skip the
+ * source boxes of the other parts.  FMM mode only (GF_ERR_UNSUPPORTED in
+ * direct mode); gf_adjoint of a partitioned plan returns GF_ERR_UNSUPPORTED.
+ * Host-side only: enqueues nothing.
+ */
+gf_status gf_plan_set_source_part(gf_plan_t plan, int32_t part, int32_t nparts, int32_t *code_lo,
+                                  int32_t *code_hi);
+
 /* Release a plan and everything it owns (waits for its device work). */
 gf_status gf_plan_destroy(gf_plan_t plan);
 

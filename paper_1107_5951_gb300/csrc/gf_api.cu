@@ -9,6 +9,7 @@
 #include <atomic>
 #include <new>
 
+#include "gf_fmm.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -330,11 +331,73 @@ gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp, int32_t
         return GF_ERR_INVALID_ARG;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->part_lo != 0 || plan->part_hi < 64) {
+        set_error("gf_adjoint of a plan restricted to a source part is not implemented");
+        return GF_ERR_UNSUPPORTED;
+    }
     if (plan->opt.mode == GF_MODE_DIRECT) {
         if (plan->opt.reserved0 & GF_FLAG_SUM_AN) return sum_an_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
         return direct_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
     }
     return fmm_adjoint(plan, r_dev, ncomp, B, grad_dev, st);
+}
+
+gf_status gf_plan_set_source_part(gf_plan_t plan, int32_t part, int32_t nparts, int32_t *code_lo,
+                                  int32_t *code_hi) {
+    if (!plan) {
+        set_error("plan is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (nparts < 1 || nparts > 64 || part < 0 || part >= nparts) {
+        set_error("need 0 <= part < nparts <= 64 (part = %d, nparts = %d)", part, nparts);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (plan->opt.mode != GF_MODE_FMM || !plan->fmm) {
+        set_error("source parts are implemented for FMM plans only");
+        return GF_ERR_UNSUPPORTED;
+    }
+    const FmmPlan *F = plan->fmm;
+    // grid voxels under each level-2 box, by Morton code
+    const int64_t side = (int64_t)F->b << (F->L - 2);   // level-2 box edge in voxels
+    double w[64];
+    double total = 0.0;
+    for (uint32_t c = 0; c < 64; ++c) {
+        const int64_t bx = (c & 1) | ((c >> 2) & 2), by = ((c >> 1) & 1) | ((c >> 3) & 2),
+                      bz = ((c >> 2) & 1) | ((c >> 4) & 2);
+        const int64_t bc[3] = {bx, by, bz};
+        double n = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t v0 = std::max<int64_t>(0, bc[a] * side - F->voff[a]);
+            const int64_t v1 = std::min<int64_t>(plan->grid.n[a], (bc[a] + 1) * side - F->voff[a]);
+            n *= (double)std::max<int64_t>(0, v1 - v0);
+        }
+        w[c] = n;
+        total += n;
+    }
+    // part k takes the codes whose cumulative count (up to the code's
+    // middle) falls in [k / nparts, (k + 1) / nparts) of the total
+    uint32_t lo = 64, hi = 0;
+    double cum = 0.0;
+    for (uint32_t c = 0; c < 64; ++c) {
+        const double mid = cum + 0.5 * w[c];
+        cum += w[c];
+        int k = total > 0.0 ? (int)(mid / total * nparts) : 0;
+        k = std::min(nparts - 1, std::max(0, k));
+        if (k == part) {
+            lo = std::min(lo, c);
+            hi = std::max(hi, c + 1);
+        }
+    }
+    if (lo >= hi) lo = hi = 0;   // an empty part
+    if (nparts == 1) {
+        lo = 0;
+        hi = 64;
+    }
+    plan->part_lo = lo;
+    plan->part_hi = hi;
+    if (code_lo) *code_lo = (int32_t)lo;
+    if (code_hi) *code_hi = (int32_t)hi;
+    return GF_OK;
 }
 
 gf_status gf_plan_check(gf_plan_t plan, void *stream) {

@@ -690,6 +690,8 @@ inline __host__ __device__ int eval_slice(int P2, int tsize) {
 }
 
 struct EvalArgs {
+    int L;                       // leaf level
+    uint32_t part_lo, part_hi;   // source partition (in_source_part)
     const int4 *items;
     int64_t n_items;
     const uint64_t *tkey;      // leaf keys
@@ -817,7 +819,8 @@ eval_kernel(EvalArgs a) {
         if (lane < 27) {
             const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
             const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1], sz = lc[2] + dz - a.blk.lo[2];
-            const bool in = sx >= 0 && sy >= 0 && sz >= 0 && sx < a.blk.n[0] && sy < a.blk.n[1] && sz < a.blk.n[2];
+            const bool in = sx >= 0 && sy >= 0 && sz >= 0 && sx < a.blk.n[0] && sy < a.blk.n[1] && sz < a.blk.n[2] &&
+                            in_source_part(lc[0] + dx, lc[1] + dy, lc[2] + dz, a.L - 2, a.part_lo, a.part_hi);
             nbl[lane] = in ? (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx : -1;
         }
         __syncwarp();
@@ -1463,6 +1466,9 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     // a7-a9: near field + L2P + combine + scatter
     if (F->n_items > 0) {
         EvalArgs a;
+        a.L = F->L;
+        a.part_lo = plan->part_lo;
+        a.part_hi = plan->part_hi;
         a.items = F->items;
         a.n_items = F->n_items;
         a.tkey = F->lev[L].tkey;

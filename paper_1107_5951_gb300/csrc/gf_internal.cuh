@@ -89,6 +89,9 @@ struct gf_plan_s {
     int *d_status = nullptr;     // device-side check word
     size_t device_bytes = 0;
     int64_t near_pairs = 0, m2l_pairs = 0;
+    // FMM source partition: only the sources whose level-2 ancestor box has
+    // a Morton code in [part_lo, part_hi) contribute (all: [0, 64))
+    uint32_t part_lo = 0, part_hi = 64;
     bool counts_done = false;    // FMM work counts computed (on first info request)
     bool timing = false;
     cudaEvent_t ev[GF_NUM_STAGES + 1] = {};
@@ -143,6 +146,18 @@ gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *k
 size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt);
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Whether box (X, Y, Z) of level 2 + shift (absolute box coordinates) lies
+// under a level-2 box whose Morton code (x -> bit 0, y -> bit 1, z -> bit 2
+// per level) is in [lo, hi).  Boxes of level 2 and deeper never straddle a
+// level-2 box, so a range of codes partitions the sources of every level.
+__host__ __device__ __forceinline__ bool in_source_part(int64_t X, int64_t Y, int64_t Z, int shift, uint32_t lo,
+                                                        uint32_t hi) {
+    if (lo == 0 && hi >= 64) return true;
+    const uint32_t x = (uint32_t)(X >> shift) & 3u, y = (uint32_t)(Y >> shift) & 3u, z = (uint32_t)(Z >> shift) & 3u;
+    const uint32_t c = (x & 1u) | ((y & 1u) << 1) | ((z & 1u) << 2) | ((x & 2u) << 2) | ((y & 2u) << 3) | ((z & 2u) << 4);
+    return c >= lo && c < hi;
+}
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory.
 template <class Kern>

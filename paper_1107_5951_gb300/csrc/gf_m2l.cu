@@ -186,6 +186,8 @@ struct M2LArgs {
     int adj;           // adjoint: columns are source boxes, inputs via imap
     const int32_t *imap;
     int64_t mlo[3], mn[3];
+    int shift;                   // level - 2
+    uint32_t part_lo, part_hi;   // source partition (forward)
 };
 
 constexpr int kCK = 32;  // input components per shared-memory chunk
@@ -282,7 +284,8 @@ m2l_simt(M2LArgs a) {
             if (slot < a.nbox && tbox[slot] >= 0) {
                 const int64_t sx = tc[slot][0] + dx, sy = tc[slot][1] + dy, sz = tc[slot][2] + dz;
                 if (!a.adj) {
-                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < a.bn[0] && sy < a.bn[1] && sz < a.bn[2])
+                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < a.bn[0] && sy < a.bn[1] && sz < a.bn[2] &&
+                        in_source_part(sx + a.blo[0], sy + a.blo[1], sz + a.blo[2], a.shift, a.part_lo, a.part_hi))
                         row = (((sz * a.bn[1] + sy) * a.bn[0] + sx) * B + bb) * a.ldk;
                 } else {
                     const int64_t wx = sx + a.blo[0] - a.mlo[0], wy = sy + a.blo[1] - a.mlo[1],
@@ -565,6 +568,7 @@ struct TcLevel {
     const uint32_t *amax;        // M2L: largest |input| of the level (float bits)
     const unsigned char *split;  // M2L: the level's inputs split into scaled FP16 parts
     int64_t tfirst;              // P2M: index of the first leaf of the targets
+    int shift;                   // M2L: level - 2 (source partition test)
     // P2M into level L-1 reading the density grid itself (TcArgs::grid): grid
     // voxel (i, j, k) of leaf (x, y, z) is i = gb x - goff[0] + (voxel in the
     // leaf), likewise j, k; leaves lie wholly inside or outside the grid
@@ -584,6 +588,7 @@ struct TcArgs {
     const float *cs;            // M2L: column scales of the image ([Npad] scale, [Npad] inverse)
     int *status;
     long wait_tries;            // bound of every barrier wait (kWaitTries)
+    uint32_t part_lo, part_hi;  // M2L forward: source partition (in_source_part)
     int test_stall;             // testing aid: the MMA issuer first waits on a barrier that
                                 // nothing completes, so the bounded-wait failure path runs
     // M2M kind over leaf masses taken straight from the FP32 density grid:
@@ -859,7 +864,8 @@ m2l_tc(TcArgs a) {
         const int cls = pc.cls;
         const int64_t sx = tc0 + c_il[cls][oi][0], sy = tc1 + c_il[cls][oi][1], sz = tc2 + c_il[cls][oi][2];
         if (!qadj) {
-            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < qbn0 && sy < qbn1 && sz < qbn2)
+            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < qbn0 && sy < qbn1 && sz < qbn2 &&
+                in_source_part(sx + L.blo[0], sy + L.blo[1], sz + L.blo[2], L.shift, a.part_lo, a.part_hi))
                 return (((sz * qbn1 + sy) * qbn0 + sx) * B + bb) * a.ldin;
             return -1;
         }
@@ -1298,6 +1304,7 @@ gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
             for (int c = 0; c <= 8; ++c) t.cls_off[c] = adj ? F->scls_off[l][c] : lv.cls_off[c];
             t.amax = F->tc_amax + (adj ? kMaxLevels + 1 : 0) + l;
             t.split = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l);
+            t.shift = l - 2;
         }
         std::vector<unsigned char> &hb = adj ? F->tc_levels_adj_host : F->tc_levels_host;
         void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
@@ -1334,6 +1341,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
             for (int c = 0; c <= 8; ++c) t.cls_off[c] = adj ? F->scls_off[l][c] : lv.cls_off[c];
             t.amax = F->tc_amax + (adj ? kMaxLevels + 1 : 0) + l;
             t.split = (adj ? F->tc_split_adj : F->tc_split) + split_offset(F, adj, l);
+            t.shift = l - 2;
         }
         std::vector<unsigned char> &hb = adj ? F->tc_levels_adj_host : F->tc_levels_host;
         void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
@@ -1548,6 +1556,8 @@ TcArgs tc_args(gf_plan_s *plan, int B) {
     a.ldin = F->KS;
     a.status = plan->d_status;
     a.wait_tries = kWaitTries;
+    a.part_lo = 0;
+    a.part_hi = 64;
     return a;
 }
 
@@ -1562,6 +1572,8 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     a.nck = T->tc_nck_h;
     a.img = (const unsigned char *)(adj ? T->am2l_tc : T->m2l_tc);
     a.cs = adj ? T->am2l_cs : T->m2l_cs;
+    a.part_lo = adj ? 0u : plan->part_lo;
+    a.part_hi = adj ? 64u : plan->part_hi;
     if (plan->opt.reserved0 & GF_FLAG_TEST_WAIT_TIMEOUT) {
         a.test_stall = 1;
         a.wait_tries = kTestWaitTries;
@@ -1708,6 +1720,9 @@ gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st
     a.order = lv.m2l_order;
     a.adj = adj ? 1 : 0;
     a.imap = F->imap[level];
+    a.shift = level - 2;
+    a.part_lo = adj ? 0u : plan->part_lo;
+    a.part_hi = adj ? 64u : plan->part_hi;
     int64_t maxc = 0;
     for (int c = 0; c <= 8; ++c) a.cls_off[c] = adj ? F->scls_off[level][c] : lv.cls_off[c];
     for (int c = 0; c < 8; ++c) maxc = std::max<int64_t>(maxc, a.cls_off[c + 1] - a.cls_off[c]);

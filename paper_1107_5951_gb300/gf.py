@@ -123,6 +123,7 @@ def load(build_if_missing: bool = True):
                                                  ctypes.c_double, _vp, _vp, _vp]
         lib.gf_direct_forward_static.restype = ctypes.c_int
         lib.gf_plan_set_timing.argtypes = [_vp, i32]
+        lib.gf_plan_set_source_part.argtypes = [_vp, i32, i32, P(i32), P(i32)]
         lib.gf_plan_stage_times.argtypes = [_vp, P(ctypes.c_double)]
         lib.gf_server_create.argtypes = [P(gf_server_options), P(_vp)]
         lib.gf_server_submit.argtypes = [_vp, P(gf_request), P(i64)]
@@ -131,7 +132,7 @@ def load(build_if_missing: bool = True):
         lib.gf_server_destroy.argtypes = [_vp]
         for name in ("gf_plan_create", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
                      "gf_plan_bytes", "gf_plan_get_info", "gf_plan_export_tree", "gf_plan_set_timing",
-                     "gf_plan_stage_times", "gf_server_create", "gf_server_submit", "gf_server_wait",
+                     "gf_plan_stage_times", "gf_plan_set_source_part", "gf_server_create", "gf_server_submit", "gf_server_wait",
                      "gf_server_stats_get", "gf_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         lib.gf_last_error.argtypes = []
@@ -205,6 +206,14 @@ def gf_plan_export_tree(plan: int, level: int, perm_ptr=None, keys_ptr=None, box
                         ilist_ptr=None, near_ptr=None):
     _check(load().gf_plan_export_tree(_vp(plan), level, _vp(perm_ptr), _vp(keys_ptr),
                                       _vp(box_keys_ptr), _vp(ilist_ptr), _vp(near_ptr)))
+
+
+def gf_plan_set_source_part(plan: int, part: int, nparts: int):
+    """Restrict a FMM plan's forward to source part `part` of `nparts`;
+    returns the part's range [lo, hi) of level-2 Morton codes."""
+    lo, hi = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().gf_plan_set_source_part(_vp(plan), int(part), int(nparts), ctypes.byref(lo), ctypes.byref(hi)))
+    return int(lo.value), int(hi.value)
 
 
 def gf_plan_set_timing(plan: int, enable: bool):
@@ -435,6 +444,12 @@ class Plan:
 
     def check(self, stream=None):
         gf_plan_check(self.handle, _stream_handle(stream))
+
+    def set_source_part(self, part, nparts):
+        """Restrict the forward to source part `part` of `nparts` (one
+        device's share of a source-partitioned solve); the sum of the parts'
+        fields is the whole field.  Returns the level-2 Morton range."""
+        return gf_plan_set_source_part(self.handle, part, nparts)
 
     def export_tree(self, level):
         """Host copies of the observer order, leaf keys, occupied boxes of

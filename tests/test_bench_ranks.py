@@ -53,11 +53,45 @@ def test_max_over_two_gloo_ranks_and_job_rate():
     assert res[0][2] == pytest.approx(2 * 1.0e9 / 0.25)
 
 
+def _sum_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # each rank holds the field of its own part of the sources
+        part = torch.arange(6, dtype=torch.float64).reshape(2, 3) * (rank + 1) + 0.25 * rank
+        bench.sum_over_ranks(part, world)
+        out.put((rank, part.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_source_parts_are_summed_over_two_gloo_ranks():
+    """The one exchange of a source-partitioned solve: a sum all-reduce of
+    the ranks' partial fields, every rank ending with the whole field."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_sum_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    want = (torch.arange(6, dtype=torch.float64).reshape(2, 3) * 3 + 0.25).tolist()
+    assert res[0][1] == want and res[1][1] == want
+
+
 def test_single_rank_helpers_need_no_process_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.job_rate(10.0, 1, 2.0) == 5.0
+    t = torch.ones(3)
+    assert bench.sum_over_ranks(t, 1) is t and t.tolist() == [1.0, 1.0, 1.0]
 
 
 def test_reference_arm_as_two_ranks_prints_one_line():
