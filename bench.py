@@ -120,8 +120,8 @@ def parse_args():
     ap.add_argument("--workload", default="scale", choices=["volume", "scale", "serving", "adjoint", "sum_an"],
                     help="scale (default): 464^3 layered model, 1024^2 stations; volume: 128^3 random "
                          "field, stations + voxel centres; serving: a stream of uneven requests; adjoint: misfit "
-                         "gradients of 16 models at 256^2 stations; sum_an: the 16^3 prism model with "
-                         "every voxel integrated in closed form (direct, FP64)")
+                         "gradients of 16 models at 256^2 stations; sum_an: voxels integrated in closed form "
+                         "(FMM: 128^3 random field at 512^2 stations; --mode direct: the 16^3 prism model)")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests on the device at once")
     ap.add_argument("--rate", type=float, default=0.0,
@@ -221,7 +221,7 @@ def job_rate(units_per_rank, world, seconds):
 # Expansion degree per workload: the headline runs the mixed-precision FMM at
 # a degree whose sampled error stays below the metric's 1e-6 with margin, and
 # the plain FP64 FMM beside it at the smallest degree that meets 1e-6.
-DEFAULT_P = {"scale": 11, "volume": 12}
+DEFAULT_P = {"scale": 11, "volume": 12, "sum_an": 12}
 FP64_P = {"scale": 10, "volume": 14}
 SWEEP_P = (4, 6, 8)
 REL_ERR_BAR = 1e-6
@@ -700,10 +700,13 @@ def bench_adjoint(args, rank, world):
 
 # ------------------------------------------------------------------ SUM-AN
 def bench_sum_an(args, rank, world):
-    """SUM-AN in direct mode (FP64): every voxel of the 16^3 prism-plus-noise
-    model (1 km voxels) integrated in closed form at the 64^2 stations 100 m
-    above it.  One step = one forward (corner-lattice weights + the sum over
-    the corner lattice).  Unit of work: a (voxel, observer) pair."""
+    """SUM-AN: every voxel integrated in closed form (Sec. 2.1).  FMM mode
+    (default): the 128^3 random-field model of 250 m voxels at 512^2 surface
+    stations, mixed precision, the voxels next to each station in closed
+    form, the far field from exact voxel moments.  Direct mode (--mode
+    direct): the 16^3 prism model (1 km voxels) at the 64^2 stations 100 m
+    above it, every (voxel, station) pair in closed form, FP64.  One step =
+    one forward.  Unit of work: a (voxel, observer) pair."""
     import torch
 
     import paper_1107_5951_gb300 as pkg
@@ -713,14 +716,21 @@ def bench_sum_an(args, rank, world):
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wk = wl.fp64_prism_noise(1)
+    fmm = args.mode != "direct"
+    if fmm:
+        wk = wl.grf_volume(n=args.side or 128, stations=args.stations or 512, volume_targets=False)
+        precision, p = args.precision, workload_p(args)
+    else:
+        wk = wl.fp64_prism_noise(1)
+        precision, p = "fp64", 8
     nvox, M = int(np.prod(wk.grid.n)), wk.n_obs
     stream = torch.cuda.Stream(device=dev)
     obs_d = torch.tensor(wk.obs, dtype=torch.float64, device=dev)
-    rho_d = torch.tensor(wk.rho, dtype=torch.float64, device=dev)
+    rdt = torch.float32 if precision == "mixed" else torch.float64
+    rho_d = torch.tensor(wk.rho, dtype=rdt, device=dev)
     g_d = torch.empty((M, 3), dtype=torch.float64, device=dev)
-    plan = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode="direct", precision="fp64",
-                    G=wk.G, stream=stream, voxels="closed_form")
+    plan = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs_d, mode="fmm" if fmm else "direct",
+                    precision=precision, p=p, G=wk.G, stream=stream, voxels="closed_form")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -746,30 +756,41 @@ def bench_sum_an(args, rank, world):
     launches = pkg.gf_launch_count() - launches0
     clk = clocks.stop()
     ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+    stages = None
+    if fmm:
+        plan.set_timing(True)
+        plan.forward(rho_d, g=g_d, stream=stream)
+        stages = plan.stage_times()
+        plan.set_timing(False)
     units = float(nvox) * M
     err, cpu = None, None
     if rank == 0 and not args.no_cpu_baseline:
         rng = np.random.default_rng(29)
-        idx = np.sort(rng.choice(M, 256, replace=False))
+        idx = np.sort(rng.choice(M, 64 if fmm else 256, replace=False))
+        rho64 = np.asarray(wk.rho, dtype=np.float32 if precision == "mixed" else np.float64).astype(np.float64)
         t1 = time.perf_counter()
-        want = direct.forward_analytic(wk.grid.n, wk.grid.origin, wk.grid.h, wk.rho, wk.obs[idx], wk.G)
+        want = direct.forward_analytic(wk.grid.n, wk.grid.origin, wk.grid.h, rho64, wk.obs[idx], wk.G)
         dt = time.perf_counter() - t1
         got = g_d.cpu().numpy()[idx]
         err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
         cpu = {"value": nvox * len(idx) / dt, "unit": "interactions/s", "cores": direct.max_threads(),
-               "kind": "oracle", "sample": "256 seeded stations of %d x all %d voxels (%.1f s)" % (M, nvox, dt)}
+               "kind": "oracle", "sample": "%d seeded stations of %d x all %d voxels in closed form (%.1f s)"
+               % (len(idx), M, nvox, dt)}
     plan.close()
     if rank != 0:
         return
     line = {"metric": "effective interactions/s (SUM-AN, closed-form voxels)",
             "value": job_rate(units, world, ms * 1e-3), "unit": "interactions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "mixed" else "f64",
+            "data": "synthetic",
             "config": {"workload": wk.name + "_sum_an", "voxels": nvox, "M_observers": M,
-                       "l2_flush": "256 MiB buffer written between timed steps",
-                       "step": "corner-lattice weights + closed-form sum over the corner lattice"},
-            "rel_err_vs_oracle_sample": err, "roofline": None, "cpu_baseline": cpu, "clocks": clk,
-            "gpu_launches": int(launches)}
+                       "l2_flush": "256 MiB buffer written between timed steps"},
+            "method": {"mode": "fmm" if fmm else "direct", "precision": precision, "p": p if fmm else None,
+                       "step": "forward (closed form next to each observer, exact voxel moments beyond)"
+                       if fmm else "corner-lattice weights + closed-form sum over the corner lattice"},
+            "stages_ms": stages, "rel_err_vs_oracle_sample": err, "roofline": None, "cpu_baseline": cpu,
+            "clocks": clk, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
 
 

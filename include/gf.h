@@ -85,11 +85,18 @@ enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
 /* Option flags (gf_options.reserved0):
  *   GF_FLAG_M2L_SIMT  FMM, mixed precision: the M2L on the SIMT cores
  *                     instead of the tensor cores.
- *   GF_FLAG_SUM_AN    direct mode, FP64 only: every voxel integrated in
- *                     closed form (SUM-AN of Sec. 2.1, the exact field of
- *                     the piecewise-constant density, finite on voxel faces,
- *                     edges and corners) instead of sampled by the quadrature
- *                     rule; the rule is then ignored.
+ *   GF_FLAG_SUM_AN    every voxel integrated in closed form (SUM-AN of
+ *                     Sec. 2.1, the exact field of the piecewise-constant
+ *                     density, finite on voxel faces, edges and corners)
+ *                     instead of sampled by the quadrature rule; the rule is
+ *                     then ignored.  Direct mode: FP64 only, every voxel in
+ *                     closed form.  FMM mode (4^3-voxel leaves, either
+ *                     precision, forward only): the voxels within 2 (mixed)
+ *                     or 4 (FP64) voxels of an observer's own voxel in closed
+ *                     form, the other voxels of its leaf's 27 neighbour
+ *                     leaves by the midpoint rule plus a uniform cube's
+ *                     l = 4 term, the far field from multipole expansions of
+ *                     the exact voxel integrals.
  *   GF_FLAG_TEST_WAIT_TIMEOUT
  *                     testing aid for the failure path of the bounded device
  *                     waits (FMM, mixed precision, tensor-core M2L): the

@@ -146,8 +146,12 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
         set_error("opt.reserved0 = %d holds unknown flags", opt->reserved0);
         return GF_ERR_INVALID_ARG;
     }
-    if ((opt->reserved0 & GF_FLAG_SUM_AN) && (opt->mode != GF_MODE_DIRECT || opt->precision != GF_PREC_FP64)) {
-        set_error("GF_FLAG_SUM_AN (closed-form voxels) is implemented in direct mode, FP64 only");
+    if ((opt->reserved0 & GF_FLAG_SUM_AN) && opt->mode == GF_MODE_DIRECT && opt->precision != GF_PREC_FP64) {
+        set_error("GF_FLAG_SUM_AN (closed-form voxels) in direct mode is implemented in FP64 only");
+        return GF_ERR_UNSUPPORTED;
+    }
+    if ((opt->reserved0 & GF_FLAG_SUM_AN) && opt->mode == GF_MODE_FMM && opt->leaf_vox != 0 && opt->leaf_vox != 4) {
+        set_error("GF_FLAG_SUM_AN (closed-form voxels) in FMM mode uses leaves of 4^3 voxels (leaf_vox 0 or 4)");
         return GF_ERR_UNSUPPORTED;
     }
     if (opt->mode == GF_MODE_FMM) {
@@ -225,15 +229,24 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
     p->nvox = grid->n[0] * grid->n[1] * grid->n[2];
     QuadRule &qr = p->quad;
     memset(&qr, 0, sizeof(qr));
-    qr.nq = quad->nq;
-    double wsum = 0.0;
-    for (int q = 0; q < quad->nq; ++q) wsum += quad->w[q];
-    for (int q = 0; q < quad->nq; ++q) {
-        qr.wn[q] = quad->w[q] / wsum;
-        qr.wnf[q] = (float)qr.wn[q];
-        for (int a = 0; a < 3; ++a) {
-            qr.xi[q][a] = quad->xi[3 * q + a];
-            qr.offf[q][a] = (float)(0.5 + 0.5 * quad->xi[3 * q + a]);
+    if ((opt->reserved0 & GF_FLAG_SUM_AN) && opt->mode == GF_MODE_FMM) {
+        // closed-form voxels in the FMM: the rule is ignored; the tree and the
+        // leaf-blocked densities are those of one node per voxel
+        qr.nq = 1;
+        qr.wn[0] = 1.0;
+        qr.wnf[0] = 1.0f;
+        for (int a = 0; a < 3; ++a) qr.offf[0][a] = 0.5f;
+    } else {
+        qr.nq = quad->nq;
+        double wsum = 0.0;
+        for (int q = 0; q < quad->nq; ++q) wsum += quad->w[q];
+        for (int q = 0; q < quad->nq; ++q) {
+            qr.wn[q] = quad->w[q] / wsum;
+            qr.wnf[q] = (float)qr.wn[q];
+            for (int a = 0; a < 3; ++a) {
+                qr.xi[q][a] = quad->xi[3 * q + a];
+                qr.offf[q][a] = (float)(0.5 + 0.5 * quad->xi[3 * q + a]);
+            }
         }
     }
     gf_status s = GF_OK;
@@ -333,6 +346,10 @@ gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp, int32_t
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (plan->part_lo != 0 || plan->part_hi < 64) {
         set_error("gf_adjoint of a plan restricted to a source part is not implemented");
+        return GF_ERR_UNSUPPORTED;
+    }
+    if ((plan->opt.reserved0 & GF_FLAG_SUM_AN) && plan->opt.mode == GF_MODE_FMM) {
+        set_error("gf_adjoint of a FMM plan with closed-form voxels is not implemented (direct mode has it)");
         return GF_ERR_UNSUPPORTED;
     }
     if (plan->opt.mode == GF_MODE_DIRECT) {

@@ -17,6 +17,7 @@
 #include "fmm_math.cuh"
 #include "gf_fmm.cuh"
 #include "gf_m2l.cuh"
+#include "gf_sum_an.cuh"
 
 namespace gf {
 
@@ -132,6 +133,77 @@ __global__ void compose_p2m_up(const double *__restrict__ P, const double *__res
         for (int i = 0; i < K; ++i) s += pv[i] * T[(size_t)i * K + k];
         Q[((size_t)o * b3 + v) * K + k] = s;
     }
+}
+
+// P2M matrix of closed-form voxels (SUM-AN): P[v][k] = the k-th real component
+// of conj R((x - c)/b) integrated over voxel v (unit volume in voxel units),
+// by a Gauss-Legendre rule of m nodes per axis, exact for every regular solid
+// harmonic of degree <= 2m - 1.
+struct GaussLeg {
+    int m;
+    double x[16], w[16];   // nodes on [-1, 1], weights summing to 2
+};
+
+__global__ void build_p2m_exact(int p, int K, int b, GaussLeg gl, double *__restrict__ pd,
+                                float *__restrict__ pf) {
+    extern __shared__ double sh[];
+    const int v = blockIdx.x;
+    const int lx = v % b, ly = (v / b) % b, lz = v / (b * b);
+    const int nt = (p + 1) * (p + 2) / 2;
+    double *re = sh, *im = sh + nt, *acc = sh + 2 * nt;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) acc[k] = 0.0;
+    __syncthreads();
+    const int m = gl.m;
+    for (int q = 0; q < m * m * m; ++q) {
+        const int qi = q % m, qj = (q / m) % m, qk = q / (m * m);
+        if (threadIdx.x == 0) {
+            const double y0 = (lx + 0.5 + 0.5 * gl.x[qi] - 0.5 * b) / b;
+            const double y1 = (ly + 0.5 + 0.5 * gl.x[qj] - 0.5 * b) / b;
+            const double y2 = (lz + 0.5 + 0.5 * gl.x[qk] - 0.5 * b) / b;
+            regular_harmonics<double>(p, y0, y1, y2, re, im);
+        }
+        __syncthreads();
+        const double w = 0.125 * gl.w[qi] * gl.w[qj] * gl.w[qk];
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            int n = (int)sqrt((double)k);
+            while (n * n > k) --n;
+            while ((n + 1) * (n + 1) <= k) ++n;
+            const int ro = k - n * n, mm = (ro + 1) / 2;
+            const bool isim = ro > 0 && (ro % 2 == 0);
+            acc[k] += isim ? -w * im[tri(n, mm)] : w * re[tri(n, mm)];
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        pd[(size_t)v * K + k] = acc[k];
+        pf[(size_t)v * K + k] = (float)acc[k];
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton's method on the
+// three-term recurrence of the Legendre polynomials).
+GaussLeg gauss_legendre(int m) {
+    GaussLeg g;
+    g.m = m;
+    for (int i = 0; i < m; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (m + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int n = 2; n <= m; ++n) {
+                const double pn = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+                p0 = p1;
+                p1 = pn;
+            }
+            const double pm = m == 1 ? x : p1, pm1 = m == 1 ? 1.0 : p0;
+            dp = m * (x * pm - pm1) / (x * x - 1.0);
+            const double dx = pm / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        g.x[i] = x;
+        g.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    return g;
 }
 
 // ---------------------------------------------------------------- sources
@@ -1115,6 +1187,96 @@ eval_kernel(EvalArgs a) {
     }
 }
 
+// Near field + far field of closed-form voxels (SUM-AN in the FMM): one warp
+// per work item, two observers per lane.  The densities of the item's 27
+// neighbour leaves (a 12^3 voxel block, 4^3-voxel leaves) are staged in the
+// warp's shared-memory slice; each observer takes the voxels within
+// Chebyshev distance RAD of its own voxel in closed form on their corner
+// lattice and the others by the midpoint rule with a uniform cube's l = 4
+// term (an_near_block); the far field is the L2P gradient of the leaf's
+// local expansion (made from exact voxel moments).
+constexpr int kAnNb = 12;                          // voxels per axis of the 27-leaf block
+constexpr int kAnBlock = kAnNb * kAnNb * kAnNb;
+
+inline __host__ __device__ int eval_an_slice(int P2) { return (kAnBlock + 3 * P2 + 27 * 2 + 7) & ~7; }
+
+template <class T, int RAD>
+__global__ void __launch_bounds__(kEvalWarps * 32) eval_an_kernel(EvalArgs a) {
+    extern __shared__ unsigned char shraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P2 = a.p * a.p;
+    T *blk = reinterpret_cast<T *>(shraw) + (size_t)warp * eval_an_slice(P2);
+    T *Dx = blk + kAnBlock, *Dy = Dx + P2, *Dz = Dy + P2;
+    int64_t *nbl = reinterpret_cast<int64_t *>(Dz + P2 + ((P2 * 3 + kAnBlock) & 1));
+    const T *tloc = reinterpret_cast<const T *>(a.tloc);
+    const T *mass = reinterpret_cast<const T *>(a.mass);
+    const T *le = reinterpret_cast<const T *>(a.le);
+    const T inv_b = T(1) / T(a.b);
+    const double far_s = -1.0 / ((double)a.b * (double)a.b);
+    for (int64_t it = (int64_t)blockIdx.x * kEvalWarps + warp; it < a.n_items; it += (int64_t)gridDim.x * kEvalWarps) {
+        const int4 item = a.items[it];
+        const int leaf = item.x;
+        const uint64_t key = a.tkey[leaf];
+        int64_t lc[3] = {0, 0, 0};
+        for (int bit = 0; bit < 21; ++bit) {
+            lc[0] |= (int64_t)((key >> (3 * bit)) & 1) << bit;
+            lc[1] |= (int64_t)((key >> (3 * bit + 1)) & 1) << bit;
+            lc[2] |= (int64_t)((key >> (3 * bit + 2)) & 1) << bit;
+        }
+        T tx[kTPL], ty[kTPL], tz[kTPL];
+        int tid[kTPL];
+#pragma unroll
+        for (int u = 0; u < kTPL; ++u) {
+            const int r = lane + 32 * u;
+            tid[u] = r < item.z ? item.y + r : -1;
+            const int64_t i = tid[u] >= 0 ? tid[u] : item.y;
+            tx[u] = tloc[3 * i + 0] + T(6);   // position in the block (own leaf at [4, 8))
+            ty[u] = tloc[3 * i + 1] + T(6);
+            tz[u] = tloc[3 * i + 2] + T(6);
+        }
+        __syncwarp();
+        if (lane < 27) {
+            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1], sz = lc[2] + dz - a.blk.lo[2];
+            const bool in = sx >= 0 && sy >= 0 && sz >= 0 && sx < a.blk.n[0] && sy < a.blk.n[1] && sz < a.blk.n[2] &&
+                            in_source_part(lc[0] + dx, lc[1] + dy, lc[2] + dz, a.L - 2, a.part_lo, a.part_hi);
+            nbl[lane] = in ? (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx : -1;
+        }
+        __syncwarp();
+        for (int bb = 0; bb < a.B; ++bb) {
+            for (int e = lane; e < kAnBlock; e += 32) {
+                const int x = e % kAnNb, y = (e / kAnNb) % kAnNb, z = e / (kAnNb * kAnNb);
+                const int64_t sl = nbl[(z >> 2) * 9 + (y >> 2) * 3 + (x >> 2)];
+                blk[e] = sl >= 0 ? mass[(sl * a.B + bb) * 64 + ((z & 3) * 4 + (y & 3)) * 4 + (x & 3)] : T(0);
+            }
+            const T *L = le + ((int64_t)leaf * a.B + bb) * a.ldk;
+            for (int e = lane; e < P2; e += 32) grad_coeff<T>(L, e, Dx[e], Dy[e], Dz[e]);
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < kTPL; ++u) {
+                if (tid[u] < 0) continue;
+                T gn[3];
+                an_near_block<T>(blk, kAnNb, tx[u], ty[u], tz[u], gn, RAD);
+                T fx, fy, fz;
+                l2p_sum<T>(a.p, Dx, Dy, Dz, (tx[u] - T(6)) * inv_b, (ty[u] - T(6)) * inv_b, (tz[u] - T(6)) * inv_b,
+                           fx, fy, fz);
+                const double gx = ((double)gn[0] + far_s * (double)fx) * a.scale;
+                const double gy = ((double)gn[1] + far_s * (double)fy) * a.scale;
+                const double gzv = ((double)gn[2] + far_s * (double)fz) * a.scale;
+                const int64_t j = a.perm[tid[u]];
+                if (a.g) {
+                    double *o = a.g + ((int64_t)bb * a.M + j) * 3;
+                    o[0] = gx;
+                    o[1] = gy;
+                    o[2] = gzv;
+                }
+                if (a.gz) a.gz[(int64_t)bb * a.M + j] = gzv;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Adjoint tables: adj[slot][i*K + o] = fwd[mslot][o*K + i], where mslot is
 // the slot of -offset for M2L and the same octant for M2M/L2L.
 __global__ void transpose_ops(const double *__restrict__ fwd, double *__restrict__ adjd, float *__restrict__ adjf,
@@ -1211,6 +1373,7 @@ gf_status get_tables(int device, int p, cudaStream_t st, const Tables **out) {
 // same rule (a solve loop, a server) do not rebuild them.
 struct P2MEntry {
     int device, p, b, nq;
+    int exact;             // closed-form voxels: moments integrated exactly
     double xi[kMaxQuad][3], wn[kMaxQuad];
     double *pd;
     float *pf;
@@ -1224,8 +1387,9 @@ gf_status get_p2m(gf_plan_s *plan, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
     const QuadRule &q = plan->quad;
     std::lock_guard<std::mutex> lk(g_p2m_mu);
+    const int exact = (plan->opt.reserved0 & GF_FLAG_SUM_AN) ? 1 : 0;
     for (P2MEntry *e : g_p2m)
-        if (e->device == plan->device && e->p == F->p && e->b == F->b && e->nq == q.nq &&
+        if (e->device == plan->device && e->p == F->p && e->b == F->b && e->nq == q.nq && e->exact == exact &&
             !memcmp(e->xi, q.xi, sizeof(double) * 3 * q.nq) && !memcmp(e->wn, q.wn, sizeof(double) * q.nq)) {
             F->p2m_d = e->pd;
             F->p2m_f = e->pf;
@@ -1236,6 +1400,7 @@ gf_status get_p2m(gf_plan_s *plan, cudaStream_t st) {
     e->p = F->p;
     e->b = F->b;
     e->nq = q.nq;
+    e->exact = exact;
     memcpy(e->xi, q.xi, sizeof(double) * 3 * q.nq);
     memcpy(e->wn, q.wn, sizeof(double) * q.nq);
     const int b3 = F->b * F->b * F->b, K = F->K;
@@ -1247,7 +1412,12 @@ gf_status get_p2m(gf_plan_s *plan, cudaStream_t st) {
         return GF_ERR_OOM;
     }
     const size_t shm = sizeof(double) * ((F->p + 1) * (F->p + 2) + K);
-    build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), e->pd, e->pf);
+    if (exact) {
+        // degree <= p exactly: ceil((p + 1) / 2) nodes per axis
+        build_p2m_exact<<<b3, 128, shm, st>>>(F->p, K, F->b, gauss_legendre((F->p + 2) / 2), e->pd, e->pf);
+    } else {
+        build_p2m<<<b3, 128, shm, st>>>(F->p, K, F->b, quad_device(plan), e->pd, e->pf);
+    }
     GF_KERNEL_DONE();
     GF_CUDA(cudaStreamSynchronize(st));   // other streams may use the cached matrix next
     g_p2m.push_back(e);
@@ -1497,7 +1667,19 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
                            sizeof(T) * kEvalWarps * eval_slice(F->p * F->p, (int)sizeof(T));
         const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
-        if (sizeof(T) == 4 && n1 == 4) {
+        if (plan->opt.reserved0 & GF_FLAG_SUM_AN) {
+            // closed-form voxels: radius 2 in FP32, 4 in FP64 (the closed form
+            // cancels like (d/h)^3, so the precision sets how far it is used;
+            // beyond it the corrected midpoint rule errs like (h/d)^6)
+            const size_t shan = sizeof(T) * kEvalWarps * eval_an_slice(F->p * F->p) + 64;
+            if (sizeof(T) == 4) {
+                GF_TRY((ensure_smem(eval_an_kernel<T, 2>, shan)));
+                eval_an_kernel<T, 2><<<grid, kEvalWarps * 32, shan, st>>>(a);
+            } else {
+                GF_TRY((ensure_smem(eval_an_kernel<T, 4>, shan)));
+                eval_an_kernel<T, 4><<<grid, kEvalWarps * 32, shan, st>>>(a);
+            }
+        } else if (sizeof(T) == 4 && n1 == 4) {
             GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
             eval_kernel<float, 4><<<grid, kEvalWarps * 32, shm, st>>>(a);
         } else {

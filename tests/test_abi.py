@@ -102,15 +102,19 @@ def test_total_voxel_count_is_bounded(n, ok):
         assert "2^40" in gf.gf_last_error()
 
 
-def test_closed_form_voxels_only_in_direct_fp64():
+def test_closed_form_voxels_modes():
     """GF_FLAG_SUM_AN is accepted in direct mode in FP64 (the plan then holds
-    the corner-lattice weights) and refused elsewhere; unknown flag bits are
-    invalid arguments."""
+    the corner-lattice weights) and in FMM mode with 4^3-voxel leaves in
+    either precision, and refused in mixed direct mode and with other leaf
+    sizes; unknown flag bits are invalid arguments."""
     grid, q, opt = _args(mode="direct")
     plain = gf.gf_plan_bytes(grid, q.c, 10, opt)
     opt.reserved0 = gf.GF_FLAG_SUM_AN
     assert gf.gf_plan_bytes(grid, q.c, 10, opt) >= plain + 5 ** 3 * 8
-    for bad in (dict(mode="fmm", p=6), dict(mode="direct", precision="mixed")):
+    for ok in (dict(mode="fmm", p=6), dict(mode="fmm", p=6, precision="mixed", leaf_vox=4)):
+        grid, q, opt = _args(flags=gf.GF_FLAG_SUM_AN, **ok)
+        assert gf.gf_plan_bytes(grid, q.c, 10, opt) > 0
+    for bad in (dict(mode="fmm", p=6, leaf_vox=2), dict(mode="direct", precision="mixed")):
         grid, q, opt = _args(flags=gf.GF_FLAG_SUM_AN, **bad)
         with pytest.raises(gf.GfError) as e:
             gf.gf_plan_bytes(grid, q.c, 10, opt)
