@@ -65,6 +65,10 @@ def _load():
             lib.gfo_adjoint_analytic.argtypes = [i64, i64, i64, _dp, _dp, _dp, i64, _dp, i32, i32, dbl, _dp, i32]
             lib.gfo_adjoint_analytic.restype = i32
             lib.gfo_max_threads.restype = i32
+            lib.gfo_hex_sources.argtypes = [i64, _dp, i32, _dp, _dp, _dp, _dp]
+            lib.gfo_hex_sources.restype = i32
+            lib.gfo_forward_points.argtypes = [i64, _dp, _dp, i64, _dp, i32, _dp, i64, dbl, _dp, i32]
+            lib.gfo_forward_points.restype = i32
             _lib = lib
     return _lib
 
@@ -239,3 +243,56 @@ def prism_norms(plo, phi, rho, G, dlo, dhi, Mbar, m, ngauss=4, nthreads=0):
                             _p(_c(dlo)), _p(_c(dhi)), int(Mbar), int(m), int(ngauss),
                             _p(_c(gx)), _p(_c(gw)), _p(out), int(nthreads))
     return out
+
+
+def hex_sources(verts, xi, w):
+    """Quadrature points and volume weights of deformed hexahedral cells
+    (trilinear maps of the reference cube, Sec. 2.1 general SUM-G1).
+
+    verts : (ncell, 8, 3) corners, corner a = i + 2 j + 4 k at reference
+            signs (2i - 1, 2j - 1, 2k - 1)
+    xi, w : (nq, 3) reference nodes in [-1, 1]^3, (nq,) weights
+    returns x : (ncell * nq, 3), a : (ncell * nq,)  (source s = c * nq + q)
+    """
+    verts = _c(verts).reshape(-1, 8, 3)
+    xi = _c(xi).reshape(-1, 3)
+    w = _c(w).reshape(-1)
+    n = verts.shape[0] * xi.shape[0]
+    x = np.zeros((n, 3), dtype=np.float64)
+    a = np.zeros(n, dtype=np.float64)
+    rc = _load().gfo_hex_sources(verts.shape[0], _p(verts), xi.shape[0], _p(xi), _p(w), _p(x), _p(a))
+    if rc != 0:
+        raise ValueError("gfo_hex_sources: bad arguments")
+    return x, a
+
+
+def forward_points(x, a, per_cell, rho, obs, G, nthreads: int = 0) -> np.ndarray:
+    """Field of weighted point sources: g(r) = G sum_s rho_{s // per_cell}
+    a_s (r - x_s) / |r - x_s|^3.
+
+    x : (S, 3),  a : (S,),  rho : (ncell,) or (B, ncell) with ncell = S / per_cell
+    returns g : (M, 3) or (B, M, 3)
+    """
+    x = _c(x).reshape(-1, 3)
+    a = _c(a).reshape(-1)
+    S = x.shape[0]
+    ncell = S // int(per_cell)
+    rho = _c(rho)
+    single = rho.ndim == 1
+    rho = rho.reshape(-1, ncell)
+    B = rho.shape[0]
+    obs = _c(obs).reshape(-1, 3)
+    M = obs.shape[0]
+    out = np.zeros((B, M, 3), dtype=np.float64)
+    rc = _load().gfo_forward_points(S, _p(x), _p(a), int(per_cell), _p(rho), B, _p(obs), M, float(G), _p(out),
+                                    int(nthreads))
+    if rc != 0:
+        raise ValueError("gfo_forward_points: bad arguments")
+    return out[0] if single else out
+
+
+def forward_hex(verts, xi, w, rho, obs, G, nthreads: int = 0) -> np.ndarray:
+    """Discretised Eq. 1 over deformed hexahedral cells of constant density:
+    :func:`hex_sources` then :func:`forward_points`."""
+    x, a = hex_sources(verts, xi, w)
+    return forward_points(x, a, np.asarray(xi).reshape(-1, 3).shape[0], rho, obs, G, nthreads)

@@ -495,3 +495,104 @@ void gfo_prism_norms(const double *plo, const double *phi_, double rho,
     out[1] = sqrt(s2);
     out[2] = mx;
 }
+
+
+/* ---- Deformed hexahedra and weighted point sources (Sec. 2.1, Sec. 4) ---- */
+
+/*
+ * Quadrature points of deformed hexahedral cells.  Sec. 2.1 allows the
+ * general SUM-G1 to take arbitrarily deformed hexahedra by integrating in a
+ * reference coordinate system: cell c is the trilinear image x(xi) of the
+ * reference cube [-1,1]^3 through its eight corners,
+ *
+ *   x(xi) = sum_a N_a(xi) X_a,  N_a(xi) = (1 + s0 xi0)(1 + s1 xi1)(1 + s2 xi2) / 8,
+ *
+ * corner a = i + 2 j + 4 k sitting at reference signs (s0, s1, s2) =
+ * (2i - 1, 2j - 1, 2k - 1), and a constant density integrates as
+ *
+ *   Int_cell rho K(r - x) dV = rho Int_ref K(r - x(xi)) |det dx/dxi| dxi
+ *                           ~ rho sum_q (8 w_q / sum w) |det J(xi_q)| K(r - x(xi_q)).
+ *
+ *   verts : [ncell][8][3] corner coordinates (m)
+ *   xi, w : [nq][3] reference nodes in [-1,1]^3 and [nq] weights
+ *   x     : [ncell * nq][3] output source points, a : [ncell * nq] output
+ *           volume weights (m^3), source s = c * nq + q
+ */
+int gfo_hex_sources(long ncell, const double *verts, int nq, const double *xi, const double *w,
+                    double *x, double *a) {
+    if (ncell < 0 || nq <= 0) return -1;
+    double wsum = 0.0;
+    for (int q = 0; q < nq; ++q) wsum += w[q];
+    for (long c = 0; c < ncell; ++c) {
+        const double *X = verts + 24 * c;
+        for (int q = 0; q < nq; ++q) {
+            const double *e = xi + 3 * q;
+            double p[3] = {0.0, 0.0, 0.0};
+            double J[3][3] = {{0.0}};   /* J[d][r] = d x_d / d xi_r */
+            for (int k = 0; k < 8; ++k) {
+                const double s0 = (k & 1) ? 1.0 : -1.0, s1 = (k & 2) ? 1.0 : -1.0, s2 = (k & 4) ? 1.0 : -1.0;
+                const double f0 = 1.0 + s0 * e[0], f1 = 1.0 + s1 * e[1], f2 = 1.0 + s2 * e[2];
+                const double N = f0 * f1 * f2 / 8.0;
+                const double dN[3] = {s0 * f1 * f2 / 8.0, f0 * s1 * f2 / 8.0, f0 * f1 * s2 / 8.0};
+                for (int d = 0; d < 3; ++d) {
+                    p[d] += N * X[3 * k + d];
+                    for (int r = 0; r < 3; ++r) J[d][r] += dN[r] * X[3 * k + d];
+                }
+            }
+            const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            const long s = c * nq + q;
+            for (int d = 0; d < 3; ++d) x[3 * s + d] = p[d];
+            a[s] = 8.0 * (w[q] / wsum) * fabs(det);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Field of weighted point sources (Eq. 7 with explicit points): source s at
+ * x_s carries the mass rho_{c(s)} a_s, c(s) = s / per_cell the density
+ * (cell or point) it samples -- the quadrature points of deformed cells, or
+ * scattered density points with their (Voronoi) volumes as Sec. 4 describes
+ * for the FMM:
+ *
+ *   g(r) = G sum_s rho_{c(s)} a_s (r - x_s) / |r - x_s|^3
+ *
+ *   x   : [S][3],  a : [S],  rho : [B][S / per_cell],  obs : [M][3]
+ *   g   : [B][M][3]
+ * A source that coincides exactly with an observer contributes nothing to it.
+ */
+int gfo_forward_points(long S, const double *x, const double *a, long per_cell, const double *rho, int B,
+                       const double *obs, long M, double G, double *g, int nthreads) {
+    if (S < 0 || per_cell <= 0 || S % per_cell != 0 || B <= 0 || M < 0) return -1;
+    set_threads(nthreads);
+    const long ncell = S / per_cell;
+#pragma omp parallel
+    {
+        nsum *acc = (nsum *)malloc(sizeof(nsum) * 3 * (size_t)B);
+#pragma omp for schedule(dynamic, 4)
+        for (long j = 0; j < M; ++j) {
+            const double r0 = obs[3 * j + 0], r1 = obs[3 * j + 1], r2 = obs[3 * j + 2];
+            memset(acc, 0, sizeof(nsum) * 3 * (size_t)B);
+            for (long s = 0; s < S; ++s) {
+                const double d0 = r0 - x[3 * s + 0], d1 = r1 - x[3 * s + 1], d2 = r2 - x[3 * s + 2];
+                const double rr = d0 * d0 + d1 * d1 + d2 * d2;
+                if (rr == 0.0) continue; /* coincident pair */
+                const double rinv = 1.0 / sqrt(rr);
+                const double k3 = rinv * rinv * rinv;
+                const long c = s / per_cell;
+                for (int b = 0; b < B; ++b) {
+                    const double m = rho[(long)b * ncell + c] * a[s];
+                    nsum_add(&acc[3 * b + 0], m * k3 * d0);
+                    nsum_add(&acc[3 * b + 1], m * k3 * d1);
+                    nsum_add(&acc[3 * b + 2], m * k3 * d2);
+                }
+            }
+            for (int b = 0; b < B; ++b)
+                for (int d = 0; d < 3; ++d) g[((long)b * M + j) * 3 + d] = G * nsum_val(&acc[3 * b + d]);
+        }
+        free(acc);
+    }
+    return 0;
+}

@@ -280,3 +280,116 @@ def random_small(seed: int, n=(5, 4, 3), npts: int = 1, n_obs: int = 17, h=(1.0,
     obs = rng.uniform(lo, hi, size=(n_obs, 3))
     xi, w = gauss_rule(npts)
     return Workload(f"random_small_{seed}", grid, rho, xi, w, obs, G=1.0)
+
+
+# ---------------------------------------------------------------- deformed cells and points
+def hex_brick_mesh(n, lo, hi, warp: float = 0.0) -> np.ndarray:
+    """Hexahedral mesh of the box [lo, hi] with n = (nx, ny, nz) cells.  Node
+    (i, j, k) sits at the regular grid position moved, along every axis, by
+    warp * extent * sin(pi u) sin(pi v) sin(pi w) with (u, v, w) its position
+    in the box scaled to [0, 1]^3: boundary nodes stay put, so the deformed
+    cells still tile the box.  Returns verts [ncell][8][3], cell
+    c = (k ny + j) nx + i, corner a = i + 2 j + 4 k of the cell."""
+    nx, ny, nz = (int(v) for v in n)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    u = [np.linspace(0.0, 1.0, m + 1) for m in (nx, ny, nz)]
+    W, V, U = np.meshgrid(u[2], u[1], u[0], indexing="ij")         # [nz+1][ny+1][nx+1]
+    bump = warp * np.sin(np.pi * U) * np.sin(np.pi * V) * np.sin(np.pi * W)
+    ext = hi - lo
+    nodes = np.stack([lo[0] + ext[0] * (U + bump), lo[1] + ext[1] * (V + bump),
+                      lo[2] + ext[2] * (W + bump)], axis=-1)
+    return _cells_of(nodes)
+
+
+def _cells_of(nodes) -> np.ndarray:
+    """Corners of the cells of a structured node array [nz+1][ny+1][nx+1][3]."""
+    corners = [nodes[k:nodes.shape[0] - 1 + k, j:nodes.shape[1] - 1 + j, i:nodes.shape[2] - 1 + i]
+               for k in (0, 1) for j in (0, 1) for i in (0, 1)]
+    return np.ascontiguousarray(np.stack(corners, axis=3).reshape(-1, 8, 3))
+
+
+def topo_surface(x, y, Lx, Ly, relief, seed):
+    """Seeded topography: five Gaussian hills and valleys of widths
+    U[0.08, 0.25] of the domain and heights U[-1, 1] * relief."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = np.zeros(np.broadcast(x, y).shape)
+    for _ in range(5):
+        cx, cy = rng.uniform(0.0, Lx), rng.uniform(0.0, Ly)
+        wdt = rng.uniform(0.08, 0.25) * min(Lx, Ly)
+        z += rng.uniform(-1.0, 1.0) * relief * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * wdt * wdt))
+    return z
+
+
+def topo_mesh(nx: int = 64, ny: int = 64, nz: int = 32, Lx: float = 16000.0, Ly: float = 16000.0,
+              depth: float = 8000.0, relief: float = 800.0, seed: int = 6):
+    """Terrain-following hexahedral mesh (Sec. 4: topography): nodes on a
+    regular horizontal grid over [0, Lx] x [0, Ly]; each node column runs from
+    the flat bottom z = -depth to the topographic surface z_t(x, y)
+    (:func:`topo_surface`) in nz equal steps.  Returns (verts
+    [nx ny nz][8][3], surface node heights [ny+1][nx+1])."""
+    xs = np.linspace(0.0, Lx, nx + 1)
+    ys = np.linspace(0.0, Ly, ny + 1)
+    Y, X = np.meshgrid(ys, xs, indexing="ij")
+    zt = topo_surface(X, Y, Lx, Ly, relief, seed)
+    t = np.linspace(0.0, 1.0, nz + 1)
+    Z = -depth + (zt[None, :, :] + depth) * t[:, None, None]
+    nodes = np.stack([np.broadcast_to(X, Z.shape), np.broadcast_to(Y, Z.shape), Z], axis=-1)
+    return _cells_of(nodes), zt
+
+
+def topo_workload(nx: int = 64, ny: int = 64, nz: int = 32, stations: int = 64, npts: int = 2,
+                  seed: int = 6):
+    """Deformed-cell workload: :func:`topo_mesh` (16 km x 16 km, 8 km deep,
+    800 m relief), densities 2670 kg/m^3 plus a seeded anomaly field that
+    follows depth below the surface (a +/-300 kg/m^3 band 1-3 km down), the
+    npts^3 Gauss rule per cell, stations^2 stations draped 50 m above the
+    surface.  Returns a dict with verts, rho [ncell], xi, w, obs."""
+    Lx = Ly = 16000.0
+    verts, _ = topo_mesh(nx, ny, nz, Lx, Ly, 8000.0, 800.0, seed)
+    cen = verts.mean(axis=1)
+    top = topo_surface(cen[:, 0], cen[:, 1], Lx, Ly, 800.0, seed)
+    d = top - cen[:, 2]
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    phase = rng.uniform(0, 2 * np.pi, 2)
+    band = np.exp(-((d - 2000.0) / 700.0) ** 2)
+    rho = 2670.0 + 300.0 * band * np.sin(2 * np.pi * cen[:, 0] / Lx * 3 + phase[0]) * \
+        np.cos(2 * np.pi * cen[:, 1] / Ly * 2 + phase[1])
+    xi, w = gauss_rule(npts)
+    sx = (np.arange(stations) + 0.5) * (Lx / stations)
+    SY, SX = np.meshgrid(sx, sx, indexing="ij")
+    obs = np.stack([SX.ravel(), SY.ravel(), topo_surface(SX, SY, Lx, Ly, 800.0, seed).ravel() + 50.0], axis=1)
+    return {"name": "topo_hex_%dx%dx%d" % (nx, ny, nz), "verts": verts, "rho": rho, "xi": xi, "w": w,
+            "obs": np.ascontiguousarray(obs), "G": G_PAPER}
+
+
+def scattered_points(n: int, lo, hi, seed: int = 7) -> np.ndarray:
+    """n density points uniform in the box [lo, hi] (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return np.ascontiguousarray(lo + (hi - lo) * rng.random((int(n), 3)))
+
+
+def voronoi_volumes(pts, lo, hi) -> np.ndarray:
+    """Volume of each point's Voronoi cell clipped to the box [lo, hi] (the
+    volume Sec. 4 associates with a scattered density point).  The points
+    are mirrored across the six faces, which makes the faces bisectors, so
+    every original cell is bounded by the box; each cell's volume is that of
+    the convex hull of its vertices."""
+    from scipy.spatial import ConvexHull, Voronoi
+    pts = np.asarray(pts, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    mirrored = [pts]
+    for a in range(3):
+        for face in (lo[a], hi[a]):
+            m = pts.copy()
+            m[:, a] = 2 * face - m[:, a]
+            mirrored.append(m)
+    vor = Voronoi(np.concatenate(mirrored))
+    vol = np.empty(len(pts))
+    for i in range(len(pts)):
+        region = vor.regions[vor.point_region[i]]
+        vol[i] = ConvexHull(vor.vertices[region]).volume
+    return vol

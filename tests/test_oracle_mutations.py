@@ -1,10 +1,13 @@
 """The oracle's pins catch plausible mistakes.  Each case plants one mistake in
 a copy of oracle/gf_oracle.c (a flipped sign, a dropped normalisation, a
-transposed index, a wrong axis, a wrong corner sign, a wrong special axis),
-builds the copy, and checks that a pin which the real oracle passes fails
-on it: the exact-arithmetic brute force, the closed-form prism field the
-quadrature sums must converge to, Table 10's vertical formula, or the axis
-relabelling of that formula."""
+transposed index, a wrong axis, a wrong corner sign, a wrong special axis;
+for deformed cells and point sources a wrong reference-cube volume, a wrong
+shape-function derivative, a wrong density index), builds the copy, and
+checks that a pin which the real oracle passes fails on it: the
+exact-arithmetic brute force, the closed-form prism field the quadrature
+sums must converge to, Table 10's vertical formula, the axis relabelling of
+that formula, the exact volume of trilinear cells, Gauss's law and the voxel
+sum that undeformed cells must reproduce."""
 import ctypes
 import os
 import shutil
@@ -32,6 +35,12 @@ MUTATIONS = {
     "gx_wrong_special_axis": ("ax += s * prism_corner(v, w, u);", "ax += s * prism_corner(u, w, v);"),
 }
 
+POINT_MUTATIONS = {
+    "hex_reference_volume": ("a[s] = 8.0 * (w[q] / wsum) * fabs(det);", "a[s] = 4.0 * (w[q] / wsum) * fabs(det);"),
+    "hex_shape_derivative": ("f0 * f1 * s2 / 8.0};", "f0 * f1 * s1 / 8.0};"),
+    "points_density_index": ("const long c = s / per_cell;", "const long c = s % ncell;"),
+}
+
 
 def _build(tmp_path, name, old, new):
     src = open(SRC).read()
@@ -46,6 +55,8 @@ def _build(tmp_path, name, old, new):
     L.gfo_forward.argtypes = [i64, i64, i64, _dp, _dp, i32, _dp, _dp, _dp, i32, _dp, i64, dbl, _dp, i32]
     L.gfo_prism_gz_many.argtypes = [_dp, _dp, dbl, dbl, _dp, i64, _dp, i32]
     L.gfo_prism_g_many.argtypes = [_dp, _dp, dbl, dbl, _dp, i64, _dp, i32]
+    L.gfo_hex_sources.argtypes = [i64, _dp, i32, _dp, _dp, _dp, _dp]
+    L.gfo_forward_points.argtypes = [i64, _dp, _dp, i64, _dp, i32, _dp, i64, dbl, _dp, i32]
     return L
 
 
@@ -118,3 +129,47 @@ def test_the_real_oracle_passes(gcc, tmp_path):
 def test_a_planted_mistake_fails_a_pin(gcc, tmp_path, name):
     old, new = MUTATIONS[name]
     assert _pins_fail(_build(tmp_path, name, old, new)), name
+
+
+def _hex_sources(L, verts, xi, w):
+    verts, xi, w = _c(verts), _c(xi).reshape(-1, 3), _c(w)
+    n = verts.shape[0] * xi.shape[0]
+    x, a = np.zeros((n, 3)), np.zeros(n)
+    L.gfo_hex_sources(verts.shape[0], _p(verts), xi.shape[0], _p(xi), _p(w), _p(x), _p(a))
+    return x, a
+
+
+def _points(L, x, a, per_cell, rho, obs):
+    x, a, rho, obs = _c(x), _c(a), _c(rho), _c(obs).reshape(-1, 3)
+    out = np.zeros((1, obs.shape[0], 3))
+    L.gfo_forward_points(x.shape[0], _p(x), _p(a), per_cell, _p(rho), 1, _p(obs), obs.shape[0], 1.0, _p(out), 0)
+    return out[0]
+
+
+def _point_pins_fail(L):
+    """True when a pin of the deformed-cell / point-source sums rejects L."""
+    xi, w = wl.gauss_rule(2)
+    # (1) warped cells tiling a 3 x 2 x 1 brick hold its volume exactly
+    _, a = _hex_sources(L, wl.hex_brick_mesh((3, 2, 2), (0.0, 0.0, 0.0), (3.0, 2.0, 1.0), warp=0.1), xi, w)
+    if abs(a.sum() - 6.0) > 1e-12:
+        return True
+    # (2) undeformed cells reproduce the real oracle's voxel sum
+    rng = np.random.default_rng(3)
+    n, lo, h = (3, 2, 2), np.array([0.0, 0.0, 0.0]), np.array([1.0, 1.0, 1.0])
+    rho = rng.normal(size=(2, 2, 3))
+    obs = rng.uniform(-2, 4, size=(10, 3))
+    x, a = _hex_sources(L, wl.hex_brick_mesh(n, lo, lo + np.array(n) * h), xi, w)
+    got = _points(L, x, a, 8, rho.ravel(), obs)
+    want = direct.forward(n, lo, h, xi, w, rho, obs, 1.0)
+    return np.linalg.norm(got - want) > 1e-13 * np.linalg.norm(want)
+
+
+def test_the_real_oracle_passes_the_point_pins(gcc, tmp_path):
+    same = POINT_MUTATIONS["hex_reference_volume"][0]
+    assert not _point_pins_fail(_build(tmp_path, "unchanged_points", same, same))
+
+
+@pytest.mark.parametrize("name", sorted(POINT_MUTATIONS))
+def test_a_planted_point_mistake_fails_a_pin(gcc, tmp_path, name):
+    old, new = POINT_MUTATIONS[name]
+    assert _point_pins_fail(_build(tmp_path, name, old, new)), name

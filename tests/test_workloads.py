@@ -101,3 +101,25 @@ def test_adjoint_batch():
     assert wk.rho.shape == (3, 12, 12, 12) and wk.extra["hidden"].shape == (12, 12, 12)
     assert not np.array_equal(wk.rho[0], wk.rho[1])
     assert np.array_equal(wk.rho[1], wl.exp_cov_grf(12, 250.0, 2000.0, 150.0, 7))
+
+
+def test_voronoi_volumes_tile_the_box():
+    """The scattered-point volumes (Sec. 4) partition the box: all positive,
+    summing to its volume."""
+    pytest.importorskip("scipy")
+    lo, hi = (0.0, 0.0, -2.0), (3.0, 2.0, 0.0)
+    pts = wl.scattered_points(400, lo, hi, seed=3)
+    vol = wl.voronoi_volumes(pts, lo, hi)
+    assert np.all(vol > 0)
+    assert vol.sum() == pytest.approx(12.0, rel=1e-10)
+
+
+def test_topography_workload_recipe():
+    """Terrain-following cells: columns from the flat bottom to the seeded
+    surface; stations 50 m above that surface."""
+    d = wl.topo_workload(nx=8, ny=6, nz=4, stations=5)
+    assert d["verts"].shape == (8 * 6 * 4, 8, 3)
+    assert np.allclose(d["verts"][:, :, 2].min(), -8000.0)
+    surf = wl.topo_surface(d["obs"][:, 0], d["obs"][:, 1], 16000.0, 16000.0, 800.0, 6)
+    assert np.allclose(d["obs"][:, 2] - surf, 50.0)
+    assert d["rho"].shape == (8 * 6 * 4,) and np.all(np.abs(d["rho"] - 2670.0) <= 300.0)
