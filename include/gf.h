@@ -144,6 +144,7 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad,
 /*
  * gf_forward -- evaluate Eq. 1 (discretised, Eq. 7 form) for B densities.
  *   rho_dev   : [B][nz][ny][nx] densities, FP64 or FP32 per rho_dtype
+ *               (a point-source plan: [B][S / per_cell])
  *   B         : 1..opt.max_batch
  *   g_dev     : [B][M][3] FP64 output, observers in caller order, or NULL
  *   gz_dev    : [B][M] FP64 vertical component, or NULL (not both NULL
@@ -288,6 +289,55 @@ gf_status gf_server_destroy(gf_server_t server);
 gf_status gf_plan_set_source_part(gf_plan_t plan, int32_t part, int32_t nparts, int32_t *code_lo,
                                   int32_t *code_hi);
 
+/*
+ * gf_hex_sources -- quadrature points of deformed hexahedral cells (the
+ * general summation of Sec. 2.1: each cell is the trilinear image of the
+ * reference cube [-1, 1]^3 and its integral is the rule's weighted sum of
+ * the integrand times |det dx/dxi| at the rule's nodes).
+ *   verts_dev : [ncell][8][3] FP64 corners (device); corner a = i + 2 j + 4 k
+ *               sits at reference coordinates (2i - 1, 2j - 1, 2k - 1)
+ *   quad      : nq nodes in [-1, 1]^3 and positive weights (host)
+ *   x_dev     : [ncell * nq][3] FP64 output, the trilinear image of node q
+ *               of cell c at source s = c * nq + q
+ *   a_dev     : [ncell * nq] FP64 output, the volume weight
+ *               8 (w_q / sum w) |det dx/dxi(xi_q)| (the cell volume for a
+ *               rule exact on the Jacobian)
+ * The outputs feed gf_plan_create_points with per_cell = nq.  Enqueues on
+ * `stream` and returns; ncell = 0 enqueues nothing.
+ */
+gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *quad,
+                         double *x_dev, double *a_dev, void *stream);
+
+/*
+ * gf_plan_create_points -- a plan over weighted point sources: source s at
+ * x_s with volume weight a_s samples the density of cell s / per_cell, so
+ *     g(r) = G sum_s rho_{s / per_cell} a_s (r - x_s) / |r - x_s|^3,
+ * the N-body form of Eq. 7 for any source layout: the quadrature points of
+ * deformed cells (gf_hex_sources) or a random point distribution whose
+ * points carry the volumes of their Voronoi cells (Sec. 4).
+ *   src_dev : [S][3] FP64 source positions (device, copied by the plan)
+ *   wt_dev  : [S] FP64 volume weights (device, copied by the plan)
+ *   S       : 0 <= S < 2^31, a multiple of per_cell
+ *   per_cell: sources per density cell, >= 1; gf_forward then takes
+ *             rho_dev as [B][S / per_cell]
+ *   obs_dev : [M][3] FP64 observers (device)
+ *   opt     : as for gf_plan_create; leaf_vox and GF_FLAG_SUM_AN do not
+ *             apply (GF_ERR_UNSUPPORTED for the flag)
+ * Direct mode sums every pair (FP64 with compensated sums, or mixed:
+ * positions split into an exact integer number of quanta of 2^-22 of the
+ * joint extent plus an FP32 fraction, FP32 pair terms, FP64 tile sums).
+ * FMM mode builds a uniform octree whose leaf side makes about 48 sources
+ * per leaf of the sources' extent; the sources are sorted by leaf, their
+ * multipole expansions come from the points themselves, and the near field
+ * sums the points of the 27 neighbour leaves.  An exact coincidence of an
+ * observer and a source contributes nothing.  gf_adjoint and
+ * gf_plan_set_source_part return GF_ERR_UNSUPPORTED on such plans.  Waits
+ * for the device.
+ */
+gf_status gf_plan_create_points(const double *src_dev, const double *wt_dev, int64_t S, int32_t per_cell,
+                                const double *obs_dev, int64_t M, const gf_options *opt, void *stream,
+                                gf_plan_t *plan);
+
 /* Release a plan and everything it owns (waits for its device work). */
 gf_status gf_plan_destroy(gf_plan_t plan);
 
@@ -318,7 +368,8 @@ typedef struct {
     int64_t src_lo[24][3];            /* source boxes per level: inclusive */
     int64_t src_hi[24][3];            /* integer bounds of the dense block */
     int64_t M, n_sources;             /* observers; quadrature points (or  */
-                                      /* voxels, with GF_FLAG_SUM_AN)      */
+                                      /* voxels, with GF_FLAG_SUM_AN; the  */
+                                      /* S points of a point-source plan)  */
     int64_t near_pairs;               /* (observer, source) pairs summed   */
                                       /* directly in the near field        */
     int64_t m2l_pairs;                /* (observer box, source box) pairs  */

@@ -85,6 +85,43 @@ const QuadRule *quad_device(gf_plan_s *plan) {
     return reinterpret_cast<const QuadRule *>(plan->d_status + 64);
 }
 
+static gf_status validate_options(int64_t M, const gf_options *opt);
+
+// A quadrature rule: 1..kMaxQuad nodes in [-1, 1]^3, finite positive weights.
+static gf_status validate_quad(const gf_quad *quad) {
+    if (quad->nq < 1 || quad->nq > kMaxQuad || !quad->xi || !quad->w) {
+        set_error("quad.nq = %d must be in [1, %d] with non-NULL xi and w", quad->nq, kMaxQuad);
+        return GF_ERR_INVALID_ARG;
+    }
+    for (int q = 0; q < quad->nq; ++q) {
+        if (!(quad->w[q] > 0.0) || !isfinite(quad->w[q])) {
+            set_error("quad.w[%d] must be finite and positive", q);
+            return GF_ERR_INVALID_ARG;
+        }
+        for (int a = 0; a < 3; ++a)
+            if (!(fabs(quad->xi[3 * q + a]) <= 1.0)) {
+                set_error("quad.xi[%d][%d] must lie in [-1, 1]", q, a);
+                return GF_ERR_INVALID_ARG;
+            }
+    }
+    return GF_OK;
+}
+
+// The device-side form of a validated rule.
+static void fill_quad_rule(const gf_quad *quad, QuadRule &qr) {
+    qr.nq = quad->nq;
+    double wsum = 0.0;
+    for (int q = 0; q < quad->nq; ++q) wsum += quad->w[q];
+    for (int q = 0; q < quad->nq; ++q) {
+        qr.wn[q] = quad->w[q] / wsum;
+        qr.wnf[q] = (float)qr.wn[q];
+        for (int a = 0; a < 3; ++a) {
+            qr.xi[q][a] = quad->xi[3 * q + a];
+            qr.offf[q][a] = (float)(0.5 + 0.5 * quad->xi[3 * q + a]);
+        }
+    }
+}
+
 static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
                           const gf_options *opt) {
     if (!grid || !quad || !opt) {
@@ -107,21 +144,16 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
                   (long long)grid->n[1], (long long)grid->n[2]);
         return GF_ERR_INVALID_ARG;
     }
-    if (quad->nq < 1 || quad->nq > kMaxQuad || !quad->xi || !quad->w) {
-        set_error("quad.nq = %d must be in [1, %d] with non-NULL xi and w", quad->nq, kMaxQuad);
-        return GF_ERR_INVALID_ARG;
+    GF_TRY(validate_quad(quad));
+    GF_TRY(validate_options(M, opt));
+    if (opt->mode == GF_MODE_FMM && !(grid->h[0] == grid->h[1] && grid->h[1] == grid->h[2])) {
+        set_error("FMM mode needs cubic voxels (h[0] == h[1] == h[2])");
+        return GF_ERR_UNSUPPORTED;
     }
-    for (int q = 0; q < quad->nq; ++q) {
-        if (!(quad->w[q] > 0.0) || !isfinite(quad->w[q])) {
-            set_error("quad.w[%d] must be finite and positive", q);
-            return GF_ERR_INVALID_ARG;
-        }
-        for (int a = 0; a < 3; ++a)
-            if (!(fabs(quad->xi[3 * q + a]) <= 1.0)) {
-                set_error("quad.xi[%d][%d] must lie in [-1, 1]", q, a);
-                return GF_ERR_INVALID_ARG;
-            }
-    }
+    return GF_OK;
+}
+
+static gf_status validate_options(int64_t M, const gf_options *opt) {
     if (M < 0 || M > (int64_t(1) << 31) - 1) {
         set_error("M = %lld out of range [0, 2^31)", (long long)M);
         return GF_ERR_INVALID_ARG;
@@ -163,11 +195,33 @@ static gf_status validate(const gf_grid *grid, const gf_quad *quad, int64_t M,
             set_error("opt.leaf_vox = %d out of range [0, 64]", opt->leaf_vox);
             return GF_ERR_INVALID_ARG;
         }
-        if (!(grid->h[0] == grid->h[1] && grid->h[1] == grid->h[2])) {
-            set_error("FMM mode needs cubic voxels (h[0] == h[1] == h[2])");
-            return GF_ERR_UNSUPPORTED;
+    }
+    return GF_OK;
+}
+
+// The end of a plan build: wait for the device, then hand the plan out or
+// free everything it holds.
+static gf_status finish_create(gf_plan_s *p, gf_status s, cudaStream_t st, gf_plan_t *out) {
+    if (s == GF_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("plan build failed on the device: %s", cudaGetErrorString(e));
+            s = GF_ERR_CUDA;
         }
     }
+    if (s != GF_OK) {
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        char keep[512];
+        snprintf(keep, sizeof(keep), "%s", get_error());
+        fmm_destroy(p);
+        p->arena.release();
+        delete p;
+        set_error("%s", keep);
+        return s;
+    }
+    p->device_bytes = p->arena.bytes;
+    *out = p;
     return GF_OK;
 }
 
@@ -237,17 +291,7 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
         qr.wnf[0] = 1.0f;
         for (int a = 0; a < 3; ++a) qr.offf[0][a] = 0.5f;
     } else {
-        qr.nq = quad->nq;
-        double wsum = 0.0;
-        for (int q = 0; q < quad->nq; ++q) wsum += quad->w[q];
-        for (int q = 0; q < quad->nq; ++q) {
-            qr.wn[q] = quad->w[q] / wsum;
-            qr.wnf[q] = (float)qr.wn[q];
-            for (int a = 0; a < 3; ++a) {
-                qr.xi[q][a] = quad->xi[3 * q + a];
-                qr.offf[q][a] = (float)(0.5 + 0.5 * quad->xi[3 * q + a]);
-            }
-        }
+        fill_quad_rule(quad, qr);
     }
     gf_status s = GF_OK;
     // status word (64 ints) followed by the quadrature rule
@@ -270,27 +314,101 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
         else
             s = fmm_create(p, obs_dev, st);
     }
+    return finish_create(p, s, st, out);
+}
+
+gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *quad, double *x_dev, double *a_dev,
+                         void *stream) {
+    if (!quad) {
+        set_error("quad must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    GF_TRY(validate_quad(quad));
+    if (ncell < 0 || ncell > ((int64_t(1) << 31) - 1) / quad->nq) {
+        set_error("ncell = %lld out of range: ncell * nq must be below 2^31", (long long)ncell);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (ncell > 0 && (!verts_dev || !x_dev || !a_dev)) {
+        set_error("verts_dev, x_dev and a_dev must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    QuadRule qr;
+    memset(&qr, 0, sizeof(qr));
+    fill_quad_rule(quad, qr);
+    return hex_sources_run(verts_dev, ncell, qr, x_dev, a_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gf_status gf_plan_create_points(const double *src_dev, const double *wt_dev, int64_t S, int32_t per_cell,
+                                const double *obs_dev, int64_t M, const gf_options *opt, void *stream,
+                                gf_plan_t *out) {
+    if (!out) {
+        set_error("plan output pointer is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!opt) {
+        set_error("opt must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    GF_TRY(validate_options(M, opt));
+    if (opt->reserved0 & GF_FLAG_SUM_AN) {
+        set_error("GF_FLAG_SUM_AN (closed-form voxels) does not apply to point sources");
+        return GF_ERR_UNSUPPORTED;
+    }
+    if (S < 0 || S > (int64_t(1) << 31) - 1) {
+        set_error("S = %lld out of range [0, 2^31)", (long long)S);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (per_cell < 1 || S % per_cell != 0) {
+        set_error("per_cell = %d must be >= 1 and divide S = %lld", per_cell, (long long)S);
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((S > 0 && (!src_dev || !wt_dev)) || (M > 0 && !obs_dev)) {
+        set_error("src_dev, wt_dev (S > 0) and obs_dev (M > 0) must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    gf_plan_s *p = new (std::nothrow) gf_plan_s();
+    if (!p) {
+        set_error("host allocation failed");
+        return GF_ERR_OOM;
+    }
+    cudaGetDevice(&p->device);
+    p->arena.stream = st;
+    p->opt = *opt;
+    p->opt.leaf_vox = 0;
+    p->G = opt->G > 0.0 ? opt->G : 6.67428e-11;
+    p->M = M;
+    p->pts.on = true;
+    p->pts.S = S;
+    p->pts.per_cell = per_cell;
+    p->pts.ncell = S / per_cell;
+    p->nvox = p->pts.ncell;
+    QuadRule &qr = p->quad;   // one unit node: the plan's rule is not used
+    memset(&qr, 0, sizeof(qr));
+    qr.nq = 1;
+    qr.wn[0] = 1.0;
+    qr.wnf[0] = 1.0f;
+    for (int a = 0; a < 3; ++a) qr.offf[0][a] = 0.5f;
+    gf_status s = p->arena.alloc(reinterpret_cast<void **>(&p->d_status), 64 * sizeof(int) + sizeof(QuadRule));
     if (s == GF_OK) {
-        cudaError_t e = cudaStreamSynchronize(st);
+        cudaError_t e = cudaMemsetAsync(p->d_status, 0, 64 * sizeof(int), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_status + 64, &qr, sizeof(QuadRule), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
-            set_error("plan build failed on the device: %s", cudaGetErrorString(e));
+            set_error("plan setup copy failed: %s", cudaGetErrorString(e));
             s = GF_ERR_CUDA;
         }
     }
-    if (s != GF_OK) {
-        cudaDeviceSynchronize();
-        cudaGetLastError();
-        char keep[512];
-        snprintf(keep, sizeof(keep), "%s", get_error());
-        fmm_destroy(p);
-        p->arena.release();
-        delete p;
-        set_error("%s", keep);
-        return s;
+    if (s == GF_OK) {
+        if (opt->mode == GF_MODE_DIRECT) {
+            s = points_prepare_direct(p, src_dev, wt_dev, obs_dev, st);
+            p->near_pairs = p->M * S;
+        } else {
+            s = points_fmm_create(p, src_dev, wt_dev, obs_dev, st);
+        }
     }
-    p->device_bytes = p->arena.bytes;
-    *out = p;
-    return GF_OK;
+    return finish_create(p, s, st, out);
 }
 
 gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int32_t B,
@@ -299,7 +417,8 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int
         set_error("plan is NULL");
         return GF_ERR_INVALID_ARG;
     }
-    if (!rho_dev || (!g_dev && !gz_dev && plan->M > 0)) {
+    const bool no_sources = plan->pts.on && plan->pts.S == 0;
+    if ((!rho_dev && !no_sources) || (!g_dev && !gz_dev && plan->M > 0)) {
         set_error("rho_dev must be non-NULL and at least one of g_dev, gz_dev given");
         return GF_ERR_INVALID_ARG;
     }
@@ -315,7 +434,9 @@ gf_status gf_forward(gf_plan_t plan, const void *rho_dev, int32_t rho_dtype, int
     for (int i = 0; i <= GF_NUM_STAGES; ++i) plan->ev_used[i] = false;
     stage_mark(plan, 0, st);
     if (plan->opt.mode == GF_MODE_DIRECT) {
-        if (plan->opt.reserved0 & GF_FLAG_SUM_AN)
+        if (plan->pts.on)
+            GF_TRY(points_direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
+        else if (plan->opt.reserved0 & GF_FLAG_SUM_AN)
             GF_TRY(sum_an_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
         else
             GF_TRY(direct_forward(plan, rho_dev, rho_dtype, B, g_dev, gz_dev, st));
@@ -344,6 +465,10 @@ gf_status gf_adjoint(gf_plan_t plan, const double *r_dev, int32_t ncomp, int32_t
         return GF_ERR_INVALID_ARG;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->pts.on) {
+        set_error("gf_adjoint of a point-source plan is not implemented");
+        return GF_ERR_UNSUPPORTED;
+    }
     if (plan->part_lo != 0 || plan->part_hi < 64) {
         set_error("gf_adjoint of a plan restricted to a source part is not implemented");
         return GF_ERR_UNSUPPORTED;
@@ -369,8 +494,8 @@ gf_status gf_plan_set_source_part(gf_plan_t plan, int32_t part, int32_t nparts, 
         set_error("need 0 <= part < nparts <= 64 (part = %d, nparts = %d)", part, nparts);
         return GF_ERR_INVALID_ARG;
     }
-    if (plan->opt.mode != GF_MODE_FMM || !plan->fmm) {
-        set_error("source parts are implemented for FMM plans only");
+    if (plan->opt.mode != GF_MODE_FMM || !plan->fmm || plan->pts.on) {
+        set_error("source parts are implemented for FMM plans over voxel grids only");
         return GF_ERR_UNSUPPORTED;
     }
     const FmmPlan *F = plan->fmm;
@@ -507,7 +632,8 @@ gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info *info) {
     info->mode = plan->opt.mode;
     info->precision = plan->opt.precision;
     info->M = plan->M;
-    info->n_sources = plan->nvox * ((plan->opt.reserved0 & GF_FLAG_SUM_AN) ? 1 : plan->quad.nq);
+    info->n_sources =
+        plan->pts.on ? plan->pts.S : plan->nvox * ((plan->opt.reserved0 & GF_FLAG_SUM_AN) ? 1 : plan->quad.nq);
     info->device_bytes = plan->arena.bytes;
     info->near_pairs = plan->near_pairs;
     info->m2l_pairs = plan->m2l_pairs;

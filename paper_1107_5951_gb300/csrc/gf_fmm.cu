@@ -1478,7 +1478,8 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
         GF_TRY(A.alloc(&lv.le, (size_t)std::max<int64_t>(lv.nt, 1) * B * F->KS * rs));
     }
     const int b3 = F->b * F->b * F->b;
-    GF_TRY(A.alloc(&F->mass, (size_t)std::max<int64_t>(F->lev[F->L].ns, 1) * B * b3 * rs));
+    const int64_t nmass = F->points ? plan->pts.S : F->lev[F->L].ns * b3;
+    GF_TRY(A.alloc(&F->mass, (size_t)std::max<int64_t>(nmass, 1) * B * rs));
     static bool il_ready[64] = {false};
     static std::mutex il_mu;
     {
@@ -1491,7 +1492,7 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
         }
     }
     GF_TRY(get_tables(plan->device, F->p, st, &F->tab));
-    GF_TRY(get_p2m(plan, st));
+    if (!F->points) GF_TRY(get_p2m(plan, st));
     return m2l_tc_prepare(plan);
 }
 
@@ -1543,8 +1544,15 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     const int K = F->K, L = F->L;
     const int b3 = F->b * F->b * F->b;
     const Tables *tab = F->tab;
-    const bool fused = p2m_fused_ok<T>(F);
+    const bool pts = F->points;
+    const bool fused = !pts && p2m_fused_ok<T>(F);
     bool up = false;   // level L-1 expansions made straight from the leaf masses
+    if (pts) {
+        // a0 + a3 for point sources: masses in leaf order, P2M over each leaf's points
+        GF_TRY(points_masses<T>(plan, rho, rho_dtype, B, st));
+        stage_mark(plan, 1, st);
+        GF_TRY(points_p2m<T>(plan, B, st));
+    }
     if (fused) {
         // a0 + a3: leaf-blocked densities and P2M (timed as P2M): on the
         // tensor cores for 4^3-voxel leaves in mixed precision, else fused
@@ -1569,7 +1577,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         }
     }
     // a0: leaf-blocked densities
-    if (!fused) {
+    if (!fused && !pts) {
         const FmmLevel &lv = F->lev[L];
         const int64_t total = lv.ns * B * b3;
         const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
@@ -1578,9 +1586,9 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
                                                  block_of(lv), F->b, B, (T *)F->mass, plan->d_status);
         GF_KERNEL_DONE();
     }
-    if (!fused) stage_mark(plan, 1, st);
+    if (!fused && !pts) stage_mark(plan, 1, st);
     // a3: P2M at the leaves
-    if (!fused) {
+    if (!fused && !pts) {
         const FmmLevel &lv = F->lev[L];
         const unsigned grid = ceil_div(lv.ns, kP2MLeaves);
         const size_t shm = sizeof(T) * kP2MLeaves * B * b3;
@@ -1634,7 +1642,9 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     }
     stage_mark(plan, 6, st);
     // a7-a9: near field + L2P + combine + scatter
-    if (F->n_items > 0) {
+    if (pts) {
+        GF_TRY(points_eval<T>(plan, B, g, gz, st));
+    } else if (F->n_items > 0) {
         EvalArgs a;
         a.L = F->L;
         a.part_lo = plan->part_lo;

@@ -71,6 +71,10 @@ struct FmmPlan {
     int L = 0, b = 0, p = 0, K = 0, B = 1, nq = 1;
     int KS = 0;                   // row stride of ME/LE arrays (K padded to 32 in mixed)
     bool mixed = false;
+    // weighted point sources: one leaf of side s_leaf is the length unit
+    // (b = 1), masses are [B][S] in leaf order, and the P2M and near field
+    // read the sources' positions (gf_points.cu)
+    bool points = false;
     int64_t voff[3] = {0, 0, 0};  // grid voxel (0,0,0) sits at tree voxel voff
     double lo[3] = {0, 0, 0};     // root lower corner (m)
     double h = 1, s_leaf = 1, inv_s = 1;
@@ -128,5 +132,9 @@ void il_offsets_host(int cls, signed char out[189][3]);
 
 // Plan-time helpers (gf_fmm.cu)
 gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st);
+// The observer side of the tree for a root geometry set in the plan, then
+// the workspaces (gf_tree.cu).
+gf_status fmm_observer_tree(gf_plan_s *plan, const double *obs, const double oz[2], const double obs_lo[3],
+                            const double obs_hi[3], const double bb[6], cudaStream_t st);
 
 }  // namespace gf

@@ -69,6 +69,21 @@ struct DeviceArena {
 
 struct FmmPlan;   // defined in gf_fmm.cuh
 
+// Weighted point sources of a plan made by gf_plan_create_points: source s
+// sits at x_s with volume weight a_s and samples density s / per_cell.
+struct PointSet {
+    bool on = false;
+    int64_t S = 0, ncell = 0;
+    int per_cell = 1;
+    double *x = nullptr;          // direct: [S][3] caller order; FMM: leaf units from the root corner, by leaf
+    double *a = nullptr;          // [S] volume weights, in the order of x
+    int32_t *perm = nullptr;      // FMM: sorted position -> caller index
+    int64_t *leaf_beg = nullptr;  // FMM: [nleaf + 1] first sorted source of each leaf of the dense block
+    double q = 0.0;               // mixed direct: the length quantum
+    float *xi = nullptr, *xf = nullptr;   // mixed direct: sources' integer and fractional parts (quanta)
+    float *oi = nullptr, *of = nullptr;   // the same for the observers
+};
+
 }  // namespace gf
 
 struct gf_plan_s {
@@ -86,6 +101,7 @@ struct gf_plan_s {
     float *d_obs_fvox = nullptr;     // [M][3] fractional voxel coordinates (mixed)
     double *d_corner = nullptr;      // closed-form voxels: [max_batch][corners] weights
     gf::FmmPlan *fmm = nullptr;
+    gf::PointSet pts;            // point-source plans only
     int *d_status = nullptr;     // device-side check word
     size_t device_bytes = 0;
     int64_t near_pairs = 0, m2l_pairs = 0;
@@ -146,6 +162,23 @@ gf_status fmm_export_tree(gf_plan_s *plan, int level, int32_t *perm, uint64_t *k
 size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_options *opt);
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Weighted point sources (gf_points.cu)
+gf_status hex_sources_run(const double *verts, int64_t ncell, const QuadRule &qr, double *x, double *a,
+                          cudaStream_t st);
+gf_status points_prepare_direct(gf_plan_s *plan, const double *src, const double *wt, const double *obs,
+                                cudaStream_t st);
+gf_status points_direct_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, double *g, double *gz,
+                                cudaStream_t st);
+gf_status points_fmm_create(gf_plan_s *plan, const double *src, const double *wt, const double *obs,
+                            cudaStream_t st);
+template <class T>
+gf_status points_masses(gf_plan_s *plan, const void *rho, int rho_dtype, int B, cudaStream_t st);
+template <class T>
+gf_status points_p2m(gf_plan_s *plan, int B, cudaStream_t st);
+template <class T>
+gf_status points_eval(gf_plan_s *plan, int B, double *g, double *gz, cudaStream_t st);
+gf_status points_count_near(gf_plan_s *plan, unsigned long long *d_out, cudaStream_t st);
 
 // Whether box (X, Y, Z) of level 2 + shift (absolute box coordinates) lies
 // under a level-2 box whose Morton code (x -> bit 0, y -> bit 1, z -> bit 2

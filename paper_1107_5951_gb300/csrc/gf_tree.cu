@@ -524,6 +524,23 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
             lv.ns *= lv.sn[a];
         }
     }
+    return fmm_observer_tree(plan, obs, oz, obs_lo, obs_hi, bb, st);
+}
+
+// The observer side of the tree, for a root geometry already set in the
+// plan (F->lo, F->s_leaf, F->L and the source block of every level): the
+// M2L's reachable source slabs, observer keys and their stable sort, the
+// leaves and every ancestor level, the parity-class order, the observers'
+// offsets from their leaf centres and the evaluation work items; then the
+// expansion workspaces.  oz: the observers' z extent; obs_lo/obs_hi: their
+// bounding box; bb: the root geometry's bounding box (observers joined with
+// the sources).
+gf_status fmm_observer_tree(gf_plan_s *plan, const double *obs, const double oz[2], const double obs_lo[3],
+                            const double obs_hi[3], const double bb[6], cudaStream_t st) {
+    FmmPlan *F = plan->fmm;
+    const int64_t M = plan->M;
+    const int L = F->L;
+    DeviceArena &A = plan->arena;
     {
         // Source z-slabs the M2L of each level reads: observer boxes lie in
         // the leaf z-range of the observers' extent (widened by one leaf
@@ -736,7 +753,9 @@ gf_status fmm_work_counts(gf_plan_s *plan, cudaStream_t st) {
     unsigned long long *d_cntw;
     GF_TRY(A.alloc_n(&d_cntw, 2));
     GF_CUDA(cudaMemsetAsync(d_cntw, 0, 2 * sizeof(unsigned long long), st));
-    if (nleaf > 0) {
+    if (F->points) {
+        GF_TRY(points_count_near(plan, d_cntw, st));
+    } else if (nleaf > 0) {
         count_near<<<ceil_div(nleaf, 256), 256, 0, st>>>(leaf.tkey, F->leaf_beg, nleaf, leaf.slo[0], leaf.slo[1],
                                                          leaf.slo[2], leaf.sn[0], leaf.sn[1], leaf.sn[2],
                                                          (int64_t)F->b * F->b * F->b * F->nq, d_cntw);

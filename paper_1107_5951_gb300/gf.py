@@ -2,10 +2,12 @@
 
 Argument marshalling only: every step of the forward model runs in the CUDA
 kernels of ``libgf.so``.  PyTorch supplies device memory and streams.  The
-functions ``gf_plan_create``, ``gf_forward``, ``gf_adjoint``,
-``gf_plan_destroy``, ``gf_plan_check``, ``gf_plan_bytes``,
-``gf_plan_get_info``, ``gf_plan_export_tree`` and ``gf_last_error`` mirror
-the C entry points one to one; :class:`Plan` wraps them for tensors.
+functions ``gf_plan_create``, ``gf_plan_create_points``, ``gf_hex_sources``,
+``gf_forward``, ``gf_adjoint``, ``gf_plan_destroy``, ``gf_plan_check``,
+``gf_plan_bytes``, ``gf_plan_get_info``, ``gf_plan_export_tree`` and ``gf_last_error`` mirror
+the C entry points one to one; :class:`Plan` (voxel grids),
+:class:`PointsPlan` (weighted point sources) and :func:`hex_sources` wrap
+them for tensors.
 
 There is no fallback: if ``libgf.so`` is missing or cannot be loaded, every
 call raises.
@@ -122,6 +124,8 @@ def load(build_if_missing: bool = True):
         lib.gf_direct_forward_static.argtypes = [P(gf_grid), P(gf_quad), _vp, i64, _vp, i32, i32,
                                                  ctypes.c_double, _vp, _vp, _vp]
         lib.gf_direct_forward_static.restype = ctypes.c_int
+        lib.gf_hex_sources.argtypes = [_vp, i64, P(gf_quad), _vp, _vp, _vp]
+        lib.gf_plan_create_points.argtypes = [_vp, _vp, i64, i32, _vp, i64, P(gf_options), _vp, P(_vp)]
         lib.gf_plan_set_timing.argtypes = [_vp, i32]
         lib.gf_plan_set_source_part.argtypes = [_vp, i32, i32, P(i32), P(i32)]
         lib.gf_plan_stage_times.argtypes = [_vp, P(ctypes.c_double)]
@@ -130,7 +134,7 @@ def load(build_if_missing: bool = True):
         lib.gf_server_wait.argtypes = [_vp, i64, ctypes.c_double, P(ctypes.c_double)]
         lib.gf_server_stats_get.argtypes = [_vp, P(gf_server_stats)]
         lib.gf_server_destroy.argtypes = [_vp]
-        for name in ("gf_plan_create", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
+        for name in ("gf_plan_create", "gf_hex_sources", "gf_plan_create_points", "gf_forward", "gf_adjoint", "gf_plan_destroy", "gf_plan_check",
                      "gf_plan_bytes", "gf_plan_get_info", "gf_plan_export_tree", "gf_plan_set_timing",
                      "gf_plan_stage_times", "gf_plan_set_source_part", "gf_server_create", "gf_server_submit", "gf_server_wait",
                      "gf_server_stats_get", "gf_server_destroy"):
@@ -158,6 +162,18 @@ def gf_plan_create(grid: gf_grid, quad: gf_quad, obs_ptr: int, M: int, opt: gf_o
     plan = _vp()
     _check(load().gf_plan_create(ctypes.byref(grid), ctypes.byref(quad), _vp(obs_ptr), M,
                                  ctypes.byref(opt), _vp(stream), ctypes.byref(plan)))
+    return plan.value
+
+
+def gf_hex_sources(verts_ptr: int, ncell: int, quad: gf_quad, x_ptr: int, a_ptr: int, stream: int = 0):
+    _check(load().gf_hex_sources(_vp(verts_ptr), ncell, ctypes.byref(quad), _vp(x_ptr), _vp(a_ptr), _vp(stream)))
+
+
+def gf_plan_create_points(src_ptr: int, wt_ptr: int, S: int, per_cell: int, obs_ptr: int, M: int,
+                          opt: gf_options, stream: int = 0) -> int:
+    plan = _vp()
+    _check(load().gf_plan_create_points(_vp(src_ptr), _vp(wt_ptr), S, per_cell, _vp(obs_ptr), M,
+                                        ctypes.byref(opt), _vp(stream), ctypes.byref(plan)))
     return plan.value
 
 
@@ -481,6 +497,101 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def hex_sources(verts, xi, w, stream=None):
+    """Quadrature points and volume weights of deformed hexahedral cells
+    (``gf_hex_sources``).  verts: CUDA float64 tensor (ncell, 8, 3), corner
+    a = i + 2 j + 4 k at reference signs (2i - 1, 2j - 1, 2k - 1); (xi, w):
+    the rule on [-1, 1]^3.  Returns x (ncell * nq, 3) and a (ncell * nq,),
+    source c * nq + q being node q of cell c."""
+    import torch
+    if not (isinstance(verts, torch.Tensor) and verts.is_cuda):
+        raise TypeError("verts must be a CUDA tensor")
+    verts = verts.to(torch.float64).contiguous()
+    if verts.numel() % 24 != 0:
+        raise ValueError("verts must have shape (ncell, 8, 3)")
+    ncell = verts.numel() // 24
+    q = _Quad(xi, w)
+    nq = int(q.c.nq)
+    x = torch.empty((ncell * nq, 3), dtype=torch.float64, device=verts.device)
+    a = torch.empty((ncell * nq,), dtype=torch.float64, device=verts.device)
+    with torch.cuda.device(verts.device):
+        gf_hex_sources(verts.data_ptr(), ncell, q.c, x.data_ptr(), a.data_ptr(), _stream_handle(stream))
+    return x, a
+
+
+class PointsPlan(Plan):
+    """A forward-model plan over weighted point sources
+    (``gf_plan_create_points``): source s at src[s] with volume weight
+    wt[s] samples density s // per_cell.  src (S, 3), wt (S,) and obs (M, 3)
+    are CUDA float64 tensors; forward takes rho of shape (ncell,) or
+    (B, ncell), ncell = S // per_cell."""
+
+    def __init__(self, src, wt, obs, per_cell=1, mode="fmm", precision="fp64", p=8, max_batch=1, G=0.0,
+                 stream=None, m2l="auto", flags=0):
+        import torch
+        for t, n in ((src, "src"), (wt, "wt"), (obs, "obs")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda):
+                raise TypeError("%s must be a CUDA tensor" % n)
+        src = src.to(torch.float64).contiguous().reshape(-1, 3)
+        wt = wt.to(torch.float64).contiguous().reshape(-1)
+        obs = obs.to(torch.float64).contiguous().reshape(-1, 3)
+        if wt.shape[0] != src.shape[0]:
+            raise ValueError("wt must hold one weight per source")
+        self.S = int(src.shape[0])
+        self.per_cell = int(per_cell)
+        self.ncell = self.S // max(self.per_cell, 1)
+        self.shape = (self.ncell,)
+        self.M = int(obs.shape[0])
+        self.max_batch = int(max_batch)
+        self.device = obs.device
+        if m2l not in ("auto", "simt"):
+            raise ValueError("m2l must be 'auto' or 'simt'")
+        self._opt = make_options(mode, precision, p, 0, max_batch, G,
+                                 (GF_FLAG_M2L_SIMT if m2l == "simt" else 0) | int(flags))
+        self.handle = None
+        with torch.cuda.device(self.device):
+            self.handle = gf_plan_create_points(src.data_ptr(), wt.data_ptr(), self.S, self.per_cell,
+                                                obs.data_ptr(), self.M, self._opt, _stream_handle(stream))
+
+    def forward(self, rho, g=None, gz=None, want_g=True, want_gz=False, stream=None):
+        """rho: CUDA tensor (ncell,) or (B, ncell), float32/float64.  Returns
+        (g, gz) as :meth:`Plan.forward` does."""
+        import torch
+        if not isinstance(rho, torch.Tensor) or rho.dim() not in (1, 2) or rho.shape[-1] != self.ncell:
+            raise ValueError("rho must be a tensor of shape (ncell,) or (B, ncell), ncell = %d" % self.ncell)
+        single = rho.dim() == 1
+        B = 1 if single else int(rho.shape[0])
+        rho = rho.contiguous().reshape(B, self.ncell)
+        _check_tensor(rho, "rho", B * self.ncell, self.device, (torch.float32, torch.float64))
+        dt = GF_DTYPE_F64 if rho.dtype == torch.float64 else GF_DTYPE_F32
+        own_g, own_gz = g is None, gz is None
+        if want_g and g is None:
+            g = torch.empty((B, self.M, 3), dtype=torch.float64, device=rho.device)
+        if want_gz and gz is None:
+            gz = torch.empty((B, self.M), dtype=torch.float64, device=rho.device)
+        if g is not None:
+            _check_tensor(g, "g", B * self.M * 3, self.device)
+        if gz is not None:
+            _check_tensor(gz, "gz", B * self.M, self.device)
+        with torch.cuda.device(self.device):
+            gf_forward(self.handle, rho.data_ptr(), dt, B, g.data_ptr() if g is not None else 0,
+                       gz.data_ptr() if gz is not None else 0, _stream_handle(stream))
+        if single:
+            g = g[0] if (g is not None and own_g) else g
+            gz = gz[0] if (gz is not None and own_gz) else gz
+        return g, gz
+
+    def adjoint(self, r, ncomp=1, grad=None, stream=None):
+        """Not implemented for point sources: the library answers
+        GF_ERR_UNSUPPORTED, raised here as GfError."""
+        import torch
+        if grad is None:
+            grad = torch.empty((1, self.ncell), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            gf_adjoint(self.handle, r.data_ptr(), ncomp, 1, grad.data_ptr(), _stream_handle(stream))
+        return grad
 
 
 def plan_bytes(shape, origin, h, xi, w, M, **opts) -> int:

@@ -195,3 +195,35 @@ def test_no_gpu_means_an_error_not_a_fallback():
     rc = lib.gf_plan_create(ctypes.byref(grid), ctypes.byref(q.c), obs.ctypes.data, 1, ctypes.byref(opt), None,
                             ctypes.byref(plan))
     assert rc != gf.GF_OK and not plan.value
+
+
+def test_point_source_arguments_rejected_on_host():
+    """gf_plan_create_points and gf_hex_sources reject bad sizes, a per_cell
+    that does not divide S, missing pointers and the closed-form flag before
+    any device call; gf_hex_sources with no cells enqueues nothing."""
+    lib = pkg.load()
+    plan = ctypes.c_void_p()
+    buf = np.zeros(64)
+    p = buf.ctypes.data
+
+    def create(S, per_cell, src=p, wt=p, obs=p, M=2, **kw):
+        opt = gf.make_options(**kw)
+        return lib.gf_plan_create_points(src, wt, S, per_cell, obs, M, ctypes.byref(opt), None,
+                                         ctypes.byref(plan))
+
+    assert create(10, 3, mode="direct") == gf.GF_ERR_INVALID_ARG
+    assert "divide" in gf.gf_last_error()
+    assert create(10, 0, mode="direct") == gf.GF_ERR_INVALID_ARG
+    assert create(-1, 1, mode="direct") == gf.GF_ERR_INVALID_ARG
+    assert create(1 << 31, 1, mode="direct") == gf.GF_ERR_INVALID_ARG
+    assert create(4, 1, src=None, mode="direct") == gf.GF_ERR_INVALID_ARG
+    assert create(4, 1, obs=None, mode="fmm", p=6) == gf.GF_ERR_INVALID_ARG
+    assert create(4, 1, mode="fmm", p=0) == gf.GF_ERR_INVALID_ARG
+    assert create(4, 1, mode="fmm", p=6, flags=gf.GF_FLAG_SUM_AN) == gf.GF_ERR_UNSUPPORTED
+    assert not plan.value
+    q = gf._Quad(*wl.gauss_rule(2))
+    assert lib.gf_hex_sources(None, 0, ctypes.byref(q.c), None, None, None) == gf.GF_OK
+    assert lib.gf_hex_sources(None, 3, ctypes.byref(q.c), None, None, None) == gf.GF_ERR_INVALID_ARG
+    assert lib.gf_hex_sources(p, -1, ctypes.byref(q.c), p, p, None) == gf.GF_ERR_INVALID_ARG
+    q.w[0] = 0.0
+    assert lib.gf_hex_sources(p, 1, ctypes.byref(q.c), p, p, None) == gf.GF_ERR_INVALID_ARG
