@@ -117,11 +117,15 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64 FMM and the lower-degree runs beside the headline")
-    ap.add_argument("--workload", default="scale", choices=["volume", "scale", "serving", "adjoint", "sum_an"],
+    ap.add_argument("--points", type=int, default=1 << 24, help="points: number of scattered points")
+    ap.add_argument("--workload", default="scale",
+                    choices=["volume", "scale", "serving", "adjoint", "sum_an", "topo_hex", "points"],
                     help="scale (default): 464^3 layered model, 1024^2 stations; volume: 128^3 random "
                          "field, stations + voxel centres; serving: a stream of uneven requests; adjoint: misfit "
                          "gradients of 16 models at 256^2 stations; sum_an: voxels integrated in closed form "
-                         "(FMM: 128^3 random field at 512^2 stations; --mode direct: the 16^3 prism model)")
+                         "(FMM: 128^3 random field at 512^2 stations; --mode direct: the 16^3 prism model); "
+                         "topo_hex: terrain-following hexahedra (256 x 256 x 64 cells, 8 nodes each) at 512^2 "
+                         "draped stations; points: 2^24 scattered points with volumes at 512^2 stations")
     ap.add_argument("--requests", type=int, default=512, help="serving: requests per pass")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests on the device at once")
     ap.add_argument("--rate", type=float, default=0.0,
@@ -221,7 +225,7 @@ def job_rate(units_per_rank, world, seconds):
 # Expansion degree per workload: the headline runs the mixed-precision FMM at
 # a degree whose sampled error stays below the metric's 1e-6 with margin, and
 # the plain FP64 FMM beside it at the smallest degree that meets 1e-6.
-DEFAULT_P = {"scale": 11, "volume": 12, "sum_an": 12}
+DEFAULT_P = {"scale": 11, "volume": 12, "sum_an": 12, "topo_hex": 12, "points": 12}
 FP64_P = {"scale": 10, "volume": 14}
 SWEEP_P = (4, 6, 8)
 REL_ERR_BAR = 1e-6
@@ -350,8 +354,54 @@ def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4):
 
 
 # ------------------------------------------------------------------ reference arm
+def points_reference(args, world):
+    """The host arm of the point-source workloads: the oracle's direct sum
+    (node images and weights included for the hexahedra) on a bounded sample
+    of stations per step."""
+    from oracle import direct
+    from paper_1107_5951_gb300 import workloads as wl
+    hexes = args.workload == "topo_hex"
+    if hexes:
+        n = args.side or 256
+        wk = wl.topo_workload(n, n, max(1, n // 4), args.stations or 512, 2)
+        S = len(wk["rho"]) * len(wk["w"])
+    else:
+        wk = wl.points_cloud(args.points, args.stations or 512)
+        S = len(wk["a"])
+    M = len(wk["obs"])
+    per_step = int(max(8, min(M, 3.0e9 / S)))
+    rng = np.random.default_rng(31)
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(M, per_step, replace=False))
+        t0 = time.perf_counter()
+        if hexes:
+            direct.forward_hex(wk["verts"], wk["xi"], wk["w"], wk["rho"], wk["obs"][idx], wk["G"])
+        else:
+            direct.forward_points(wk["x"], wk["a"], 1, wk["rho"], wk["obs"][idx], wk["G"])
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = S * per_step * len(times) / sum(times)
+    sample = "%d seeded stations per step of %d x all %d sources" % (per_step, M, S)
+    line = {"impl": "reference",
+            "metric": "effective interactions/s (%s)" % ("deformed hexahedra" if hexes else "scattered points"),
+            "value": value, "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wk["name"], "N_sources": int(S), "M_observers": int(M),
+                       "rel_err_bar": REL_ERR_BAR, "l2_flush": "host arm: n/a"},
+            "method": {"impl": "FP64 direct sum on the host cores (the oracle)"},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": direct.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args, rank, world):
     if rank != 0:
+        return
+    if args.workload in ("topo_hex", "points"):
+        points_reference(args, world)
         return
     wk = make_workload(args)
     n_src = wk.n_sources
@@ -794,6 +844,137 @@ def bench_sum_an(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ point sources
+def bench_points(args, rank, world):
+    """Weighted point sources.  topo_hex: a terrain-following hexahedral
+    mesh (256 x 256 x 64 cells over 16 km x 16 km, 8 km deep, 800 m relief;
+    the 2^3 Gauss rule per cell: 33.5M sources) at 512^2 stations draped
+    50 m over the terrain; a step = gf_hex_sources (node images and |det J|
+    weights) + plan build + forward + release.  points: 2^24 scattered
+    points with volumes in a 16 km x 16 km x 4 km slab at 512^2 stations; a
+    step = plan build + forward + release.  Unit of work: a (source,
+    observer) pair."""
+    import torch
+
+    import paper_1107_5951_gb300 as pkg
+    from oracle import direct
+    from paper_1107_5951_gb300 import workloads as wl
+
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hexes = args.workload == "topo_hex"
+    mode = "direct" if args.mode == "direct" else "fmm"
+    precision = args.precision
+    p = args.p if args.p else (DEFAULT_P[args.workload] if precision == "mixed" else 14)
+    if hexes:
+        n = args.side or 256
+        wk = wl.topo_workload(n, n, max(1, n // 4), args.stations or 512, 2)
+        per_cell = len(wk["w"])
+        S = len(wk["rho"]) * per_cell
+        verts_d = torch.tensor(wk["verts"], dtype=torch.float64, device=dev)
+        name = wk["name"]
+    else:
+        wk = wl.points_cloud(args.points, args.stations or 512)
+        per_cell, S = 1, len(wk["a"])
+        x_d = torch.tensor(wk["x"], dtype=torch.float64, device=dev)
+        a_d = torch.tensor(wk["a"], dtype=torch.float64, device=dev)
+        name = wk["name"]
+    M = len(wk["obs"])
+    stream = torch.cuda.Stream(device=dev)
+    obs_d = torch.tensor(wk["obs"], dtype=torch.float64, device=dev)
+    rdt = torch.float32 if precision == "mixed" else torch.float64
+    rho_d = torch.tensor(wk["rho"], dtype=rdt, device=dev)
+    g_d = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    kw = dict(per_cell=per_cell, mode=mode, precision=precision, p=p, G=wk["G"], stream=stream,
+              m2l=args.m2l)
+
+    def sources():
+        if hexes:
+            return pkg.hex_sources(verts_d, wk["xi"], wk["w"], precision=precision, stream=stream)
+        return x_d, a_d
+
+    def step():
+        with torch.cuda.stream(stream):
+            x, a = sources()
+            plan = pkg.PointsPlan(x, a, obs_d, **kw)
+            plan.forward(rho_d, g=g_d, stream=stream)
+            plan.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local_rank, not args.no_clocks)
+    launches0 = pkg.gf_launch_count()
+    ev = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        step()
+        b0.record(stream)
+        ev.append((a0, b0))
+    torch.cuda.synchronize()
+    launches = pkg.gf_launch_count() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+    # the forward alone, with the plan built; its stages
+    with torch.cuda.stream(stream):
+        x, a = sources()
+        plan = pkg.PointsPlan(x, a, obs_d, **kw)
+    torch.cuda.synchronize()
+    ms_solve = timed_forwards(plan, rho_d, g_d, stream, flush, max(3, args.steps))
+    stages = None
+    roof = None
+    info = plan.info
+    if mode == "fmm":
+        plan.set_timing(True)
+        plan.forward(rho_d, g=g_d, stream=stream)
+        stages = plan.stage_times()
+        plan.set_timing(False)
+        roof = fmm_roofline(stages, info, args, load_peaks(), name)
+        if roof["stage"] == "eval":
+            roof["kernel"] = "point_eval (near field over the neighbour leaves' points + L2P + combine)"
+    torch.cuda.synchronize()
+    g_host = g_d.cpu().numpy()
+    work = {"near_pairs": int(info.near_pairs), "m2l_box_pairs": int(info.m2l_pairs), "levels": int(info.L),
+            "leaf_side_m": float(info.leaf_side)}
+    plan.close()
+    err, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(31)
+        idx = np.sort(rng.choice(M, min(M, 64), replace=False))
+        rho64 = np.asarray(wk["rho"], dtype=np.float32 if precision == "mixed" else np.float64).astype(np.float64)
+        t1 = time.perf_counter()
+        if hexes:
+            want = direct.forward_hex(wk["verts"], wk["xi"], wk["w"], rho64, wk["obs"][idx], wk["G"])
+        else:
+            want = direct.forward_points(wk["x"], wk["a"], 1, rho64, wk["obs"][idx], wk["G"])
+        dt = time.perf_counter() - t1
+        err = float(np.linalg.norm(g_host[idx] - want) / np.linalg.norm(want))
+        cpu = {"value": S * len(idx) / dt, "unit": "interactions/s", "cores": direct.max_threads(),
+               "kind": "oracle", "sample": "%d seeded stations of %d x all %d sources%s (%.1f s)"
+               % (len(idx), M, S, ", node images and weights included" if hexes else "", dt)}
+    if rank != 0:
+        return
+    line = {"metric": "effective interactions/s (%s)" % ("deformed hexahedra" if hexes else "scattered points"),
+            "value": job_rate(float(S) * M, world, ms * 1e-3), "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": name, "N_sources": int(S), "M_observers": int(M), "rel_err_bar": REL_ERR_BAR,
+                       "l2_flush": "256 MiB buffer written between timed steps"},
+            "method": {"mode": mode, "precision": precision, "p": p if mode == "fmm" else None,
+                       "step": ("gf_hex_sources + " if hexes else "") + "plan build + forward + release"},
+            "ms_per_solve": ms_solve, "stages_ms": stages, "work": work, "rel_err_vs_oracle_sample": err,
+            "meets_rel_err_bar": None if err is None else bool(err <= REL_ERR_BAR),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": None, "clocks": clk, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 def bench_serving(args, rank, world):
     """Serving stream: `--requests` forward solves, grid side n log-uniform
@@ -947,6 +1128,8 @@ def main():
             bench_adjoint(args, rank, world)
         elif args.workload == "sum_an":
             bench_sum_an(args, rank, world)
+        elif args.workload in ("topo_hex", "points"):
+            bench_points(args, rank, world)
         else:
             bench_gf(args, rank, world)
     finally:

@@ -297,6 +297,11 @@ gf_status gf_plan_set_source_part(gf_plan_t plan, int32_t part, int32_t nparts, 
  *   verts_dev : [ncell][8][3] FP64 corners (device); corner a = i + 2 j + 4 k
  *               sits at reference coordinates (2i - 1, 2j - 1, 2k - 1)
  *   quad      : nq nodes in [-1, 1]^3 and positive weights (host)
+ *   precision : GF_PREC_FP64: every step in FP64.  GF_PREC_MIXED (for
+ *               mixed-precision plans): the corners as 64-bit fixed point,
+ *               the image relative to the cell's first corner and the
+ *               Jacobian in FP32 -- positions within about 1e-6 of the
+ *               cell's extent, weights within about 1e-6 relative.
  *   x_dev     : [ncell * nq][3] FP64 output, the trilinear image of node q
  *               of cell c at source s = c * nq + q
  *   a_dev     : [ncell * nq] FP64 output, the volume weight
@@ -305,7 +310,7 @@ gf_status gf_plan_set_source_part(gf_plan_t plan, int32_t part, int32_t nparts, 
  * The outputs feed gf_plan_create_points with per_cell = nq.  Enqueues on
  * `stream` and returns; ncell = 0 enqueues nothing.
  */
-gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *quad,
+gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *quad, int32_t precision,
                          double *x_dev, double *a_dev, void *stream);
 
 /*

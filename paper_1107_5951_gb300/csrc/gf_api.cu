@@ -317,10 +317,14 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
     return finish_create(p, s, st, out);
 }
 
-gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *quad, double *x_dev, double *a_dev,
-                         void *stream) {
+gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *quad, int32_t precision,
+                         double *x_dev, double *a_dev, void *stream) {
     if (!quad) {
         set_error("quad must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (precision != GF_PREC_FP64 && precision != GF_PREC_MIXED) {
+        set_error("precision = %d is neither GF_PREC_FP64 nor GF_PREC_MIXED", precision);
         return GF_ERR_INVALID_ARG;
     }
     GF_TRY(validate_quad(quad));
@@ -335,7 +339,7 @@ gf_status gf_hex_sources(const double *verts_dev, int64_t ncell, const gf_quad *
     QuadRule qr;
     memset(&qr, 0, sizeof(qr));
     fill_quad_rule(quad, qr);
-    return hex_sources_run(verts_dev, ncell, qr, x_dev, a_dev, reinterpret_cast<cudaStream_t>(stream));
+    return hex_sources_run(verts_dev, ncell, qr, precision, x_dev, a_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
 gf_status gf_plan_create_points(const double *src_dev, const double *wt_dev, int64_t S, int32_t per_cell,

@@ -132,6 +132,12 @@ void il_offsets_host(int cls, signed char out[189][3]);
 
 // Plan-time helpers (gf_fmm.cu)
 gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st);
+// Fixed point with k fractional bits for the coordinates of a root box and
+// the bounding box bb (every coordinate below 2^61 in magnitude): the root
+// corner and half a leaf side in those units, and 2^-k / h.  Returns k, or
+// -1 when the coordinates are too large for 64-bit fixed point (gf_tree.cu).
+int fixed_point_frame(const FmmPlan *F, const double bb[6], long long lofix[3], long long *halfleaf_fix,
+                      float *fix_to_unit);
 // The observer side of the tree for a root geometry set in the plan, then
 // the workspaces (gf_tree.cu).
 gf_status fmm_observer_tree(gf_plan_s *plan, const double *obs, const double oz[2], const double obs_lo[3],

@@ -75,8 +75,10 @@ struct PointSet {
     bool on = false;
     int64_t S = 0, ncell = 0;
     int per_cell = 1;
-    double *x = nullptr;          // direct: [S][3] caller order; FMM: leaf units from the root corner, by leaf
-    double *a = nullptr;          // [S] volume weights, in the order of x
+    double *x = nullptr;          // direct: [S][3] positions, caller order
+    double *a = nullptr;          // direct: [S] volume weights
+    void *loc = nullptr;          // FMM: [S][4] in the plan's precision, sorted by leaf: offset from the
+                                  // leaf's centre and volume, in leaf units
     int32_t *perm = nullptr;      // FMM: sorted position -> caller index
     int64_t *leaf_beg = nullptr;  // FMM: [nleaf + 1] first sorted source of each leaf of the dense block
     double q = 0.0;               // mixed direct: the length quantum
@@ -164,8 +166,8 @@ size_t fmm_bytes_estimate(const gf_grid *grid, int nq, int64_t M, const gf_optio
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // Weighted point sources (gf_points.cu)
-gf_status hex_sources_run(const double *verts, int64_t ncell, const QuadRule &qr, double *x, double *a,
-                          cudaStream_t st);
+gf_status hex_sources_run(const double *verts, int64_t ncell, const QuadRule &qr, int precision, double *x,
+                          double *a, cudaStream_t st);
 gf_status points_prepare_direct(gf_plan_s *plan, const double *src, const double *wt, const double *obs,
                                 cudaStream_t st);
 gf_status points_direct_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, double *g, double *gz,

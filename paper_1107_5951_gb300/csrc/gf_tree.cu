@@ -10,6 +10,7 @@
 
 #include "gf_fmm.cuh"
 #include "gf_prim.cuh"
+#include "gf_simd.cuh"
 
 namespace gf {
 namespace {
@@ -58,42 +59,6 @@ struct Geo {
     long long lofix[3], halfleaf_fix;
     float fix_to_vox;
 };
-
-// Sign, exponent and the top 23 mantissa bits of a double repacked as a
-// float (truncation: relative error below 2^-23), integer operations only;
-// false when the value is outside the normal FP32 range (zero excepted).
-__device__ __forceinline__ bool trunc_f32(double x, float &f) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < -126 || e > 127) {
-        f = 0.f;
-        return (b << 1) == 0;
-    }
-    f = __uint_as_float((unsigned)((b >> 32) & 0x80000000ull) | ((unsigned)(e + 127) << 23) |
-                        (unsigned)((b >> 29) & 0x7fffffull));
-    return true;
-}
-
-// trunc(x 2^k) for |x 2^k| < 2^62, integer operations only.
-__device__ __forceinline__ long long to_fix(double x, int k) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e == 0) return 0;
-    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
-    const int sh = e - 1075 + k;
-    const long long v = sh >= 0 ? (long long)(m << sh) : (sh > -64 ? (long long)(m >> -sh) : 0);
-    return (b >> 63) ? -v : v;
-}
-
-// |v| < 2^63 as a float, truncating, integer operations only.
-__device__ __forceinline__ float fix_to_f32(long long v) {
-    if (v == 0) return 0.f;
-    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int lz = __clzll((long long)a);
-    const unsigned long long n = a << lz;   // leading one at bit 63
-    return __uint_as_float((v < 0 ? 0x80000000u : 0u) | ((unsigned)(63 - lz + 127) << 23) |
-                           (unsigned)((n >> 40) & 0x7fffffull));
-}
 
 // Leaf key of every observer: floor((x - lo) * inv_s) with one rounded
 // subtraction and one rounded multiplication, clamped to the root.
@@ -527,6 +492,25 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     return fmm_observer_tree(plan, obs, oz, obs_lo, obs_hi, bb, st);
 }
 
+int fixed_point_frame(const FmmPlan *F, const double bb[6], long long lofix[3], long long *halfleaf_fix,
+                      float *fix_to_unit) {
+    // k fractional bits such that every coordinate of the observers, the
+    // sources and the root box stays below 2^61 in magnitude
+    double xmax = 0.0;
+    for (int a = 0; a < 3; ++a)
+        xmax = std::max({xmax, std::fabs(bb[a]), std::fabs(bb[3 + a]), std::fabs(F->lo[a]),
+                         std::fabs(F->lo[a] + std::ldexp(F->s_leaf, F->L))});
+    int ex = 0;
+    std::frexp(std::max(xmax, 1e-300), &ex);   // xmax < 2^ex
+    const int k = std::min(80, 61 - ex);
+    if (k < 0) return -1;
+    const double hl = 0.5 * F->b * F->h;
+    for (int a = 0; a < 3; ++a) lofix[a] = (long long)std::llround(std::ldexp(F->lo[a], k));
+    *halfleaf_fix = (long long)std::llround(std::ldexp(hl, k));
+    *fix_to_unit = (float)(std::ldexp(1.0, -k) / F->h);
+    return k;
+}
+
 // The observer side of the tree, for a root geometry already set in the
 // plan (F->lo, F->s_leaf, F->L and the source block of every level): the
 // M2L's reachable source slabs, observer keys and their stable sort, the
@@ -564,24 +548,7 @@ gf_status fmm_observer_tree(gf_plan_s *plan, const double *obs, const double oz[
     g.b = F->b;
     for (int a = 0; a < 3; ++a) g.lof[a] = (float)F->lo[a];
     g.isf = (float)F->inv_s;
-    {
-        // fixed point with k fractional bits such that every coordinate of the
-        // observers and of the root box stays below 2^61 in magnitude
-        double xmax = 0.0;
-        for (int a = 0; a < 3; ++a)
-            xmax = std::max({xmax, std::fabs(bb[a]), std::fabs(bb[3 + a]), std::fabs(F->lo[a]),
-                             std::fabs(F->lo[a] + std::ldexp(F->s_leaf, L))});
-        int ex = 0;
-        std::frexp(std::max(xmax, 1e-300), &ex);   // xmax < 2^ex
-        const int k = std::min(80, 61 - ex);
-        g.fixk = k >= 0 ? k : -1;
-        if (g.fixk >= 0) {
-            const double hl = 0.5 * F->b * F->h;
-            for (int a = 0; a < 3; ++a) g.lofix[a] = (long long)std::llround(std::ldexp(F->lo[a], k));
-            g.halfleaf_fix = (long long)std::llround(std::ldexp(hl, k));
-            g.fix_to_vox = (float)(std::ldexp(1.0, -k) / F->h);
-        }
-    }
+    g.fixk = fixed_point_frame(F, bb, g.lofix, &g.halfleaf_fix, &g.fix_to_vox);
 
     // ---- observer keys and stable sort by (key, index)
     const int64_t Mx = std::max<int64_t>(M, 1);

@@ -124,7 +124,7 @@ def load(build_if_missing: bool = True):
         lib.gf_direct_forward_static.argtypes = [P(gf_grid), P(gf_quad), _vp, i64, _vp, i32, i32,
                                                  ctypes.c_double, _vp, _vp, _vp]
         lib.gf_direct_forward_static.restype = ctypes.c_int
-        lib.gf_hex_sources.argtypes = [_vp, i64, P(gf_quad), _vp, _vp, _vp]
+        lib.gf_hex_sources.argtypes = [_vp, i64, P(gf_quad), i32, _vp, _vp, _vp]
         lib.gf_plan_create_points.argtypes = [_vp, _vp, i64, i32, _vp, i64, P(gf_options), _vp, P(_vp)]
         lib.gf_plan_set_timing.argtypes = [_vp, i32]
         lib.gf_plan_set_source_part.argtypes = [_vp, i32, i32, P(i32), P(i32)]
@@ -165,8 +165,10 @@ def gf_plan_create(grid: gf_grid, quad: gf_quad, obs_ptr: int, M: int, opt: gf_o
     return plan.value
 
 
-def gf_hex_sources(verts_ptr: int, ncell: int, quad: gf_quad, x_ptr: int, a_ptr: int, stream: int = 0):
-    _check(load().gf_hex_sources(_vp(verts_ptr), ncell, ctypes.byref(quad), _vp(x_ptr), _vp(a_ptr), _vp(stream)))
+def gf_hex_sources(verts_ptr: int, ncell: int, quad: gf_quad, precision: int, x_ptr: int, a_ptr: int,
+                   stream: int = 0):
+    _check(load().gf_hex_sources(_vp(verts_ptr), ncell, ctypes.byref(quad), precision, _vp(x_ptr), _vp(a_ptr),
+                                 _vp(stream)))
 
 
 def gf_plan_create_points(src_ptr: int, wt_ptr: int, S: int, per_cell: int, obs_ptr: int, M: int,
@@ -499,12 +501,14 @@ class Plan:
         self.close()
 
 
-def hex_sources(verts, xi, w, stream=None):
+def hex_sources(verts, xi, w, precision="fp64", stream=None):
     """Quadrature points and volume weights of deformed hexahedral cells
     (``gf_hex_sources``).  verts: CUDA float64 tensor (ncell, 8, 3), corner
     a = i + 2 j + 4 k at reference signs (2i - 1, 2j - 1, 2k - 1); (xi, w):
-    the rule on [-1, 1]^3.  Returns x (ncell * nq, 3) and a (ncell * nq,),
-    source c * nq + q being node q of cell c."""
+    the rule on [-1, 1]^3; precision "fp64" or "mixed" (FP32 relative to
+    each cell's first corner, for mixed-precision plans).  Returns x
+    (ncell * nq, 3) and a (ncell * nq,), source c * nq + q being node q of
+    cell c."""
     import torch
     if not (isinstance(verts, torch.Tensor) and verts.is_cuda):
         raise TypeError("verts must be a CUDA tensor")
@@ -517,7 +521,9 @@ def hex_sources(verts, xi, w, stream=None):
     x = torch.empty((ncell * nq, 3), dtype=torch.float64, device=verts.device)
     a = torch.empty((ncell * nq,), dtype=torch.float64, device=verts.device)
     with torch.cuda.device(verts.device):
-        gf_hex_sources(verts.data_ptr(), ncell, q.c, x.data_ptr(), a.data_ptr(), _stream_handle(stream))
+        prec = {"fp64": GF_PREC_FP64, "mixed": GF_PREC_MIXED}[precision] if isinstance(precision, str) \
+            else int(precision)
+        gf_hex_sources(verts.data_ptr(), ncell, q.c, prec, x.data_ptr(), a.data_ptr(), _stream_handle(stream))
     return x, a
 
 

@@ -393,3 +393,27 @@ def voronoi_volumes(pts, lo, hi) -> np.ndarray:
         region = vor.regions[vor.point_region[i]]
         vol[i] = ConvexHull(vor.vertices[region]).volume
     return vol
+
+
+def points_cloud(n: int = 1 << 24, stations: int = 512, seed: int = 8):
+    """Scattered-density workload (Sec. 4: a random point distribution once
+    each point carries a volume): n points uniform in a 16 km x 16 km x 4 km
+    slab below the surface z = 0, densities 2670 kg/m^3 plus a seeded
+    +/-250 kg/m^3 smooth field, stations^2 stations 50 m above the surface.
+    Every point carries the slab volume / n, the mean volume of its Voronoi
+    cell (the tests compute true Voronoi volumes on small clouds; at this
+    size their construction would dominate).  Returns a dict with x, a, rho,
+    per_cell = 1, obs."""
+    Lx = Ly = 16000.0
+    lo, hi = np.array([0.0, 0.0, -4000.0]), np.array([Lx, Ly, 0.0])
+    x = scattered_points(n, lo, hi, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    rho = 2670.0 + 250.0 * np.sin(2 * np.pi * x[:, 0] / Lx * 2 + ph[0]) * \
+        np.sin(2 * np.pi * x[:, 1] / Ly * 3 + ph[1]) * np.cos(np.pi * x[:, 2] / 4000.0 + ph[2])
+    a = np.full(n, float(np.prod(hi - lo)) / n)
+    sx = (np.arange(stations) + 0.5) * (Lx / stations)
+    SY, SX = np.meshgrid(sx, sx, indexing="ij")
+    obs = np.stack([SX.ravel(), SY.ravel(), np.full(SX.size, 50.0)], axis=1)
+    return {"name": "points_cloud_%d" % n, "x": x, "a": a, "rho": rho, "per_cell": 1,
+            "obs": np.ascontiguousarray(obs), "G": G_PAPER}

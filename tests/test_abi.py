@@ -222,8 +222,10 @@ def test_point_source_arguments_rejected_on_host():
     assert create(4, 1, mode="fmm", p=6, flags=gf.GF_FLAG_SUM_AN) == gf.GF_ERR_UNSUPPORTED
     assert not plan.value
     q = gf._Quad(*wl.gauss_rule(2))
-    assert lib.gf_hex_sources(None, 0, ctypes.byref(q.c), None, None, None) == gf.GF_OK
-    assert lib.gf_hex_sources(None, 3, ctypes.byref(q.c), None, None, None) == gf.GF_ERR_INVALID_ARG
-    assert lib.gf_hex_sources(p, -1, ctypes.byref(q.c), p, p, None) == gf.GF_ERR_INVALID_ARG
+    for prec in (gf.GF_PREC_FP64, gf.GF_PREC_MIXED):
+        assert lib.gf_hex_sources(None, 0, ctypes.byref(q.c), prec, None, None, None) == gf.GF_OK
+        assert lib.gf_hex_sources(None, 3, ctypes.byref(q.c), prec, None, None, None) == gf.GF_ERR_INVALID_ARG
+        assert lib.gf_hex_sources(p, -1, ctypes.byref(q.c), prec, p, p, None) == gf.GF_ERR_INVALID_ARG
+    assert lib.gf_hex_sources(p, 1, ctypes.byref(q.c), 7, p, p, None) == gf.GF_ERR_INVALID_ARG
     q.w[0] = 0.0
-    assert lib.gf_hex_sources(p, 1, ctypes.byref(q.c), p, p, None) == gf.GF_ERR_INVALID_ARG
+    assert lib.gf_hex_sources(p, 1, ctypes.byref(q.c), gf.GF_PREC_FP64, p, p, None) == gf.GF_ERR_INVALID_ARG

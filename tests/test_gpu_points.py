@@ -80,6 +80,23 @@ def test_hex_sources_match_the_oracle():
     assert np.allclose(a.cpu().numpy().reshape(-1, 8).sum(axis=1), 2.0, rtol=1e-14, atol=0)
 
 
+def test_hex_sources_mixed_within_their_bound():
+    """The FP32 form (fixed-point corners, image relative to the first
+    corner): positions within 1e-6 of the cell extent, weights within 1e-6
+    relative, on warped bricks far from the origin and on the terrain mesh."""
+    meshes = [wl.hex_brick_mesh((7, 5, 4), (4.0e5, 6.2e6, -3000.0), (4.3e5, 6.23e6, 200.0), warp=0.2),
+              wl.topo_mesh(12, 10, 6)[0]]
+    for verts in meshes:
+        cell = float(np.ptp(verts, axis=1).max())
+        for npts in (1, 2, 3):
+            xi, w = wl.gauss_rule(npts)
+            x, a = pkg.hex_sources(t(verts), xi, w, precision="mixed")
+            torch.cuda.synchronize()
+            xr, ar = direct.hex_sources(verts, xi, w)
+            assert np.abs(x.cpu().numpy() - xr).max() <= 1e-6 * cell
+            assert np.abs(a.cpu().numpy() / ar - 1.0).max() <= 1e-6
+
+
 @pytest.mark.parametrize("mode,precision", [("direct", "fp64"), ("direct", "mixed"), ("fmm", "fp64"),
                                             ("fmm", "mixed")])
 @pytest.mark.parametrize("seed", [1, 2])
@@ -105,7 +122,7 @@ def test_deformed_hexahedra_match_the_oracle(mode, precision):
     wk, _, _ = hex_case()
     rho = wk["rho"].astype(np.float32).astype(np.float64) if precision == "mixed" else wk["rho"]
     ref = direct.forward_hex(wk["verts"], wk["xi"], wk["w"], rho, wk["obs"], wk["G"])
-    x, a = pkg.hex_sources(t(wk["verts"]), wk["xi"], wk["w"])
+    x, a = pkg.hex_sources(t(wk["verts"]), wk["xi"], wk["w"], precision=precision)
     dt = torch.float32 if precision == "mixed" else torch.float64
     with pkg.PointsPlan(x, a, t(wk["obs"]), per_cell=len(wk["w"]), mode=mode, precision=precision,
                         p=P[precision], G=wk["G"]) as plan:
