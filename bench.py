@@ -285,7 +285,10 @@ def level_boxes(info, l):
     return n
 
 
-def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4):
+P2M_FLOPS_PER_HARMONIC = 10.0   # point P2M: one recursion step (6 flops) + the mass-weighted sum (4)
+
+
+def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4, n_points=None):
     """Roofline of the kernel that dominates the forward: the near-field
     evaluation (ALU: 20 flops per pair, the paper's count; its SFU share
     beside it), the M2L (tensor: 2 K^2 flops per interaction-list box pair),
@@ -313,6 +316,16 @@ def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4):
                        else ("block_rows + m2l_tc P2M kind" if tensor else "p2m_fused"))
         work["m2m"] = ("hbm", float(sum(ns[l] * K * fbytes for l in range(3, top + 1))
                                     + sum(ns[l] * K * fbytes for l in range(2, top))),
+                       "m2l_tc M2M kind + m2m_kernel (FP64 into level 2)" if tensor else "xlate_simt")
+    if n_points is not None and L >= 2:
+        # point sources: the P2M evaluates (p+1)(p+2)/2 complex harmonics per
+        # point; the M2M reads each level's expansions once and writes the
+        # parents' once
+        ns = {l: level_boxes(info, l) for l in range(2, L + 1)}
+        work["p2m"] = ("alu", P2M_FLOPS_PER_HARMONIC * (p + 1) * (p + 2) / 2 * float(n_points),
+                       "point_p2m_f32 (packed pair recursion)" if args.precision == "mixed" else "point_p2m")
+        work["m2m"] = ("hbm", float(sum(ns[l] * K * fbytes for l in range(3, L + 1))
+                                    + sum(ns[l] * K * fbytes for l in range(2, L))),
                        "m2l_tc M2M kind + m2m_kernel (FP64 into level 2)" if tensor else "xlate_simt")
     dom = max(work, key=lambda k: stages.get(k, 0.0))
     bound, amount, kern = work[dom]
@@ -935,7 +948,7 @@ def bench_points(args, rank, world):
         plan.forward(rho_d, g=g_d, stream=stream)
         stages = plan.stage_times()
         plan.set_timing(False)
-        roof = fmm_roofline(stages, info, args, load_peaks(), name)
+        roof = fmm_roofline(stages, info, args, load_peaks(), name, n_points=S)
         if roof["stage"] == "eval":
             roof["kernel"] = "point_eval (near field over the neighbour leaves' points + L2P + combine)"
     torch.cuda.synchronize()

@@ -109,3 +109,17 @@ def test_plain_fp64_path_against_the_fp64_rate():
     assert r["stage"] == "m2l" and r["bound"] == "alu"
     assert r["peak"] == pytest.approx(bench.FP64_TFLOPS_NOMINAL)
     assert r["traffic"] is None
+
+
+def test_point_p2m_dominant():
+    """Point sources: the P2M is ALU-bound at 10 flops per complex harmonic,
+    (p+1)(p+2)/2 harmonics per point, against the FP32 rate."""
+    info = scale_info()
+    r = bench.fmm_roofline({"eval": 0.3, "m2l": 0.8, "p2m": 3.0, "m2m": 0.6}, info, args(p=12), PEAKS,
+                           "topo_hex_256x256x64", n_points=33554432)
+    assert r["stage"] == "p2m" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(10.0 * 91 * 33554432 / 3.0e-3 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    r = bench.fmm_roofline({"eval": 0.3, "m2l": 0.8, "p2m": 0.5, "m2m": 0.9}, info, args(p=12), PEAKS,
+                           "topo_hex_256x256x64", n_points=33554432)
+    assert r["stage"] == "m2m" and r["bound"] == "hbm"
