@@ -32,6 +32,11 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
+// The same rounding (to nearest, ties away from zero, on the magnitude) with
+// two integer operations: add half a TF32 ulp to the bits and clear the 13
+// dropped bits.  Finite inputs only (the callers flag non-finite ones).
+__device__ __forceinline__ uint32_t to_tf32_int(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
+
 // Byte offset of element (row, k), k < 16, in a [rows][16] FP32 tile stored
 // K-major with the 64-byte swizzle: 8-row atoms of 512 bytes, the 16-byte
 // chunk index XOR-ed with bits 1-2 of the row inside the atom.
@@ -581,6 +586,7 @@ struct TcArgs {
     int lmin, nent;             // entries e = (level - lmin) * 8 + class
     int tile_begin[kMaxLevels * 8 + 1];
     int K, ldk, B, Npad, nck, nst;
+    int S;                      // input chunks per pipeline stage
     int kind, noff;             // TcKind; offsets per target (189, 8 or 1)
     int ntiles;                 // tiles of the launch (persistent kinds)
     int kin, ldin;              // input coefficients per row and input row stride
@@ -707,21 +713,28 @@ constexpr int kTcMaxStages = 8;
 constexpr uint32_t kTcCols = 512;           // two banks of 256 columns
 constexpr uint32_t kTcA = 2u * 8192u;       // A hi + lo: 128 rows x 64 bytes each
 
-constexpr int kTcRaw = 8;                   // input chunks in flight per producer thread
+constexpr int kTcRaw = 4;                   // input chunks in flight per producer thread (TF32 kinds)
 
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int Npad) { return kTcA + 2u * (uint32_t)Npad * 64u; }
-// raw FP32 input ring of the producers: [kTcRaw][128 rows][32 or 16 floats]
+// raw FP32 input ring of the TF32 producers: [kTcRaw][128 rows][16 floats]
 __host__ __device__ constexpr uint32_t tc_raw_bytes(bool h16) { return h16 ? 0u : kTcRaw * 128u * 64u; }
-// Chunks per pipeline stage: the FP16 M2L moves two 32-input chunks per
-// stage (12 MMAs per barrier wait), the TF32 kinds one 16-input chunk.
-__host__ __device__ constexpr int tc_chunks_per_stage(bool h16) { return h16 ? 2 : 1; }
 constexpr size_t kTcSmemBudget = 227 * 1024 - 2048;
+// Chunks per pipeline stage: the FP16 M2L moves two 32-input chunks per
+// stage (12 MMAs per barrier wait); the TF32 kinds two 16-input chunks
+// when two such stages fit in shared memory, else one.
+inline int tc_chunks_per_stage(int Npad, bool h16) {
+    if (h16) return 2;
+    const size_t two = 2u * (size_t)tc_stage_bytes(Npad);
+    return (kTcSmemBudget - tc_raw_bytes(false)) / two >= 2 ? 2 : 1;
+}
 inline int tc_stages(int Npad, bool h16) {
-    const int n = (int)((kTcSmemBudget - tc_raw_bytes(h16)) / (tc_chunks_per_stage(h16) * tc_stage_bytes(Npad)));
+    const int n = (int)((kTcSmemBudget - tc_raw_bytes(h16)) /
+                        ((size_t)tc_chunks_per_stage(Npad, h16) * tc_stage_bytes(Npad)));
     return n > kTcMaxStages ? kTcMaxStages : n;
 }
 size_t tc_smem_bytes(int Npad, bool h16) {
-    return (size_t)tc_stages(Npad, h16) * tc_chunks_per_stage(h16) * tc_stage_bytes(Npad) + tc_raw_bytes(h16) + 1024;
+    return (size_t)tc_stages(Npad, h16) * tc_chunks_per_stage(Npad, h16) * tc_stage_bytes(Npad) +
+           tc_raw_bytes(h16) + 1024;
 }
 
 // 16-byte asynchronous global -> shared copy; nbytes = 0 fills zeros.
@@ -750,7 +763,8 @@ m2l_tc(TcArgs a) {
     const int B = a.B, Npad = a.Npad, nck = a.nck, NST = a.nst;
     const int nsum = Npad / 2;
     const uint32_t b_bytes = 2u * (uint32_t)Npad * 64u;
-    constexpr int S = tc_chunks_per_stage(H16);   // chunks per stage
+    constexpr int SH = 2;                  // chunks per stage of the FP16 M2L
+    const int S = H16 ? SH : a.S;          // chunks per stage
     const uint32_t stage_bytes = S * tc_stage_bytes(Npad);   // [A: S x (hi, lo)][B: S x (hi, lo)]
     volatile int *abortp = &abort_flag;
     const int nbox = 128 / B;
@@ -936,16 +950,16 @@ m2l_tc(TcArgs a) {
             for (int it = 0; it < iters; ++it) {
                 if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp, a.wait_tries)) break;
                 unsigned char *stage = base + (size_t)s * stage_bytes;
-                int c0 = 0, nc = S;
+                int c0 = 0, nc = SH;
 #pragma unroll
-                for (int q = 0; q < S; ++q) {
+                for (int q = 0; q < SH; ++q) {
                     if (q > 0 && c0 + q >= nck) break;   // the offset's last stage may hold fewer chunks
                     int cc;
                     int64_t sr;
                     take(cc, sr);
                     if (q == 0) {
                         c0 = cc;
-                        nc = min(S, nck - c0);
+                        nc = min(SH, nck - c0);
                     }
                     // chunks run from the highest inputs down (chunk_of), and the
                     // stage keeps its chunks in ascending order
@@ -977,15 +991,15 @@ m2l_tc(TcArgs a) {
             asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the loop (abort)
         } else {
             // TF32 inputs, split here
-            constexpr int kW = 16;     // inputs per stage
-            constexpr int kV = kW / 4; // 16-byte pieces per row and stage
+            constexpr int kW = 16;     // inputs per chunk
+            constexpr int kV = kW / 4; // 16-byte pieces per row and chunk
             const float *me = a.grid ? a.grid : pc.L->me;   // every tile of a launch reads the same input array
-            // Each thread copies its own row's chunks kTcRaw - 1 stages ahead into
+            // Each thread copies its own row's chunks kTcRaw - 1 chunks ahead into
             // a raw ring (16-byte pieces XOR-swizzled by row, so that a warp's
             // reads of one piece hit distinct banks); a missing source copies
             // zeros.  Only the copying thread reads them back.
             unsigned char *raw = base + (size_t)NST * stage_bytes + (size_t)row * (kW * 4);
-            auto issue = [&](int j) {
+            auto issue = [&](int64_t j) {
                 int cc;
                 int64_t sr;
                 take(cc, sr);
@@ -999,45 +1013,59 @@ m2l_tc(TcArgs a) {
                 for (int q = 0; q < kV; ++q)
                     cp_async16(d0 + ((q ^ (row & (kV - 1))) << 4), src + q * qs, sr >= 0 ? 16u : 0u);
             };
+            // chunks are issued and consumed in take() order: stage `it` holds
+            // the chunks at positions [c0, c0 + nc) of its offset (the offset's
+            // last stage may hold fewer), slot nc - 1 - q for the q-th
+            const int64_t nchunks = (int64_t)offs * nck;
 #pragma unroll 1
             for (int j = 0; j < kTcRaw - 1; ++j) {
-                if (j < iters) issue(j);
+                if (j < nchunks) issue(j);
                 asm volatile("cp.async.commit_group;" ::: "memory");
             }
             int s = 0;
             uint32_t ph = 0;
             bool bad = false;   // a non-finite input (densities read from the grid)
-            for (int it = 0; it < iters; ++it) {
-                if (it + kTcRaw - 1 < iters) issue(it + kTcRaw - 1);
-                asm volatile("cp.async.commit_group;" ::: "memory");
-                asm volatile("cp.async.wait_group %0;" ::"n"(kTcRaw - 1) : "memory");   // chunk `it` has landed
-                if (it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp, a.wait_tries)) break;
-                const int c0 = chunk_of(nck, it % nck);   // every offset runs all nck chunks, in order
-                float4 cur[kV];
-                {
-                    const float4 *rr = reinterpret_cast<const float4 *>(raw + (size_t)(it % kTcRaw) * 128 * (kW * 4));
-#pragma unroll
-                    for (int q = 0; q < kV; ++q) cur[q] = rr[q ^ (row & (kV - 1))];
-                }
+            int64_t jc = 0;     // next chunk to consume
+            bool stop = false;
+            for (int it = 0; it < iters && !stop; ++it) {
+                const int c0 = (it % nsp) * S;
+                const int nc = min(S, nck - c0);
                 unsigned char *stage = base + (size_t)s * stage_bytes;
-                {
+                for (int q = 0; q < nc; ++q, ++jc) {
+                    if (jc + kTcRaw - 1 < nchunks) issue(jc + kTcRaw - 1);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    asm volatile("cp.async.wait_group %0;" ::"n"(kTcRaw - 1) : "memory");   // chunk jc has landed
+                    if (q == 0 && it >= NST && !mbar_wait_ab(smem_u32(&empty[s]), ph ^ 1, abortp, a.wait_tries)) {
+                        stop = true;
+                        break;
+                    }
+                    const int cin = chunk_of(nck, c0 + q);   // input chunk
+                    float4 cur[kV];
+                    {
+                        const float4 *rr =
+                            reinterpret_cast<const float4 *>(raw + (size_t)(jc % kTcRaw) * 128 * (kW * 4));
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float x4[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
+                        for (int v = 0; v < kV; ++v) cur[v] = rr[v ^ (row & (kV - 1))];
+                    }
+                    unsigned char *sub = stage + (size_t)(nc - 1 - q) * kTcA;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float x4[4] = {cur[v].x, cur[v].y, cur[v].z, cur[v].w};
                         uint32_t h[4], l[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const int kin = 16 * c0 + 4 * q + j;
+                            const int kin = 16 * cin + 4 * v + j;
                             const float x = kin < a.kin ? x4[j] : 0.f;
                             bad |= !isfinite(x);
-                            h[j] = to_tf32(x);
-                            l[j] = to_tf32(x - __uint_as_float(h[j]));
+                            h[j] = to_tf32_int(x);
+                            l[j] = to_tf32_int(x - __uint_as_float(h[j]));
                         }
-                        const uint32_t o = swz64(row, 4 * q);
-                        *reinterpret_cast<uint4 *>(stage + o) = make_uint4(h[0], h[1], h[2], h[3]);
-                        *reinterpret_cast<uint4 *>(stage + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+                        const uint32_t o = swz64(row, 4 * v);
+                        *reinterpret_cast<uint4 *>(sub + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4 *>(sub + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
                     }
                 }
+                if (stop) break;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&afull[s]));
                 if (++s == NST) {
@@ -1518,6 +1546,7 @@ gf_status tc_launch(TcArgs &a, int tiles, cudaStream_t st) {
     const bool h16 = a.kind == kTcM2L;
     const size_t shm = tc_smem_bytes(a.Npad, h16);
     a.nst = tc_stages(a.Npad, h16);
+    a.S = tc_chunks_per_stage(a.Npad, h16);
     const int nsum = a.Npad / 2;
 #define GF_TC_LAUNCH(NS)                                                  \
     do {                                                                  \
