@@ -285,6 +285,7 @@ def level_boxes(info, l):
     return n
 
 
+SPLIT_PRODUCTS = 3              # tensor-core products per algorithmic one (FP16 or TF32 high/low parts)
 P2M_FLOPS_PER_HARMONIC = 10.0   # point P2M: one recursion step (6 flops) + the mass-weighted sum (4)
 
 
@@ -335,6 +336,10 @@ def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4, n_
         note = ("FP16 dense = measured BF16 burst x nominal FP16/BF16 (1); the high/low split "
                 "executes 3 MMAs per algorithmic flop")
         achieved = amount / (stages[dom] * 1e-3) / 1e12
+        # three products per algorithmic one: the algorithmic fraction is at
+        # most 1/3; pipe_frac is the tensor pipe's share of its peak
+        extra = {"pipe_frac": SPLIT_PRODUCTS * achieved / peak,
+                 "pipe_source": "algorithmic rate x 3 (high/low parts: hi*lo + lo*hi + hi*hi per product)"}
     elif bound == "hbm":
         peak, unit = peaks.get("hbm_gbs", 6774.6), "GB/s"
         note = "measured HBM copy bandwidth"

@@ -123,3 +123,11 @@ def test_point_p2m_dominant():
     r = bench.fmm_roofline({"eval": 0.3, "m2l": 0.8, "p2m": 0.5, "m2m": 0.9}, info, args(p=12), PEAKS,
                            "topo_hex_256x256x64", n_points=33554432)
     assert r["stage"] == "m2m" and r["bound"] == "hbm"
+
+
+def test_tensor_pipe_fraction_counts_the_three_products():
+    """The M2L's algorithmic fraction is capped at 1/3 by the high/low split;
+    pipe_frac reports the tensor pipe's share (three products each)."""
+    r = bench.fmm_roofline({"eval": 0.3, "m2l": 1.25}, INFO, args(), PEAKS, WORKLOAD)
+    assert r["stage"] == "m2l" and r["bound"] == "tensor"
+    assert r["pipe_frac"] == pytest.approx(3 * r["frac"])
