@@ -50,33 +50,43 @@ MUFU_RSQRT_PROBE = 4.63e12
 
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture (the
-# ncu summaries under profiles/), with the SHA-1 of the kernel's source file
-# at capture time: once the source changes the figure no longer describes
-# the kernel and the bench reports null.  The 464^3 figures are captures of
+# ncu summaries under profiles/), with the SHA-1 of the kernel's source files
+# at capture time: once a source changes the figure no longer describes the
+# kernel and the bench reports null.  The 464^3 figures are captures of
 # the same recipe at 320^3 (the full size holds too much device memory for a
 # multi-pass capture) scaled by the work units of a launch: near pairs for
 # the evaluation (the traffic grows in proportion: a full-size list of the
 # same kernel read 29.4 MB), interaction-list box pairs for the M2L.
 NCU_TRAFFIC = {
-    ("eval", "layered_scale_464^3", 11): (round(13978624 * 596922624 / 280629504),
-                                          "paper_1107_5951_gb300/csrc/gf_fmm.cu",
-                                          "5cedea733d9acbcc59b824709d6afedfd0051c94"),
-    ("m2l", "layered_scale_464^3", 11): (round((25330432 + 8960) * 1125279 / 510295),
-                                         "paper_1107_5951_gb300/csrc/gf_m2l.cu",
-                                         "1c1dcde692396f46cbf2eacedf368f8727af01d2"),
+    ("eval", "layered_scale_464^3", 11): (round((13981952 + 12800) * 596922624 / 280629504),
+                                          ("paper_1107_5951_gb300/csrc/gf_fmm.cu",
+                                           "paper_1107_5951_gb300/csrc/gf_simd.cuh",
+                                           "paper_1107_5951_gb300/csrc/fmm_math.cuh"),
+                                          "aff8ef7477ae3a987f60766cc5e3f212ece3fd42"),
+    ("m2l", "layered_scale_464^3", 11): (round((25346560 + 2304) * 1125279 / 510295),
+                                         ("paper_1107_5951_gb300/csrc/gf_m2l.cu",),
+                                         "d64e86d5903172fce1255cae17c8f43b6cd50cfd"),
 }
 
 
-def ncu_traffic(stage, workload, p, precision, m2l):
+def sources_sha1(files):
+    """SHA-1 of the concatenated sources a kernel is compiled from."""
     import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(stage, workload, p, precision, m2l):
     key = (stage, workload, p)
     if precision != "mixed" or m2l != "auto" or key not in NCU_TRAFFIC:
         return None
-    nbytes, src, sha = NCU_TRAFFIC[key]
+    nbytes, srcs, sha = NCU_TRAFFIC[key]
     try:
-        with open(os.path.join(ROOT, src), "rb") as f:
-            if hashlib.sha1(f.read()).hexdigest() != sha:
-                return None
+        if sources_sha1(srcs) != sha:
+            return None
     except OSError:
         return None
     return nbytes

@@ -27,10 +27,8 @@ def args(precision="mixed", p=11, m2l="auto"):
 def captured(stage):
     """The table's traffic while the kernel's source still has the captured
     SHA-1, else None."""
-    import hashlib
-    nbytes, src, sha = bench.NCU_TRAFFIC[(stage, WORKLOAD, 11)]
-    with open(os.path.join(ROOT, src), "rb") as f:
-        return nbytes if hashlib.sha1(f.read()).hexdigest() == sha else None
+    nbytes, srcs, sha = bench.NCU_TRAFFIC[(stage, WORKLOAD, 11)]
+    return nbytes if bench.sources_sha1(srcs) == sha else None
 
 
 def test_evaluation_dominant():
