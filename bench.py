@@ -307,7 +307,7 @@ def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4, n_
     once; each child expansion read once and each parent written once)."""
     K = int(info.K)
     p = workload_p(args)
-    tensor = args.precision == "mixed" and p <= 15 and args.m2l != "simt"
+    tensor = (args.precision == "mixed" or args.m2l == "tensor") and p <= 15 and args.m2l != "simt"
     fbytes = 4 if args.precision == "mixed" else 8
     L = int(getattr(info, "L", 0))
     work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P + combine)"),
@@ -503,10 +503,10 @@ def bench_gf(args, rank, world):
 
     parts = world > 1 and args.parallel == "sources"
 
-    def make_plan(precision=args.precision, pp=p, obs=obs_d):
+    def make_plan(precision=args.precision, pp=p, obs=obs_d, m2l=args.m2l):
         pl = pkg.Plan(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, obs, mode=mode,
                       precision=precision, p=pp, leaf_vox=args.leaf_vox, G=wk.G,
-                      stream=stream, m2l=args.m2l)
+                      stream=stream, m2l=m2l)
         if parts:
             pl.set_source_part(rank, world)
         return pl
@@ -589,6 +589,20 @@ def bench_gf(args, rank, world):
             sampled["fp64_fmm"] = g_d.cpu().numpy()
         compare["fp64_fmm"] = {"precision": "fp64", "p": pf, "ms_per_solve": ms,
                                "value": units / (ms * 1e-3), "unit": "interactions/s"}
+        # the FP64 FMM with its M2L on the tensor cores (FP16 parts; the rest FP64)
+        with make_plan("fp64", pf, m2l="tensor") as pl:
+            pl.forward(rho64, g=g_d, stream=stream)
+            ms = timed_forwards(pl, rho64, g_d, stream, flush, 2)
+            sampled["fp64_tc_m2l"] = g_d.cpu().numpy()
+            pl.set_timing(True)
+            pl.forward(rho64, g=g_d, stream=stream)
+            st64 = pl.stage_times()
+            info64 = pl.info
+        a64 = argparse.Namespace(precision="fp64", p=pf, m2l="tensor", workload=args.workload)
+        compare["fp64_tc_m2l"] = {"precision": "fp64", "m2l": "tensor cores (FP16 parts)", "p": pf,
+                                  "ms_per_solve": ms, "value": units / (ms * 1e-3), "unit": "interactions/s",
+                                  "stages_ms": st64,
+                                  "roofline": fmm_roofline(st64, info64, a64, peaks, wk.name + "_fp64")}
         del rho64
         if args.precision == "mixed":
             for ps in SWEEP_P:
@@ -609,7 +623,7 @@ def bench_gf(args, rank, world):
         nref = np.linalg.norm(ref)
         rel_err = float(np.linalg.norm(g_main[idx] - ref) / nref)
         for key, gs in sampled.items():
-            ck = "fp64_fmm" if key == "fp64_fmm" else "mixed_" + key
+            ck = key if key.startswith("fp64") else "mixed_" + key
             compare[ck]["rel_err_vs_oracle_sample"] = float(np.linalg.norm(gs[idx] - ref) / nref)
         cpu = {"value": N * len(idx) / dt, "unit": "interactions/s", "cores": cores, "kind": "oracle",
                "sample": "%d seeded observers of %d x all %d sources (%.1f s)" % (len(idx), M, N, dt)}

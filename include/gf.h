@@ -105,8 +105,15 @@ enum { GF_DTYPE_F64 = 0, GF_DTYPE_F32 = 1 };
  *                     kernel's roles stop, wait for their copies in flight,
  *                     free their tensor memory and return, and the next
  *                     gf_plan_check reports GF_ERR_DEVICE_CHECK (the
- *                     forward's output is then not valid). */
-enum { GF_FLAG_M2L_SIMT = 1, GF_FLAG_SUM_AN = 2, GF_FLAG_TEST_WAIT_TIMEOUT = 4 };
+ *                     forward's output is then not valid).
+ *   GF_FLAG_M2L_TENSOR FMM, FP64 precision: the forward M2L on the tensor
+ *                     cores as in mixed precision (the FP64 inputs scaled
+ *                     and split into FP16 high/low parts, three products,
+ *                     FP32 accumulation per interaction-list offset);
+ *                     every other stage in FP64.  The M2L then carries
+ *                     about 22 bits (relative error near 1e-7 of its
+ *                     output); gf_adjoint keeps the FP64 M2L. */
+enum { GF_FLAG_M2L_SIMT = 1, GF_FLAG_SUM_AN = 2, GF_FLAG_TEST_WAIT_TIMEOUT = 4, GF_FLAG_M2L_TENSOR = 8 };
 
 typedef struct {
     int32_t mode;        /* GF_MODE_DIRECT or GF_MODE_FMM                  */

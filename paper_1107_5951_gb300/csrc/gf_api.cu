@@ -174,9 +174,14 @@ static gf_status validate_options(int64_t M, const gf_options *opt) {
         set_error("opt.G must be finite and >= 0 (0 selects 6.67428e-11)");
         return GF_ERR_INVALID_ARG;
     }
-    if (opt->reserved0 & ~(GF_FLAG_M2L_SIMT | GF_FLAG_SUM_AN | GF_FLAG_TEST_WAIT_TIMEOUT)) {
+    if (opt->reserved0 & ~(GF_FLAG_M2L_SIMT | GF_FLAG_SUM_AN | GF_FLAG_TEST_WAIT_TIMEOUT | GF_FLAG_M2L_TENSOR)) {
         set_error("opt.reserved0 = %d holds unknown flags", opt->reserved0);
         return GF_ERR_INVALID_ARG;
+    }
+    if ((opt->reserved0 & GF_FLAG_M2L_TENSOR) &&
+        (opt->mode != GF_MODE_FMM || opt->precision != GF_PREC_FP64 || (opt->reserved0 & GF_FLAG_M2L_SIMT))) {
+        set_error("GF_FLAG_M2L_TENSOR applies to FP64 FMM plans (without GF_FLAG_M2L_SIMT)");
+        return GF_ERR_UNSUPPORTED;
     }
     if ((opt->reserved0 & GF_FLAG_SUM_AN) && opt->mode == GF_MODE_DIRECT && opt->precision != GF_PREC_FP64) {
         set_error("GF_FLAG_SUM_AN (closed-form voxels) in direct mode is implemented in FP64 only");

@@ -1333,7 +1333,7 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     DeviceArena &A = plan->arena;
     const size_t rs = F->mixed ? sizeof(float) : sizeof(double);
     const int K = F->K, B = F->B;
-    F->KS = F->mixed ? (K + 31) & ~31 : K;
+    F->KS = (F->mixed || F->m2l_tc64) ? (K + 31) & ~31 : K;
     for (int l = 2; l <= F->L; ++l) {
         FmmLevel &lv = F->lev[l];
         GF_TRY(A.alloc(&lv.me, (size_t)std::max<int64_t>(lv.ns, 1) * B * F->KS * rs));

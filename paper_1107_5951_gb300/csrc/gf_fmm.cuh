@@ -71,6 +71,7 @@ struct FmmPlan {
     int L = 0, b = 0, p = 0, K = 0, B = 1, nq = 1;
     int KS = 0;                   // row stride of ME/LE arrays (K padded to 32 in mixed)
     bool mixed = false;
+    bool m2l_tc64 = false;        // FP64 plan whose forward M2L runs on the tensor cores
     // weighted point sources: one leaf of side s_leaf is the length unit
     // (b = 1), masses are [B][S] in leaf order, and the P2M and near field
     // read the sources' positions (gf_points.cu)

@@ -587,6 +587,7 @@ struct TcArgs {
     int tile_begin[kMaxLevels * 8 + 1];
     int K, ldk, B, Npad, nck, nst;
     int S;                      // input chunks per pipeline stage
+    int le_f64;                 // M2L: the output rows are FP64 (an FP64 plan's local expansions)
     int kind, noff;             // TcKind; offsets per target (189, 8 or 1)
     int ntiles;                 // tiles of the launch (persistent kinds)
     int kin, ldin;              // input coefficients per row and input row stride
@@ -1275,13 +1276,27 @@ m2l_tc(TcArgs a) {
                     float sig, sig_inv;
                     input_scale(*L.amax, sig, sig_inv);
                     const float4 *ci = reinterpret_cast<const float4 *>(a.cs + Npad + ph_half * nsum);
+                    if (a.le_f64) {
+                        // an FP64 plan's local expansions: rows of ldk >= Npad doubles
+                        double *dd = reinterpret_cast<double *>(L.le) + (obox * B + obb) * a.ldk + ph_half * nsum;
 #pragma unroll
-                    for (int q = 0; q < NS; q += 4)
-                        if (q < nsum) {
-                            const float4 c4 = __ldg(ci + q / 4);
-                            dst[q / 4] = make_float4(acc[q] * c4.x * sig_inv, acc[q + 1] * c4.y * sig_inv,
-                                                     acc[q + 2] * c4.z * sig_inv, acc[q + 3] * c4.w * sig_inv);
-                        }
+                        for (int q = 0; q < NS; q += 4)
+                            if (q < nsum) {
+                                const float4 c4 = __ldg(ci + q / 4);
+                                dd[q] = (double)(acc[q] * c4.x * sig_inv);
+                                dd[q + 1] = (double)(acc[q + 1] * c4.y * sig_inv);
+                                dd[q + 2] = (double)(acc[q + 2] * c4.z * sig_inv);
+                                dd[q + 3] = (double)(acc[q + 3] * c4.w * sig_inv);
+                            }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NS; q += 4)
+                            if (q < nsum) {
+                                const float4 c4 = __ldg(ci + q / 4);
+                                dst[q / 4] = make_float4(acc[q] * c4.x * sig_inv, acc[q + 1] * c4.y * sig_inv,
+                                                         acc[q + 2] * c4.z * sig_inv, acc[q + 3] * c4.w * sig_inv);
+                            }
+                    }
                 } else {
 #pragma unroll
                     for (int q = 0; q < NS; q += 4)
@@ -1345,7 +1360,7 @@ gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
 
 gf_status m2l_tc_prepare(gf_plan_s *plan) {
     FmmPlan *F = plan->fmm;
-    if (!F->mixed || !F->tab->m2l_tc) return GF_OK;
+    if (!(F->mixed || F->m2l_tc64) || !F->tab->m2l_tc) return GF_OK;
     GF_TRY(plan->arena.alloc((void **)&F->tc_amax, 2 * (kMaxLevels + 1) * sizeof(uint32_t)));
     GF_TRY(plan->arena.alloc((void **)&F->tc_split, std::max<size_t>(16, split_offset(F, 0, F->L + 1))));
     for (int adj = 0; adj < 1; ++adj) {
@@ -1381,7 +1396,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
     // the P2M of every leaf (entry 2L+2), the P2M into level L-1 straight
     // from the leaf masses (entry 2L+3) and the P2M of the leaves in the
     // z-slabs the leaf level's M2L reads (entry 2L+4)
-    if (F->tab->m2m_tc && F->tab->l2l_tc) {
+    if (F->mixed && F->tab->m2m_tc && F->tab->l2l_tc) {
         std::vector<TcLevel> h(2 * (F->L + 1) + 3);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
         for (int l = 2; l <= F->L; ++l) {
@@ -1464,14 +1479,29 @@ namespace {
 // M2L input (forward: ME_l; adjoint: the LE_l duals), as the bits of a
 // non-negative float, combined with atomicMax (out[] zeroed before).
 struct AmaxArgs {
-    const float4 *in[kMaxLevels + 1];
+    const float4 *in[kMaxLevels + 1];   // FP32 rows, or (f64) FP64 rows read through in64
+    const double *in64[kMaxLevels + 1];
     int64_t rows[kMaxLevels + 1];
     uint32_t *out;
     int lmin, ld4, kin;
+    int f64;                            // inputs are FP64 rows of 4 ld4 doubles
 };
 
 __global__ void __launch_bounds__(256) input_absmax(AmaxArgs a) {
     const int l = a.lmin + (int)blockIdx.y;
+    if (a.f64) {
+        // FP64 rows: element by element
+        const double *p = a.in64[l];
+        const int ld = 4 * a.ld4;
+        const int64_t n = a.rows[l] * ld;
+        float m = 0.f;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            if ((int)(i % ld) < a.kin) m = fmaxf(m, fabsf((float)__ldg(p + i)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(a.out + l, __float_as_uint(m));
+        return;
+    }
     const float4 *p = a.in[l];
     const int64_t n = a.rows[l] * a.ld4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1511,10 +1541,20 @@ __global__ void __launch_bounds__(256) input_split(AmaxArgs a, SplitArgs o, int 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / nck;
         const int c = (int)(i - r * nck);
-        const float4 *src = a.in[l] + r * a.ld4 + 8 * c;
         float4 v[8];
+        if (a.f64) {
+            // FP64 rows (4 ld4 doubles): 32 inputs rounded to FP32 (the parts carry 22 bits)
+            const double2 *s2 = reinterpret_cast<const double2 *>(a.in64[l] + r * 4 * a.ld4 + 32 * c);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = __ldg(src + q);
+            for (int q = 0; q < 8; ++q) {
+                const double2 d0 = __ldg(s2 + 2 * q), d1 = __ldg(s2 + 2 * q + 1);
+                v[q] = make_float4((float)d0.x, (float)d0.y, (float)d1.x, (float)d1.y);
+            }
+        } else {
+            const float4 *src = a.in[l] + r * a.ld4 + 8 * c;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldg(src + q);
+        }
         uint4 *dst = reinterpret_cast<uint4 *>(o.out[l] + (size_t)i * 128);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1601,6 +1641,7 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     a.nck = T->tc_nck_h;
     a.img = (const unsigned char *)(adj ? T->am2l_tc : T->m2l_tc);
     a.cs = adj ? T->am2l_cs : T->m2l_cs;
+    a.le_f64 = F->m2l_tc64 ? 1 : 0;
     a.part_lo = adj ? 0u : plan->part_lo;
     a.part_hi = adj ? 64u : plan->part_hi;
     if (plan->opt.reserved0 & GF_FLAG_TEST_WAIT_TIMEOUT) {
@@ -1616,6 +1657,7 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
         m.lmin = 2;
         m.ld4 = F->KS / 4;
         m.kin = F->K;
+        m.f64 = F->m2l_tc64 ? 1 : 0;
         int64_t most = 0;
         // forward: only the z-slabs of each level's source block that an
         // interaction list reaches (rows run x fastest, then y, then z)
@@ -1630,6 +1672,7 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
             }
             row0[l] = r0;
             m.in[l] = (const float4 *)(adj ? lv.le : lv.me) + r0 * m.ld4;
+            m.in64[l] = (const double *)(adj ? lv.le : lv.me) + r0 * 4 * m.ld4;
             m.rows[l] = nr;
             most = std::max(most, m.rows[l] * m.ld4);
         }
@@ -1918,7 +1961,7 @@ template gf_status translate_run<double, double>(gf_plan_s *, int, int, int, cud
 template <class T>
 gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     FmmPlan *F = plan->fmm;
-    const bool tc = sizeof(T) == 4 && F->tab->m2l_tc && (adj ? F->tc_levels_adj : F->tc_levels) &&
+    const bool tc = (sizeof(T) == 4 || (F->m2l_tc64 && !adj)) && F->tab->m2l_tc && (adj ? F->tc_levels_adj : F->tc_levels) &&
                     !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
                     tc_stages(F->tab->tc_npad, true) >= 2;
     if (tc) return m2l_run_tc(plan, B, adj, st);

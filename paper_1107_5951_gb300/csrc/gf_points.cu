@@ -1152,6 +1152,7 @@ gf_status points_fmm_create(gf_plan_s *plan, const double *src, const double *wt
     F->B = plan->opt.max_batch;
     F->nq = 1;
     F->mixed = plan->opt.precision == GF_PREC_MIXED;
+    F->m2l_tc64 = !F->mixed && (plan->opt.reserved0 & GF_FLAG_M2L_TENSOR);
     F->b = 1;
     F->points = true;
     DeviceArena &A = plan->arena;

@@ -422,6 +422,7 @@ gf_status fmm_create(gf_plan_s *plan, const double *obs, cudaStream_t st) {
     F->B = plan->opt.max_batch;
     F->nq = plan->quad.nq;
     F->mixed = plan->opt.precision == GF_PREC_MIXED;
+    F->m2l_tc64 = !F->mixed && (plan->opt.reserved0 & GF_FLAG_M2L_TENSOR);
     F->b = plan->opt.leaf_vox > 0 ? plan->opt.leaf_vox : default_leaf_vox(F->nq);
     F->h = gr.h[0];
     DeviceArena &A = plan->arena;

@@ -305,6 +305,7 @@ class _Quad:
 GF_FLAG_M2L_SIMT = 1
 GF_FLAG_SUM_AN = 2
 GF_FLAG_TEST_WAIT_TIMEOUT = 4
+GF_FLAG_M2L_TENSOR = 8
 
 
 def make_options(mode="fmm", precision="fp64", p=8, leaf_vox=0, max_batch=1, G=0.0, flags=0) -> gf_options:
@@ -364,7 +365,8 @@ class Plan:
     observer set (see ``gf_plan_create``).
 
     obs must be a CUDA float64 tensor of shape (M, 3).  m2l="simt" runs the
-    mixed-precision M2L on the SIMT cores; voxels="closed_form" integrates
+    mixed-precision M2L on the SIMT cores; m2l="tensor" runs an FP64 plan's
+    M2L on the tensor cores (FP16 parts, the rest FP64); voxels="closed_form" integrates
     every voxel exactly (SUM-AN; direct mode, FP64) instead of sampling it
     with the rule (xi, w).  flags: further GF_FLAG_* bits (testing aids)."""
 
@@ -381,10 +383,11 @@ class Plan:
         self.device = obs.device
         self._grid = make_grid(shape, origin, h)
         self._quad = _Quad(xi, w)
-        if m2l not in ("auto", "simt") or voxels not in ("quadrature", "closed_form"):
-            raise ValueError("m2l must be 'auto' or 'simt', voxels 'quadrature' or 'closed_form'")
+        if m2l not in ("auto", "simt", "tensor") or voxels not in ("quadrature", "closed_form"):
+            raise ValueError("m2l must be 'auto', 'simt' or 'tensor', voxels 'quadrature' or 'closed_form'")
         self._opt = make_options(mode, precision, p, leaf_vox, max_batch, G,
                                  (GF_FLAG_M2L_SIMT if m2l == "simt" else 0)
+                                 | (GF_FLAG_M2L_TENSOR if m2l == "tensor" else 0)
                                  | (GF_FLAG_SUM_AN if voxels == "closed_form" else 0) | int(flags))
         self.handle = None
         with torch.cuda.device(self.device):

@@ -119,7 +119,7 @@ def test_closed_form_voxels_modes():
         with pytest.raises(gf.GfError) as e:
             gf.gf_plan_bytes(grid, q.c, 10, opt)
         assert e.value.status == gf.GF_ERR_UNSUPPORTED
-    grid, q, opt = _args(mode="direct", flags=8)
+    grid, q, opt = _args(mode="direct", flags=16)
     with pytest.raises(gf.GfError) as e:
         gf.gf_plan_bytes(grid, q.c, 10, opt)
     assert e.value.status == gf.GF_ERR_INVALID_ARG
@@ -229,3 +229,17 @@ def test_point_source_arguments_rejected_on_host():
     assert lib.gf_hex_sources(p, 1, ctypes.byref(q.c), 7, p, p, None) == gf.GF_ERR_INVALID_ARG
     q.w[0] = 0.0
     assert lib.gf_hex_sources(p, 1, ctypes.byref(q.c), gf.GF_PREC_FP64, p, p, None) == gf.GF_ERR_INVALID_ARG
+
+
+def test_tensor_m2l_flag_only_for_fp64_fmm():
+    """GF_FLAG_M2L_TENSOR is accepted for FP64 FMM plans and refused in mixed
+    precision, in direct mode and together with GF_FLAG_M2L_SIMT."""
+    grid, q, opt = _args(mode="fmm", precision="fp64", p=8, flags=gf.GF_FLAG_M2L_TENSOR)
+    assert gf.gf_plan_bytes(grid, q.c, 10, opt) > 0
+    for bad in (dict(mode="fmm", precision="mixed", p=8), dict(mode="direct", precision="fp64"),
+                dict(mode="fmm", precision="fp64", p=8, flags_extra=gf.GF_FLAG_M2L_SIMT)):
+        extra = bad.pop("flags_extra", 0)
+        grid, q, opt = _args(flags=gf.GF_FLAG_M2L_TENSOR | extra, **bad)
+        with pytest.raises(gf.GfError) as e:
+            gf.gf_plan_bytes(grid, q.c, 10, opt)
+        assert e.value.status == gf.GF_ERR_UNSUPPORTED

@@ -256,3 +256,19 @@ def test_fmm_grf_volume_full_size_sampled():
     print("grf_volume 128^3 mixed p=12 sampled rel L2 %.3e" % err)
     assert err <= 1e-5
     assert rel_l2(ref, ref32) < 1e-6  # float32 storage of rho changes little
+
+
+@pytest.mark.parametrize("seed,npts", [(41, 1), (42, 2)])
+def test_fp64_plan_with_tensor_core_m2l(seed, npts):
+    """An FP64 plan whose M2L runs on the tensor cores (FP16 parts of the
+    scaled FP64 inputs, FP32 accumulation per offset; every other stage FP64)
+    meets the 1e-6 bar at p = 14 and stays within 1e-6 of the all-FP64 FMM."""
+    wk = cube_case(seed, n=32, npts=npts, vol_targets=400)
+    ref = direct.forward(wk.grid.n, wk.grid.origin, wk.grid.h, wk.xi, wk.w, wk.rho, wk.obs, wk.G)
+    g64, _, _ = run(wk, "fp64", p=P64)
+    gtc, gz, info = run(wk, "fp64", p=P64, m2l="tensor")
+    assert info.L >= 3
+    print("fp64 %.3e  fp64 + tensor-core M2L %.3e" % (rel_l2(g64, ref), rel_l2(gtc, ref)))
+    assert rel_l2(gtc, ref) <= 1e-6
+    assert rel_l2(gtc, g64) <= 1e-6
+    assert np.array_equal(gz, gtc[:, 2])
