@@ -632,13 +632,17 @@ constexpr int kTPL = 2;            // targets per lane: a work item has <= 64 ta
 constexpr int kSrcTable = 512;     // per-block table of a leaf's source offsets
 constexpr int kMaxLat = 8;         // lattice planes per axis of a leaf (lattice near field)
 
+constexpr int kLatGroups = 4;      // lattice form: lane groups sharing a small item
+
 // Elements of one warp's shared-memory slice of the evaluation kernel
-// (a multiple of 8): 4 kEvalChunk staged source values, three gradient
+// (a multiple of 8): 4 kEvalChunk staged source values (FP32: 8, the
+// duplicated lattice weights of up to kLatGroups leaves), three gradient
 // expansions of P2 coefficients (FP32: duplicated pairs) and 27
-// neighbour-leaf indices (int64).
+// neighbour-leaf entries (int64).
+inline __host__ __device__ int eval_stage(int tsize) { return (tsize == 4 ? 2 : 1) * 4 * kEvalChunk; }
 inline __host__ __device__ int eval_slice(int P2, int tsize) {
     const int dmul = tsize == 4 ? 2 : 1;
-    return (4 * kEvalChunk + 3 * dmul * P2 + 27 * 8 / tsize + 7) & ~7;
+    return (eval_stage(tsize) + 3 * dmul * P2 + 27 * 8 / tsize + 7) & ~7;
 }
 
 struct EvalArgs {
@@ -646,6 +650,7 @@ struct EvalArgs {
     uint32_t part_lo, part_hi;   // source partition (in_source_part)
     const int4 *items;
     int64_t n_items;
+    unsigned long long *queue; // [0]: next item, [1]: warps done (zero between launches)
     const uint64_t *tkey;      // leaf keys
     const int32_t *perm;
     const void *tloc;          // [M][3] T
@@ -672,14 +677,18 @@ struct EvalArgs {
 };
 
 // Near field + far field of the observers of one leaf, one warp per work
-// item.  The sources of each neighbouring leaf are staged in the warp's
-// shared-memory slice in chunks of 64 (position relative to the target
-// leaf's centre, mass times quadrature weight) and every lane sweeps them
-// for its two observers.  Per-leaf partial sums are merged with TwoSum.
-// N1 > 0 (FP32, sources on an N1^3 lattice per leaf): the lattice form of
-// the near field below.
+// item; warps take items from a queue (one atomic per item), so a warp that
+// drew a short item takes the next one at once.  The sources of each
+// neighbouring leaf are staged in the warp's shared-memory slice in chunks
+// of 64 (position relative to the target leaf's centre, mass times
+// quadrature weight) and every lane sweeps them for its two observers.
+// Per-leaf partial sums are merged with TwoSum.  N1 > 0 (FP32, sources on
+// an N1^3 lattice per leaf): the lattice form of the near field below; an
+// item of at most 32 observers there splits its neighbour leaves over 2 or
+// 4 groups of lanes that hold the same observers, and the groups' sums are
+// merged by shuffles.
 template <class T, int N1>
-__global__ void __launch_bounds__(kEvalWarps * 32, sizeof(T) == 4 ? 6 : 1)   // FP32: 6 blocks (24 warps) per SM
+__global__ void __launch_bounds__(kEvalWarps * 32, sizeof(T) == 4 ? 5 : 1)   // FP32: 5 blocks (20 warps, 96 registers) per SM
 eval_kernel(EvalArgs a) {
     extern __shared__ unsigned char shraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -697,7 +706,7 @@ eval_kernel(EvalArgs a) {
     const int wstride = eval_slice(P2, sizeof(T));
     T *wsh = reinterpret_cast<T *>(tvox + kSrcTable) + (size_t)warp * wstride;
     Vec4<T> *src = reinterpret_cast<Vec4<T> *>(wsh);
-    T *Dx = wsh + 4 * kEvalChunk, *Dy = Dx + (kF32 ? 2 : 1) * P2, *Dz = Dy + (kF32 ? 2 : 1) * P2;
+    T *Dx = wsh + eval_stage(sizeof(T)), *Dy = Dx + (kF32 ? 2 : 1) * P2, *Dz = Dy + (kF32 ? 2 : 1) * P2;
     int64_t *nbl = reinterpret_cast<int64_t *>(Dz + (kF32 ? 2 : 1) * P2);
     const T *tloc = reinterpret_cast<const T *>(a.tloc);
     const T *mass = reinterpret_cast<const T *>(a.mass);
@@ -740,11 +749,22 @@ eval_kernel(EvalArgs a) {
         lv0 = tvox[lane];
         lv1 = tvox[lane + 32];
     }
-    for (int64_t it = (int64_t)blockIdx.x * kEvalWarps + warp; it < a.n_items;
-         it += (int64_t)gridDim.x * kEvalWarps) {
+    for (;;) {
+        int64_t it = 0;
+        if (lane == 0) it = (int64_t)atomicAdd(a.queue, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= a.n_items) break;
         const int4 item = a.items[it];
         const int leaf = item.x;
         const uint64_t key = a.tkey[leaf];
+        // lattice form: lanes per group (gs) and groups (ns) for this item;
+        // lane = grp * gs + r0 holds observers r0 and r0 + gs of the item
+        int gs = 32;
+        if constexpr (N1 > 0 && kF32) {
+            const int np = (item.z + 1) >> 1;
+            gs = np > 16 ? 32 : np > 8 ? 16 : 32 / kLatGroups;
+        }
+        const int ns = 32 / gs, grp = lane / gs, r0 = lane - grp * gs;
         int64_t lc[3];
         {
             uint64_t k = key;
@@ -759,31 +779,45 @@ eval_kernel(EvalArgs a) {
         int tid[kTPL];
 #pragma unroll
         for (int u = 0; u < kTPL; ++u) {
-            const int r = lane + 32 * u;
+            const int r = r0 + gs * u;
             tid[u] = r < item.z ? item.y + r : -1;
             const int64_t i = tid[u] >= 0 ? tid[u] : item.y;
             tx[u] = tloc[3 * i + 0];
             ty[u] = tloc[3 * i + 1];
             tz[u] = tloc[3 * i + 2];
         }
-        // the item's neighbour leaves: source-block index, or -1 outside the block
+        // the item's neighbour leaves inside the source block, in the order of
+        // nb = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): source-block index * 32 + nb
         __syncwarp();
-        if (lane < 27) {
-            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-            const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1], sz = lc[2] + dz - a.blk.lo[2];
-            const bool in = sx >= 0 && sy >= 0 && sz >= 0 && sx < a.blk.n[0] && sy < a.blk.n[1] && sz < a.blk.n[2] &&
-                            in_source_part(lc[0] + dx, lc[1] + dy, lc[2] + dz, a.L - 2, a.part_lo, a.part_hi);
-            nbl[lane] = in ? (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx : -1;
+        int nv;
+        {
+            bool in = false;
+            int64_t sidx = 0;
+            if (lane < 27) {
+                const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+                const int64_t sx = lc[0] + dx - a.blk.lo[0], sy = lc[1] + dy - a.blk.lo[1],
+                              sz = lc[2] + dz - a.blk.lo[2];
+                in = sx >= 0 && sy >= 0 && sz >= 0 && sx < a.blk.n[0] && sy < a.blk.n[1] && sz < a.blk.n[2] &&
+                     in_source_part(lc[0] + dx, lc[1] + dy, lc[2] + dz, a.L - 2, a.part_lo, a.part_hi);
+                sidx = (sz * a.blk.n[1] + sy) * a.blk.n[0] + sx;
+            }
+            const unsigned vm = __ballot_sync(0xffffffffu, in);
+            if (in) nbl[__popc(vm & ((1u << lane) - 1u))] = sidx * 32 + lane;
+            nv = __popc(vm);
         }
         __syncwarp();
         for (int bb = 0; bb < a.B; ++bb) {
             T hx[kTPL], hy[kTPL], hz[kTPL], lx[kTPL], ly[kTPL], lz[kTPL];
 #pragma unroll
             for (int u = 0; u < kTPL; ++u) hx[u] = hy[u] = hz[u] = lx[u] = ly[u] = lz[u] = T(0);
-            // ---- near field: the leaf itself and its nearest neighbours
-            for (int nb = 0; nb < 27; ++nb) {
-                const int64_t sl = nbl[nb];
-                if (sl < 0) continue;
+            // ---- near field: the leaf itself and its nearest neighbours (in the
+            // lattice form, group grp takes entries grp, grp + ns, ...; a group
+            // past the end computes entry c0's leaf and drops the result)
+            for (int c0 = 0; c0 < nv; c0 += ns) {
+                const bool act = c0 + grp < nv;
+                const int64_t ent = nbl[act ? c0 + grp : c0];
+                const int64_t sl = ent >> 5;
+                const int nb = (int)(ent & 31);
                 const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
                 const T *ms = mass + (sl * a.B + bb) * b3;
                 const T ox = T(dx * a.b), oy = T(dy * a.b), oz = T(dz * a.b);
@@ -797,12 +831,17 @@ eval_kernel(EvalArgs a) {
                     // three adds; the lane's two observers form one packed pair.
                     constexpr int N3 = N1 * N1 * N1;
                     __syncwarp();
-                    float2 *wl = reinterpret_cast<float2 *>(wsh);
+                    float2 *wl = reinterpret_cast<float2 *>(wsh) + grp * N3;
                     static_assert(N1 == 4, "two lattice points per lane, rows of four");
-                    {
+                    if (gs == 32) {
                         const float w0 = lw0 * ms[lv0], w1 = lw1 * ms[lv1];
                         wl[lane] = make_float2(w0, w0);
                         wl[lane + 32] = make_float2(w1, w1);
+                    } else {
+                        for (int n = r0; n < N3; n += gs) {
+                            const float w = (float)tab[n].w * ms[tvox[n]];
+                            wl[n] = make_float2(w, w);
+                        }
                     }
                     __syncwarp();
                     const uint64_t PX = pk2(tx[0], tx[1]), PY = pk2(ty[0], ty[1]), PZ = pk2(tz[0], tz[1]);
@@ -853,7 +892,7 @@ eval_kernel(EvalArgs a) {
                             QZ = fma2(SZ, ez, QZ);
                         }
                     };
-                    if (a.guard_all || nb == 13)
+                    if (a.guard_all || __any_sync(0xffffffffu, nb == 13))
                         lattice(std::true_type{});
                     else
                         lattice(std::false_type{});
@@ -868,11 +907,13 @@ eval_kernel(EvalArgs a) {
                     up2(QX, gx[0], gx[1]);
                     up2(QY, gy[0], gy[1]);
                     up2(QZ, gz[0], gz[1]);
+                    if (act) {
 #pragma unroll
-                    for (int u = 0; u < kTPL; ++u) {
-                        two_sum(hx[u], lx[u], (T)gx[u]);
-                        two_sum(hy[u], ly[u], (T)gy[u]);
-                        two_sum(hz[u], lz[u], (T)gz[u]);
+                        for (int u = 0; u < kTPL; ++u) {
+                            two_sum(hx[u], lx[u], (T)gx[u]);
+                            two_sum(hy[u], ly[u], (T)gy[u]);
+                            two_sum(hz[u], lz[u], (T)gz[u]);
+                        }
                     }
                     continue;
                 }
@@ -1006,6 +1047,21 @@ eval_kernel(EvalArgs a) {
                     two_sum(hz[u], lz[u], pz[u]);
                 }
             }
+            // the groups' sums of the same observers, merged into every group
+            for (int o = gs; o < 32; o <<= 1) {
+#pragma unroll
+                for (int u = 0; u < kTPL; ++u) {
+                    const T vx = __shfl_xor_sync(0xffffffffu, hx[u], o), wx = __shfl_xor_sync(0xffffffffu, lx[u], o);
+                    const T vy = __shfl_xor_sync(0xffffffffu, hy[u], o), wy = __shfl_xor_sync(0xffffffffu, ly[u], o);
+                    const T vz = __shfl_xor_sync(0xffffffffu, hz[u], o), wz = __shfl_xor_sync(0xffffffffu, lz[u], o);
+                    two_sum(hx[u], lx[u], vx);
+                    two_sum(hy[u], ly[u], vy);
+                    two_sum(hz[u], lz[u], vz);
+                    lx[u] += wx;
+                    ly[u] += wy;
+                    lz[u] += wz;
+                }
+            }
             // ---- far field: gradient of the leaf's local expansion
             __syncwarp();
             const T *L = le + ((int64_t)leaf * a.B + bb) * a.ldk;
@@ -1048,7 +1104,7 @@ eval_kernel(EvalArgs a) {
             }
 #pragma unroll
             for (int u = 0; u < kTPL; ++u) {
-                if (tid[u] < 0) continue;
+                if (tid[u] < 0 || grp != 0) continue;
                 const T fx = fxa[u], fy = fya[u], fz = fza[u];
                 // near (hi + lo) + far and the scale in FP64, in both precisions
                 const double gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
@@ -1063,6 +1119,14 @@ eval_kernel(EvalArgs a) {
                 }
                 if (a.gz) a.gz[(int64_t)bb * a.M + j] = gzv;
             }
+        }
+    }
+    // the last warp out leaves the queue at zero for the next launch
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 1, 1ull) == (unsigned long long)gridDim.x * kEvalWarps - 1) {
+            a.queue[0] = 0;
+            a.queue[1] = 0;
         }
     }
 }
@@ -1513,6 +1577,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         a.part_hi = plan->part_hi;
         a.items = F->items;
         a.n_items = F->n_items;
+        a.queue = F->eval_queue;
         a.tkey = F->lev[L].tkey;
         a.perm = F->perm;
         a.tloc = sizeof(T) == 8 ? (const void *)F->tloc_d : (const void *)F->tloc_f;
@@ -1552,11 +1617,14 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
                 eval_an_kernel<T, 4><<<grid, kEvalWarps * 32, shan, st>>>(a);
             }
         } else if (sizeof(T) == 4 && n1 == 4) {
+            // resident blocks only: the warps drain the item queue
             GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
-            eval_kernel<float, 4><<<grid, kEvalWarps * 32, shm, st>>>(a);
+            const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<float, 4>, kEvalWarps * 32, shm));
+            eval_kernel<float, 4><<<rg, kEvalWarps * 32, shm, st>>>(a);
         } else {
             GF_TRY((ensure_smem(eval_kernel<T, 0>, shm)));
-            eval_kernel<T, 0><<<grid, kEvalWarps * 32, shm, st>>>(a);
+            const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<T, 0>, kEvalWarps * 32, shm));
+            eval_kernel<T, 0><<<rg, kEvalWarps * 32, shm, st>>>(a);
         }
         GF_KERNEL_DONE();
     }

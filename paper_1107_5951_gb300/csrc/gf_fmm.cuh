@@ -87,6 +87,7 @@ struct FmmPlan {
     double *tloc_d = nullptr;
     int4 *items = nullptr;        // evaluation work: (leaf, first, count <= 64, 0)
     int64_t n_items = 0;
+    unsigned long long *eval_queue = nullptr;   // evaluation item queue (2 counters, zero between launches)
     void *mass = nullptr;         // [ns_L][B][b^3] voxel densities, leaf-blocked
     double *p2m_d = nullptr;      // [b^3][K] quadrature-folded P2M matrix
     float *p2m_f = nullptr;

@@ -207,6 +207,17 @@ inline gf_status ensure_smem(Kern kernel, size_t bytes) {
     return GF_OK;
 }
 
+// Blocks of `kernel` that are resident on the current device at once, for
+// grids whose warps take their work from a queue (at least 1).
+template <class Kern>
+inline unsigned resident_blocks(Kern kernel, int threads, size_t shm) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, shm) != cudaSuccess)
+        return 1;
+    return (unsigned)(per > 0 ? per : 1) * (unsigned)(sms > 0 ? sms : 1);
+}
+
 // Number of kernels the library has launched (all plans, all threads).
 void count_launch(int n = 1);
 #define GF_KERNEL_DONE() \

@@ -598,11 +598,13 @@ gf_status fmm_observer_tree(gf_plan_s *plan, const double *obs, const double oz[
             ub[l] = cap;
         }
     }
-    int64_t *d_cnt;   // [0, L]: boxes per level, [kMaxLevels + 1]: items
+    int64_t *d_cnt;   // [0, L]: boxes per level, [kMaxLevels + 1]: items, then the
+                      // evaluation kernel's item queue (2 counters)
     int *d_ccnt;      // [8 (kMaxLevels + 1)]: boxes per parity class and level
-    GF_TRY(A.alloc_n(&d_cnt, kMaxLevels + 2));
+    GF_TRY(A.alloc_n(&d_cnt, kMaxLevels + 4));
     GF_TRY(A.alloc_n(&d_ccnt, 8 * (kMaxLevels + 1)));
-    GF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * (kMaxLevels + 2), st));
+    GF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * (kMaxLevels + 4), st));
+    F->eval_queue = reinterpret_cast<unsigned long long *>(d_cnt + kMaxLevels + 2);
     GF_CUDA(cudaMemsetAsync(d_ccnt, 0, sizeof(int) * 8 * (kMaxLevels + 1), st));
     GF_TRY(A.alloc_n(&leaf.tkey, ub[L]));
     GF_TRY(A.alloc_n(&F->leaf_beg, ub[L] + 1));
