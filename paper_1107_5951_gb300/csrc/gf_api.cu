@@ -76,6 +76,9 @@ void plan_release(gf_plan_s *plan) {
     plan->arena.release();
     for (int i = 0; i <= GF_NUM_STAGES; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->side) cudaStreamDestroy(plan->side);
     delete plan;
 }
 
@@ -224,6 +227,17 @@ static gf_status finish_create(gf_plan_s *p, gf_status s, cudaStream_t st, gf_pl
         delete p;
         set_error("%s", keep);
         return s;
+    }
+    if (p->fmm && !p->fmm->points) {
+        // the near field's stream (it runs beside the M2L; see the forward)
+        cudaError_t e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            set_error("cannot create the plan's second stream: %s", cudaGetErrorString(e));
+            plan_release(p);
+            return GF_ERR_CUDA;
+        }
     }
     p->device_bytes = p->arena.bytes;
     *out = p;

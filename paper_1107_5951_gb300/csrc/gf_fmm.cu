@@ -651,6 +651,9 @@ struct EvalArgs {
     const int4 *items;
     int64_t n_items;
     unsigned long long *queue; // [0]: next item, [1]: warps done (zero between launches)
+    int mode;                  // 0: near + far field; 1: near field only, sums to nsum;
+                               // 2: far field, near sums from nsum
+    void *nsum;                // [B][M][6] T: (hi, lo) of x, y, z per observer (key order)
     const uint64_t *tkey;      // leaf keys
     const int32_t *perm;
     const void *tloc;          // [M][3] T
@@ -762,7 +765,7 @@ eval_kernel(EvalArgs a) {
         int gs = 32;
         if constexpr (N1 > 0 && kF32) {
             const int np = (item.z + 1) >> 1;
-            gs = np > 16 ? 32 : np > 8 ? 16 : 32 / kLatGroups;
+            if (a.mode != 2) gs = np > 16 ? 32 : np > 8 ? 16 : 32 / kLatGroups;
         }
         const int ns = 32 / gs, grp = lane / gs, r0 = lane - grp * gs;
         int64_t lc[3];
@@ -789,8 +792,8 @@ eval_kernel(EvalArgs a) {
         // the item's neighbour leaves inside the source block, in the order of
         // nb = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): source-block index * 32 + nb
         __syncwarp();
-        int nv;
-        {
+        int nv = 0;
+        if (a.mode != 2) {
             bool in = false;
             int64_t sidx = 0;
             if (lane < 27) {
@@ -1061,6 +1064,31 @@ eval_kernel(EvalArgs a) {
                     ly[u] += wy;
                     lz[u] += wz;
                 }
+            }
+            // split evaluation: the near sums go to nsum (mode 1) or come from it (mode 2)
+            if (a.mode != 0) {
+                T *ns = reinterpret_cast<T *>(a.nsum);
+#pragma unroll
+                for (int u = 0; u < kTPL; ++u) {
+                    if (tid[u] < 0 || grp != 0) continue;
+                    T *q = ns + ((int64_t)bb * a.M + tid[u]) * 6;
+                    if (a.mode == 1) {
+                        q[0] = hx[u];
+                        q[1] = lx[u];
+                        q[2] = hy[u];
+                        q[3] = ly[u];
+                        q[4] = hz[u];
+                        q[5] = lz[u];
+                    } else {
+                        hx[u] = q[0];
+                        lx[u] = q[1];
+                        hy[u] = q[2];
+                        ly[u] = q[3];
+                        hz[u] = q[4];
+                        lz[u] = q[5];
+                    }
+                }
+                if (a.mode == 1) continue;
             }
             // ---- far field: gradient of the leaf's local expansion
             __syncwarp();
@@ -1406,6 +1434,7 @@ gf_status fmm_alloc_workspaces(gf_plan_s *plan, cudaStream_t st) {
     const int b3 = F->b * F->b * F->b;
     const int64_t nmass = F->points ? plan->pts.S : F->lev[F->L].ns * b3;
     GF_TRY(A.alloc(&F->mass, (size_t)std::max<int64_t>(nmass, 1) * B * rs));
+    if (!F->points) GF_TRY(A.alloc(&F->nsum, (size_t)std::max<int64_t>(plan->M, 1) * B * 6 * rs));
     static bool il_ready[64] = {false};
     static std::mutex il_mu;
     {
@@ -1461,6 +1490,67 @@ static int lattice_of(const QuadRule &qr, int b, EvalArgs &a) {
         for (int i = 0; i < b * m; ++i)
             a.lat_c[d][i] = ((float)(i / m) + (float)(0.5 + 0.5 * nodes[i % m])) - half_b;
     return b * m;
+}
+
+// Arguments of the evaluation kernels; returns the lattice size N1 of the
+// near field's lattice form (0: the generic source list).
+template <class T>
+int eval_setup(gf_plan_s *plan, int B, double *g, double *gz, EvalArgs &a) {
+    const FmmPlan *F = plan->fmm;
+    const int L = F->L;
+    a.L = L;
+    a.part_lo = plan->part_lo;
+    a.part_hi = plan->part_hi;
+    a.items = F->items;
+    a.n_items = F->n_items;
+    a.queue = F->eval_queue;
+    a.mode = 0;
+    a.nsum = F->nsum;
+    a.tkey = F->lev[L].tkey;
+    a.perm = F->perm;
+    a.tloc = sizeof(T) == 8 ? (const void *)F->tloc_d : (const void *)F->tloc_f;
+    a.mass = F->mass;
+    a.le = F->lev[L].le;
+    a.qr = quad_device(plan);
+    a.blk = block_of(F->lev[L]);
+    a.b = F->b;
+    a.nq = F->nq;
+    a.B = B;
+    a.K = F->K;
+    a.ldk = F->KS;
+    a.p = F->p;
+    a.M = plan->M;
+    a.scale = plan->G * F->h;
+    a.eps2 = sizeof(T) == 8 ? 1e-18 : 1e-12;
+    a.guard_all = 0;
+    for (int q = 0; q < plan->quad.nq; ++q)
+        for (int d = 0; d < 3; ++d)
+            if (fabs(plan->quad.xi[q][d]) >= 1.0) a.guard_all = 1;
+    a.g = g;
+    a.gz = gz;
+    return sizeof(T) == 4 ? lattice_of(plan->quad, F->b, a) : 0;
+}
+
+// One evaluation kernel (mode 0: whole, 1: near field, 2: far field) on
+// the blocks that fit the device at once; the warps drain the item queue.
+template <class T>
+gf_status eval_launch(gf_plan_s *plan, EvalArgs a, int n1, int mode, cudaStream_t st) {
+    const FmmPlan *F = plan->fmm;
+    a.mode = mode;
+    const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
+                       sizeof(T) * kEvalWarps * eval_slice(F->p * F->p, (int)sizeof(T));
+    const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
+    if (sizeof(T) == 4 && n1 == 4) {
+        GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
+        const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<float, 4>, kEvalWarps * 32, shm));
+        eval_kernel<float, 4><<<rg, kEvalWarps * 32, shm, st>>>(a);
+    } else {
+        GF_TRY((ensure_smem(eval_kernel<T, 0>, shm)));
+        const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<T, 0>, kEvalWarps * 32, shm));
+        eval_kernel<T, 0><<<rg, kEvalWarps * 32, shm, st>>>(a);
+    }
+    GF_KERNEL_DONE();
+    return GF_OK;
 }
 
 template <class T>
@@ -1544,9 +1634,25 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
         }
     }
     stage_mark(plan, 3, st);
+    // a7-a9 set up before the M2L: the near field of the evaluation only
+    // reads the leaf masses, so it runs on the plan's second stream beside
+    // the M2L and the L2L chain (from the M2L's launch on); the far field
+    // (L2P, near + far in FP64, scatter) joins it once the L2L is done.
+    // With stage timing on, both halves run in line on the forward's stream.
+    const bool eval_on = !pts && F->n_items > 0;
+    const bool an = (plan->opt.reserved0 & GF_FLAG_SUM_AN) != 0;
+    EvalArgs ea;
+    int n1 = 0;
+    if (eval_on) n1 = eval_setup<T>(plan, B, g, gz, ea);
+    const bool beside = eval_on && !an && plan->side && !plan->timing;
     // a5/a6: M2L at every level (each overwrites its level's LE), then the
     // L2L chain from level 3 down, which adds each finished parent LE.
-    GF_TRY(m2l_run<T>(plan, B, false, st));   // marks the end of the input split (4)
+    GF_TRY(m2l_run<T>(plan, B, false, st, beside ? plan->ev_fork : nullptr));   // marks the input split's end (4)
+    if (beside) {
+        GF_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
+        GF_TRY(eval_launch<T>(plan, ea, n1, 1, plan->side));
+        GF_CUDA(cudaEventRecord(plan->ev_join, plan->side));
+    }
     stage_mark(plan, 5, st);
     for (int l = 3; l <= L; ++l) {
         const FmmLevel &lv = F->lev[l];
@@ -1570,63 +1676,26 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     // a7-a9: near field + L2P + combine + scatter
     if (pts) {
         GF_TRY(points_eval<T>(plan, B, g, gz, st));
-    } else if (F->n_items > 0) {
-        EvalArgs a;
-        a.L = F->L;
-        a.part_lo = plan->part_lo;
-        a.part_hi = plan->part_hi;
-        a.items = F->items;
-        a.n_items = F->n_items;
-        a.queue = F->eval_queue;
-        a.tkey = F->lev[L].tkey;
-        a.perm = F->perm;
-        a.tloc = sizeof(T) == 8 ? (const void *)F->tloc_d : (const void *)F->tloc_f;
-        a.mass = F->mass;
-        a.le = F->lev[L].le;
-        a.qr = quad_device(plan);
-        a.blk = block_of(F->lev[L]);
-        a.b = F->b;
-        a.nq = F->nq;
-        a.B = B;
-        a.K = K;
-        a.ldk = F->KS;
-        a.p = F->p;
-        a.M = plan->M;
-        a.scale = plan->G * F->h;
-        a.eps2 = sizeof(T) == 8 ? 1e-18 : 1e-12;
-        a.guard_all = 0;
-        for (int q = 0; q < plan->quad.nq; ++q)
-            for (int d = 0; d < 3; ++d)
-                if (fabs(plan->quad.xi[q][d]) >= 1.0) a.guard_all = 1;
-        a.g = g;
-        a.gz = gz;
-        const int n1 = sizeof(T) == 4 ? lattice_of(plan->quad, F->b, a) : 0;
-        const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
-                           sizeof(T) * kEvalWarps * eval_slice(F->p * F->p, (int)sizeof(T));
+    } else if (eval_on && an) {
+        // closed-form voxels: radius 2 in FP32, 4 in FP64 (the closed form
+        // cancels like (d/h)^3, so the precision sets how far it is used;
+        // beyond it the corrected midpoint rule errs like (h/d)^6)
         const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
-        if (plan->opt.reserved0 & GF_FLAG_SUM_AN) {
-            // closed-form voxels: radius 2 in FP32, 4 in FP64 (the closed form
-            // cancels like (d/h)^3, so the precision sets how far it is used;
-            // beyond it the corrected midpoint rule errs like (h/d)^6)
-            const size_t shan = sizeof(T) * kEvalWarps * eval_an_slice(F->p * F->p) + 64;
-            if (sizeof(T) == 4) {
-                GF_TRY((ensure_smem(eval_an_kernel<T, 2>, shan)));
-                eval_an_kernel<T, 2><<<grid, kEvalWarps * 32, shan, st>>>(a);
-            } else {
-                GF_TRY((ensure_smem(eval_an_kernel<T, 4>, shan)));
-                eval_an_kernel<T, 4><<<grid, kEvalWarps * 32, shan, st>>>(a);
-            }
-        } else if (sizeof(T) == 4 && n1 == 4) {
-            // resident blocks only: the warps drain the item queue
-            GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
-            const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<float, 4>, kEvalWarps * 32, shm));
-            eval_kernel<float, 4><<<rg, kEvalWarps * 32, shm, st>>>(a);
+        const size_t shan = sizeof(T) * kEvalWarps * eval_an_slice(F->p * F->p) + 64;
+        if (sizeof(T) == 4) {
+            GF_TRY((ensure_smem(eval_an_kernel<T, 2>, shan)));
+            eval_an_kernel<T, 2><<<grid, kEvalWarps * 32, shan, st>>>(ea);
         } else {
-            GF_TRY((ensure_smem(eval_kernel<T, 0>, shm)));
-            const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<T, 0>, kEvalWarps * 32, shm));
-            eval_kernel<T, 0><<<rg, kEvalWarps * 32, shm, st>>>(a);
+            GF_TRY((ensure_smem(eval_an_kernel<T, 4>, shan)));
+            eval_an_kernel<T, 4><<<grid, kEvalWarps * 32, shan, st>>>(ea);
         }
         GF_KERNEL_DONE();
+    } else if (eval_on) {
+        if (beside)
+            GF_CUDA(cudaStreamWaitEvent(st, plan->ev_join, 0));
+        else
+            GF_TRY(eval_launch<T>(plan, ea, n1, 1, st));
+        GF_TRY(eval_launch<T>(plan, ea, n1, 2, st));
     }
     stage_mark(plan, 7, st);
     return GF_OK;

@@ -89,6 +89,7 @@ struct FmmPlan {
     int64_t n_items = 0;
     unsigned long long *eval_queue = nullptr;   // evaluation item queue (2 counters, zero between launches)
     void *mass = nullptr;         // [ns_L][B][b^3] voxel densities, leaf-blocked
+    void *nsum = nullptr;         // [B][M][6] near-field sums (hi, lo per component) in observer-key order
     double *p2m_d = nullptr;      // [b^3][K] quadrature-folded P2M matrix
     float *p2m_f = nullptr;
     const Tables *tab = nullptr;

@@ -113,6 +113,11 @@ struct gf_plan_s {
     bool counts_done = false;    // FMM work counts computed (on first info request)
     bool timing = false;
     cudaEvent_t ev[GF_NUM_STAGES + 1] = {};
+    // FMM plans: a second stream for the near field of the evaluation, which
+    // runs beside the M2L and the L2L chain, and the events that fork it from
+    // the forward's stream and join it back
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool ev_used[GF_NUM_STAGES + 1] = {};
 };
 

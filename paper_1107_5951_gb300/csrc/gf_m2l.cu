@@ -1630,7 +1630,7 @@ TcArgs tc_args(gf_plan_s *plan, int B) {
     return a;
 }
 
-gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
+gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st, cudaEvent_t fork) {
     FmmPlan *F = plan->fmm;
     const Tables *T = F->tab;
     TcArgs a = tc_args(plan, B);
@@ -1688,6 +1688,7 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
         GF_KERNEL_DONE();
     }
     if (!adj) stage_mark(plan, 4, st);
+    if (fork) GF_CUDA(cudaEventRecord(fork, st));
     const int nbox = 128 / B;
     int tiles = 0, e = 0;
     for (int l = 2; l <= F->L; ++l)
@@ -1959,13 +1960,14 @@ template gf_status translate_run<float, double>(gf_plan_s *, int, int, int, cuda
 template gf_status translate_run<double, double>(gf_plan_s *, int, int, int, cudaStream_t);
 
 template <class T>
-gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
+gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st, cudaEvent_t fork) {
     FmmPlan *F = plan->fmm;
     const bool tc = (sizeof(T) == 4 || (F->m2l_tc64 && !adj)) && F->tab->m2l_tc && (adj ? F->tc_levels_adj : F->tc_levels) &&
                     !(plan->opt.reserved0 & GF_FLAG_M2L_SIMT) && B <= 128 &&
                     tc_stages(F->tab->tc_npad, true) >= 2;
-    if (tc) return m2l_run_tc(plan, B, adj, st);
+    if (tc) return m2l_run_tc(plan, B, adj, st, fork);
     if (!adj) stage_mark(plan, 4, st);   // no input split on this path
+    if (fork) GF_CUDA(cudaEventRecord(fork, st));
     for (int l = 2; l <= F->L; ++l) {
         if (F->lev[l].nt == 0 && !adj) continue;   // the adjoint writes every source box
         GF_TRY(m2l_level<T>(plan, l, B, adj, st));
@@ -1973,7 +1975,7 @@ gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st) {
     return GF_OK;
 }
 
-template gf_status m2l_run<float>(gf_plan_s *, int, bool, cudaStream_t);
-template gf_status m2l_run<double>(gf_plan_s *, int, bool, cudaStream_t);
+template gf_status m2l_run<float>(gf_plan_s *, int, bool, cudaStream_t, cudaEvent_t);
+template gf_status m2l_run<double>(gf_plan_s *, int, bool, cudaStream_t, cudaEvent_t);
 
 }  // namespace gf

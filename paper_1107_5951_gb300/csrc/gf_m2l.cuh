@@ -19,8 +19,10 @@ gf_status build_p2m_up_tc_image(const double *q, int K, int npad, int b3, float 
 // for the SIMT kernel; FP64 runs on the SIMT kernel.
 // adj: the transpose, MEdual_l[s] = sum_{o in IL(class of s)} T_{-o}^T LEdual_l[s + o]
 // over every source box s (observer boxes found through the level's map).
+// fork: when non-null, recorded on st right before the M2L kernels are
+// launched (after the input split).
 template <class T>
-gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st);
+gf_status m2l_run(gf_plan_s *plan, int B, bool adj, cudaStream_t st, cudaEvent_t fork = nullptr);
 template <class T>
 gf_status m2l_level(gf_plan_s *plan, int level, int B, bool adj, cudaStream_t st);
 
