@@ -256,7 +256,7 @@ GF_HD void lget(const T *L, int n, int m, T &r, T &i) {   // L_n^m, any sign of 
 // gradient expansions D^x, D^y, D^z of the local expansion L (degree p).
 template <class T>
 GF_HD void grad_coeff(const T *L, int idx, T &dx, T &dy, T &dz) {
-    int n = (int)sqrt((double)idx);
+    int n = (int)sqrtf((float)idx);   // corrected below (idx < 2^24)
     while (n * n > idx) --n;
     while ((n + 1) * (n + 1) <= idx) ++n;
     const int ro = idx - n * n;

@@ -7,7 +7,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "gf_fmm.cuh"
 #include "gf_internal.cuh"
@@ -70,15 +72,61 @@ void DeviceArena::release() {
     bytes = 0;
 }
 
+// Second streams of FMM plans (with their fork and join events), kept per
+// device once created: a plan takes one when it is built and gives it back
+// when it is freed, so building a plan creates no stream after the first.
+namespace {
+struct SideSet {
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+std::mutex g_side_mu;
+std::vector<SideSet> g_side_free[64];
+}  // namespace
+
+static gf_status side_take(gf_plan_s *p) {
+    {
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        std::vector<SideSet> &v = g_side_free[p->device & 63];
+        if (!v.empty()) {
+            p->side = v.back().s;
+            p->ev_fork = v.back().fork;
+            p->ev_join = v.back().join;
+            v.pop_back();
+            return GF_OK;
+        }
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        set_error("cannot create the plan's second stream: %s", cudaGetErrorString(e));
+        return GF_ERR_CUDA;
+    }
+    return GF_OK;
+}
+
+// The plan's device work has completed (its second stream is idle).
+static void side_give(gf_plan_s *p) {
+    if (p->side && p->ev_fork && p->ev_join) {
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        g_side_free[p->device & 63].push_back(SideSet{p->side, p->ev_fork, p->ev_join});
+    } else {
+        if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+        if (p->ev_join) cudaEventDestroy(p->ev_join);
+        if (p->side) cudaStreamDestroy(p->side);
+    }
+    p->side = nullptr;
+    p->ev_fork = p->ev_join = nullptr;
+}
+
 // Free a plan whose device work has all completed (no device-wide wait).
 void plan_release(gf_plan_s *plan) {
     fmm_destroy(plan);
     plan->arena.release();
     for (int i = 0; i <= GF_NUM_STAGES; ++i)
         if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
-    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
-    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
-    if (plan->side) cudaStreamDestroy(plan->side);
+    side_give(plan);
     delete plan;
 }
 
@@ -230,13 +278,10 @@ static gf_status finish_create(gf_plan_s *p, gf_status s, cudaStream_t st, gf_pl
     }
     if (p->fmm && !p->fmm->points) {
         // the near field's stream (it runs beside the M2L; see the forward)
-        cudaError_t e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            set_error("cannot create the plan's second stream: %s", cudaGetErrorString(e));
+        const gf_status ss = side_take(p);
+        if (ss != GF_OK) {
             plan_release(p);
-            return GF_ERR_CUDA;
+            return ss;
         }
     }
     p->device_bytes = p->arena.bytes;

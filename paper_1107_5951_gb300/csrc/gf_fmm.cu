@@ -743,6 +743,7 @@ eval_kernel(EvalArgs a) {
     __syncthreads();
     // far-field scale of the L2P gradient (voxel units)
     const double far_s = -1.0 / ((double)a.b * (double)a.b);
+    const float far_sf = (float)far_s;
     // lattice form: this lane's two lattice points (weight, voxel)
     float lw0 = 0.f, lw1 = 0.f;
     int lv0 = 0, lv1 = 0;
@@ -759,7 +760,6 @@ eval_kernel(EvalArgs a) {
         if (it >= a.n_items) break;
         const int4 item = a.items[it];
         const int leaf = item.x;
-        const uint64_t key = a.tkey[leaf];
         // lattice form: lanes per group (gs) and groups (ns) for this item;
         // lane = grp * gs + r0 holds observers r0 and r0 + gs of the item
         int gs = 32;
@@ -768,10 +768,9 @@ eval_kernel(EvalArgs a) {
             if (a.mode != 2) gs = np > 16 ? 32 : np > 8 ? 16 : 32 / kLatGroups;
         }
         const int ns = 32 / gs, grp = lane / gs, r0 = lane - grp * gs;
-        int64_t lc[3];
-        {
-            uint64_t k = key;
-            lc[0] = lc[1] = lc[2] = 0;
+        int64_t lc[3] = {0, 0, 0};   // the leaf's box coordinates (near field only)
+        if (a.mode != 2) {
+            const uint64_t k = a.tkey[leaf];
             for (int bit = 0; bit < 21; ++bit) {
                 lc[0] |= (int64_t)((k >> (3 * bit)) & 1) << bit;
                 lc[1] |= (int64_t)((k >> (3 * bit + 1)) & 1) << bit;
@@ -1134,10 +1133,25 @@ eval_kernel(EvalArgs a) {
             for (int u = 0; u < kTPL; ++u) {
                 if (tid[u] < 0 || grp != 0) continue;
                 const T fx = fxa[u], fy = fya[u], fz = fza[u];
-                // near (hi + lo) + far and the scale in FP64, in both precisions
-                const double gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
-                const double gy = ((double)hy[u] + (double)ly[u] + far_s * (double)fy) * a.scale;
-                const double gzv = ((double)hz[u] + (double)lz[u] + far_s * (double)fz) * a.scale;
+                double gx, gy, gzv;
+                if constexpr (kF32) {
+                    // near (hi + lo) + far as a compensated FP32 pair (TwoSum), then
+                    // the pair's sum and the scale in FP64; the FP32 -> FP64
+                    // conversions use integer operations (FP64 runs at 1/64 of
+                    // the FP32 rate on this GPU)
+                    float sx = hx[u], ex = lx[u], sy = hy[u], ey = ly[u], sz = hz[u], ez = lz[u];
+                    two_sum(sx, ex, far_sf * fx);
+                    two_sum(sy, ey, far_sf * fy);
+                    two_sum(sz, ez, far_sf * fz);
+                    gx = (f32_to_f64(sx) + f32_to_f64(ex)) * a.scale;
+                    gy = (f32_to_f64(sy) + f32_to_f64(ey)) * a.scale;
+                    gzv = (f32_to_f64(sz) + f32_to_f64(ez)) * a.scale;
+                } else {
+                    // near (hi + lo) + far and the scale in FP64
+                    gx = ((double)hx[u] + (double)lx[u] + far_s * (double)fx) * a.scale;
+                    gy = ((double)hy[u] + (double)ly[u] + far_s * (double)fy) * a.scale;
+                    gzv = ((double)hz[u] + (double)lz[u] + far_s * (double)fz) * a.scale;
+                }
                 const int64_t j = a.perm[tid[u]];
                 if (a.g) {
                     double *o = a.g + ((int64_t)bb * a.M + j) * 3;
@@ -1153,6 +1167,113 @@ eval_kernel(EvalArgs a) {
     if (lane == 0) {
         __threadfence();
         if (atomicAdd(a.queue + 1, 1ull) == (unsigned long long)gridDim.x * kEvalWarps - 1) {
+            a.queue[0] = 0;
+            a.queue[1] = 0;
+        }
+    }
+}
+
+// Far field of the split evaluation in FP32 (after the near-field kernel
+// has left each observer's compensated near sums in nsum): the L2P gradient
+// of the leaf's local expansion, near + far, the scale and the scatter.  One
+// warp takes up to 128 observers of one leaf, four per lane as two packed
+// pairs that share every coefficient load; the warps take the evaluation
+// items (64 observers each) from the queue and skip every second item of a
+// leaf, which the warp holding the item before it covers.
+constexpr int kFarWarps = 4;
+constexpr int kFarTargets = 128;
+static_assert(kFarTargets == 2 * kTPL * 32, "two evaluation items per far item");
+inline __host__ __device__ int far_slice(int P2) { return (6 * P2 + 7) & ~7; }   // floats per warp
+
+__global__ void __launch_bounds__(kFarWarps * 32, 6) eval_far_kernel(EvalArgs a, const int32_t *__restrict__ leaf_beg) {
+    extern __shared__ float fsh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P2 = a.p * a.p;
+    float2 *Dx2 = reinterpret_cast<float2 *>(fsh + (size_t)warp * far_slice(P2));
+    float2 *Dy2 = Dx2 + P2, *Dz2 = Dy2 + P2;
+    const float *tloc = reinterpret_cast<const float *>(a.tloc);
+    const float *le = reinterpret_cast<const float *>(a.le);
+    const float *ns = reinterpret_cast<const float *>(a.nsum);
+    const float inv_b = 1.f / (float)a.b;
+    const float far_sf = (float)(-1.0 / ((double)a.b * (double)a.b));
+    for (;;) {
+        int64_t it = 0;
+        if (lane == 0) it = (int64_t)atomicAdd(a.queue, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= a.n_items) break;
+        const int4 item = a.items[it];
+        const int leaf = item.x;
+        const int lb = leaf_beg[leaf];
+        if (((item.y - lb) / (kFarTargets / 2)) & 1) continue;   // covered with the item before it
+        const int cnt = min(kFarTargets, leaf_beg[leaf + 1] - item.y);
+        int tid[4];
+        float tx[4], ty[4], tz[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = lane + 32 * u;
+            tid[u] = r < cnt ? item.y + r : -1;
+            const int64_t i = tid[u] >= 0 ? tid[u] : item.y;
+            tx[u] = tloc[3 * i + 0] * inv_b;
+            ty[u] = tloc[3 * i + 1] * inv_b;
+            tz[u] = tloc[3 * i + 2] * inv_b;
+        }
+        for (int bb = 0; bb < a.B; ++bb) {
+            const float *L = le + ((int64_t)leaf * a.B + bb) * a.ldk;
+            __syncwarp();
+            // duplicated pairs, the factor 2 of the m > 0 terms folded in
+            for (int e = lane; e < P2; e += 32) {
+                float vx, vy, vz;
+                grad_coeff<float>(L, e, vx, vy, vz);
+                int n = 0;
+                while ((n + 1) * (n + 1) <= e) ++n;
+                const float f2 = e == n * n ? 1.f : 2.f;
+                Dx2[e] = make_float2(f2 * vx, f2 * vx);
+                Dy2[e] = make_float2(f2 * vy, f2 * vy);
+                Dz2[e] = make_float2(f2 * vz, f2 * vz);
+            }
+            __syncwarp();
+            uint64_t G0[3], G1[3] = {0, 0, 0};
+            if (cnt > kFarTargets / 2)
+                l2p_sum2x2(a.p, Dx2, Dy2, Dz2, pk2(tx[0], tx[1]), pk2(ty[0], ty[1]), pk2(tz[0], tz[1]),
+                           pk2(tx[2], tx[3]), pk2(ty[2], ty[3]), pk2(tz[2], tz[3]), G0, G1);
+            else   // at most 64 observers: one pair per lane
+                l2p_sum2(a.p, Dx2, Dy2, Dz2, pk2(tx[0], tx[1]), pk2(ty[0], ty[1]), pk2(tz[0], tz[1]), G0[0], G0[1],
+                         G0[2]);
+            float fx[4], fy[4], fz[4];
+            up2(G0[0], fx[0], fx[1]);
+            up2(G0[1], fy[0], fy[1]);
+            up2(G0[2], fz[0], fz[1]);
+            up2(G1[0], fx[2], fx[3]);
+            up2(G1[1], fy[2], fy[3]);
+            up2(G1[2], fz[2], fz[3]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (tid[u] < 0) continue;
+                // near (hi + lo) + far as a compensated FP32 pair, then the pair's
+                // sum and the scale in FP64 (integer conversions)
+                const float *q = ns + ((int64_t)bb * a.M + tid[u]) * 6;
+                float sx = q[0], ex = q[1], sy = q[2], ey = q[3], sz = q[4], ez = q[5];
+                two_sum(sx, ex, far_sf * fx[u]);
+                two_sum(sy, ey, far_sf * fy[u]);
+                two_sum(sz, ez, far_sf * fz[u]);
+                const double gx = (f32_to_f64(sx) + f32_to_f64(ex)) * a.scale;
+                const double gy = (f32_to_f64(sy) + f32_to_f64(ey)) * a.scale;
+                const double gzv = (f32_to_f64(sz) + f32_to_f64(ez)) * a.scale;
+                const int64_t j = a.perm[tid[u]];
+                if (a.g) {
+                    double *o = a.g + ((int64_t)bb * a.M + j) * 3;
+                    o[0] = gx;
+                    o[1] = gy;
+                    o[2] = gzv;
+                }
+                if (a.gz) a.gz[(int64_t)bb * a.M + j] = gzv;
+            }
+        }
+    }
+    // the last warp out leaves the queue at zero for the next launch
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 1, 1ull) == (unsigned long long)gridDim.x * kFarWarps - 1) {
             a.queue[0] = 0;
             a.queue[1] = 0;
         }
@@ -1540,7 +1661,13 @@ gf_status eval_launch(gf_plan_s *plan, EvalArgs a, int n1, int mode, cudaStream_
     const size_t shm = kSrcTable * (sizeof(Vec4<T>) + sizeof(int)) +
                        sizeof(T) * kEvalWarps * eval_slice(F->p * F->p, (int)sizeof(T));
     const unsigned grid = (unsigned)std::min<int64_t>((F->n_items + kEvalWarps - 1) / kEvalWarps, 152 * 64);
-    if (sizeof(T) == 4 && n1 == 4) {
+    if (sizeof(T) == 4 && mode == 2) {
+        const size_t fshm = sizeof(float) * kFarWarps * far_slice(F->p * F->p);
+        GF_TRY((ensure_smem(eval_far_kernel, fshm)));
+        const unsigned fg = (unsigned)std::min<int64_t>((F->n_items + kFarWarps - 1) / kFarWarps, 152 * 64);
+        const unsigned rg = std::min<unsigned>(fg, resident_blocks(eval_far_kernel, kFarWarps * 32, fshm));
+        eval_far_kernel<<<rg, kFarWarps * 32, fshm, st>>>(a, F->leaf_beg);
+    } else if (sizeof(T) == 4 && n1 == 4) {
         GF_TRY((ensure_smem(eval_kernel<float, 4>, shm)));
         const unsigned rg = std::min<unsigned>(grid, resident_blocks(eval_kernel<float, 4>, kEvalWarps * 32, shm));
         eval_kernel<float, 4><<<rg, kEvalWarps * 32, shm, st>>>(a);

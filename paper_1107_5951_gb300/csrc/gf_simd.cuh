@@ -134,6 +134,81 @@ __device__ __forceinline__ void l2p_sum2(int p, const float2 *Dx, const float2 *
 }
 
 
+// l2p_sum2 for two packed pairs of points at once (four points): the
+// recursion coefficients and every coefficient of D are loaded once for both.
+__device__ __forceinline__ void l2p_sum2x2(int p, const float2 *Dx, const float2 *Dy, const float2 *Dz,
+                                           uint64_t X0, uint64_t Y0, uint64_t Z0, uint64_t X1, uint64_t Y1,
+                                           uint64_t Z1, uint64_t g0[3], uint64_t g1[3]) {
+    const uint64_t q0 = fma2(Z0, Z0, fma2(Y0, Y0, mul2(X0, X0)));
+    const uint64_t q1 = fma2(Z1, Z1, fma2(Y1, Y1, mul2(X1, X1)));
+    uint64_t sr0 = pk2(1.f, 1.f), si0 = 0, sr1 = sr0, si1 = 0;
+    uint64_t ax0 = 0, ay0 = 0, az0 = 0, ax1 = 0, ay1 = 0, az1 = 0;
+    auto ld = [](const float2 *d, int k) { return *reinterpret_cast<const uint64_t *>(d + k); };
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) {
+            const float f = c_rf[m];
+            const uint64_t F = pk2(f, f), FN = pk2(-f, -f);
+            uint64_t nr = fma2(mul2(X0, F), sr0, mul2(mul2(Y0, FN), si0));
+            uint64_t ni = fma2(mul2(X0, F), si0, mul2(mul2(Y0, F), sr0));
+            sr0 = nr;
+            si0 = ni;
+            nr = fma2(mul2(X1, F), sr1, mul2(mul2(Y1, FN), si1));
+            ni = fma2(mul2(X1, F), si1, mul2(mul2(Y1, F), sr1));
+            sr1 = nr;
+            si1 = ni;
+        }
+        uint64_t r10 = sr0, i10 = si0, r00 = 0, i00 = 0;
+        uint64_t r11 = sr1, i11 = si1, r01 = 0, i01 = 0;
+        for (int n = m; n < p; ++n) {
+            uint64_t cr0 = sr0, ci0 = si0, cr1 = sr1, ci1 = si1;
+            if (n > m) {
+                const int t = n * (n + 1) / 2 + m;
+                const float av = c_ra[t], bv = c_rb[t];
+                const uint64_t A = pk2(av, av), BN = pk2(-bv, -bv);
+                const uint64_t AZ0 = mul2(Z0, A), BQ0 = mul2(q0, BN), AZ1 = mul2(Z1, A), BQ1 = mul2(q1, BN);
+                cr0 = fma2(AZ0, r10, mul2(BQ0, r00));
+                ci0 = fma2(AZ0, i10, mul2(BQ0, i00));
+                cr1 = fma2(AZ1, r11, mul2(BQ1, r01));
+                ci1 = fma2(AZ1, i11, mul2(BQ1, i01));
+                r00 = r10;
+                i00 = i10;
+                r10 = cr0;
+                i10 = ci0;
+                r01 = r11;
+                i01 = i11;
+                r11 = cr1;
+                i11 = ci1;
+            }
+            if (m == 0) {
+                const int k = n * n;
+                const uint64_t dx = ld(Dx, k), dy = ld(Dy, k), dz = ld(Dz, k);
+                ax0 = fma2(dx, cr0, ax0);
+                ay0 = fma2(dy, cr0, ay0);
+                az0 = fma2(dz, cr0, az0);
+                ax1 = fma2(dx, cr1, ax1);
+                ay1 = fma2(dy, cr1, ay1);
+                az1 = fma2(dz, cr1, az1);
+            } else {
+                const int k = n * n + 2 * m - 1;
+                const uint64_t dxr = ld(Dx, k), dxi = ld(Dx, k + 1), dyr = ld(Dy, k), dyi = ld(Dy, k + 1),
+                               dzr = ld(Dz, k), dzi = ld(Dz, k + 1);
+                ax0 = fma2(dxr, cr0, fma2(dxi, ci0, ax0));
+                ay0 = fma2(dyr, cr0, fma2(dyi, ci0, ay0));
+                az0 = fma2(dzr, cr0, fma2(dzi, ci0, az0));
+                ax1 = fma2(dxr, cr1, fma2(dxi, ci1, ax1));
+                ay1 = fma2(dyr, cr1, fma2(dyi, ci1, ay1));
+                az1 = fma2(dzr, cr1, fma2(dzi, ci1, az1));
+            }
+        }
+    }
+    g0[0] = ax0;
+    g0[1] = ay0;
+    g0[2] = az0;
+    g1[0] = ax1;
+    g1[1] = ay1;
+    g1[2] = az1;
+}
+
 // The recursion coefficients of l2p_sum2 for the current device.
 inline gf_status upload_l2p_coefs() {
     constexpr int NT = kMaxP * (kMaxP + 1) / 2;
@@ -213,11 +288,14 @@ __device__ __forceinline__ long long f32_to_fix(float f, int k) {
     return (b >> 31) ? -v : v;
 }
 
-// A normal float as a double (subnormals read as zero).
+// A float as a double (subnormals read as zero; infinities and NaNs kept).
 __device__ __forceinline__ double f32_to_f64(float f) {
     const unsigned b = __float_as_uint(f);
     const unsigned e = (b >> 23) & 0xff;
     if (e == 0) return 0.0;
+    if (e == 0xff)   // infinity or NaN
+        return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | 0x7ff0000000000000ull |
+                                                ((unsigned long long)(b & 0x7fffffu) << 29)));
     return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
                                             ((unsigned long long)(e - 127 + 1023) << 52) |
                                             ((unsigned long long)(b & 0x7fffffu) << 29)));

@@ -142,19 +142,20 @@ def test_fmm_mixed_matches_oracle(seed, npts):
     assert rel_l2(g, ref) <= 1e-5
 
 
-def test_mixed_item_sizes_1_to_80_observers_per_leaf():
+def test_mixed_item_sizes_1_to_200_observers_per_leaf():
     """Evaluation work items of every size: the 4^3-voxel blocks of a 32^3
-    grid hold 1 to 80 observers each (items of 1-64 observers, the small
-    ones split over lane groups in the lattice near field).  Mixed p = 12
-    meets the oracle, and a second forward on the same plan repeats the
-    first bit for bit (items are taken from a queue in any order)."""
+    grid hold 1 to 200 observers each (near-field items of 1-64 observers,
+    the small ones split over lane groups in the lattice near field; far-field
+    passes of up to 128 observers of a leaf).  Mixed p = 12 meets the oracle,
+    and a second forward on the same plan repeats the first bit for bit
+    (items are taken from a queue in any order)."""
     rng = np.random.default_rng(71)
     n = 32
     wk = wl.random_small(71, n=(n, n, n), npts=1, n_obs=1, h=(1.0, 1.0, 1.0), origin=(-5.0, 3.0, -20.0))
     pts = []
     for idx in range((n // 4) ** 3):
         bx, by, bz = idx % 8, (idx // 8) % 8, idx // 64
-        c = 1 + (idx * 37) % 80
+        c = 1 + (idx * 37) % 200
         lo = np.array(wk.grid.origin) + 4.0 * np.array([bx, by, bz])
         pts.append(rng.uniform(lo + 0.01, lo + 3.99, size=(c, 3)))
     wk.obs = np.concatenate(pts)
@@ -166,7 +167,7 @@ def test_mixed_item_sizes_1_to_80_observers_per_leaf():
         torch.cuda.synchronize()
         plan.check()
         g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
-    print("item sizes 1-80: rel L2 %.3e" % rel_l2(g1, ref))
+    print("item sizes 1-200: rel L2 %.3e" % rel_l2(g1, ref))
     assert rel_l2(g1, ref) <= 1e-5
     assert np.array_equal(g1, g2)
 
