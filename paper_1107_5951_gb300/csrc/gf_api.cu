@@ -48,18 +48,27 @@ gf_status DeviceArena::alloc(void **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 16;
     n = (n + 255) & ~size_t(255);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    keep_pool_memory(dev);
-    cudaError_t e = cudaMallocAsync(p, n, stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        set_error("device allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? GF_ERR_OOM : GF_ERR_CUDA;
+    if (n > left) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        keep_pool_memory(dev);
+        const size_t c = std::max(n, next);
+        void *chunk = nullptr;
+        cudaError_t e = cudaMallocAsync(&chunk, c, stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation of %zu bytes failed: %s", c, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? GF_ERR_OOM : GF_ERR_CUDA;
+        }
+        blocks.push_back(chunk);
+        bytes += c;
+        cur = static_cast<unsigned char *>(chunk);
+        left = c;
+        if (c == next) next = std::min(next * 2, size_t(64) << 20);
     }
-    blocks.push_back(*p);
-    bytes += n;
+    *p = cur;
+    cur += n;
+    left -= n;
     return GF_OK;
 }
 
@@ -70,6 +79,9 @@ void DeviceArena::release() {
     for (void *p : blocks) cudaFreeAsync(p, 0);
     blocks.clear();
     bytes = 0;
+    cur = nullptr;
+    left = 0;
+    next = size_t(1) << 20;
 }
 
 // Second streams of FMM plans (with their fork and join events), kept per

@@ -55,9 +55,16 @@ struct QuadRule {
 // Allocations are stream-ordered (cudaMallocAsync from the device's default
 // pool, which keeps freed memory for reuse), so building and releasing a
 // plan inside a timed loop costs no driver round trips after the first time.
+// A plan's device memory: chunks from the stream-ordered allocator, handed
+// out by bumping a pointer (256-byte alignment), all returned together when
+// the plan is freed.  Chunks grow from 1 MiB by doubling up to 64 MiB; a
+// larger request gets a chunk of its own size.
 struct DeviceArena {
-    std::vector<void *> blocks;
-    size_t bytes = 0;
+    std::vector<void *> blocks;   // chunks
+    size_t bytes = 0;             // bytes held in chunks
+    unsigned char *cur = nullptr; // free tail of the newest chunk
+    size_t left = 0;
+    size_t next = size_t(1) << 20;
     cudaStream_t stream = nullptr;
     gf_status alloc(void **p, size_t n);
     template <class T>
