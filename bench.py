@@ -55,17 +55,18 @@ MUFU_RSQRT_PROBE = 4.63e12
 # kernel and the bench reports null.  The 464^3 figures are captures of
 # the same recipe at 320^3 (the full size holds too much device memory for a
 # multi-pass capture) scaled by the work units of a launch: near pairs for
-# the evaluation (the traffic grows in proportion: a full-size list of the
-# same kernel read 29.4 MB), interaction-list box pairs for the M2L.
+# the evaluation (its near-field and far-field kernels together),
+# interaction-list box pairs for the M2L.
 NCU_TRAFFIC = {
-    ("eval", "layered_scale_464^3", 11): (round((13981952 + 12800) * 596922624 / 280629504),
+    # evaluation: near-field and far-field kernels of one forward, scaled by the pairs
+    ("eval", "layered_scale_464^3", 11): (round((7901952 + 0 + 24222464 + 1536000) * 596922624 / 280629504),
                                           ("paper_1107_5951_gb300/csrc/gf_fmm.cu",
                                            "paper_1107_5951_gb300/csrc/gf_simd.cuh",
                                            "paper_1107_5951_gb300/csrc/fmm_math.cuh"),
-                                          "aff8ef7477ae3a987f60766cc5e3f212ece3fd42"),
-    ("m2l", "layered_scale_464^3", 11): (round((25346560 + 2304) * 1125279 / 510295),
+                                          "b037f64f5be2cfcd52839dde1bf559ce8b3bca27"),
+    ("m2l", "layered_scale_464^3", 11): (round((25337600 + 5376000) * 1125279 / 510295),
                                          ("paper_1107_5951_gb300/csrc/gf_m2l.cu",),
-                                         "d64e86d5903172fce1255cae17c8f43b6cd50cfd"),
+                                         "cbd14c2e46c70f3d822171ef09ee48146f2a2817"),
 }
 
 
@@ -310,7 +311,8 @@ def fmm_roofline(stages, info, args, peaks, workload, nvox=None, rho_bytes=4, n_
     tensor = (args.precision == "mixed" or args.m2l == "tensor") and p <= 15 and args.m2l != "simt"
     fbytes = 4 if args.precision == "mixed" else 8
     L = int(getattr(info, "L", 0))
-    work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs), "eval_kernel (near field + L2P + combine)"),
+    work = {"eval": ("alu", FLOPS_PER_PAIR * float(info.near_pairs),
+                     "eval_kernel (near field) + eval_far_kernel (L2P, near + far, scatter)"),
             "m2l": ("tensor" if tensor else "alu", 2.0 * K * K * float(info.m2l_pairs),
                     "m2l_tc (tcgen05 FP16 parts, 3 products, all levels)" if tensor
                     else "m2l_simt (all levels)")}
