@@ -823,6 +823,10 @@ m2l_tc(TcArgs a) {
     Ctx pc = ctx_of(0);
     int64_t tbox = -1, tc0 = 0, tc1 = 0, tc2 = 0;
     int64_t qbn0 = 0, qbn1 = 0, qbn2 = 0;   // the level's source block extent, kept in registers
+    // M2M kind: the row of this parent's first child (position 0), the row
+    // steps of a child move along x, y and z, and which of the 8 children exist
+    int64_t qbase = 0, qsx = 0, qsy = 0, qsz = 0;
+    uint32_t qmask = 0;
     int qadj = 0;
     auto set_target = [&]() {
         tbox = -1;
@@ -841,6 +845,39 @@ m2l_tc(TcArgs a) {
             tc0 = sidx % L.bn[0];
             tc1 = (sidx / L.bn[0]) % L.bn[1];
             tc2 = sidx / (L.bn[0] * L.bn[1]);
+            const int64_t c0 = 2 * (tc0 + L.blo[0]) - L.clo[0], c1 = 2 * (tc1 + L.blo[1]) - L.clo[1],
+                          c2 = 2 * (tc2 + L.blo[2]) - L.clo[2];
+            uint32_t v0 = 0, v1 = 0, v2 = 0;   // bit d: the child at step d along the axis exists
+            for (int d = 0; d < 2; ++d) {
+                bool ok0 = c0 + d >= 0 && c0 + d < L.cn[0], ok1 = c1 + d >= 0 && c1 + d < L.cn[1],
+                     ok2 = c2 + d >= 0 && c2 + d < L.cn[2];
+                if (a.grid) {   // and its first voxel lies in the density grid
+                    const int64_t i = (L.clo[0] + c0 + d) * L.gb - L.goff[0], j = (L.clo[1] + c1 + d) * L.gb - L.goff[1],
+                                  k = (L.clo[2] + c2 + d) * L.gb - L.goff[2];
+                    ok0 = ok0 && i >= 0 && i < L.gn[0];
+                    ok1 = ok1 && j >= 0 && j < L.gn[1];
+                    ok2 = ok2 && k >= 0 && k < L.gn[2];
+                }
+                v0 |= (uint32_t)ok0 << d;
+                v1 |= (uint32_t)ok1 << d;
+                v2 |= (uint32_t)ok2 << d;
+            }
+            qmask = 0;
+            for (int oi = 0; oi < 8; ++oi)
+                if (((v0 >> (oi & 1)) & (v1 >> ((oi >> 1) & 1)) & (v2 >> (oi >> 2))) & 1u) qmask |= 1u << oi;
+            if (a.grid) {   // the child leaf's first voxel in the density grid
+                const int64_t i0 = (L.clo[0] + c0) * L.gb - L.goff[0], j0 = (L.clo[1] + c1) * L.gb - L.goff[1],
+                              k0 = (L.clo[2] + c2) * L.gb - L.goff[2];
+                qbase = bb * L.gnvox + (k0 * L.gn[1] + j0) * L.gn[0] + i0;
+                qsx = L.gb;
+                qsy = (int64_t)L.gb * L.gn[0];
+                qsz = qsy * L.gn[1];
+            } else {
+                qsx = (int64_t)B * a.ldin;
+                qsy = L.cn[0] * qsx;
+                qsz = L.cn[1] * qsy;
+                qbase = ((c2 * L.cn[1] + c1) * L.cn[0] + c0) * qsx + (int64_t)bb * a.ldin;
+            }
         } else if (a.kind == kTcL2L) {
             tbox = L.order[pc.cbeg + sidx];
         } else if (!L.adj) {
@@ -859,21 +896,8 @@ m2l_tc(TcArgs a) {
     auto src_row = [&](int oi) -> int64_t {
         if (tbox < 0) return -1;
         const TcLevel &L = *pc.L;
-        if (a.kind == kTcM2M) {   // child at position oi of this parent
-            const int64_t cx = 2 * (tc0 + L.blo[0]) + (oi & 1) - L.clo[0],
-                          cy = 2 * (tc1 + L.blo[1]) + ((oi >> 1) & 1) - L.clo[1],
-                          cz = 2 * (tc2 + L.blo[2]) + ((oi >> 2) & 1) - L.clo[2];
-            if (cx >= 0 && cy >= 0 && cz >= 0 && cx < L.cn[0] && cy < L.cn[1] && cz < L.cn[2]) {
-                if (a.grid) {   // the child leaf's first voxel in the density grid
-                    const int64_t i0 = (L.clo[0] + cx) * L.gb - L.goff[0], j0 = (L.clo[1] + cy) * L.gb - L.goff[1],
-                                  k0 = (L.clo[2] + cz) * L.gb - L.goff[2];
-                    if (i0 < 0 || j0 < 0 || k0 < 0 || i0 >= L.gn[0] || j0 >= L.gn[1] || k0 >= L.gn[2]) return -1;
-                    return bb * L.gnvox + (k0 * L.gn[1] + j0) * L.gn[0] + i0;
-                }
-                return (((cz * L.cn[1] + cy) * L.cn[0] + cx) * B + bb) * a.ldin;
-            }
-            return -1;
-        }
+        if (a.kind == kTcM2M)   // child at position oi of this parent
+            return ((qmask >> oi) & 1u) ? qbase + (oi & 1) * qsx + ((oi >> 1) & 1) * qsy + (oi >> 2) * qsz : -1;
         if (a.kind == kTcL2L) return ((int64_t)L.tparent[tbox] * B + bb) * a.ldin;
         if (a.kind == kTcP2M) return (tbox * B + bb) * a.ldin;
         const int cls = pc.cls;
