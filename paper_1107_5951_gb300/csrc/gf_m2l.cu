@@ -1073,22 +1073,32 @@ m2l_tc(TcArgs a) {
                         for (int v = 0; v < kV; ++v) cur[v] = rr[v ^ (row & (kV - 1))];
                     }
                     unsigned char *sub = stage + (size_t)(nc - 1 - q) * kTcA;
+                    // inputs past kin (the last chunk) read as zero; densities read
+                    // from the grid are checked for non-finite values
+                    auto split = [&](auto tail, auto check) {
+                        constexpr bool kTail = decltype(tail)::value, kCheck = decltype(check)::value;
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const float x4[4] = {cur[v].x, cur[v].y, cur[v].z, cur[v].w};
-                        uint32_t h[4], l[4];
+                        for (int v = 0; v < 4; ++v) {
+                            const float x4[4] = {cur[v].x, cur[v].y, cur[v].z, cur[v].w};
+                            uint32_t h[4], l[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int kin = 16 * cin + 4 * v + j;
-                            const float x = kin < a.kin ? x4[j] : 0.f;
-                            bad |= !isfinite(x);
-                            h[j] = to_tf32_int(x);
-                            l[j] = to_tf32_int(x - __uint_as_float(h[j]));
+                            for (int j = 0; j < 4; ++j) {
+                                const float x = (!kTail || 16 * cin + 4 * v + j < a.kin) ? x4[j] : 0.f;
+                                if (kCheck) bad |= !isfinite(x);
+                                h[j] = to_tf32_int(x);
+                                l[j] = to_tf32_int(x - __uint_as_float(h[j]));
+                            }
+                            const uint32_t o = swz64(row, 4 * v);
+                            *reinterpret_cast<uint4 *>(sub + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                            *reinterpret_cast<uint4 *>(sub + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
                         }
-                        const uint32_t o = swz64(row, 4 * v);
-                        *reinterpret_cast<uint4 *>(sub + o) = make_uint4(h[0], h[1], h[2], h[3]);
-                        *reinterpret_cast<uint4 *>(sub + 8192 + o) = make_uint4(l[0], l[1], l[2], l[3]);
-                    }
+                    };
+                    if (16 * (cin + 1) > a.kin)
+                        split(std::true_type{}, std::true_type{});
+                    else if (a.grid)
+                        split(std::false_type{}, std::true_type{});
+                    else
+                        split(std::false_type{}, std::false_type{});
                 }
                 if (stop) break;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
