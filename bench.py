@@ -236,7 +236,7 @@ def job_rate(units_per_rank, world, seconds):
 # Expansion degree per workload: the headline runs the mixed-precision FMM at
 # a degree whose sampled error stays below the metric's 1e-6 with margin, and
 # the plain FP64 FMM beside it at the smallest degree that meets 1e-6.
-DEFAULT_P = {"scale": 11, "volume": 12, "sum_an": 12, "topo_hex": 12, "points": 12}
+DEFAULT_P = {"scale": 10, "volume": 12, "sum_an": 12, "topo_hex": 12, "points": 12}
 FP64_P = {"scale": 10, "volume": 14}
 SWEEP_P = (4, 6, 8)
 REL_ERR_BAR = 1e-6

@@ -98,6 +98,9 @@ struct FmmPlan {
     // [0, kMaxLevels]: forward, [kMaxLevels + 1, 2 kMaxLevels + 1]: adjoint),
     // reduced on the device before each tensor-core M2L
     uint32_t *tc_amax = nullptr;
+    float *m2l_part = nullptr;    // forward M2L with two CTAs per tile: [tiles][2][128][Npad] partial rows
+    int *m2l_cnt = nullptr;       // [tiles][8] arrivals
+    int m2l_part_tiles = 0;       // tiles m2l_part holds (0: no sharing)
     // the M2L inputs of levels 2..L split into scaled FP16 high and low
     // parts: for every input row and 32-wide chunk, 64 bytes of high parts
     // then 64 bytes of low parts (the same byte offsets as the FP32 rows)

@@ -219,6 +219,18 @@ inline gf_status ensure_smem(Kern kernel, size_t bytes) {
     return GF_OK;
 }
 
+// Streaming multiprocessors of the current device (cached per device).
+inline int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int n = 0;
+        cache[dev] = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+    }
+    return cache[dev];
+}
+
 // Blocks of `kernel` that are resident on the current device at once, for
 // grids whose warps take their work from a queue (at least 1).
 template <class Kern>

@@ -596,6 +596,14 @@ struct TcArgs {
     int *status;
     long wait_tries;            // bound of every barrier wait (kWaitTries)
     uint32_t part_lo, part_hi;  // M2L forward: source partition (in_source_part)
+    // M2L forward with msplit = 2: each tile's active offsets are shared by two
+    // CTAs (blockIdx 2 t and 2 t + 1); each writes its partial rows to mpart
+    // (slot = blockIdx, [128][Npad]) and counts itself in mcnt ([tile][8]
+    // promoter warps, zero at launch); the second to arrive adds the other's
+    // rows to its own and writes the tile.
+    int msplit;
+    float *mpart;
+    int *mcnt;
     int test_stall;             // testing aid: the MMA issuer first waits on a barrier that
                                 // nothing completes, so the bounded-wait failure path runs
     // M2M kind over leaf masses taken straight from the FP32 density grid:
@@ -776,6 +784,8 @@ m2l_tc(TcArgs a) {
     // b, b + gridDim.x, ... and runs every offset of each.
     const bool persist = a.kind != kTcM2L;
     const int ntl = persist ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 1;
+    const int msplit = persist ? 1 : max(1, a.msplit);
+    const int utile = (int)blockIdx.x / msplit, uhalf = (int)blockIdx.x - utile * msplit;   // M2L: tile, share
     struct Ctx {
         const TcLevel *L;
         int cls, tile;
@@ -783,7 +793,7 @@ m2l_tc(TcArgs a) {
     };
     // (level, class, tile within the class) of this CTA's j-th tile
     auto ctx_of = [&](int j) -> Ctx {
-        const int t = (int)blockIdx.x + (persist ? j * (int)gridDim.x : 0);
+        const int t = persist ? (int)blockIdx.x + j * (int)gridDim.x : utile;
         int e = 0;
         while (e + 1 < a.nent && a.tile_begin[e + 1] <= t) ++e;
         Ctx c;
@@ -928,6 +938,27 @@ m2l_tc(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    if (msplit > 1) {
+        // keep this CTA's share of the tile's active offsets: ranks
+        // [uhalf tot / msplit, (uhalf + 1) tot / msplit) in offset order
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < 6; ++w) tot += __popc(omask[w]);
+            const int lo = uhalf * tot / msplit, hi = (uhalf + 1) * tot / msplit;
+            int rank = 0;
+            for (int w = 0; w < 6; ++w) {
+                uint32_t m = omask[w], keep = 0;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    if (rank >= lo && rank < hi) keep |= 1u << b;
+                    ++rank;
+                }
+                omask[w] = keep;
+            }
+        }
+        __syncthreads();
+    }
     const uint32_t tmem = tslot;
     int G = noff;   // offsets per tile
     if (!persist) {
@@ -1277,7 +1308,54 @@ m2l_tc(TcArgs a) {
             const int r = pq * 32 + lane;
             const int oslot = r / B, obb = r - oslot * B;
             const int64_t os = (int64_t)oc.tile * nbox + oslot;
-            if (oslot < nbox && os < oc.ccnt) {
+            bool write = true;
+            if (H16) {
+                // undo the column scales of the image and the input scale
+                float sig, sig_inv;
+                input_scale(*L.amax, sig, sig_inv);
+                const float4 *ci = reinterpret_cast<const float4 *>(a.cs + Npad + ph_half * nsum);
+#pragma unroll
+                for (int q = 0; q < NS; q += 4)
+                    if (q < nsum) {
+                        const float4 c4 = __ldg(ci + q / 4);
+                        acc[q] = acc[q] * c4.x * sig_inv;
+                        acc[q + 1] = acc[q + 1] * c4.y * sig_inv;
+                        acc[q + 2] = acc[q + 2] * c4.z * sig_inv;
+                        acc[q + 3] = acc[q + 3] * c4.w * sig_inv;
+                    }
+                if (msplit > 1) {
+                    // this warp's slice of the tile (32 rows, half the columns):
+                    // partial rows out, then the second CTA to arrive adds the
+                    // other's rows (a + b = b + a, so the sum does not depend on
+                    // which CTA is second) and writes the tile
+                    float4 *mine = reinterpret_cast<float4 *>(a.mpart + ((size_t)blockIdx.x * 128 + r) * Npad +
+                                                              ph_half * nsum);
+#pragma unroll
+                    for (int q = 0; q < NS; q += 4)
+                        if (q < nsum) mine[q / 4] = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+                    __threadfence();
+                    __syncwarp();
+                    int second = 0;
+                    if (lane == 0) second = atomicAdd(a.mcnt + (size_t)utile * 8 + pw, 1) == msplit - 1;
+                    second = __shfl_sync(0xffffffffu, second, 0);
+                    write = second != 0;
+                    if (write) {
+                        __threadfence();
+                        const float4 *other = reinterpret_cast<const float4 *>(
+                            a.mpart + ((size_t)(utile * msplit + (1 - uhalf)) * 128 + r) * Npad + ph_half * nsum);
+#pragma unroll
+                        for (int q = 0; q < NS; q += 4)
+                            if (q < nsum) {
+                                const float4 o4 = __ldcg(other + q / 4);
+                                acc[q] += o4.x;
+                                acc[q + 1] += o4.y;
+                                acc[q + 2] += o4.z;
+                                acc[q + 3] += o4.w;
+                            }
+                    }
+                }
+            }
+            if (write && oslot < nbox && os < oc.ccnt) {
                 int64_t obox;
                 if (a.kind == kTcM2M) {   // dense targets
                     obox = os;
@@ -1305,31 +1383,22 @@ m2l_tc(TcArgs a) {
                             v.w += acc[q + 3];
                             dst[q / 4] = v;
                         }
-                } else if (H16) {
-                    // undo the column scales of the image and the input scale
-                    float sig, sig_inv;
-                    input_scale(*L.amax, sig, sig_inv);
-                    const float4 *ci = reinterpret_cast<const float4 *>(a.cs + Npad + ph_half * nsum);
+                } else if (H16) {   // rows already unscaled (above)
                     if (a.le_f64) {
                         // an FP64 plan's local expansions: rows of ldk >= Npad doubles
                         double *dd = reinterpret_cast<double *>(L.le) + (obox * B + obb) * a.ldk + ph_half * nsum;
 #pragma unroll
                         for (int q = 0; q < NS; q += 4)
                             if (q < nsum) {
-                                const float4 c4 = __ldg(ci + q / 4);
-                                dd[q] = (double)(acc[q] * c4.x * sig_inv);
-                                dd[q + 1] = (double)(acc[q + 1] * c4.y * sig_inv);
-                                dd[q + 2] = (double)(acc[q + 2] * c4.z * sig_inv);
-                                dd[q + 3] = (double)(acc[q + 3] * c4.w * sig_inv);
+                                dd[q] = (double)acc[q];
+                                dd[q + 1] = (double)acc[q + 1];
+                                dd[q + 2] = (double)acc[q + 2];
+                                dd[q + 3] = (double)acc[q + 3];
                             }
                     } else {
 #pragma unroll
                         for (int q = 0; q < NS; q += 4)
-                            if (q < nsum) {
-                                const float4 c4 = __ldg(ci + q / 4);
-                                dst[q / 4] = make_float4(acc[q] * c4.x * sig_inv, acc[q + 1] * c4.y * sig_inv,
-                                                         acc[q + 2] * c4.z * sig_inv, acc[q + 3] * c4.w * sig_inv);
-                            }
+                            if (q < nsum) dst[q / 4] = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
                     }
                 } else {
 #pragma unroll
@@ -1397,6 +1466,22 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
     if (!(F->mixed || F->m2l_tc64) || !F->tab->m2l_tc) return GF_OK;
     GF_TRY(plan->arena.alloc((void **)&F->tc_amax, 2 * (kMaxLevels + 1) * sizeof(uint32_t)));
     GF_TRY(plan->arena.alloc((void **)&F->tc_split, std::max<size_t>(16, split_offset(F, 0, F->L + 1))));
+    {
+        // partial rows of the forward M2L's tiles when two CTAs share each
+        // (tiles counted for the plan's largest batch: the most tiles)
+        const int nbox = 128 / std::max(1, std::min(F->B, 128));
+        int64_t tiles = 0;
+        for (int l = 2; l <= F->L; ++l)
+            for (int c = 0; c < 8; ++c) {
+                const int64_t cnt = F->lev[l].nt > 0 ? F->lev[l].cls_off[c + 1] - F->lev[l].cls_off[c] : 0;
+                tiles += (cnt + nbox - 1) / nbox;
+            }
+        if (tiles > 0 && 2 * tiles <= (int64_t)sm_count()) {
+            GF_TRY(plan->arena.alloc((void **)&F->m2l_part, (size_t)tiles * 2 * 128 * F->tab->tc_npad * sizeof(float)));
+            GF_TRY(plan->arena.alloc((void **)&F->m2l_cnt, (size_t)tiles * 8 * sizeof(int)));
+            F->m2l_part_tiles = (int)tiles;
+        }
+    }
     for (int adj = 0; adj < 1; ++adj) {
         std::vector<TcLevel> h(F->L + 1);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
@@ -1616,7 +1701,7 @@ gf_status tc_launch(TcArgs &a, int tiles, cudaStream_t st) {
     if (tiles == 0) return GF_OK;
     a.ntiles = tiles;
     // the M2L runs one tile per CTA; the other kinds loop over tiles, one CTA per SM
-    const int grid = a.kind == kTcM2L ? tiles : std::min(tiles, 152);
+    const int grid = a.kind == kTcM2L ? tiles * std::max(1, a.msplit) : std::min(tiles, 152);
     const bool h16 = a.kind == kTcM2L;
     const size_t shm = tc_smem_bytes(a.Npad, h16);
     a.nst = tc_stages(a.Npad, h16);
@@ -1661,6 +1746,7 @@ TcArgs tc_args(gf_plan_s *plan, int B) {
     a.wait_tries = kWaitTries;
     a.part_lo = 0;
     a.part_hi = 64;
+    a.msplit = 1;
     return a;
 }
 
@@ -1722,7 +1808,6 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st, cudaEven
         GF_KERNEL_DONE();
     }
     if (!adj) stage_mark(plan, 4, st);
-    if (fork) GF_CUDA(cudaEventRecord(fork, st));
     const int nbox = 128 / B;
     int tiles = 0, e = 0;
     for (int l = 2; l <= F->L; ++l)
@@ -1734,6 +1819,16 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st, cudaEven
         }
     a.tile_begin[e] = tiles;
     a.nent = e;
+    // when two CTAs per tile still fit the SMs at once, every tile's offsets
+    // are shared by two: each chain of offsets is half as long (and each
+    // FP32 sum of offsets half as deep)
+    if (!adj && F->m2l_part && tiles <= F->m2l_part_tiles && 2 * tiles <= sm_count()) {
+        a.msplit = 2;
+        a.mpart = F->m2l_part;
+        a.mcnt = F->m2l_cnt;
+        GF_CUDA(cudaMemsetAsync(F->m2l_cnt, 0, (size_t)tiles * 8 * sizeof(int), st));
+    }
+    if (fork) GF_CUDA(cudaEventRecord(fork, st));
     return tc_launch(a, tiles, st);
 }
 

@@ -3,8 +3,8 @@ direct-sum oracle (discretised Eq. 1) on seeded observer samples.
 
 * 464^3 layered model (99,897,344 voxels of 100 m, FP32 densities, 1024^2
   stations on the top face): the mixed-precision FMM at the benchmark's
-  degree p = 11 within the metric's 1e-6, at p = 8 within the mixed bar 1e-5,
-  and the plain FP64 FMM at p = 10 within 1e-6.
+  degree p = 10 and at p = 11 within the metric's 1e-6, at p = 8 within the
+  mixed bar 1e-5, and the plain FP64 FMM at p = 10 within 1e-6.
 * 128^3 random-field volume workload (2,097,152 sources, 2,359,296
   observers): the plain FP64 FMM at p = 14 within 1e-6.
 
@@ -54,7 +54,8 @@ def scale_run(scale, precision, p):
         return g[idx]
 
 
-@pytest.mark.parametrize("precision,p,tol", [("mixed", 11, 1e-6), ("mixed", 8, 1e-5), ("fp64", 10, 1e-6)])
+@pytest.mark.parametrize("precision,p,tol", [("mixed", 10, 1e-6), ("mixed", 11, 1e-6), ("mixed", 8, 1e-5),
+                                              ("fp64", 10, 1e-6)])
 def test_layered_scale_464_full_size(scale, precision, p, tol):
     g = scale_run(scale, precision, p)
     err = rel_l2(g, scale[2])
