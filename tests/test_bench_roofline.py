@@ -15,19 +15,19 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-INFO = SimpleNamespace(K=144, near_pairs=596922624, m2l_pairs=1125279)
+INFO = SimpleNamespace(K=121, near_pairs=596922624, m2l_pairs=1125279)
 PEAKS = {"bf16_tflops": 1870.7, "sm_max_mhz": 2070.0}
 WORKLOAD = "layered_scale_464^3"
 
 
-def args(precision="mixed", p=11, m2l="auto"):
+def args(precision="mixed", p=10, m2l="auto"):
     return argparse.Namespace(precision=precision, p=p, m2l=m2l)
 
 
 def captured(stage):
     """The table's traffic while the kernel's source still has the captured
     SHA-1, else None."""
-    nbytes, srcs, sha = bench.NCU_TRAFFIC[(stage, WORKLOAD, 11)]
+    nbytes, srcs, sha = bench.NCU_TRAFFIC[(stage, WORKLOAD, 10)]
     return nbytes if bench.sources_sha1(srcs) == sha else None
 
 
@@ -44,7 +44,7 @@ def test_tensor_core_m2l_dominant():
     r = bench.fmm_roofline({"eval": 1.0, "m2l": 1.25}, INFO, args(), PEAKS, WORKLOAD)
     assert r["stage"] == "m2l" and r["bound"] == "tensor"
     assert r["peak"] == pytest.approx(1870.7 * bench.F16_PER_BF16)
-    assert r["achieved"] == pytest.approx(2.0 * 144 * 144 * INFO.m2l_pairs / 1.25e-3 / 1e12)
+    assert r["achieved"] == pytest.approx(2.0 * INFO.K * INFO.K * INFO.m2l_pairs / 1.25e-3 / 1e12)
     assert r["traffic"] == captured("m2l")
 
 
@@ -55,7 +55,7 @@ def test_traffic_only_for_the_captured_configuration():
 
 
 def test_traffic_dropped_when_the_source_changes(monkeypatch):
-    key = ("eval", WORKLOAD, 11)
+    key = ("eval", WORKLOAD, 10)
     nbytes, src, _ = bench.NCU_TRAFFIC[key]
     monkeypatch.setitem(bench.NCU_TRAFFIC, key, (nbytes, src, "0" * 40))
     assert bench.fmm_roofline({"eval": 1.3, "m2l": 1.0}, INFO, args(), PEAKS, WORKLOAD)["traffic"] is None
