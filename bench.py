@@ -1104,6 +1104,13 @@ def bench_serving(args, rank, world):
     lat_h, open_h = open_loop(0.8 * sat_rate)
     light = min(100.0, 0.25 * sat_rate)
     lat_l, open_l = open_loop(light)
+    # the same stream one request at a time (submit, wait): the sum of these
+    # solo times against a saturated pass shows how much the slots overlap
+    solo_s = 0.0
+    for i, r in enumerate(reqs):
+        t1 = time.perf_counter()
+        srv.wait(srv.submit(r["grid"].n[0], rho_of(i), gz=gz_pool[i]))
+        solo_s += time.perf_counter() - t1
     st = srv.stats()
     srv.close()
     # accuracy of a few requests on a station sample, against the FP64 oracle
@@ -1146,6 +1153,8 @@ def bench_serving(args, rank, world):
             "latency_light_load": lat_summary(light, lat_l, open_l),
             "cold_pass": {"seconds": cold_s, "plans_created": int(st_cold["plans_created"]),
                           "solves_per_s": len(reqs) / cold_s},
+            "overlap": {"solo_sum_ms": 1e3 * solo_s, "saturated_pass_ms": 1e3 * sum(pass_s) / args.steps,
+                        "concurrency": solo_s / (sum(pass_s) / args.steps)},
             "server": {k: st[k] for k in ("completed", "failed", "plans_created", "plans_evicted",
                                           "graph_launches", "resident_bytes", "mem_budget")},
             "rel_err_vs_oracle_sample": errs, "roofline": None, "cpu_baseline": cpu,
