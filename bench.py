@@ -648,7 +648,9 @@ def bench_gf(args, rank, world):
         roof = fmm_roofline(stages, info, args, peaks, wk.name, nvox=wk.grid.nvox,
                             rho_bytes=4 if args.precision == "mixed" else 8)
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers: the observers
+    # are copied first (the plan build needs them), the densities on a second
+    # stream while the plan is built, and the forward waits for them
     e2e = None
     if not args.no_e2e:
         obs_h = torch.tensor(wk.obs, dtype=torch.float64).pin_memory()
@@ -656,6 +658,7 @@ def bench_gf(args, rank, world):
         g_h = torch.empty((M, 3), dtype=torch.float64).pin_memory()
         obs_e = torch.empty_like(obs_d)
         rho_e = torch.empty_like(rho_d)
+        copy_stream = torch.cuda.Stream(device=dev)
         e_ev = []
         for k in range(args.warmup + args.steps):   # warm-up passes first, as for the device leg
             flush.fill_(float(k))
@@ -664,8 +667,14 @@ def bench_gf(args, rank, world):
             a.record(stream)
             with torch.cuda.stream(stream):
                 obs_e.copy_(obs_h, non_blocking=True)
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
                 rho_e.copy_(rho_h, non_blocking=True)
+                rho_ready = torch.cuda.Event()
+                rho_ready.record(copy_stream)
+            with torch.cuda.stream(stream):
                 pl = make_plan(obs=obs_e)
+                stream.wait_event(rho_ready)
                 pl.forward(rho_e, g=g_d, stream=stream)
                 if parts:
                     sum_over_ranks(g_d, world)

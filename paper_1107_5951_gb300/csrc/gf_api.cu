@@ -374,11 +374,11 @@ gf_status gf_plan_create(const gf_grid *grid, const gf_quad *quad, const double 
     s = p->arena.alloc(reinterpret_cast<void **>(&p->d_status), 64 * sizeof(int) + sizeof(QuadRule));
     if (s == GF_OK) {
         cudaError_t e = cudaMemsetAsync(p->d_status, 0, 64 * sizeof(int), st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(p->d_status + 64, &qr, sizeof(QuadRule), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
-            set_error("plan setup copy failed: %s", cudaGetErrorString(e));
+            set_error("plan setup failed: %s", cudaGetErrorString(e));
             s = GF_ERR_CUDA;
+        } else {
+            s = upload_small(p->d_status + 64, &qr, sizeof(QuadRule), st);
         }
     }
     if (s == GF_OK) {
@@ -473,11 +473,11 @@ gf_status gf_plan_create_points(const double *src_dev, const double *wt_dev, int
     gf_status s = p->arena.alloc(reinterpret_cast<void **>(&p->d_status), 64 * sizeof(int) + sizeof(QuadRule));
     if (s == GF_OK) {
         cudaError_t e = cudaMemsetAsync(p->d_status, 0, 64 * sizeof(int), st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(p->d_status + 64, &qr, sizeof(QuadRule), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
-            set_error("plan setup copy failed: %s", cudaGetErrorString(e));
+            set_error("plan setup failed: %s", cudaGetErrorString(e));
             s = GF_ERR_CUDA;
+        } else {
+            s = upload_small(p->d_status + 64, &qr, sizeof(QuadRule), st);
         }
     }
     if (s == GF_OK) {

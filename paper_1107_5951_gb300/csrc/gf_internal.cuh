@@ -219,6 +219,11 @@ inline gf_status ensure_smem(Kern kernel, size_t bytes) {
     return GF_OK;
 }
 
+// Copies nbytes (whole 4-byte words, dst word-aligned) of host memory to the
+// device on stream st as kernel arguments rather than as a host-to-device
+// copy (gf_prim.cu): the host memory may be reused once the call returns.
+gf_status upload_small(void *dst, const void *src, size_t nbytes, cudaStream_t st);
+
 // Streaming multiprocessors of the current device (cached per device).
 inline int sm_count() {
     static int cache[64] = {0};

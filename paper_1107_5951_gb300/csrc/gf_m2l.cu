@@ -1456,7 +1456,7 @@ gf_status m2l_tc_prepare_adj(gf_plan_s *plan) {
         void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
         hb.assign(reinterpret_cast<unsigned char *>(h.data()), reinterpret_cast<unsigned char *>(h.data() + h.size()));
         GF_TRY(plan->arena.alloc(&dev, hb.size()));
-        GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
+        GF_TRY(upload_small(dev, hb.data(), hb.size(), plan->arena.stream));
     }
     return GF_OK;
 }
@@ -1509,7 +1509,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
         void *&dev = adj ? F->tc_levels_adj : F->tc_levels;
         hb.assign(reinterpret_cast<unsigned char *>(h.data()), reinterpret_cast<unsigned char *>(h.data() + h.size()));
         GF_TRY(plan->arena.alloc(&dev, hb.size()));
-        GF_CUDA(cudaMemcpyAsync(dev, hb.data(), hb.size(), cudaMemcpyHostToDevice, plan->arena.stream));
+        GF_TRY(upload_small(dev, hb.data(), hb.size(), plan->arena.stream));
     }
     // M2M into level l (entries [0, L]), L2L into level l (entries [L+1, 2L+1]),
     // the P2M of every leaf (entry 2L+2), the P2M into level L-1 straight
@@ -1586,8 +1586,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
         F->tc_xlate_host.assign(reinterpret_cast<unsigned char *>(h.data()),
                                 reinterpret_cast<unsigned char *>(h.data() + h.size()));
         GF_TRY(plan->arena.alloc(&F->tc_xlate, F->tc_xlate_host.size()));
-        GF_CUDA(cudaMemcpyAsync(F->tc_xlate, F->tc_xlate_host.data(), F->tc_xlate_host.size(),
-                                cudaMemcpyHostToDevice, plan->arena.stream));
+        GF_TRY(upload_small(F->tc_xlate, F->tc_xlate_host.data(), F->tc_xlate_host.size(), plan->arena.stream));
     }
     return GF_OK;
 }

@@ -1,6 +1,7 @@
 // gf_prim.cu -- exclusive scan, stable LSD radix sort and a bounding-box
 // reduction, written for the octree build.
 #include <float.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -303,6 +304,38 @@ gf_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int3
     if (ka != keys) {
         GF_CUDA(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
         GF_CUDA(cudaMemcpyAsync(vals, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    return GF_OK;
+}
+
+// Small host arrays travel to the device as kernel arguments (pieces of
+// kUploadWords words), not as host-to-device copies: a plan build then
+// never queues behind a large copy the caller has in flight on another
+// stream, and the host memory may be reused as soon as the call returns.
+namespace {
+constexpr int kUploadWords = 960;
+struct UploadPiece {
+    uint32_t w[kUploadWords];
+};
+__global__ void upload_piece(UploadPiece pc, int nw, uint32_t *__restrict__ dst) {
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = pc.w[i];
+}
+}  // namespace
+
+gf_status upload_small(void *dst, const void *src, size_t nbytes, cudaStream_t st) {
+    if (nbytes % 4 != 0 || ((uintptr_t)dst & 3) != 0) {
+        set_error("upload_small: %zu bytes to %p (whole aligned words only)", nbytes, dst);
+        return GF_ERR_INVALID_ARG;
+    }
+    const size_t nw = nbytes / 4;
+    const unsigned char *s8 = static_cast<const unsigned char *>(src);
+    uint32_t *d = static_cast<uint32_t *>(dst);
+    for (size_t w0 = 0; w0 < nw; w0 += kUploadWords) {
+        UploadPiece pc;
+        const int n = (int)std::min<size_t>(kUploadWords, nw - w0);
+        memcpy(pc.w, s8 + 4 * w0, 4 * (size_t)n);
+        upload_piece<<<1, 256, 0, st>>>(pc, n, d + w0);
+        GF_KERNEL_DONE();
     }
     return GF_OK;
 }

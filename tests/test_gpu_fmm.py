@@ -172,6 +172,26 @@ def test_mixed_item_sizes_1_to_200_observers_per_leaf():
     assert np.array_equal(g1, g2)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_near_field_beside_the_m2l_equals_in_line(precision):
+    """The evaluation's near field runs on the plan's second stream beside the
+    M2L unless stage timing is on, when it runs in line on the forward's
+    stream: the same kernels either way, so the fields agree bit for bit."""
+    wk = cube_case(61, n=24, vol_targets=300)
+    r = torch.tensor(wk.rho, device=DEV)
+    with plan_for(wk, precision, p=12) as plan:
+        g1, _ = plan.forward(r)
+        plan.set_timing(True)
+        g2, _ = plan.forward(r)
+        ms = plan.stage_times()
+        plan.set_timing(False)
+        g3, _ = plan.forward(r)
+        torch.cuda.synchronize()
+        plan.check()
+    assert ms["eval"] > 0.0
+    assert torch.equal(g1, g2) and torch.equal(g1, g3)
+
+
 @pytest.mark.parametrize("p", [4, 8, 12, 14, 15])
 def test_m2l_tensor_cores_match_simt(p):
     """Mixed precision: the tcgen05 M2L (three FP16 products of scaled
