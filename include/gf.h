@@ -419,7 +419,11 @@ gf_status gf_plan_export_tree(gf_plan_t plan, int32_t level, int32_t *perm_host,
  *   [3] M2L input split (mixed precision: scaled FP16 parts of every level's
  *       multipole expansions)  [4] M2L  [5] L2L
  *   [6] evaluation (near field + L2P + combine)  [7] whole forward
- * (direct mode: only [6] and [7]).  Timing must be off while a forward is
+ * (direct mode: only [6] and [7]).  Without timing, an FMM plan runs the
+ * evaluation's near field on a second stream of its own beside the M2L and
+ * the L2L (forked from and joined back into the forward's stream); with
+ * timing on it runs in line, so that every stage is timed alone (the field
+ * is the same bit for bit).  Timing must be off while a forward is
  * captured in a CUDA graph. */
 #define GF_NUM_STAGES 8
 gf_status gf_plan_set_timing(gf_plan_t plan, int32_t enable);
