@@ -527,6 +527,25 @@ constexpr int kTopWarps = 8;
 
 // Batch members [b0, b0 + nb) of B are handled by one launch (nb bounded by
 // shared memory).
+// sum_{i0 <= i < i1} t[i K] x[i] with four partial sums, so that four
+// table loads are in flight at once (the FP64 top-level translations are
+// bound by the latency of these loads, not by arithmetic)
+template <class Tc>
+__device__ __forceinline__ Tc dot_strided(const Tc *__restrict__ t, const Tc *x, int i0, int i1, int K) {
+    Tc a0 = Tc(0), a1 = Tc(0), a2 = Tc(0), a3 = Tc(0);
+    int i = i0;
+    for (; i + 3 < i1; i += 4) {
+        const Tc t0 = t[(size_t)i * K], t1 = t[(size_t)(i + 1) * K], t2 = t[(size_t)(i + 2) * K],
+                 t3 = t[(size_t)(i + 3) * K];
+        a0 += t0 * x[i];
+        a1 += t1 * x[i + 1];
+        a2 += t2 * x[i + 2];
+        a3 += t3 * x[i + 3];
+    }
+    for (; i < i1; ++i) a0 += t[(size_t)i * K] * x[i];
+    return (a0 + a1) + (a2 + a3);
+}
+
 __host__ __device__ inline size_t top_smem(int nexp, int nb, int K) {
     return sizeof(double) * ((size_t)nexp * nb * K + (size_t)kTopWarps * nb * 32);
 }
@@ -565,7 +584,7 @@ m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3
                 if (!present[oct]) continue;
                 const Tc *t = tab + (size_t)oct * K * K + k;
                 const Tc *x = xs + (oct * nb + bb) * K;
-                for (int i = i0; i < i1; ++i) acc += t[(size_t)i * K] * x[i];
+                acc += dot_strided(t, x, i0, i1, K);
             }
         red[(warp * nb + bb) * 32 + lane] = acc;
     }
@@ -603,8 +622,7 @@ l2l_kernel(const Ts *__restrict__ le_p, const uint64_t *__restrict__ tkey, const
     const Tc *tb = tab + (size_t)oct * K * K + k;
     for (int bb = 0; bb < nb; ++bb) {
         Tc acc = Tc(0);
-        if (k < K)
-            for (int i = i0; i < i1; ++i) acc += tb[(size_t)i * K] * xs[bb * K + i];
+        if (k < K) acc = dot_strided(tb, xs + bb * K, i0, i1, K);
         red[(warp * nb + bb) * 32 + lane] = acc;
     }
     __syncthreads();
