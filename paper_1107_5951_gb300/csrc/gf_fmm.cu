@@ -551,11 +551,12 @@ __host__ __device__ inline size_t top_smem(int nexp, int nb, int K) {
 }
 
 // M2M: parent ME[k] = sum over existing children c, inputs i of
-// T_oct(c)[i][k] * child ME[i].
+// T_oct(c)[i][k] * child ME[i].  amax (may be null): the largest |ME[k]|
+// written into parents [alo, ahi), as float bits with atomicMax.
 template <class Ts, class Tc>
 __global__ void __launch_bounds__(kTopWarps * 32)
 m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3 bp, int B, int b0, int nb, int K,
-           int ldk, const Tc *__restrict__ tab) {
+           int ldk, const Tc *__restrict__ tab, uint32_t *amax = nullptr, int64_t alo = 0, int64_t ahi = 0) {
     extern __shared__ unsigned char shraw[];
     Tc *xs = reinterpret_cast<Tc *>(shraw);   // [8][nb][K] child expansions
     Tc *red = xs + 8 * nb * K;                // [kTopWarps][nb][32] partial sums
@@ -594,7 +595,10 @@ m2m_kernel(const Ts *__restrict__ me_c, Block3 bc, Ts *__restrict__ me_p, Block3
         if (kk >= K) continue;
         Tc acc = Tc(0);
         for (int w = 0; w < kTopWarps; ++w) acc += red[(w * nb + bb) * 32 + (e & 31)];
-        me_p[(pi * B + b0 + bb) * ldk + kk] = (Ts)acc;
+        const Ts v = (Ts)acc;
+        me_p[(pi * B + b0 + bb) * ldk + kk] = v;
+        if (amax && pi >= alo && pi < ahi && v != Ts(0) && v == v)   // NaN is skipped, as fmaxf does
+            atomicMax(amax, __float_as_uint(fabsf((float)v)));
     }
 }
 
@@ -1708,6 +1712,7 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
     const bool pts = F->points;
     const bool fused = !pts && p2m_fused_ok<T>(F);
     bool up = false;   // level L-1 expansions made straight from the leaf masses
+    F->amax_fused = false;
     if (pts) {
         // a0 + a3 for point sources: masses in leaf order, P2M over each leaf's points
         GF_TRY(points_masses<T>(plan, rho, rho_dtype, B, st));
@@ -1727,6 +1732,12 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
             // level's M2L (and so the near field) reaches.
             up = p2m_up_ok(plan, B);
             const bool from_grid = up && p2m_up_grid_ok(plan, rho, rho_dtype);
+            // the kernels that write each level's expansions (the tensor-core
+            // P2M and M2M kinds, the FP64 M2M into level 2) also take the
+            // largest |input| of the slabs the M2L reads, in place of a pass
+            // over those rows before the M2L
+            F->amax_fused = F->tc_amax != nullptr;
+            if (F->amax_fused) GF_CUDA(cudaMemsetAsync(F->tc_amax, 0, (kMaxLevels + 1) * sizeof(uint32_t), st));
             const FmmLevel &lf = F->lev[L];
             const int64_t z0 = from_grid ? lf.m2l_z0 : 0;
             const int64_t nz = from_grid ? std::max<int64_t>(0, lf.m2l_z1 - lf.m2l_z0 + 1) : lb.n[2];
@@ -1769,9 +1780,14 @@ gf_status run_forward(gf_plan_s *plan, const void *rho, int rho_dtype, int B, do
             GF_TRY((ensure_smem(m2m_kernel<T, double>, top_smem(8, nbc, K))));
             for (int b0 = 0; b0 < B; b0 += nbc) {
                 const int nb = std::min(nbc, B - b0);
+                const int64_t slab = pa.sn[0] * pa.sn[1];
+                const bool am = F->amax_fused && pa.m2l_z1 >= pa.m2l_z0;
                 m2m_kernel<T, double><<<dim3((unsigned)pa.ns, ceil_div(K, 32)), kTopWarps * 32,
                                         top_smem(8, nb, K), st>>>((const T *)ch.me, block_of(ch), (T *)pa.me,
-                                                                  block_of(pa), B, b0, nb, K, F->KS, tab->m2m_d);
+                                                                  block_of(pa), B, b0, nb, K, F->KS, tab->m2m_d,
+                                                                  am ? F->tc_amax + l : nullptr,
+                                                                  am ? pa.m2l_z0 * slab : 0,
+                                                                  am ? (pa.m2l_z1 + 1) * slab : 0);
                 GF_KERNEL_DONE();
             }
         } else {

@@ -98,6 +98,7 @@ struct FmmPlan {
     // [0, kMaxLevels]: forward, [kMaxLevels + 1, 2 kMaxLevels + 1]: adjoint),
     // reduced on the device before each tensor-core M2L
     uint32_t *tc_amax = nullptr;
+    bool amax_fused = false;      // this forward's expansion writers took the M2L input maxima
     float *m2l_part = nullptr;    // forward M2L with two CTAs per tile: [tiles][2][128][Npad] partial rows
     int *m2l_cnt = nullptr;       // [tiles][8] arrivals
     int m2l_part_tiles = 0;       // tiles m2l_part holds (0: no sharing)

@@ -579,6 +579,12 @@ struct TcLevel {
     // leaf), likewise j, k; leaves lie wholly inside or outside the grid
     int64_t goff[3], gn[3], gnvox;
     int gb;
+    // M2M and P2M kinds (forward, mixed): the largest |value| written into
+    // the target boxes [amax_lo, amax_hi) -- the z-slabs of the output level
+    // that its M2L reads -- as float bits combined with atomicMax into
+    // amax_out (the level's M2L input scale; null: not collected here)
+    uint32_t *amax_out;
+    int64_t amax_lo, amax_hi;
 };
 
 struct TcArgs {
@@ -1355,6 +1361,7 @@ m2l_tc(TcArgs a) {
                     }
                 }
             }
+            float am = 0.f;   // this row's largest |value| (M2M / P2M kinds with amax_out)
             if (write && oslot < nbox && os < oc.ccnt) {
                 int64_t obox;
                 if (a.kind == kTcM2M) {   // dense targets
@@ -1404,7 +1411,17 @@ m2l_tc(TcArgs a) {
 #pragma unroll
                     for (int q = 0; q < NS; q += 4)
                         if (q < nsum) dst[q / 4] = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+                    if (L.amax_out && obox >= L.amax_lo && obox < L.amax_hi) {
+#pragma unroll
+                        for (int q = 0; q < NS; ++q)
+                            if (q < nsum && ph_half * nsum + q < a.K) am = fmaxf(am, fabsf(acc[q]));
+                    }
                 }
+            }
+            if (!H16 && L.amax_out) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+                if (lane == 0 && am > 0.f) atomicMax(L.amax_out, __float_as_uint(am));
             }
         }
     }
@@ -1516,6 +1533,14 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
     // from the leaf masses (entry 2L+3) and the P2M of the leaves in the
     // z-slabs the leaf level's M2L reads (entry 2L+4)
     if (F->mixed && F->tab->m2m_tc && F->tab->l2l_tc) {
+        // the output level's M2L-reachable boxes (the rows input_absmax reads)
+        auto set_amax = [&](TcLevel &t, int l) {
+            const FmmLevel &lv = F->lev[l];
+            const int64_t slab = lv.sn[0] * lv.sn[1];
+            t.amax_out = F->tc_amax + l;
+            t.amax_lo = lv.m2l_z1 >= lv.m2l_z0 ? lv.m2l_z0 * slab : 0;
+            t.amax_hi = lv.m2l_z1 >= lv.m2l_z0 ? (lv.m2l_z1 + 1) * slab : 0;
+        };
         std::vector<TcLevel> h(2 * (F->L + 1) + 3);
         memset(h.data(), 0, h.size() * sizeof(TcLevel));
         for (int l = 2; l <= F->L; ++l) {
@@ -1532,6 +1557,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
                 }
                 t.cls_off[0] = 0;
                 for (int c = 1; c <= 8; ++c) t.cls_off[c] = pa.ns;
+                set_amax(t, l);
             }
             if (l > 2) {
                 const FmmLevel &lv = F->lev[l], &pa = F->lev[l - 1];
@@ -1555,6 +1581,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
             t.le = (float *)lv.me;
             t.cls_off[0] = 0;
             for (int c = 1; c <= 8; ++c) t.cls_off[c] = lv.ns;
+            set_amax(t, F->L);
             if ((F->b * F->b * F->b) % 16 == 0) GF_TRY(get_p2m_tc(plan, plan->arena.stream));
             TcLevel &r = h[2 * (F->L + 1) + 2];
             r = t;
@@ -1577,6 +1604,7 @@ gf_status m2l_tc_prepare(gf_plan_s *plan) {
             t.cls_off[0] = 0;
             for (int c = 1; c <= 8; ++c) t.cls_off[c] = pa.ns;
             t.gb = F->b;
+            set_amax(t, F->L - 1);
             t.gnvox = plan->nvox;
             for (int d = 0; d < 3; ++d) {
                 t.goff[d] = F->voff[d];
@@ -1795,10 +1823,12 @@ gf_status m2l_run_tc(gf_plan_s *plan, int B, bool adj, cudaStream_t st, cudaEven
             m.rows[l] = nr;
             most = std::max(most, m.rows[l] * m.ld4);
         }
-        GF_CUDA(cudaMemsetAsync(m.out, 0, (kMaxLevels + 1) * sizeof(uint32_t), st));
         const int gx = (int)std::min<int64_t>(8 * 152, std::max<int64_t>(1, (most + 1023) / 1024));
-        input_absmax<<<dim3(gx, F->L - 1), 256, 0, st>>>(m);
-        GF_KERNEL_DONE();
+        if (adj || !F->amax_fused) {   // else the kernels that wrote the expansions took it
+            GF_CUDA(cudaMemsetAsync(m.out, 0, (kMaxLevels + 1) * sizeof(uint32_t), st));
+            input_absmax<<<dim3(gx, F->L - 1), 256, 0, st>>>(m);
+            GF_KERNEL_DONE();
+        }
         SplitArgs o;
         memset(&o, 0, sizeof(o));
         for (int l = 2; l <= F->L; ++l)
