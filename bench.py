@@ -59,14 +59,14 @@ MUFU_RSQRT_PROBE = 4.63e12
 # interaction-list box pairs for the M2L.
 NCU_TRAFFIC = {
     # evaluation: near-field and far-field kernels of one forward, scaled by the pairs
-    ("eval", "layered_scale_464^3", 10): (round((7901952 + 0 + 23402752 + 0) * 596922624 / 280629504),
+    ("eval", "layered_scale_464^3", 10): (round((7902720 + 0 + 23410176 + 0) * 596922624 / 280629504),
                                           ("paper_1107_5951_gb300/csrc/gf_fmm.cu",
                                            "paper_1107_5951_gb300/csrc/gf_simd.cuh",
                                            "paper_1107_5951_gb300/csrc/fmm_math.cuh"),
-                                          "26ee0f2f353adcce223bceb9c289ed48ac15297d"),
-    ("m2l", "layered_scale_464^3", 10): (round((19055360 + 0) * 1125279 / 510295),
+                                          "e6e19973d3feff22bec7f445f4c523b35d9d346b"),
+    ("m2l", "layered_scale_464^3", 10): (round((19061248 + 0) * 1125279 / 510295),
                                          ("paper_1107_5951_gb300/csrc/gf_m2l.cu",),
-                                         "f048c1661ef0a87063a8e32f296b58830561d4a4"),
+                                         "06e97124d0ebb1d513f65faa28dd3a3ea34f260c"),
 }
 
 
